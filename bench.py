@@ -1,0 +1,286 @@
+"""Throughput of the GB300 Lamb-Helmholtz vortex FMM on the single-ring workload.
+
+One step = one classical RK4 step (four evaluations of v and s = (w . grad) v,
+each with its own octree) of a 262,144-element vortex ring (R = 1, radial and
+axial jitter sigma = 0.03, Gaussian core a = 2 pi / 1000, p = 12, <= 64 per
+leaf, dt = 1e-3).  Metric: element evaluations (v and s at one element) per
+second = 4 N / step time.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun): every rank advances its own replica of the ring (the
+path has no data exchange to shard); value = all ranks' evaluations / the
+slowest rank's time ("replicas", weak scaling).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+WORKLOAD = "ring_262144"
+METRIC = "vortex-element v+stretching evals/sec at ε=1e-6 vs plain FP32 GPU FMM; % roofline"
+UNIT = "evals/s"
+# algorithmic FP32 work of one near-field pair ("P2P"): d, r^2, 1/r^3,
+# g = f'/r, w_j x d, v += f (w_j x d), sum f w_j, (w_i . d), s += g (w_i . d)(w_j x d)
+P2P_FLOPS_PER_PAIR = 46
+FP32_LANES_PER_SM = 128
+
+
+def _measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _traffic_record(kernel_file):
+    """dram bytes per launch from the committed ncu summary, if it was taken on
+    the current source of the kernel (null otherwise)."""
+    path = os.path.join(ROOT, "profiles", "p2p_ring262144_traffic.txt")
+    src = os.path.join(ROOT, "paper_1201_5430_gb300", "csrc", kernel_file)
+    if not (os.path.exists(path) and os.path.exists(src)):
+        return None
+    rec = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            rec[k.strip()] = v.strip()
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if rec.get("source_sha256_16") != sha:
+        return None
+    try:
+        return float(rec["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(x, w, spec, budget_s=12.0):
+    """The oracle's direct sum (O1) as it stands, at a bounded random sample of
+    target elements (all N sources each): evals/s = targets / CPU seconds."""
+    from oracle import direct
+    rng = np.random.default_rng(0)
+    order = rng.permutation(x.shape[0])
+    done, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        direct.direct_at(x, w, spec["a"], order[done:done + 16])
+        done += 16
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"O1 direct sum (FP64 numpy) at {done} random targets of the {x.shape[0]}-element ring, "
+                      f"all sources each, {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    x, w, spec = workloads.make(WORKLOAD)
+    steps = []
+    if args.warmup > 0:
+        cpu_baseline(x, w, spec, budget_s=0.5)
+    per_step_budget = 4.0
+    for _ in range(args.steps):
+        cb = cpu_baseline(x, w, spec, budget_s=per_step_budget)
+        steps.append(cb["value"])
+    val = float(statistics.mean(steps)) if steps else 0.0
+    cb["value"] = val
+    n = x.shape[0]
+    out = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 4 * n / val * 1e3 if val else None,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "impl": "reference",
+           "config": {"workload": WORKLOAD, "n": n, "p": spec["p"], "leaf_max": spec["leaf_max"],
+                      "core_a": spec["a"], "dt": spec["dt"]},
+           "cpu_baseline": cb,
+           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1201_5430_gb300 import LHV
+    x, w, spec = workloads.make(WORKLOAD)
+    n = x.shape[0]
+    ctx = LHV(p=spec["p"], leaf_max=spec["leaf_max"], core_a=spec["a"], eps=spec["eps"], precision="fp32")
+    x0 = torch.from_numpy(workloads.to_f4(x)).cuda()
+    w0 = torch.from_numpy(workloads.to_f4(w)).cuda()
+    x4, w4 = x0.clone(), w0.clone()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    for _ in range(max(args.warmup, 3)):
+        x4.copy_(x0)
+        w4.copy_(w0)
+        ctx.step(x4, w4, spec["dt"])
+    torch.cuda.synchronize()
+
+    ctx.set_timing(True)
+    ctx.reset_stats()
+    times = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for _ in range(args.steps):
+            x4.copy_(x0)
+            w4.copy_(w0)
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.step(x4, w4, spec["dt"])
+            b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    st = ctx.stats()
+    total_ms = float(sum(times))
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    evals = 4 * n * args.steps * world
+    value = evals / (total_ms / 1e3)
+
+    # roofline of the dominant kernel (P2P): algorithmic FP32 flops per launch / its mean duration
+    peaks, peak_kind = _measured_peaks()
+    p2p_ms = st["stage_ms"]["p2p"] / max(st["stage_launches"]["p2p"], 1)
+    pairs = st["p2p_pairs"]
+    achieved = P2P_FLOPS_PER_PAIR * pairs / (p2p_ms / 1e3) / 1e12
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    peak = sms * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    traffic = _traffic_record("p2p.cu")
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    hx = x0.cpu().pin_memory()
+    hw = w0.cpu().pin_memory()
+    hx0, hw0 = hx.clone(), hw.clone()
+    e2e_times = []
+    for i in range(args.steps):
+        hx.copy_(hx0)
+        hw.copy_(hw0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.step_host(hx, hw, spec["dt"])
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_val = 4 * n * world / statistics.mean(e2e_times)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cb = None
+    if not args.no_cpu_baseline:
+        cb = cpu_baseline(x, w, spec)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "p": spec["p"], "leaf_max": spec["leaf_max"],
+                   "core_a": spec["a"], "eps": spec["eps"], "dt": spec["dt"], "rk4_evals_per_step": 4,
+                   "l2": "flushed between steps (256 MB write)", "parallelism": "replicas" if world > 1 else "1 GPU",
+                   "leaf_level": st["leaf_level"], "boxes": st["nbox"]},
+        "roofline": {"kernel": "k_p2p (near field)", "bound": "alu", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                     "peak_kind": f"FP32 FMA pipe: {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x "
+                                  f"{peaks.get('sm_max_mhz', 2070.0)} MHz ({peak_kind} max clock)",
+                     "pairs_per_launch": pairs, "flops_per_pair": P2P_FLOPS_PER_PAIR, "mean_launch_ms": p2p_ms},
+        "stage_ms_per_step": {k: v / args.steps for k, v in st["stage_ms"].items() if v > 0},
+        "cpu_baseline": cb,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(2 * n * 16),
+                "d2h_bytes_per_step": int(2 * n * 16)},
+        "gpu_launches": st["kernel_launches"],
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

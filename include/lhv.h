@@ -1,0 +1,175 @@
+/*
+ * lhv.h -- C ABI of the GB300 Lamb-Helmholtz vortex FMM (liblhv.so).
+ *
+ * The library evaluates, for N vortex elements with positions x_i and strength
+ * vectors w_i, the velocity and the vortex-stretching term of Eq. s1.1 of
+ * Gumerov & Duraiswami, "Efficient FMM accelerated vortex methods in three
+ * dimensions via the Lamb-Helmholtz decomposition":
+ *
+ *   v_i = sum_{j != i} K(|x_i - x_j|; a) w_j x (x_i - x_j) / |x_i - x_j|^3   (Eqs. 1, 2)
+ *   s_i = (w_i . grad) v |_{x_i}                                           (Eq. s1.1)
+ *
+ * with the Gaussian core K of Eq. vem1 (K = 1 when a = 0), and advances
+ * (x_i, w_i) by dx/dt = v, dw/dt = s with classical RK4 (Sec. 5.3).  The far
+ * field is carried by the two harmonic potentials phi and chi of Eq. 4, with the
+ * conversion operators of Eqs. drt10/drt11 applied after every translation
+ * (Sec. 4); the near field (colleague leaves) is summed directly.
+ *
+ * Conventions shared by every entry point:
+ *  - Element buffers are caller-owned DEVICE memory (unless the name ends in
+ *    _host), contiguous [n][4]: float4 for the FP32 entry points, double[4]
+ *    (32-byte aligned) for the _f64 ones.  Lanes 0..2 hold (x, y, z) or
+ *    (w_x, w_y, w_z); lane 3 is ignored on input and written 0 on output.
+ *  - Outputs are in the caller's element order.
+ *  - All work is enqueued on the stream given to lhv_create, in stream order.
+ *    Calls that build a tree read a few sizes back to the host (one short
+ *    synchronisation of that stream per tree build).
+ *  - Every call returns a status code (LHV_OK = 0, negative on error); no C++
+ *    exception crosses the ABI.  After an error the outputs are unspecified and
+ *    the context stays usable; lhv_last_error() describes the last error.
+ *  - The context owns every internal buffer (tree, expansions, operator tables,
+ *    RK4 stages); it is freed by lhv_destroy.
+ */
+#ifndef LHV_H
+#define LHV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define LHV_OK            0
+#define LHV_EINVAL       -1  /* bad argument: null/misaligned pointer, n < 0, p out of range, a < 0 */
+#define LHV_ENOMEM       -2  /* device allocation failed */
+#define LHV_ECUDA        -3  /* a CUDA runtime call or kernel launch failed */
+#define LHV_ETIMEOUT     -4  /* a device-side bounded wait gave up */
+#define LHV_ENONFINITE   -5  /* NaN or Inf in the positions or strengths */
+#define LHV_EUNSUPPORTED -6  /* valid request this build does not implement */
+
+/* ---- arithmetic of the evaluation (lhv_config.precision) --------------- */
+#define LHV_FP32 0  /* all kernels in FP32; operator tables built in FP64, stored FP32 */
+#define LHV_FP64 1  /* all kernels in FP64 (use the _f64 entry points) */
+
+/* ---- which parts of Eq. fmm1 to evaluate (lhv_config.terms) ------------ */
+#define LHV_TERMS_NEAR 1  /* sparse part only: direct sum over colleague leaves */
+#define LHV_TERMS_FAR  2  /* dense part only: P2M, M2M, M2L, L2L, L2P */
+#define LHV_TERMS_ALL  3
+
+typedef struct lhv_ctx lhv_ctx;
+
+typedef struct {
+    int    p;          /* truncation number: terms n = 0 .. p-1 (Sec. 5.1); 1 <= p <= 24 */
+    int    leaf_max;   /* leaf bound: leaf level = shallowest level with <= leaf_max
+                          elements per box, capped by the core rule below; >= 1 */
+    double core_a;     /* Gaussian core a of Eq. vem1; 0 selects the singular Eq. 1 */
+    double eps;        /* target accuracy in (0, 1): leaf boxes are kept no smaller
+                          than r_K = x_K a with 1 - K(x_K a; a) = eps/10, so far pairs
+                          see K = 1 to eps/10 (Eq. 2) */
+    int    precision;  /* LHV_FP32 or LHV_FP64 */
+    int    terms;      /* LHV_TERMS_* (0 means LHV_TERMS_ALL) */
+    int    max_level;  /* cap on the leaf level, 0 = none (21, the key depth) */
+} lhv_config;
+
+#define LHV_MAX_LEVELS 22
+#define LHV_NUM_STAGES 10
+/* stage indices of lhv_stats.stage_ms */
+#define LHV_STAGE_TREE   0  /* Morton keys, sort, boxes, lists */
+#define LHV_STAGE_P2M    1  /* Sec. 4.3 */
+#define LHV_STAGE_M2M    2  /* Sec. 4.4, S conversion Eq. drt11 */
+#define LHV_STAGE_M2L    3  /* Sec. 4.4, R conversion Eq. drt10 */
+#define LHV_STAGE_L2L    4  /* Sec. 4.4, R conversion Eq. drt10 */
+#define LHV_STAGE_L2P    5  /* Sec. 4.5 */
+#define LHV_STAGE_P2P    6  /* Eq. fmm1 sparse part, Eqs. 2 and vem1 */
+#define LHV_STAGE_RK4    7  /* Sec. 5.3 RK4 combine */
+#define LHV_STAGE_OPS    8  /* FP64 operator build (once per context) */
+#define LHV_STAGE_COPY   9  /* host <-> device copies of the _host entry points */
+
+typedef struct {
+    int     leaf_level;                      /* L of the last tree */
+    int     nbox[LHV_MAX_LEVELS];            /* occupied boxes per level of the last tree */
+    int64_t n;                               /* elements of the last tree */
+    int64_t p2p_pairs;                       /* ordered (target, source) pairs, j != i, of the
+                                                last near-field evaluation */
+    int64_t m2l_pairs;                       /* (target, source) box pairs of the last M2L */
+    double  stage_ms[LHV_NUM_STAGES];        /* summed device time per stage since the last
+                                                reset (only while timing is enabled) */
+    int64_t stage_launches[LHV_NUM_STAGES];  /* timed stage executions since the last reset */
+    int64_t kernel_launches;                 /* kernels launched since the last reset */
+} lhv_stats;
+
+/* Create a context for one configuration on one CUDA stream (a cudaStream_t,
+ * NULL = the legacy default stream) of the current device.  *out receives the
+ * handle.  Returns LHV_EINVAL for a null cfg/out or out-of-range fields. */
+int lhv_create(const lhv_config* cfg, void* cuda_stream, lhv_ctx** out);
+
+/* Free every buffer the context owns.  NULL is accepted. */
+void lhv_destroy(lhv_ctx* ctx);
+
+/* Static text for a status code. */
+const char* lhv_status_string(int status);
+
+/* Text of the last error of this context (empty when none). */
+const char* lhv_last_error(lhv_ctx* ctx);
+
+/* Build the octree of n FP32 positions (device [n][4]): cube, Morton keys,
+ * stable sort, boxes per level, colleague lists (Sec. 4, "Create data
+ * structure").  Evaluation calls rebuild it themselves; this entry point exists
+ * to time or inspect the tree alone. */
+int lhv_build_tree(lhv_ctx* ctx, int64_t n, const float* x4);
+
+/* v and s (Eq. s1.1) of n elements: x4, w4 in, v4, s4 out (device [n][4], FP32
+ * context).  Builds the tree of x4 first.  n = 0 is a no-op. */
+int lhv_evaluate_velocity_stretching(lhv_ctx* ctx, int64_t n, const float* x4, const float* w4,
+                                     float* v4, float* s4);
+
+/* One classical RK4 step of Eq. s1.1 in place on x4 and w4 (device [n][4],
+ * FP32 context); four evaluations, each with its own tree (Sec. 5.3). */
+int lhv_step(lhv_ctx* ctx, int64_t n, float* x4, float* w4, double dt);
+
+/* lhv_step on HOST buffers (pageable or pinned [n][4] FP32): copies in, steps,
+ * copies back, all on the context stream; returns when the results are in
+ * x4_host and w4_host. */
+int lhv_step_host(lhv_ctx* ctx, int64_t n, float* x4_host, float* w4_host, double dt);
+
+/* FP64 twins (FP64 context; element buffers are double[n][4], 32-byte aligned). */
+int lhv_evaluate_velocity_stretching_f64(lhv_ctx* ctx, int64_t n, const double* x4, const double* w4,
+                                         double* v4, double* s4);
+int lhv_step_f64(lhv_ctx* ctx, int64_t n, double* x4, double* w4, double dt);
+
+/* Statistics of the last tree/evaluation and the accumulated stage timings. */
+int lhv_get_stats(lhv_ctx* ctx, lhv_stats* out);
+
+/* Enable (1) or disable (0) per-stage CUDA-event timing on the context stream. */
+int lhv_set_timing(lhv_ctx* ctx, int enable);
+
+/* Zero the accumulated stage timings and the launch counter. */
+int lhv_reset_stats(lhv_ctx* ctx);
+
+/* Copy an internal array of the last tree/evaluation into a caller DEVICE
+ * buffer of capacity_bytes (stream-ordered).  *bytes_out receives the size of
+ * the array (also when dst is NULL, to query it).  `level` selects the octree
+ * level where the array is per level.  Returns LHV_EINVAL if the array does
+ * not exist or does not fit.  Arrays:                                         */
+#define LHV_EXPORT_KEYS        1  /* uint64[n] Morton keys, sorted */
+#define LHV_EXPORT_PERM        2  /* int32[n] sorted position -> caller index */
+#define LHV_EXPORT_BOX_KEYS    3  /* uint64[nbox(level)] key prefixes of the level's boxes */
+#define LHV_EXPORT_BOX_RANGE   4  /* int32[nbox(level)][2] sorted element range [begin, end) */
+#define LHV_EXPORT_COLLEAGUES  5  /* int32[nbox(level)][27] colleague box index or -1,
+                                     offset (dx,dy,dz) at ((dx+1)*3+(dy+1))*3+(dz+1) */
+#define LHV_EXPORT_MULTIPOLE   6  /* real[nbox(level)][2][p*p] scaled S coefficients (phi, chi) */
+#define LHV_EXPORT_LOCAL       7  /* real[nbox(level)][2][p*p] scaled R coefficients (phi, chi) */
+#define LHV_EXPORT_CUBE        8  /* double[4]: x0, y0, z0 of the cube and its side */
+/* Scaled real coefficient layout (both potentials, box side h at that level):
+ * real index n*n for Re c_n^0, n*n + 2m - 1 / n*n + 2m for Re / Im c_n^m (m >= 1);
+ * S coefficients are stored as  c_n^m nu_n^m / h^(n+1) (phi) and c_n^m nu_n^m / h^n (chi),
+ * R coefficients as             c_n^m h^n / nu_n^m (phi)    and c_n^m h^(n+1) / nu_n^m (chi),
+ * nu_n^m = sqrt((n-|m|)! (n+|m|)!), c_n^m the coefficients of Eq. rsbf6. */
+int lhv_export(lhv_ctx* ctx, int what, int level, void* dst, int64_t capacity_bytes, int64_t* bytes_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LHV_H */

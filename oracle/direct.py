@@ -39,15 +39,22 @@ def pair_terms(d, w_src, a):
     """Contribution of sources with strengths w_src at offsets d = y - x_j.
 
     Returns (v, u) with v_k = f (w x d)_k and
-    u_{lk} = f' d_l (w x d)_k / r + f (w x e_l)_k,  f = K / r^3, f' = df/dr."""
+    u_{lk} = f' d_l (w x d)_k / r + f (w x e_l)_k,  f = K / r^3, f' = df/dr.
+    For a > 0 and r = 0 (a distinct element at the same point) f and f'/r take
+    their limits from Eq. vem1: K = sqrt(2/pi) (r/a)^3 (1/3 - (r/a)^2/10 + ...),
+    so f -> sqrt(2/pi) / (3 a^3) and f'/r -> -sqrt(2/pi) / (5 a^5)."""
     d = np.asarray(d, dtype=np.float64)
     r = np.sqrt((d * d).sum(axis=-1))
     K, dK = core_K(r, a), core_dK(r, a)
-    f = K / r ** 3
-    fp = dK / r ** 3 - 3.0 * K / r ** 4
+    with np.errstate(invalid="ignore", divide="ignore"):
+        f = K / r ** 3
+        fp_r = (dK / r ** 3 - 3.0 * K / r ** 4) / r
+    if a > 0:
+        f = np.where(r == 0, SQRT_2_OVER_PI / (3.0 * a ** 3), f)
+        fp_r = np.where(r == 0, -SQRT_2_OVER_PI / (5.0 * a ** 5), fp_r)
     wxd = np.cross(w_src, d)
     v = f[..., None] * wxd
-    u = (fp / r)[..., None, None] * d[..., :, None] * wxd[..., None, :]
+    u = fp_r[..., None, None] * d[..., :, None] * wxd[..., None, :]
     eye = np.eye(3)
     # (w x e_l)_k for l = 0..2 -> array [..., l, k]
     wxe = np.stack([np.cross(w_src, eye[l]) for l in range(3)], axis=-2)

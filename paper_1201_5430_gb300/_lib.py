@@ -1,0 +1,72 @@
+"""ctypes declarations of the C ABI in include/lhv.h (argument marshalling only)."""
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblhv.so")
+
+LHV_OK, LHV_EINVAL, LHV_ENOMEM, LHV_ECUDA, LHV_ETIMEOUT, LHV_ENONFINITE, LHV_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+LHV_FP32, LHV_FP64 = 0, 1
+LHV_TERMS_NEAR, LHV_TERMS_FAR, LHV_TERMS_ALL = 1, 2, 3
+LHV_MAX_LEVELS = 22
+LHV_NUM_STAGES = 10
+STAGES = ["tree", "p2m", "m2m", "m2l", "l2l", "l2p", "p2p", "rk4", "ops", "copy"]
+EXPORT = {"keys": 1, "perm": 2, "box_keys": 3, "box_range": 4, "colleagues": 5,
+          "multipole": 6, "local": 7, "cube": 8}
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("leaf_max", ctypes.c_int), ("core_a", ctypes.c_double),
+                ("eps", ctypes.c_double), ("precision", ctypes.c_int), ("terms", ctypes.c_int),
+                ("max_level", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("leaf_level", ctypes.c_int), ("nbox", ctypes.c_int * LHV_MAX_LEVELS), ("n", ctypes.c_int64),
+                ("p2p_pairs", ctypes.c_int64), ("m2l_pairs", ctypes.c_int64),
+                ("stage_ms", ctypes.c_double * LHV_NUM_STAGES),
+                ("stage_launches", ctypes.c_int64 * LHV_NUM_STAGES), ("kernel_launches", ctypes.c_int64)]
+
+
+# exported function -> (restype, argtypes); every name here is declared in include/lhv.h
+_vp, _i64, _dbl, _int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+SIGNATURES = {
+    "lhv_create": (_int, [ctypes.POINTER(Config), _vp, ctypes.POINTER(_vp)]),
+    "lhv_destroy": (None, [_vp]),
+    "lhv_status_string": (ctypes.c_char_p, [_int]),
+    "lhv_last_error": (ctypes.c_char_p, [_vp]),
+    "lhv_build_tree": (_int, [_vp, _i64, _vp]),
+    "lhv_evaluate_velocity_stretching": (_int, [_vp, _i64, _vp, _vp, _vp, _vp]),
+    "lhv_step": (_int, [_vp, _i64, _vp, _vp, _dbl]),
+    "lhv_step_host": (_int, [_vp, _i64, _vp, _vp, _dbl]),
+    "lhv_evaluate_velocity_stretching_f64": (_int, [_vp, _i64, _vp, _vp, _vp, _vp]),
+    "lhv_step_f64": (_int, [_vp, _i64, _vp, _vp, _dbl]),
+    "lhv_get_stats": (_int, [_vp, ctypes.POINTER(Stats)]),
+    "lhv_set_timing": (_int, [_vp, _int]),
+    "lhv_reset_stats": (_int, [_vp]),
+    "lhv_export": (_int, [_vp, _int, _int, _vp, _i64, ctypes.POINTER(_i64)]),
+}
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load liblhv.so; raises if it has not been built (there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1201_5430_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class LHVError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status

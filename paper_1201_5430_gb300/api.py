@@ -1,0 +1,123 @@
+"""Thin Python binding over the C ABI: torch tensors in, raw pointers to liblhv.so.
+
+Every step of the computation runs in the library's CUDA kernels; this module
+only checks tensor shapes/dtypes and passes pointers, sizes and the current
+CUDA stream."""
+import ctypes
+
+import torch
+
+from . import _lib as L
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class LHV:
+    """One library context (operator tables, tree and work buffers) on one stream."""
+
+    def __init__(self, p, leaf_max=64, core_a=0.0, eps=1e-6, precision="fp32", terms="all",
+                 max_level=0, stream=None, device=None):
+        self.lib = L.load()
+        self.precision = precision
+        self.dtype = torch.float32 if precision == "fp32" else torch.float64
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        cfg = L.Config(p=int(p), leaf_max=int(leaf_max), core_a=float(core_a), eps=float(eps),
+                       precision=L.LHV_FP32 if precision == "fp32" else L.LHV_FP64,
+                       terms={"near": 1, "far": 2, "all": 3}[terms], max_level=int(max_level))
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            st = self.lib.lhv_create(ctypes.byref(cfg), ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h))
+        if st != 0:
+            raise L.LHVError(st, "lhv_create: " + self.lib.lhv_status_string(st).decode())
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lhv_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st != 0:
+            msg = self.lib.lhv_last_error(self.h).decode() or self.lib.lhv_status_string(st).decode()
+            raise L.LHVError(st, f"{what}: {msg}")
+
+    def _elems(self, t):
+        if t.device.type != "cuda" or t.dtype != self.dtype or t.dim() != 2 or t.shape[1] != 4 or not t.is_contiguous():
+            raise ValueError(f"expected a contiguous CUDA {self.dtype} tensor of shape [n, 4]")
+        return t
+
+    def build_tree(self, x4):
+        self._elems(x4)
+        self._check(self.lib.lhv_build_tree(self.h, x4.shape[0], _ptr(x4)), "lhv_build_tree")
+
+    def evaluate_velocity_stretching(self, x4, w4, v4=None, s4=None):
+        self._elems(x4)
+        self._elems(w4)
+        n = x4.shape[0]
+        v4 = torch.empty_like(x4) if v4 is None else self._elems(v4)
+        s4 = torch.empty_like(x4) if s4 is None else self._elems(s4)
+        fn = self.lib.lhv_evaluate_velocity_stretching if self.precision == "fp32" else \
+            self.lib.lhv_evaluate_velocity_stretching_f64
+        self._check(fn(self.h, n, _ptr(x4), _ptr(w4), _ptr(v4), _ptr(s4)), "evaluate_velocity_stretching")
+        return v4, s4
+
+    def step(self, x4, w4, dt):
+        self._elems(x4)
+        self._elems(w4)
+        fn = self.lib.lhv_step if self.precision == "fp32" else self.lib.lhv_step_f64
+        self._check(fn(self.h, x4.shape[0], _ptr(x4), _ptr(w4), float(dt)), "step")
+
+    def step_host(self, x4_host, w4_host, dt):
+        """x4_host, w4_host: contiguous CPU float32 [n, 4] tensors (pinned or pageable)."""
+        for t in (x4_host, w4_host):
+            if t.device.type != "cpu" or t.dtype != torch.float32 or not t.is_contiguous() or t.shape[1] != 4:
+                raise ValueError("expected contiguous CPU float32 [n, 4] tensors")
+        self._check(self.lib.lhv_step_host(self.h, x4_host.shape[0], _ptr(x4_host), _ptr(w4_host), float(dt)),
+                    "step_host")
+
+    def set_timing(self, on=True):
+        self._check(self.lib.lhv_set_timing(self.h, 1 if on else 0), "set_timing")
+
+    def reset_stats(self):
+        self._check(self.lib.lhv_reset_stats(self.h), "reset_stats")
+
+    def stats(self):
+        s = L.Stats()
+        self._check(self.lib.lhv_get_stats(self.h, ctypes.byref(s)), "get_stats")
+        return {
+            "leaf_level": s.leaf_level, "nbox": list(s.nbox)[: s.leaf_level + 1], "n": s.n,
+            "p2p_pairs": s.p2p_pairs, "m2l_pairs": s.m2l_pairs,
+            "stage_ms": dict(zip(L.STAGES, list(s.stage_ms))),
+            "stage_launches": dict(zip(L.STAGES, list(s.stage_launches))),
+            "kernel_launches": s.kernel_launches,
+        }
+
+    def export(self, what, level=0):
+        """Copy an internal array (see lhv_export) into a new CUDA tensor."""
+        code = L.EXPORT[what]
+        nbytes = ctypes.c_int64(0)
+        self._check(self.lib.lhv_export(self.h, code, int(level), None, 0, ctypes.byref(nbytes)), f"export {what}")
+        buf = torch.empty(max(int(nbytes.value), 1), dtype=torch.uint8, device=self.device)
+        self._check(self.lib.lhv_export(self.h, code, int(level), _ptr(buf), buf.numel(), ctypes.byref(nbytes)),
+                    f"export {what}")
+        buf = buf[: int(nbytes.value)]
+        if what == "keys":
+            return buf.view(torch.int64)
+        if what in ("perm", "box_range", "colleagues"):
+            return buf.view(torch.int32)
+        if what == "box_keys":
+            return buf.view(torch.int64)
+        if what == "cube":
+            return buf.view(torch.float64)
+        return buf.view(self.dtype)

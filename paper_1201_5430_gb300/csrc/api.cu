@@ -1,0 +1,553 @@
+// C ABI of liblhv.so: context, evaluation pipeline (Sec. 4 "FMM run"), RK4
+// step (Sec. 5.3), statistics and array export.  See include/lhv.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lhv_group.cuh"
+#include "lhv_internal.cuh"
+
+namespace lhv {
+
+struct TimedRange {
+    int stage;
+    cudaEvent_t a, b;
+};
+
+struct Ctx {
+    lhv_config cfg{};
+    cudaStream_t stream = nullptr;
+    double rK = 0.0;
+    std::string last_error;
+    int64_t launches = 0;
+    bool timing = false;
+    double stage_ms[LHV_NUM_STAGES] = {0};
+    int64_t stage_launches[LHV_NUM_STAGES] = {0};
+    std::vector<TimedRange> pending;
+    std::vector<cudaEvent_t> pool;
+    TreeBufs tb;
+    Levels lv;
+    TreeParams hp{};
+    int64_t tree_n = 0;
+    OpTables ops;
+    int ops_type = 0;  // sizeof(T) of the built tables
+    Buf tmp[8];
+    Buf xs, ws, mult, loc, table, vfar, sfar, counters, W, cf;
+    Grouped gp_leaf, gp_m2m, gp_m2l, gp_l2l;
+    Buf rk[6];         // kv, ks, ax, aw, sx, sw
+    Buf hx, hw;        // device copies for lhv_step_host
+    bool have_far = false;
+};
+
+// ---- helpers used by every translation unit ------------------------------
+void count_launch(Ctx* c) { ++c->launches; }
+cudaStream_t stream_of(Ctx* c) { return c->stream; }
+int ctx_leaf_max(Ctx* c) { return c->cfg.leaf_max; }
+int ctx_max_level(Ctx* c) { return c->cfg.max_level; }
+double ctx_rK(Ctx* c) { return c->rK; }
+Buf& ctx_tmp(Ctx* c, int i) { return c->tmp[i]; }
+
+void cuda_check(cudaError_t e, const char* what) {
+    if (e != cudaSuccess) throw Error{LHV_ECUDA, std::string(what) + ": " + cudaGetErrorString(e)};
+}
+
+void check_launch(const char* what) { cuda_check(cudaGetLastError(), what); }
+
+void ensure(Ctx* c, Buf& b, int64_t bytes) {
+    (void)c;
+    if (bytes <= 0) bytes = 16;
+    if ((size_t)bytes <= b.cap) return;
+    if (b.ptr) cudaFree(b.ptr);
+    b.ptr = nullptr;
+    b.cap = 0;
+    size_t want = (size_t)bytes + (size_t)bytes / 4 + 256;
+    if (cudaMalloc(&b.ptr, want) != cudaSuccess) {
+        cudaGetLastError();
+        b.ptr = nullptr;
+        throw Error{LHV_ENOMEM, "cudaMalloc of " + std::to_string(want) + " bytes failed"};
+    }
+    b.cap = want;
+}
+
+static void release(Buf& b) {
+    if (b.ptr) cudaFree(b.ptr);
+    b.ptr = nullptr;
+    b.cap = 0;
+}
+
+// ---- stage timing ----------------------------------------------------------
+struct StageScope {
+    Ctx* c;
+    int stage;
+    cudaEvent_t a = nullptr, b = nullptr;
+    StageScope(Ctx* ctx, int s) : c(ctx), stage(s) {
+        if (!c->timing) return;
+        a = take();
+        b = take();
+        cuda_check(cudaEventRecord(a, c->stream), "event");
+    }
+    ~StageScope() {
+        if (!c->timing || !a) return;
+        if (cudaEventRecord(b, c->stream) == cudaSuccess) c->pending.push_back({stage, a, b});
+    }
+    cudaEvent_t take() {
+        if (!c->pool.empty()) {
+            cudaEvent_t e = c->pool.back();
+            c->pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e;
+        cuda_check(cudaEventCreate(&e), "event create");
+        return e;
+    }
+};
+
+static void harvest(Ctx* c) {
+    if (c->pending.empty()) return;
+    cuda_check(cudaStreamSynchronize(c->stream), "sync stats");
+    for (auto& r : c->pending) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            c->stage_ms[r.stage] += ms;
+            c->stage_launches[r.stage] += 1;
+        }
+        c->pool.push_back(r.a);
+        c->pool.push_back(r.b);
+    }
+    c->pending.clear();
+}
+
+// ---- the evaluation pipeline ----------------------------------------------
+template <typename T>
+static void ensure_ops(Ctx* c) {
+    if (c->ops.p == c->cfg.p && c->ops_type == (int)sizeof(T)) return;
+    free_operators(c->ops);
+    StageScope sc(c, LHV_STAGE_OPS);
+    build_operators<T>(c, c->cfg.p, c->ops);
+    c->ops_type = (int)sizeof(T);
+}
+
+template <typename T>
+static int tree_stage(Ctx* c, int64_t n, const vec4_t<T>* x4, const vec4_t<T>* w4, Error& err) {
+    StageScope sc(c, LHV_STAGE_TREE);
+    int st = build_tree<T>(c, n, x4, w4, c->tb, c->lv, c->hp, err);
+    if (st != LHV_OK) return st;
+    c->tree_n = n;
+    ensure(c, c->xs, n * (int64_t)sizeof(vec4_t<T>));
+    ensure(c, c->ws, n * (int64_t)sizeof(vec4_t<T>));
+    gather_sorted<T>(c, n, c->tb.perm.as<int>(), x4, w4, c->xs.as<vec4_t<T>>(), c->ws.as<vec4_t<T>>());
+    return LHV_OK;
+}
+
+template <typename T>
+static int evaluate(Ctx* c, int64_t n, const vec4_t<T>* x4, const vec4_t<T>* w4, vec4_t<T>* v4, vec4_t<T>* s4) {
+    if (n == 0) return LHV_OK;
+    ensure_ops<T>(c);
+    ensure(c, c->counters, 64);
+    unsigned long long* cnt = c->counters.as<unsigned long long>();
+    cuda_check(cudaMemsetAsync(cnt, 0, 16, c->stream), "counters");
+    Error err{LHV_OK, ""};
+    int st = tree_stage<T>(c, n, x4, w4, err);
+    if (st != LHV_OK) throw err;
+    const Levels& lv = c->lv;
+    const int L = lv.L, P = c->ops.P;
+    const int terms = c->cfg.terms ? c->cfg.terms : LHV_TERMS_ALL;
+    const bool far = (terms & LHV_TERMS_FAR) && L >= 2;
+    const bool near = (terms & LHV_TERMS_NEAR) != 0;
+    const vec4_t<T>* xs = c->xs.as<vec4_t<T>>();
+    const vec4_t<T>* ws = c->ws.as<vec4_t<T>>();
+    vec4_t<T>* vfar = nullptr;
+    vec4_t<T>* sfar = nullptr;
+    c->have_far = far;
+    if (far) {
+        const int64_t nbt = lv.off[L + 1];
+        const int64_t nleaf = lv.nbox[L];
+        ensure(c, c->mult, nbt * 2 * P * (int64_t)sizeof(T));
+        ensure(c, c->loc, nbt * 2 * P * (int64_t)sizeof(T));
+        ensure(c, c->table, (nbt - lv.off[2]) * (int64_t)NUM_OFFSETS * 4);
+        ensure(c, c->W, nleaf * 3 * P * (int64_t)sizeof(T));
+        ensure(c, c->cf, nleaf * 12 * P * (int64_t)sizeof(T));
+        ensure(c, c->vfar, n * (int64_t)sizeof(vec4_t<T>));
+        ensure(c, c->sfar, n * (int64_t)sizeof(vec4_t<T>));
+        T* mult = c->mult.as<T>();
+        T* loc = c->loc.as<T>();
+        {
+            StageScope sc(c, LHV_STAGE_P2M);
+            run_p2m<T>(c, c->ops, c->tb, lv, c->hp, xs, ws, c->W.as<T>(), c->gp_leaf, mult);
+        }
+        {
+            StageScope sc(c, LHV_STAGE_M2M);
+            run_m2m<T>(c, c->ops, c->tb, lv, c->gp_m2m, mult);
+        }
+        {
+            StageScope sc(c, LHV_STAGE_M2L);
+            cuda_check(cudaMemsetAsync(loc + (int64_t)lv.off[2] * 2 * P, 0,
+                                       sizeof(T) * (size_t)(nbt - lv.off[2]) * 2 * P, c->stream),
+                       "zero locals");
+            run_m2l<T>(c, c->ops, c->tb, lv, c->table.as<int>(), c->gp_m2l, mult, loc, cnt + 1);
+        }
+        {
+            StageScope sc(c, LHV_STAGE_L2L);
+            run_l2l<T>(c, c->ops, c->tb, lv, c->gp_l2l, loc);
+        }
+        vfar = c->vfar.as<vec4_t<T>>();
+        sfar = c->sfar.as<vec4_t<T>>();
+        {
+            StageScope sc(c, LHV_STAGE_L2P);
+            run_l2p<T>(c, c->ops, c->tb, lv, c->hp, xs, ws, loc, c->cf.as<T>(), c->gp_leaf, vfar, sfar);
+        }
+    }
+    {
+        StageScope sc(c, LHV_STAGE_P2P);
+        run_p2p<T>(c, c->tb, lv, xs, ws, c->tb.perm.as<int>(), vfar, sfar, v4, s4, c->cfg.core_a, near, n, cnt);
+    }
+    return LHV_OK;
+}
+
+template <typename T>
+static int step(Ctx* c, int64_t n, vec4_t<T>* x4, vec4_t<T>* w4, double dt) {
+    if (n == 0) return LHV_OK;
+    const int64_t bytes = n * (int64_t)sizeof(vec4_t<T>);
+    for (int i = 0; i < 6; ++i) ensure(c, c->rk[i], bytes);
+    vec4_t<T>* kv = c->rk[0].as<vec4_t<T>>();
+    vec4_t<T>* ks = c->rk[1].as<vec4_t<T>>();
+    vec4_t<T>* ax = c->rk[2].as<vec4_t<T>>();
+    vec4_t<T>* aw = c->rk[3].as<vec4_t<T>>();
+    vec4_t<T>* sx = c->rk[4].as<vec4_t<T>>();
+    vec4_t<T>* sw = c->rk[5].as<vec4_t<T>>();
+    // k1..k4 of the classical tableau; the caller's x, w are y0 until the end
+    const double c_acc[4] = {1.0, 2.0, 2.0, 1.0};
+    const double c_stage[4] = {0.5 * dt, 0.5 * dt, dt, 0.0};
+    for (int k = 0; k < 4; ++k) {
+        const vec4_t<T>* xin = (k == 0) ? x4 : sx;
+        const vec4_t<T>* win = (k == 0) ? w4 : sw;
+        int st = evaluate<T>(c, n, xin, win, kv, ks);
+        if (st != LHV_OK) return st;
+        StageScope sc(c, LHV_STAGE_RK4);
+        run_rk4_stage<T>(c, n, x4, w4, kv, ks, ax, aw, sx, sw, c_acc[k], c_stage[k], k == 0);
+    }
+    StageScope sc(c, LHV_STAGE_RK4);
+    run_rk4_final<T>(c, n, x4, w4, ax, aw, dt / 6.0);  // y = y0 + dt/6 (k1 + 2 k2 + 2 k3 + k4)
+    return LHV_OK;
+}
+
+}  // namespace lhv
+
+using lhv::Ctx;
+using lhv::Error;
+
+struct lhv_ctx {
+    Ctx c;
+};
+
+namespace {
+
+template <typename F>
+int guarded(lhv_ctx* ctx, F&& f) {
+    if (!ctx) return LHV_EINVAL;
+    try {
+        int st = f();
+        if (st == LHV_OK) ctx->c.last_error.clear();
+        return st;
+    } catch (const Error& e) {
+        ctx->c.last_error = e.msg;
+        return e.status;
+    } catch (const std::bad_alloc&) {
+        ctx->c.last_error = "host allocation failed";
+        return LHV_ENOMEM;
+    } catch (...) {
+        ctx->c.last_error = "unexpected exception";
+        return LHV_ECUDA;
+    }
+}
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+int check_elems(lhv_ctx* ctx, int64_t n, std::initializer_list<const void*> ptrs, size_t align, int want_prec) {
+    if (!ctx) return LHV_EINVAL;
+    if (n < 0 || n > (int64_t)INT32_MAX / 2) {
+        ctx->c.last_error = "n out of range";
+        return LHV_EINVAL;
+    }
+    if (ctx->c.cfg.precision != want_prec) {
+        ctx->c.last_error = "entry point does not match the context precision";
+        return LHV_EINVAL;
+    }
+    if (n == 0) return LHV_OK;
+    for (const void* p : ptrs)
+        if (!p || !aligned(p, align)) {
+            ctx->c.last_error = "null or misaligned element buffer";
+            return LHV_EINVAL;
+        }
+    return LHV_OK;
+}
+
+// r_K = x_K a with 1 - K(x_K a; a) = eps / 10 (Eq. vem1), by bisection.
+double core_cutoff(double a, double eps) {
+    if (a <= 0.0) return 0.0;
+    const double target = eps / 10.0;
+    auto g = [&](double x) { return std::erfc(x / std::sqrt(2.0)) + std::sqrt(2.0 / 3.14159265358979323846) * x * std::exp(-0.5 * x * x) - target; };
+    double lo = 0.0, hi = 60.0;
+    for (int it = 0; it < 200; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (g(mid) > 0.0) lo = mid; else hi = mid;
+    }
+    return 0.5 * (lo + hi) * a;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lhv_status_string(int status) {
+    switch (status) {
+        case LHV_OK: return "ok";
+        case LHV_EINVAL: return "invalid argument";
+        case LHV_ENOMEM: return "out of device memory";
+        case LHV_ECUDA: return "CUDA error";
+        case LHV_ETIMEOUT: return "device wait timed out";
+        case LHV_ENONFINITE: return "non-finite input";
+        case LHV_EUNSUPPORTED: return "unsupported";
+        default: return "unknown status";
+    }
+}
+
+int lhv_create(const lhv_config* cfg, void* cuda_stream, lhv_ctx** out) {
+    if (!cfg || !out) return LHV_EINVAL;
+    *out = nullptr;
+    if (cfg->p < 1 || cfg->p > 24 || cfg->leaf_max < 1 || !(cfg->core_a >= 0.0) || !std::isfinite(cfg->core_a))
+        return LHV_EINVAL;
+    if (cfg->core_a > 0.0 && !(cfg->eps > 0.0 && cfg->eps < 1.0)) return LHV_EINVAL;
+    if (cfg->precision != LHV_FP32 && cfg->precision != LHV_FP64) return LHV_EINVAL;
+    if (cfg->terms < 0 || cfg->terms > 3 || cfg->max_level < 0 || cfg->max_level > 21) return LHV_EINVAL;
+    lhv_ctx* h = new (std::nothrow) lhv_ctx();
+    if (!h) return LHV_ENOMEM;
+    h->c.cfg = *cfg;
+    h->c.stream = static_cast<cudaStream_t>(cuda_stream);
+    h->c.rK = core_cutoff(cfg->core_a, cfg->eps);
+    *out = h;
+    return LHV_OK;
+}
+
+void lhv_destroy(lhv_ctx* ctx) {
+    if (!ctx) return;
+    Ctx& c = ctx->c;
+    if (c.stream) cudaStreamSynchronize(c.stream); else cudaDeviceSynchronize();
+    for (auto& r : c.pending) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : c.pool) cudaEventDestroy(e);
+    lhv::free_operators(c.ops);
+    lhv::TreeBufs& t = c.tb;
+    lhv::Buf* tree[] = {&t.keys_a, &t.keys_b, &t.idx_a, &t.idx_b, &t.hist, &t.boxof_a, &t.boxof_b, &t.flags,
+                        &t.scan_tmp, &t.perm, &t.params, &t.counts, &t.bkey, &t.bbeg, &t.bend, &t.bparent,
+                        &t.bcbeg, &t.bcend, &t.bcol, &t.tiles, &t.tile_count};
+    for (auto* b : tree) lhv::release(*b);
+    for (auto& b : c.tmp) lhv::release(b);
+    lhv::Buf* rest[] = {&c.xs, &c.ws, &c.mult, &c.loc, &c.table, &c.vfar, &c.sfar, &c.counters, &c.hx, &c.hw,
+                        &c.W, &c.cf};
+    for (auto* b : rest) lhv::release(*b);
+    for (lhv::Grouped* g : {&c.gp_leaf, &c.gp_m2m, &c.gp_m2l, &c.gp_l2l}) {
+        lhv::Buf* gb[] = {&g->gcount, &g->goff, &g->gcursor, &g->choff, &g->chunks, &g->pairs, &g->tmp,
+                          &g->scan_tmp, &g->work};
+        for (auto* b : gb) lhv::release(*b);
+    }
+    for (auto& b : c.rk) lhv::release(b);
+    delete ctx;
+}
+
+const char* lhv_last_error(lhv_ctx* ctx) { return ctx ? ctx->c.last_error.c_str() : ""; }
+
+int lhv_build_tree(lhv_ctx* ctx, int64_t n, const float* x4) {
+    int st = check_elems(ctx, n, {x4}, 16, LHV_FP32);
+    if (st != LHV_OK || n == 0) return st;
+    return guarded(ctx, [&] {
+        Error err{LHV_OK, ""};
+        int s = lhv::tree_stage<float>(&ctx->c, n, reinterpret_cast<const float4*>(x4),
+                                       reinterpret_cast<const float4*>(x4), err);
+        if (s != LHV_OK) throw err;
+        return LHV_OK;
+    });
+}
+
+int lhv_evaluate_velocity_stretching(lhv_ctx* ctx, int64_t n, const float* x4, const float* w4, float* v4,
+                                     float* s4) {
+    int st = check_elems(ctx, n, {x4, w4, v4, s4}, 16, LHV_FP32);
+    if (st != LHV_OK) return st;
+    return guarded(ctx, [&] {
+        return lhv::evaluate<float>(&ctx->c, n, reinterpret_cast<const float4*>(x4),
+                                    reinterpret_cast<const float4*>(w4), reinterpret_cast<float4*>(v4),
+                                    reinterpret_cast<float4*>(s4));
+    });
+}
+
+int lhv_evaluate_velocity_stretching_f64(lhv_ctx* ctx, int64_t n, const double* x4, const double* w4, double* v4,
+                                         double* s4) {
+    int st = check_elems(ctx, n, {x4, w4, v4, s4}, 32, LHV_FP64);
+    if (st != LHV_OK) return st;
+    return guarded(ctx, [&] {
+        return lhv::evaluate<double>(&ctx->c, n, reinterpret_cast<const lhv::dbl4*>(x4),
+                                     reinterpret_cast<const lhv::dbl4*>(w4), reinterpret_cast<lhv::dbl4*>(v4),
+                                     reinterpret_cast<lhv::dbl4*>(s4));
+    });
+}
+
+int lhv_step(lhv_ctx* ctx, int64_t n, float* x4, float* w4, double dt) {
+    int st = check_elems(ctx, n, {x4, w4}, 16, LHV_FP32);
+    if (st != LHV_OK) return st;
+    if (!std::isfinite(dt)) return LHV_EINVAL;
+    return guarded(ctx, [&] {
+        return lhv::step<float>(&ctx->c, n, reinterpret_cast<float4*>(x4), reinterpret_cast<float4*>(w4), dt);
+    });
+}
+
+int lhv_step_f64(lhv_ctx* ctx, int64_t n, double* x4, double* w4, double dt) {
+    int st = check_elems(ctx, n, {x4, w4}, 32, LHV_FP64);
+    if (st != LHV_OK) return st;
+    if (!std::isfinite(dt)) return LHV_EINVAL;
+    return guarded(ctx, [&] {
+        return lhv::step<double>(&ctx->c, n, reinterpret_cast<lhv::dbl4*>(x4), reinterpret_cast<lhv::dbl4*>(w4), dt);
+    });
+}
+
+int lhv_step_host(lhv_ctx* ctx, int64_t n, float* x4_host, float* w4_host, double dt) {
+    if (!ctx) return LHV_EINVAL;
+    if (ctx->c.cfg.precision != LHV_FP32 || n < 0 || (n > 0 && (!x4_host || !w4_host)) || !std::isfinite(dt))
+        return LHV_EINVAL;
+    if (n == 0) return LHV_OK;
+    return guarded(ctx, [&] {
+        Ctx& c = ctx->c;
+        const int64_t bytes = n * 16;
+        lhv::ensure(&c, c.hx, bytes);
+        lhv::ensure(&c, c.hw, bytes);
+        {
+            lhv::StageScope sc(&c, LHV_STAGE_COPY);
+            lhv::cuda_check(cudaMemcpyAsync(c.hx.ptr, x4_host, bytes, cudaMemcpyHostToDevice, c.stream), "h2d x");
+            lhv::cuda_check(cudaMemcpyAsync(c.hw.ptr, w4_host, bytes, cudaMemcpyHostToDevice, c.stream), "h2d w");
+        }
+        int st = lhv::step<float>(&c, n, c.hx.as<float4>(), c.hw.as<float4>(), dt);
+        if (st != LHV_OK) return st;
+        {
+            lhv::StageScope sc(&c, LHV_STAGE_COPY);
+            lhv::cuda_check(cudaMemcpyAsync(x4_host, c.hx.ptr, bytes, cudaMemcpyDeviceToHost, c.stream), "d2h x");
+            lhv::cuda_check(cudaMemcpyAsync(w4_host, c.hw.ptr, bytes, cudaMemcpyDeviceToHost, c.stream), "d2h w");
+        }
+        lhv::cuda_check(cudaStreamSynchronize(c.stream), "sync step_host");
+        return LHV_OK;
+    });
+}
+
+int lhv_set_timing(lhv_ctx* ctx, int enable) {
+    if (!ctx) return LHV_EINVAL;
+    ctx->c.timing = enable != 0;
+    return LHV_OK;
+}
+
+int lhv_reset_stats(lhv_ctx* ctx) {
+    return guarded(ctx, [&] {
+        lhv::harvest(&ctx->c);
+        for (int i = 0; i < LHV_NUM_STAGES; ++i) {
+            ctx->c.stage_ms[i] = 0;
+            ctx->c.stage_launches[i] = 0;
+        }
+        ctx->c.launches = 0;
+        return LHV_OK;
+    });
+}
+
+int lhv_get_stats(lhv_ctx* ctx, lhv_stats* out) {
+    if (!out) return LHV_EINVAL;
+    return guarded(ctx, [&] {
+        Ctx& c = ctx->c;
+        lhv::harvest(&c);
+        std::memset(out, 0, sizeof(*out));
+        out->leaf_level = c.lv.L;
+        for (int l = 0; l < LHV_MAX_LEVELS; ++l) out->nbox[l] = c.lv.nbox[l];
+        out->n = c.tree_n;
+        if (c.counters.ptr) {
+            unsigned long long h[2] = {0, 0};
+            lhv::cuda_check(cudaMemcpyAsync(h, c.counters.ptr, 16, cudaMemcpyDeviceToHost, c.stream), "stats");
+            lhv::cuda_check(cudaStreamSynchronize(c.stream), "stats sync");
+            out->p2p_pairs = (int64_t)h[0];
+            out->m2l_pairs = (int64_t)h[1];
+        }
+        for (int i = 0; i < LHV_NUM_STAGES; ++i) {
+            out->stage_ms[i] = c.stage_ms[i];
+            out->stage_launches[i] = c.stage_launches[i];
+        }
+        out->kernel_launches = c.launches;
+        return LHV_OK;
+    });
+}
+
+int lhv_export(lhv_ctx* ctx, int what, int level, void* dst, int64_t capacity_bytes, int64_t* bytes_out) {
+    return guarded(ctx, [&]() -> int {
+        Ctx& c = ctx->c;
+        const lhv::Levels& lv = c.lv;
+        const int64_t n = c.tree_n;
+        const void* src = nullptr;
+        int64_t bytes = 0;
+        const bool lvl_ok = level >= 0 && level <= lv.L;
+        const int nb = lvl_ok ? lv.nbox[level] : 0;
+        const int off = lvl_ok ? lv.off[level] : 0;
+        const int64_t coef = (int64_t)2 * c.ops.P * c.ops_type;
+        std::vector<double> cube;
+        switch (what) {
+            case LHV_EXPORT_KEYS: src = c.tb.keys_a.ptr; bytes = n * 8; break;
+            case LHV_EXPORT_PERM: src = c.tb.perm.ptr; bytes = n * 4; break;
+            case LHV_EXPORT_BOX_KEYS:
+                if (!lvl_ok) return LHV_EINVAL;
+                src = c.tb.bkey.as<uint64_t>() + off;
+                bytes = (int64_t)nb * 8;
+                break;
+            case LHV_EXPORT_BOX_RANGE: {
+                if (!lvl_ok) return LHV_EINVAL;
+                bytes = (int64_t)nb * 8;
+                if (bytes_out) *bytes_out = bytes;
+                if (!dst) return LHV_OK;
+                if (capacity_bytes < bytes) return LHV_EINVAL;
+                lhv::cuda_check(cudaMemcpy2DAsync(dst, 8, c.tb.bbeg.as<int>() + off, 4, 4, nb,
+                                                  cudaMemcpyDeviceToDevice, c.stream), "export begin");
+                lhv::cuda_check(cudaMemcpy2DAsync(static_cast<char*>(dst) + 4, 8, c.tb.bend.as<int>() + off, 4, 4, nb,
+                                                  cudaMemcpyDeviceToDevice, c.stream), "export end");
+                return LHV_OK;
+            }
+            case LHV_EXPORT_COLLEAGUES:
+                if (!lvl_ok) return LHV_EINVAL;
+                src = c.tb.bcol.as<int>() + (int64_t)off * 27;
+                bytes = (int64_t)nb * 27 * 4;
+                break;
+            case LHV_EXPORT_MULTIPOLE:
+            case LHV_EXPORT_LOCAL:
+                if (!lvl_ok || !c.have_far || level < 2) return LHV_EINVAL;
+                src = static_cast<const char*>(what == LHV_EXPORT_MULTIPOLE ? c.mult.ptr : c.loc.ptr) + off * coef;
+                bytes = nb * coef;
+                break;
+            case LHV_EXPORT_CUBE: {
+                bytes = 32;
+                if (bytes_out) *bytes_out = bytes;
+                if (!dst) return LHV_OK;
+                if (capacity_bytes < bytes) return LHV_EINVAL;
+                lhv::cuda_check(cudaMemcpyAsync(dst, c.tb.params.ptr, 32, cudaMemcpyDeviceToDevice, c.stream),
+                                "export cube");
+                return LHV_OK;
+            }
+            default:
+                return LHV_EINVAL;
+        }
+        if (bytes_out) *bytes_out = bytes;
+        if (!dst) return LHV_OK;
+        if (capacity_bytes < bytes || !src) return LHV_EINVAL;
+        if (bytes > 0)
+            lhv::cuda_check(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, c.stream), "export");
+        return LHV_OK;
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,350 @@
+// P2M (Sec. 4.3), M2M and L2L with conversion (Sec. 4.4), L2P (Sec. 4.5).
+//
+// All coefficient vectors are in the scaled real layout described in
+// operators.cu; the operator tables come from there, and every dense map runs
+// through the grouped GEMM of group_gemm.cu.  Per-element work builds
+// the normalised regular solid harmonics Q_n^m(rho) = rho^n sqrt((n-m)!/(n+m)!)
+// P_n^m(cos theta) e^{i m phi} on the fly by their three-term recurrences, with
+// rho = (x - box centre) / h, so no element ever stores p^2 values.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "lhv_group.cuh"
+#include "lhv_internal.cuh"
+
+namespace lhv {
+
+namespace {
+
+__device__ inline double box_centre(const TreeParams* tp, uint64_t key, int axis, int level, double h) {
+    // key prefix at `level`: bits interleaved x, y, z from bit 0
+    uint64_t v = key >> axis;
+    uint64_t c = 0;
+    for (int b = 0; b < level; ++b) c |= ((v >> (3 * b)) & 1ull) << b;
+    return tp->x0[axis] + ((double)c + 0.5) * h;
+}
+
+// Walks every (n, m), 0 <= m <= n < p, of the recurrence of Q_n^m at (x, y, z)
+// and calls f(n, m, Re Q, Im Q).  State is O(1).
+template <typename T, typename F>
+__device__ inline void for_each_Q(int p, T x, T y, T z, F&& f) {
+    const T r2 = x * x + y * y + z * z;
+    T dre = 1, dim = 0;  // Q_m^m
+    for (int m = 0; m < p; ++m) {
+        if (m > 0) {
+            T c = -sqrt((T)(2 * m - 1) / (T)(2 * m));
+            T nre = c * (x * dre - y * dim);
+            T nim = c * (x * dim + y * dre);
+            dre = nre;
+            dim = nim;
+        }
+        f(m, m, dre, dim);
+        if (m + 1 >= p) continue;
+        T c1 = sqrt((T)(2 * m + 1)) * z;
+        T pre = dre, pim = dim;             // Q_{n-2}
+        T qre = c1 * dre, qim = c1 * dim;   // Q_{n-1} = Q_{m+1}^m
+        f(m + 1, m, qre, qim);
+        for (int n = m + 2; n < p; ++n) {
+            T inv = (T)1 / sqrt((T)((n + m) * (n - m)));
+            T a = (T)(2 * n - 1) * inv * z;
+            T b = sqrt((T)((n + m - 1) * (n - m - 1))) * inv * r2;
+            T nre = a * qre - b * pre;
+            T nim = a * qim - b * pim;
+            pre = qre;
+            pim = qim;
+            qre = nre;
+            qim = nim;
+            f(n, m, qre, qim);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// P2M, part 1 (per leaf): W_k = sum_e w_{e,k} g_hat(rho_e), where
+// g_hat_n^m = nu_n^m R_n^{-m}(-rho) = i^m conj(Q_n^m(rho)), rho = (x - c)/h.
+// Part 2 is the grouped GEMM  M_hat = (1/h) [G_x G_y G_z] [W_x; W_y; W_z]
+// with G_k the scaled real form of Eq. eve4 for w = i_k.
+// ---------------------------------------------------------------------------
+constexpr int P2M_THREADS = 128;
+
+template <typename T>
+__global__ void __launch_bounds__(P2M_THREADS) k_p2m_w(int nleaf, int level, const uint64_t* __restrict__ bkey,
+                                                     const int* __restrict__ bbeg, const int* __restrict__ bend,
+                                                     const TreeParams* __restrict__ tp,
+                                                     const vec4_t<T>* __restrict__ xs,
+                                                     const vec4_t<T>* __restrict__ ws, T* __restrict__ Wout, int p,
+                                                     int chunk) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int P = p * p;
+    T* gh = reinterpret_cast<T*>(smem_raw);  // [chunk][P]
+    T* wk = gh + (size_t)chunk * P;          // [chunk][3]
+    const double h = ldexp(tp->side, -level);
+    for (int b = blockIdx.x; b < nleaf; b += gridDim.x) {
+        const uint64_t key = bkey[b];
+        const double cx = box_centre(tp, key, 0, level, h), cy = box_centre(tp, key, 1, level, h),
+                     cz = box_centre(tp, key, 2, level, h);
+        T* Wb = Wout + (int64_t)b * 3 * P;  // entry i is owned by thread i mod blockDim
+        for (int i = threadIdx.x; i < 3 * P; i += blockDim.x) Wb[i] = 0;
+        const int e0 = bbeg[b], e1 = bend[b];
+        for (int c0 = e0; c0 < e1; c0 += chunk) {
+            const int ne = min(chunk, e1 - c0);
+            __syncthreads();
+            for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+                vec4_t<T> xv = xs[c0 + e], wv = ws[c0 + e];
+                wk[e * 3 + 0] = wv.x;
+                wk[e * 3 + 1] = wv.y;
+                wk[e * 3 + 2] = wv.z;
+                T* g = gh + (size_t)e * P;
+                const T rx = (T)(((double)xv.x - cx) / h), ry = (T)(((double)xv.y - cy) / h),
+                        rz = (T)(((double)xv.z - cz) / h);
+                for_each_Q<T>(p, rx, ry, rz, [&](int n, int m, T qr, T qi) {
+                    T re, im;  // i^m conj(Q)
+                    switch (m & 3) {
+                        case 0: re = qr; im = -qi; break;
+                        case 1: re = qi; im = qr; break;
+                        case 2: re = -qr; im = qi; break;
+                        default: re = -qi; im = -qr; break;
+                    }
+                    if (m == 0) {
+                        g[n * n] = re;
+                    } else {
+                        g[n * n + 2 * m - 1] = re;
+                        g[n * n + 2 * m] = im;
+                    }
+                });
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < 3 * P; i += blockDim.x) {
+                const int k = i / P, j = i - k * P;
+                T s = 0;
+                for (int e = 0; e < ne; ++e) s += wk[e * 3 + k] * gh[(size_t)e * P + j];
+                Wb[i] += s;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// L2P (per leaf, after the grouped GEMM cf = E L_hat that forms the 12
+// coefficient vectors of v_k (Eq. evf3) and u_lk = D_{i_l} v_k (Eq. dt3)):
+//   v_k = (1/h) c_k . b(rho),   u_lk = (1/h^2) c_{3+3l+k} . b(rho),
+//   s_k = sum_l w_l u_lk (Eq. evf6),
+// b = real form of R_hat = nu R:  b[n^2] = R_hat_n^0,  2 Re R_hat_n^m,  -2 Im R_hat_n^m,
+// R_hat_n^m = (-1)^n i^m Q_n^m.
+// ---------------------------------------------------------------------------
+constexpr int L2P_THREADS = 128;
+
+template <typename T>
+__global__ void __launch_bounds__(L2P_THREADS) k_l2p_eval(int nleaf, int level, const uint64_t* __restrict__ bkey,
+                                                        const int* __restrict__ bbeg, const int* __restrict__ bend,
+                                                        const TreeParams* __restrict__ tp,
+                                                        const vec4_t<T>* __restrict__ xs,
+                                                        const vec4_t<T>* __restrict__ ws, const T* __restrict__ cfg,
+                                                        vec4_t<T>* __restrict__ vfar, vec4_t<T>* __restrict__ sfar,
+                                                        int p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int P = p * p;
+    T* cf = reinterpret_cast<T*>(smem_raw);  // [P][12]
+    const double h = ldexp(tp->side, -level);
+    for (int b = blockIdx.x; b < nleaf; b += gridDim.x) {
+        const uint64_t key = bkey[b];
+        const double cx = box_centre(tp, key, 0, level, h), cy = box_centre(tp, key, 1, level, h),
+                     cz = box_centre(tp, key, 2, level, h);
+        __syncthreads();
+        const T* src = cfg + (int64_t)b * 12 * P;
+        for (int idx = threadIdx.x; idx < 12 * P; idx += blockDim.x) {
+            const int j = idx / P, i = idx - j * P;
+            cf[i * 12 + j] = src[idx];
+        }
+        __syncthreads();
+        const T invh = (T)(1.0 / h);
+        for (int e = bbeg[b] + threadIdx.x; e < bend[b]; e += blockDim.x) {
+            vec4_t<T> xv = xs[e], wv = ws[e];
+            const T rx = (T)(((double)xv.x - cx) / h), ry = (T)(((double)xv.y - cy) / h),
+                    rz = (T)(((double)xv.z - cz) / h);
+            T acc[12];
+#pragma unroll
+            for (int j = 0; j < 12; ++j) acc[j] = 0;
+            for_each_Q<T>(p, rx, ry, rz, [&](int n, int m, T qr, T qi) {
+                T re, im;  // (-1)^n i^m Q
+                switch (m & 3) {
+                    case 0: re = qr; im = qi; break;
+                    case 1: re = -qi; im = qr; break;
+                    case 2: re = -qr; im = -qi; break;
+                    default: re = qi; im = -qr; break;
+                }
+                if (n & 1) {
+                    re = -re;
+                    im = -im;
+                }
+                if (m == 0) {
+                    const T* c = cf + (n * n) * 12;
+#pragma unroll
+                    for (int j = 0; j < 12; ++j) acc[j] += c[j] * re;
+                } else {
+                    const T* c1 = cf + (n * n + 2 * m - 1) * 12;
+                    const T* c2 = c1 + 12;
+                    const T b1 = 2 * re, b2 = -2 * im;
+#pragma unroll
+                    for (int j = 0; j < 12; ++j) acc[j] += c1[j] * b1 + c2[j] * b2;
+                }
+            });
+            vec4_t<T> v, s;
+            v.x = acc[0] * invh;
+            v.y = acc[1] * invh;
+            v.z = acc[2] * invh;
+            v.w = 0;
+            const T invh2 = invh * invh;
+            s.x = (wv.x * acc[3] + wv.y * acc[6] + wv.z * acc[9]) * invh2;
+            s.y = (wv.x * acc[4] + wv.y * acc[7] + wv.z * acc[10]) * invh2;
+            s.z = (wv.x * acc[5] + wv.y * acc[8] + wv.z * acc[11]) * invh2;
+            s.w = 0;
+            vfar[e] = v;
+            sfar[e] = s;
+        }
+    }
+}
+
+}  // namespace
+
+template <typename T>
+void run_p2m(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& lv, const TreeParams& hp,
+             const vec4_t<T>* xs, const vec4_t<T>* ws, T* W, Grouped& gp, T* mult) {
+    const int L = lv.L, nl = lv.nbox[L], o = lv.off[L], P = ops.P;
+    int chunk = (int)std::min<size_t>(128, (160 * 1024) / (sizeof(T) * (P + 3)));
+    chunk = std::max(32, chunk / 32 * 32);
+    const size_t smem = sizeof(T) * (size_t)chunk * (P + 3);
+    cuda_check(cudaFuncSetAttribute(k_p2m_w<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "p2m attr");
+    k_p2m_w<T><<<grid_for(nl, 1, 152 * 16), P2M_THREADS, smem, stream_of(c)>>>(
+        nl, L, tb.bkey.as<uint64_t>() + o, tb.bbeg.as<int>() + o, tb.bend.as<int>() + o, tb.params.as<TreeParams>(), xs,
+        ws, W, ops.p, chunk);
+    count_launch(c);
+    check_launch("p2m w");
+    build_grouped(c, gp, 1, nl, nl, gemm_nc<T>(3 * P), IdentItems{0, o});
+    GemmArgs<T> a{};
+    a.g0 = 0;
+    a.g1 = 1;
+    a.ops = ops.p2m.as<T>();
+    a.ops_mod = 1;
+    a.R = 2 * P;
+    a.C = 3 * P;
+    a.psplit = 0;
+    a.in = W;
+    a.ldin = 3 * P;
+    a.out = mult;
+    a.ldout = 2 * P;
+    a.mode = GEMM_STORE;
+    a.scale = (T)(1.0 / ldexp(hp.side, -L));
+    run_group_gemm<T>(c, gp, a);
+}
+
+template <typename T>
+static OctItems oct_items(const TreeBufs& tb, const Levels& lv, bool up) {
+    OctItems it{};
+    it.bkey = tb.bkey.as<uint64_t>();
+    it.bparent = tb.bparent.as<int>();
+    for (int l = 0; l <= MAX_LEVELS; ++l) it.off[l] = lv.off[l];
+    it.lo = 3;
+    it.hi = lv.L;
+    it.up = up;
+    return it;
+}
+
+template <typename T>
+void run_m2m(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& lv, Grouped& gp, T* mult) {
+    const int L = lv.L, P = ops.P;
+    if (L < 3) return;
+    // parents of the levels 2 .. L-1 accumulate atomically
+    cuda_check(cudaMemsetAsync(mult + (int64_t)lv.off[2] * 2 * P, 0,
+                               sizeof(T) * (size_t)(lv.off[L] - lv.off[2]) * 2 * P, stream_of(c)),
+               "m2m zero");
+    const int nitems = lv.off[L + 1] - lv.off[3];
+    build_grouped(c, gp, (L - 2) * 8, nitems, nitems, gemm_nc<T>(2 * P), oct_items<T>(tb, lv, true));
+    for (int l = L - 1; l >= 2; --l) {
+        GemmArgs<T> a{};
+        a.g0 = (l + 1 - 3) * 8;
+        a.g1 = a.g0 + 8;
+        a.ops = ops.m2m.as<T>();
+        a.ops_mod = 8;
+        a.R = 2 * P;
+        a.C = 2 * P;
+        a.psplit = P;
+        a.in = mult;
+        a.ldin = 2 * P;
+        a.out = mult;
+        a.ldout = 2 * P;
+        a.mode = GEMM_ATOMIC;
+        a.scale = (T)1;
+        run_group_gemm<T>(c, gp, a);
+    }
+}
+
+template <typename T>
+void run_l2l(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& lv, Grouped& gp, T* loc) {
+    const int L = lv.L, P = ops.P;
+    if (L < 3) return;
+    const int nitems = lv.off[L + 1] - lv.off[3];
+    build_grouped(c, gp, (L - 2) * 8, nitems, nitems, gemm_nc<T>(2 * P), oct_items<T>(tb, lv, false));
+    for (int l = 2; l < L; ++l) {
+        GemmArgs<T> a{};
+        a.g0 = (l + 1 - 3) * 8;
+        a.g1 = a.g0 + 8;
+        a.ops = ops.l2l.as<T>();
+        a.ops_mod = 8;
+        a.R = 2 * P;
+        a.C = 2 * P;
+        a.psplit = P;
+        a.in = loc;
+        a.ldin = 2 * P;
+        a.out = loc;
+        a.ldout = 2 * P;
+        a.mode = GEMM_ADD;
+        a.scale = (T)1;
+        run_group_gemm<T>(c, gp, a);
+    }
+}
+
+template <typename T>
+void run_l2p(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& lv, const TreeParams& hp,
+             const vec4_t<T>* xs, const vec4_t<T>* ws, const T* loc, T* cf, Grouped& gp, vec4_t<T>* vfar,
+             vec4_t<T>* sfar) {
+    const int L = lv.L, nl = lv.nbox[L], o = lv.off[L], P = ops.P;
+    build_grouped(c, gp, 1, nl, nl, gemm_nc<T>(2 * P), IdentItems{o, 0});
+    GemmArgs<T> a{};
+    a.g0 = 0;
+    a.g1 = 1;
+    a.ops = ops.l2p.as<T>();
+    a.ops_mod = 1;
+    a.R = 12 * P;
+    a.C = 2 * P;
+    a.psplit = 0;
+    a.in = loc;
+    a.ldin = 2 * P;
+    a.out = cf;
+    a.ldout = 12 * P;
+    a.mode = GEMM_STORE;
+    a.scale = (T)1;
+    run_group_gemm<T>(c, gp, a);
+    const size_t smem = sizeof(T) * 12 * P;
+    cuda_check(cudaFuncSetAttribute(k_l2p_eval<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "l2p attr");
+    k_l2p_eval<T><<<grid_for(nl, 1, 152 * 16), L2P_THREADS, smem, stream_of(c)>>>(
+        nl, L, tb.bkey.as<uint64_t>() + o, tb.bbeg.as<int>() + o, tb.bend.as<int>() + o, tb.params.as<TreeParams>(), xs,
+        ws, cf, vfar, sfar, ops.p);
+    count_launch(c);
+    check_launch("l2p");
+}
+
+#define LHV_INST(T)                                                                                             \
+    template void run_p2m<T>(Ctx*, const OpTables&, const TreeBufs&, const Levels&, const TreeParams&,         \
+                             const vec4_t<T>*, const vec4_t<T>*, T*, Grouped&, T*);                            \
+    template void run_m2m<T>(Ctx*, const OpTables&, const TreeBufs&, const Levels&, Grouped&, T*);            \
+    template void run_l2l<T>(Ctx*, const OpTables&, const TreeBufs&, const Levels&, Grouped&, T*);            \
+    template void run_l2p<T>(Ctx*, const OpTables&, const TreeBufs&, const Levels&, const TreeParams&,         \
+                             const vec4_t<T>*, const vec4_t<T>*, const T*, T*, Grouped&, vec4_t<T>*, vec4_t<T>*);
+LHV_INST(float)
+LHV_INST(double)
+#undef LHV_INST
+
+}  // namespace lhv

@@ -1,0 +1,139 @@
+// Grouped scatter GEMM (group_gemm.cu): pairs (source box, destination box)
+// bucketed by the operator they need, and the kernel arguments.
+#pragma once
+
+#include "lhv_internal.cuh"
+
+namespace lhv {
+
+enum GemmMode : int { GEMM_STORE = 0, GEMM_ADD = 1, GEMM_ATOMIC = 2 };
+
+struct Grouped {
+    int ngroups = 0;
+    int nc = 64;                 // pairs per chunk (columns of one GEMM work item)
+    Buf gcount, goff, gcursor;   // per group: pairs, first pair, fill cursor
+    Buf choff;                   // per group: first chunk (ngroups + 1 entries)
+    Buf chunks;                  // int4 (group, first pair, pairs, 0)
+    Buf pairs;                   // int2 (source, destination), group-major
+    Buf tmp, scan_tmp, work;
+};
+
+template <typename T>
+struct GemmArgs {
+    const int4* chunks;
+    const int2* pairs;
+    const int* choff;
+    int* work;
+    int g0, g1;           // groups [g0, g1) of this launch
+    const T* ops;         // operator of group g at ops + (g % ops_mod) * C * R, k-major [C][R]
+    int ops_mod;
+    int R, C;
+    int psplit;           // > 0: rows >= psplit use inputs >= psplit only (zero lower-left block)
+    const T* in;          // source vectors: in + src * ldin, C entries
+    int64_t ldin;
+    T* out;               // destination vectors: out + dst * ldout, R entries
+    int64_t ldout;
+    int mode;             // GemmMode
+    T scale;
+};
+
+// Items -> bucketed pairs.  An item functor `it(i, g, src, dst)` returns false
+// for items that emit nothing.
+template <class Items>
+__global__ void k_emit(int64_t n, Items it, int fill, int* __restrict__ gcount, int* __restrict__ gcursor,
+                       int2* __restrict__ pairs) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int g, s, d;
+        if (!it(i, g, s, d)) continue;
+        if (!fill) {
+            atomicAdd(gcount + g, 1);
+        } else {
+            const int pos = atomicAdd(gcursor + g, 1);
+            pairs[pos] = make_int2(s, d);
+        }
+    }
+}
+
+void grouped_prepare(Ctx* c, Grouped& gp, int ngroups, int64_t max_pairs, int nc);
+void grouped_offsets(Ctx* c, Grouped& gp);
+void grouped_finish(Ctx* c, Grouped& gp, int nc);
+
+template <class Items>
+void build_grouped(Ctx* c, Grouped& gp, int ngroups, int64_t nitems, int64_t max_pairs, int nc, const Items& it) {
+    grouped_prepare(c, gp, ngroups, max_pairs, nc);
+    gp.nc = nc;
+    if (nitems > 0) {
+        k_emit<Items><<<grid_for(nitems, 256), 256, 0, stream_of(c)>>>(nitems, it, 0, gp.gcount.as<int>(),
+                                                                         gp.gcursor.as<int>(), gp.pairs.as<int2>());
+        count_launch(c);
+    }
+    grouped_offsets(c, gp);
+    if (nitems > 0) {
+        k_emit<Items><<<grid_for(nitems, 256), 256, 0, stream_of(c)>>>(nitems, it, 1, gp.gcount.as<int>(),
+                                                                         gp.gcursor.as<int>(), gp.pairs.as<int2>());
+        count_launch(c);
+    }
+    grouped_finish(c, gp, nc);
+    check_launch("grouped pairs");
+}
+
+template <typename T>
+int gemm_nc(int C);
+
+template <typename T>
+void run_group_gemm(Ctx* c, Grouped& gp, GemmArgs<T> a);
+
+// Item sources ---------------------------------------------------------------
+
+// Every box b of the global range [b0, b0 + n) to itself shifted: (src_off + i, dst_off + i), group 0.
+struct IdentItems {
+    int src_off, dst_off;
+    __device__ bool operator()(int64_t i, int& g, int& s, int& d) const {
+        g = 0;
+        s = src_off + (int)i;
+        d = dst_off + (int)i;
+        return true;
+    }
+};
+
+// Children of the levels [lo, hi] (global box indices off[lo] .. off[hi+1]-1)
+// with their parents; group = (level - lo) * 8 + octant (key & 7).
+// up = true : child -> parent (M2M);  up = false : parent -> child (L2L).
+struct OctItems {
+    const uint64_t* bkey;
+    const int* bparent;
+    int off[MAX_LEVELS + 1];
+    int lo, hi;
+    bool up;
+    __device__ bool operator()(int64_t i, int& g, int& s, int& d) const {
+        const int b = off[lo] + (int)i;
+        int l = lo;
+        while (l < hi && b >= off[l + 1]) ++l;
+        const int par = off[l - 1] + bparent[b];
+        g = (l - lo) * 8 + (int)(bkey[b] & 7ull);
+        if (up) {
+            s = b;
+            d = par;
+        } else {
+            s = par;
+            d = b;
+        }
+        return true;
+    }
+};
+
+// M2L: rows of the interaction table (global target box, 316 slots -> global source box or -1).
+struct M2LItems {
+    const int* table;  // rows for the targets [t0, ...)
+    int t0;
+    __device__ bool operator()(int64_t i, int& g, int& s, int& d) const {
+        const int src = table[i];
+        if (src < 0) return false;
+        g = (int)(i % NUM_OFFSETS);
+        s = src;
+        d = t0 + (int)(i / NUM_OFFSETS);
+        return true;
+    }
+};
+
+}  // namespace lhv

@@ -1,0 +1,164 @@
+// Internal declarations shared by the translation units of liblhv.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "lhv.h"
+
+namespace lhv {
+
+constexpr int KEY_BITS = 21;           // bits per axis of a Morton key
+constexpr int MAX_LEVELS = LHV_MAX_LEVELS;
+constexpr int NUM_OFFSETS = 316;       // M2L offsets: [-3,3]^3 minus [-1,1]^3
+constexpr int P2P_TILE = 128;          // targets per P2P work item
+
+// 32-byte aligned four-double element (the _f64 element layout).
+struct alignas(32) dbl4 {
+    double x, y, z, w;
+};
+
+template <typename T> struct Vec4;
+template <> struct Vec4<float> { using type = float4; };
+template <> struct Vec4<double> { using type = dbl4; };
+template <typename T> using vec4_t = typename Vec4<T>::type;
+
+// Cube and level of the current tree, written by the tree kernels.
+struct TreeParams {
+    double x0[3];       // cube origin (FP32 minimum per axis)
+    double side;        // power-of-two side
+    int L;              // leaf level
+    int nonfinite;      // 1 if a position or strength is NaN/Inf
+    int deepest_shared; // deepest level at which leaf_max+1 consecutive keys share a box
+    int pad;
+};
+
+// Growable device allocation.
+struct Buf {
+    void* ptr = nullptr;
+    size_t cap = 0;
+    template <typename U> U* as() const { return static_cast<U*>(ptr); }
+};
+
+struct Error {
+    int status;
+    std::string msg;
+};
+
+// Per-level box arrays inside the flat box arrays.
+struct Levels {
+    int L = -1;
+    int nbox[MAX_LEVELS] = {0};
+    int off[MAX_LEVELS + 1] = {0};   // global box index of the first box of each level
+    int cap_off[MAX_LEVELS + 1] = {0};
+};
+
+struct Ctx;
+
+// ---- context accessors and helpers (api.cu) ---------------------------------
+void count_launch(Ctx* c);
+cudaStream_t stream_of(Ctx* c);
+void check_launch(const char* what);                 // throws Error{LHV_ECUDA} on a launch failure
+void cuda_check(cudaError_t e, const char* what);    // throws Error{LHV_ECUDA}
+void ensure(Ctx* c, Buf& b, int64_t bytes);          // grow b to >= bytes (throws Error{LHV_ENOMEM})
+int ctx_leaf_max(Ctx* c);
+int ctx_max_level(Ctx* c);
+double ctx_rK(Ctx* c);
+Buf& ctx_tmp(Ctx* c, int i);                         // scratch buffers 0..7 owned by the context
+
+inline int grid_for(int64_t n, int block, int cap = 152 * 32) {
+    int64_t g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+// ---- tree (tree.cu) ---------------------------------------------------------
+struct TreeBufs {
+    Buf keys_a, keys_b, idx_a, idx_b, hist, boxof_a, boxof_b, flags, scan_tmp;
+    Buf perm;                  // int32[n]
+    Buf params;                // TreeParams (device)
+    Buf counts;                // int32[64] (device)
+    Buf bkey, bbeg, bend, bparent, bcbeg, bcend, bcol;  // per box (global index)
+    Buf tiles, tile_count;     // P2P work items: int2 (leaf, first element)
+};
+
+// Builds keys, sort, levels and lists for n positions (device [n][4] of T).
+// On return `lv` (host) is filled; one stream synchronisation happens inside.
+template <typename T>
+int build_tree(Ctx* c, int64_t n, const vec4_t<T>* x4, const vec4_t<T>* w4, TreeBufs& tb, Levels& lv,
+               TreeParams& hp, Error& err);
+
+// Device-wide exclusive scan of int32 (in may equal out); *total_out (device) gets the sum.
+void exclusive_scan(Ctx* c, int64_t n, const int* in, int* out, int* tmp, int* total_out);
+int64_t scan_tmp_ints(int64_t n);
+
+// Gathers x and w into sorted order: xs[i] = x[perm[i]].
+template <typename T>
+void gather_sorted(Ctx* c, int64_t n, const int* perm, const vec4_t<T>* x4, const vec4_t<T>* w4,
+                   vec4_t<T>* xs, vec4_t<T>* ws);
+
+// ---- operators (operators.cu) -----------------------------------------------
+struct OpTables {
+    int p = 0;
+    int P = 0;                 // p*p
+    // every matrix is k-major: element (input j, output i) at j * rows + i
+    Buf m2l;                   // [316][2P][2P] fused (S|R) + Eq. drt10 per offset slot
+    Buf m2m;                   // [8][2P][2P]   fused (S|S) + Eq. drt11 per child octant
+    Buf l2l;                   // [8][2P][2P]   fused (R|R) + Eq. drt10 per child octant
+    Buf l2p;                   // [2P][12P]     v_k (Eq. evf3) and u_lk (Eq. dt3) coefficients
+    Buf p2m;                   // [3P][2P]      Eq. eve4 for w = i_x, i_y, i_z
+    Buf offsets;               // int[316][3] M2L offsets (dx, dy, dz)
+    Buf slot_of;               // int[343] offset (dx+3)*49+(dy+3)*7+(dz+3) -> slot or -1
+};
+
+// Builds every table in FP64 on the GPU and stores it in T.
+template <typename T>
+void build_operators(Ctx* c, int p, OpTables& ops);
+void free_operators(OpTables& ops);
+int m2l_slot_host(int dx, int dy, int dz);   // same mapping as slot_of, on the host
+
+struct Grouped;
+
+// ---- expansions (expansions.cu) ----------------------------------------------
+// P2M into mult (leaf level), work buffer W: nleaf * 3P reals.
+template <typename T>
+void run_p2m(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& lv, const TreeParams& hp,
+             const vec4_t<T>* xs, const vec4_t<T>* ws, T* W, Grouped& gp, T* mult);
+// M2M for all levels L-1 .. 2 (mult of the levels < L is overwritten).
+template <typename T>
+void run_m2m(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& lv, Grouped& gp, T* mult);
+// L2L for all levels 2 -> 3 .. L-1 -> L (adds into loc).
+template <typename T>
+void run_l2l(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& lv, Grouped& gp, T* loc);
+// L2P at the leaves; work buffer cf: nleaf * 12P reals.
+template <typename T>
+void run_l2p(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& lv, const TreeParams& hp,
+             const vec4_t<T>* xs, const vec4_t<T>* ws, const T* loc, T* cf, Grouped& gp, vec4_t<T>* vfar,
+             vec4_t<T>* sfar);
+
+// ---- M2L (m2l.cu) ------------------------------------------------------------
+// table: (off[L+1] - off[2]) * 316 ints.  loc must be zero for levels >= 2.
+template <typename T>
+void run_m2l(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& lv, int* table, Grouped& gp,
+             const T* mult, T* loc, unsigned long long* pair_counter);
+
+// ---- P2P (p2p.cu) ------------------------------------------------------------
+template <typename T>
+void run_p2p(Ctx* c, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs, const vec4_t<T>* ws,
+             const int* perm, const vec4_t<T>* vfar, const vec4_t<T>* sfar, vec4_t<T>* v_out, vec4_t<T>* s_out,
+             double a, bool near, int64_t n, unsigned long long* pair_counter);
+
+// ---- RK4 (p2p.cu) ------------------------------------------------------------
+template <typename T>
+void run_rk4_stage(Ctx* c, int64_t n, const vec4_t<T>* x0, const vec4_t<T>* w0, const vec4_t<T>* kv,
+                   const vec4_t<T>* ks, vec4_t<T>* ax, vec4_t<T>* aw, vec4_t<T>* sx, vec4_t<T>* sw,
+                   double c_acc, double c_stage, int first);
+template <typename T>
+void run_rk4_final(Ctx* c, int64_t n, vec4_t<T>* x, vec4_t<T>* w, const vec4_t<T>* ax, const vec4_t<T>* aw,
+                   double cf);
+
+}  // namespace lhv

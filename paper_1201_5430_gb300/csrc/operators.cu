@@ -1,0 +1,519 @@
+// FP64 construction of every operator table of the FMM, on the GPU.
+//
+// Each table is a real matrix acting on "scaled real" coefficient vectors.  A
+// real harmonic function has c_n^{-m} = (-1)^m conj(c_n^m) and real c_n^0, so
+// it is fixed by p*p reals: index n*n for Re c_n^0 and n*n + 2m - 1, n*n + 2m
+// for Re, Im c_n^m (m = 1..n).  Coefficients are scaled by box size h and by
+// nu_n^m = sqrt((n-|m|)! (n+|m|)!) so that every translation is level
+// independent and every entry is O(1):
+//   S expansions: phi: c nu / h^(n+1),  chi: c nu / h^n
+//   R expansions: phi: c h^n / nu,      chi: c h^(n+1) / nu
+// (chi carries one extra length because v = grad phi + curl(r chi), Eq. 4).
+// A table is  D_out A D_in  with A the complex map of the paper's formula in
+// the unscaled basis, D_in / D_out the diagonal scalings, then "realified".
+//
+// Complex maps (unscaled, new_{n'}^{m'} = sum A_{n'm',nm} old_n^m, Eq. mr2):
+//   translations (Eq. mr3):  (R|R) R_{n-n'}^{m-m'}(t), (S|R) S_{n+n'}^{m-m'}(t),
+//                            (S|S) R_{n'-n}^{m-m'}(t), t = new - old centre (Eq. bas1);
+//   conversions:             Eq. drt10 (R basis) and Eq. drt11 (S basis);
+//   velocity coefficients:   Eq. evf3; gradient coefficients: Eq. dt3 with t = i_l;
+//   S-expansion of elements: Eq. eve4 (per strength component).
+// Solid harmonics are evaluated through Q_n^m = r^n sqrt((n-m)!/(n+m)!) P_n^m e^{i m phi}
+// by the three-term recurrences derived from the Legendre recurrence, with
+// R_n^m = (-1)^n i^m Q_n^m / nu_n^m and S_n^m = (-1)^m i^m nu_n^m Q_n^m / r^(2n+1)
+// (m >= 0; Eqs. rsbf2 and rsbf4), and the symmetry above for m < 0.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <vector>
+
+#include "lhv_internal.cuh"
+
+namespace lhv {
+
+namespace {
+
+struct cplx {
+    double re, im;
+};
+__device__ inline cplx C(double a, double b = 0.0) { return {a, b}; }
+__device__ inline cplx operator+(cplx a, cplx b) { return {a.re + b.re, a.im + b.im}; }
+__device__ inline cplx operator-(cplx a, cplx b) { return {a.re - b.re, a.im - b.im}; }
+__device__ inline cplx operator*(cplx a, cplx b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+__device__ inline cplx operator*(double s, cplx a) { return {s * a.re, s * a.im}; }
+__device__ inline cplx conj(cplx a) { return {a.re, -a.im}; }
+__device__ inline cplx ipow(int m) {  // i^m
+    switch (((m % 4) + 4) % 4) {
+        case 0: return C(1, 0);
+        case 1: return C(0, 1);
+        case 2: return C(-1, 0);
+        default: return C(0, -1);
+    }
+}
+__device__ inline double sgn(int k) { return (k & 1) ? -1.0 : 1.0; }
+
+// Operator kinds (one CTA per instance).
+enum Kind : int {
+    K_M2L = 0,      // 2P x 2P fused [[T, C12 T], [0, C22 T]], (S|R) and Eq. drt10, S(h=1) -> R(h=1)
+    K_M2M = 1,      // 2P x 2P fused, (S|S) and Eq. drt11, child S(h=1) -> parent S(h=2)
+    K_L2L = 2,      // 2P x 2P fused, (R|R) and Eq. drt10, parent R(h=2) -> child R(h=1)
+    K_L2P_V = 5,    // P x 2P: v_k coefficients (Eq. evf3), aux = k
+    K_L2P_U = 6,    // P x 2P: u_lk = D_{i_l} v_k coefficients, aux = l, aux2 = k
+    K_P2M = 7,      // 2P x P: Eq. eve4 for w = i_k, aux = k
+};
+
+struct Spec {
+    int kind;
+    int aux, aux2;
+    int row0;        // first row of this block in the destination matrix
+    int64_t ld;      // rows of the destination matrix (k-major: element (col, row) at col * ld + row)
+    double t[3];
+};
+
+constexpr int MAXD = 48;             // highest degree of a solid harmonic needed (2p - 2 <= 46)
+constexpr int MAXTRI = (MAXD + 1) * (MAXD + 2) / 2;
+
+__device__ inline int tri(int n, int m) { return n * (n + 1) / 2 + m; }
+
+struct Ctx2 {
+    const cplx* Q;       // Q_n^m, m >= 0
+    double rho;
+    const double* fact;  // k!
+    int p;
+    double t[3];
+};
+
+__device__ inline double nu(const double* fact, int n, int m) {
+    m = m < 0 ? -m : m;
+    return sqrt(fact[n - m] * fact[n + m]);
+}
+
+__device__ cplx R_at(const Ctx2& g, int n, int m) {
+    int am = m < 0 ? -m : m;
+    if (n < 0 || am > n) return C(0);
+    cplx v = (sgn(n) / nu(g.fact, n, am)) * (ipow(am) * g.Q[tri(n, am)]);
+    if (m < 0) v = sgn(am) * conj(v);
+    return v;
+}
+
+__device__ cplx S_at(const Ctx2& g, int n, int m) {
+    int am = m < 0 ? -m : m;
+    if (n < 0 || am > n) return C(0);
+    cplx v = (sgn(am) * nu(g.fact, n, am) / pow(g.rho, 2 * n + 1)) * (ipow(am) * g.Q[tri(n, am)]);
+    if (m < 0) v = sgn(am) * conj(v);
+    return v;
+}
+
+__device__ inline bool valid_nm(int n, int m, int p) { return n >= 0 && n < p && (m < 0 ? -m : m) <= n; }
+
+// Translation map entries, Eqs. mr2/mr3.  tk: 0 = (R|R), 1 = (S|R), 2 = (S|S).
+__device__ cplx T_entry(const Ctx2& g, int tk, int n2, int m2, int n, int m) {
+    if (!valid_nm(n2, m2, g.p) || !valid_nm(n, m, g.p)) return C(0);
+    if (tk == 0) return R_at(g, n - n2, m - m2);
+    if (tk == 1) return S_at(g, n + n2, m - m2);
+    return R_at(g, n2 - n, m - m2);
+}
+
+// Sparse maps as lists of terms: output (n2, m2) <- coef * input (n2 + dn, m2 + dm).
+struct Terms {
+    int k;
+    int dn[4], dm[4];
+    cplx co[4];
+    __device__ void add(int a, int b, cplx c) {
+        dn[k] = a;
+        dm[k] = b;
+        co[k] = c;
+        ++k;
+    }
+};
+
+// Eq. drt10 (R basis): C12 (chi -> phi) and C22 - I (chi -> chi).
+__device__ Terms conv12R(const double* t, int n, int m) {
+    Terms r{0};
+    if (n == 0) return r;
+    double inv = 1.0 / n;
+    r.add(0, +1, (-inv * (n - m) / 2.0) * C(t[0], t[1]));
+    r.add(0, -1, (inv * (n + m) / 2.0) * C(t[0], -t[1]));
+    r.add(0, 0, C(0, inv * t[2] * m));
+    return r;
+}
+__device__ Terms conv22R(const double* t, int n, int m) {
+    Terms r{0};
+    double inv = 1.0 / (n + 1);
+    r.add(1, -1, (0.5 * inv) * C(t[1], t[0]));
+    r.add(1, +1, (-0.5 * inv) * C(t[1], -t[0]));
+    r.add(1, 0, C(-inv * t[2], 0));
+    return r;
+}
+// Eq. drt11 (S basis).
+__device__ Terms conv12S(const double* t, int n, int m) {
+    Terms r{0};
+    double inv = 1.0 / (n + 1);
+    r.add(0, +1, (-inv * (n + m + 1) / 2.0) * C(t[0], t[1]));
+    r.add(0, -1, (inv * (n - m + 1) / 2.0) * C(t[0], -t[1]));
+    r.add(0, 0, C(0, -inv * t[2] * m));
+    return r;
+}
+__device__ Terms conv22S(const double* t, int n, int m) {
+    Terms r{0};
+    if (n == 0) return r;
+    double inv = 1.0 / n;
+    r.add(-1, -1, (-0.5 * inv) * C(t[1], t[0]));
+    r.add(-1, +1, (0.5 * inv) * C(t[1], -t[0]));
+    r.add(-1, 0, C(inv * t[2], 0));
+    return r;
+}
+// Eq. evf3: v_k from phi (pot 0) or chi (pot 1).
+__device__ Terms evf3(int k, int pot, int n, int m) {
+    Terms r{0};
+    if (k == 0) {
+        if (pot == 0) {
+            r.add(1, -1, C(0, 0.5));
+            r.add(1, +1, C(0, 0.5));
+        } else {
+            r.add(0, +1, C(0.5 * (n - m)));
+            r.add(0, -1, C(-0.5 * (n + m)));
+        }
+    } else if (k == 1) {
+        if (pot == 0) {
+            r.add(1, -1, C(0.5));
+            r.add(1, +1, C(-0.5));
+        } else {
+            r.add(0, +1, C(0, 0.5 * (n - m)));
+            r.add(0, -1, C(0, 0.5 * (n + m)));
+        }
+    } else {
+        if (pot == 0) r.add(1, 0, C(-1.0));
+        else r.add(0, 0, C(0, -(double)m));
+    }
+    return r;
+}
+// Eq. dt3, R basis, t = i_l.
+__device__ Terms dt3R(int l, int n, int m) {
+    double t[3] = {0, 0, 0};
+    t[l] = 1.0;
+    Terms r{0};
+    r.add(1, -1, 0.5 * C(t[1], t[0]));
+    r.add(1, +1, -0.5 * C(t[1], -t[0]));
+    r.add(1, 0, C(-t[2]));
+    return r;
+}
+// Eq. eve4 for w = i_k: phi (pot 0) and chi (pot 1) from g.
+__device__ Terms eve4(int k, int pot, int n, int m) {
+    double w[3] = {0, 0, 0};
+    w[k] = 1.0;
+    Terms r{0};
+    if (pot == 0) {
+        double inv = 1.0 / (n + 1);
+        r.add(0, -1, (inv * (n - m + 1) / 2.0) * C(w[0], -w[1]));
+        r.add(0, +1, (-inv * (n + m + 1) / 2.0) * C(w[0], w[1]));
+        r.add(0, 0, C(0, -inv * w[2] * m));
+    } else {
+        if (n == 0) return r;
+        double inv = 1.0 / n;
+        r.add(-1, -1, (-0.5 * inv) * C(w[1], w[0]));
+        r.add(-1, +1, (0.5 * inv) * C(w[1], -w[0]));
+        r.add(-1, 0, C(inv * w[2]));
+    }
+    return r;
+}
+
+__device__ cplx terms_entry(const Terms& tr, int p, int n2, int m2, int n, int m) {
+    cplx s = C(0);
+    for (int i = 0; i < tr.k; ++i)
+        if (n == n2 + tr.dn[i] && m == m2 + tr.dm[i] && valid_nm(n, m, p)) s = s + tr.co[i];
+    return s;
+}
+
+// (Terms o T)(n2 m2; n m) with T a translation map.
+__device__ cplx terms_T(const Ctx2& g, const Terms& tr, int tk, int n2, int m2, int n, int m) {
+    cplx s = C(0);
+    for (int i = 0; i < tr.k; ++i) {
+        int a = n2 + tr.dn[i], b = m2 + tr.dm[i];
+        if (valid_nm(a, b, g.p)) s = s + tr.co[i] * T_entry(g, tk, a, b, n, m);
+    }
+    return s;
+}
+
+// Complex entry of the unscaled map of one operator block.
+__device__ cplx op_entry(const Ctx2& g, const Spec& sp, int pot_out, int pot_in, int n2, int m2, int n, int m) {
+    const int p = g.p;
+    switch (sp.kind) {
+        case K_M2L: {
+            if (pot_out == 0 && pot_in == 0) return T_entry(g, 1, n2, m2, n, m);
+            if (pot_out == 1 && pot_in == 0) return C(0);
+            if (pot_out == 0) return terms_T(g, conv12R(sp.t, n2, m2), 1, n2, m2, n, m);
+            return T_entry(g, 1, n2, m2, n, m) + terms_T(g, conv22R(sp.t, n2, m2), 1, n2, m2, n, m);
+        }
+        case K_M2M: {
+            if (pot_out == 0 && pot_in == 0) return T_entry(g, 2, n2, m2, n, m);
+            if (pot_out == 1 && pot_in == 0) return C(0);
+            if (pot_out == 0) return terms_T(g, conv12S(sp.t, n2, m2), 2, n2, m2, n, m);
+            return T_entry(g, 2, n2, m2, n, m) + terms_T(g, conv22S(sp.t, n2, m2), 2, n2, m2, n, m);
+        }
+        case K_L2L: {
+            if (pot_out == 0 && pot_in == 0) return T_entry(g, 0, n2, m2, n, m);
+            if (pot_out == 1 && pot_in == 0) return C(0);
+            if (pot_out == 0) return terms_T(g, conv12R(sp.t, n2, m2), 0, n2, m2, n, m);
+            return T_entry(g, 0, n2, m2, n, m) + terms_T(g, conv22R(sp.t, n2, m2), 0, n2, m2, n, m);
+        }
+        case K_L2P_V:
+            return terms_entry(evf3(sp.aux, pot_in, n2, m2), p, n2, m2, n, m);
+        case K_L2P_U: {
+            Terms d = dt3R(sp.aux, n2, m2);
+            cplx s = C(0);
+            for (int i = 0; i < d.k; ++i) {
+                int a = n2 + d.dn[i], b = m2 + d.dm[i];
+                if (valid_nm(a, b, p)) s = s + d.co[i] * terms_entry(evf3(sp.aux2, pot_in, a, b), p, a, b, n, m);
+            }
+            return s;
+        }
+        case K_P2M:
+            return terms_entry(eve4(sp.aux, pot_out, n2, m2), p, n2, m2, n, m);
+    }
+    return C(0);
+}
+
+// Diagonal scalings.  pot: 0 = phi, 1 = chi.
+__device__ double scale_in(const Ctx2& g, const Spec& sp, int pot, int n, int m) {
+    double v = nu(g.fact, n, m);
+    switch (sp.kind) {
+        case K_M2L: return 1.0 / v;                                          // S, h = 1
+        case K_M2M: return 1.0 / v;                                          // S, h = 1 (both)
+        case K_L2L: return v / ldexp(1.0, n + pot);                          // R, h = 2
+        case K_L2P_V: case K_L2P_U: return v;                                // R, h = 1
+        case K_P2M: return 1.0 / v;                                          // g_hat = nu g
+    }
+    return 1.0;
+}
+__device__ double scale_out(const Ctx2& g, const Spec& sp, int pot, int n, int m) {
+    double v = nu(g.fact, n, m);
+    switch (sp.kind) {
+        case K_M2L: return 1.0 / v;                                          // R, h = 1
+        case K_M2M: return v / ldexp(1.0, n + 1 - pot);                      // S, h = 2
+        case K_L2L: return 1.0 / v;                                          // R, h = 1
+        case K_L2P_V: case K_L2P_U: return 1.0 / v;                          // R_hat basis
+        case K_P2M: return v;                                                // S, h = 1
+    }
+    return 1.0;
+}
+
+__device__ inline void decode(int r, int& n, int& m, int& part) {
+    n = (int)sqrt((double)r);
+    while (n * n > r) --n;
+    while ((n + 1) * (n + 1) <= r) ++n;
+    int rem = r - n * n;
+    if (rem == 0) {
+        m = 0;
+        part = 0;
+    } else {
+        m = (rem + 1) / 2;
+        part = (rem & 1) ? 0 : 1;
+    }
+}
+
+__device__ void dims(int kind, int P, int& pots_out, int& pots_in) {
+    switch (kind) {
+        case K_M2L: case K_M2M: case K_L2L: pots_out = 2; pots_in = 2; return;
+        case K_L2P_V: case K_L2P_U: pots_out = 1; pots_in = 2; return;
+        case K_P2M: pots_out = 2; pots_in = 1; return;
+        default: pots_out = 1; pots_in = 1; return;
+    }
+}
+
+__global__ void k_build_ops(int p, const Spec* __restrict__ specs, double* __restrict__ out,
+                            const int64_t* __restrict__ out_off) {
+    __shared__ cplx Q[MAXTRI];
+    __shared__ double fact[2 * MAXD + 2];
+    const Spec sp = specs[blockIdx.x];
+    const int P = p * p;
+    int D;
+    switch (sp.kind) {
+        case K_M2L: D = 2 * p - 2; break;
+        case K_M2M: case K_L2L: D = p - 1; break;
+        default: D = 0; break;
+    }
+    for (int k = threadIdx.x; k < 2 * MAXD + 2; k += blockDim.x) {
+        double f = 1.0;
+        for (int j = 2; j <= k; ++j) f *= j;
+        fact[k] = f;
+    }
+    const double x = sp.t[0], y = sp.t[1], z = sp.t[2];
+    const double r2 = x * x + y * y + z * z;
+    // Q_m^m along the diagonal, then each column m by the recurrence in n.
+    if (threadIdx.x == 0) {
+        Q[0] = C(1, 0);
+        for (int m = 1; m <= D; ++m) {
+            double c = -sqrt((2.0 * m - 1.0) / (2.0 * m));
+            Q[tri(m, m)] = c * (C(x, y) * Q[tri(m - 1, m - 1)]);
+        }
+    }
+    __syncthreads();
+    for (int m = threadIdx.x; m <= D; m += blockDim.x) {
+        if (m + 1 <= D) Q[tri(m + 1, m)] = (sqrt(2.0 * m + 1.0) * z) * Q[tri(m, m)];
+        for (int n = m + 2; n <= D; ++n) {
+            double a = (2.0 * n - 1.0) / sqrt((double)(n + m) * (n - m));
+            double b = sqrt((double)(n + m - 1) * (n - m - 1)) / sqrt((double)(n + m) * (n - m));
+            Q[tri(n, m)] = (a * z) * Q[tri(n - 1, m)] - (b * r2) * Q[tri(n - 2, m)];
+        }
+    }
+    __syncthreads();
+    Ctx2 g{Q, sqrt(r2), fact, p, {x, y, z}};
+    int po, pi;
+    dims(sp.kind, P, po, pi);
+    const int rows = po * P, cols = pi * P;
+    double* dst = out + out_off[blockIdx.x] + sp.row0;
+    for (int64_t e = threadIdx.x; e < (int64_t)rows * cols; e += blockDim.x) {
+        int row = (int)(e % rows), col = (int)(e / rows);  // k-major: element (col, row) at col*rows + row
+        int pot_out = row / P, pot_in = col / P;
+        int n2, m2, pt2, n, m, q;
+        decode(row % P, n2, m2, pt2);
+        decode(col % P, n, m, q);
+        // realify: the input unit vector sets c_n^m = 1 or i, and c_n^{-m} by symmetry
+        cplx cin = q ? C(0, 1) : C(1, 0);
+        cplx yv = op_entry(g, sp, pot_out, pot_in, n2, m2, n, m) * cin;
+        if (m > 0) yv = yv + op_entry(g, sp, pot_out, pot_in, n2, m2, n, -m) * (sgn(m) * conj(cin));
+        double val = pt2 ? yv.im : yv.re;
+        val *= scale_out(g, sp, pot_out, n2, m2) * scale_in(g, sp, pot_in, n, m);
+        dst[(int64_t)col * sp.ld + row] = val;
+    }
+}
+
+template <typename T>
+__global__ void k_cast(int64_t n, const double* __restrict__ in, T* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (T)in[i];
+}
+
+}  // namespace
+
+int m2l_slot_host(int dx, int dy, int dz) {
+    if (dx < -3 || dx > 3 || dy < -3 || dy > 3 || dz < -3 || dz > 3) return -1;
+    if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1) return -1;
+    int slot = 0;
+    for (int a = -3; a <= 3; ++a)
+        for (int b = -3; b <= 3; ++b)
+            for (int c = -3; c <= 3; ++c) {
+                if (a >= -1 && a <= 1 && b >= -1 && b <= 1 && c >= -1 && c <= 1) continue;
+                if (a == dx && b == dy && c == dz) return slot;
+                ++slot;
+            }
+    return -1;
+}
+
+void free_operators(OpTables& ops) {
+    Buf* all[] = {&ops.m2l, &ops.m2m, &ops.l2l, &ops.l2p, &ops.p2m, &ops.offsets, &ops.slot_of};
+    for (Buf* b : all) {
+        if (b->ptr) cudaFree(b->ptr);
+        b->ptr = nullptr;
+        b->cap = 0;
+    }
+    ops.p = 0;
+}
+
+template <typename T>
+void build_operators(Ctx* c, int p, OpTables& ops) {
+    cudaStream_t s = stream_of(c);
+    const int P = p * p;
+    ops.p = p;
+    ops.P = P;
+    std::vector<Spec> specs;
+    std::vector<int64_t> off;
+    int64_t total = 0;
+    // size: entries of the block; ld / row0: placement inside a wider destination (0 = own block)
+    auto push = [&](int kind, int aux, int aux2, double tx, double ty, double tz, int64_t rows, int64_t size,
+                    int64_t ld = 0, int row0 = 0, int64_t at = -1) {
+        Spec sp{};
+        sp.kind = kind;
+        sp.aux = aux;
+        sp.aux2 = aux2;
+        sp.row0 = row0;
+        sp.ld = ld ? ld : rows;
+        sp.t[0] = tx;
+        sp.t[1] = ty;
+        sp.t[2] = tz;
+        specs.push_back(sp);
+        off.push_back(at >= 0 ? at : total);
+        if (at < 0) total += size;
+    };
+    // M2L: offset d = source - target (box units), t = target - source = -d
+    std::vector<int> offs, slot_of(343, -1);
+    int slot = 0;
+    for (int a = -3; a <= 3; ++a)
+        for (int b = -3; b <= 3; ++b)
+            for (int cc = -3; cc <= 3; ++cc) {
+                if (a >= -1 && a <= 1 && b >= -1 && b <= 1 && cc >= -1 && cc <= 1) continue;
+                offs.push_back(a);
+                offs.push_back(b);
+                offs.push_back(cc);
+                slot_of[(a + 3) * 49 + (b + 3) * 7 + (cc + 3)] = slot++;
+                push(K_M2L, 0, 0, -a, -b, -cc, 2 * P, 4ll * P * P);
+            }
+    const int64_t m2l_end = total;
+    // child octant o = (ox, oy, oz): child = 2 parent + o; in child units t(M2M) = 0.5 - o, t(L2L) = o - 0.5
+    for (int o = 0; o < 8; ++o) {
+        int ox = o & 1, oy = (o >> 1) & 1, oz = (o >> 2) & 1;
+        push(K_M2M, 0, 0, 0.5 - ox, 0.5 - oy, 0.5 - oz, 2 * P, 4ll * P * P);
+    }
+    const int64_t m2m_end = total;
+    for (int o = 0; o < 8; ++o) {
+        int ox = o & 1, oy = (o >> 1) & 1, oz = (o >> 2) & 1;
+        push(K_L2L, 0, 0, ox - 0.5, oy - 0.5, oz - 0.5, 2 * P, 4ll * P * P);
+    }
+    const int64_t l2l_end = total;
+    // L2P: one [2P][12P] matrix; block j (v_x, v_y, v_z, u_xx, u_xy, ..., u_zz) at rows j*P
+    const int64_t l2p_beg = total;
+    total += 24ll * P * P;
+    for (int k = 0; k < 3; ++k) push(K_L2P_V, k, 0, 0, 0, 0, P, 0, 12ll * P, k * P, l2p_beg);
+    for (int l = 0; l < 3; ++l)
+        for (int k = 0; k < 3; ++k) push(K_L2P_U, l, k, 0, 0, 0, P, 0, 12ll * P, (3 + 3 * l + k) * P, l2p_beg);
+    const int64_t l2p_end = total;
+    // P2M: [3P][2P], the three strength components stacked along the input
+    for (int k = 0; k < 3; ++k) push(K_P2M, k, 0, 0, 0, 0, 2 * P, 2ll * P * P);
+    const int64_t p2m_end = total;
+
+    const int nspec = (int)specs.size();
+    Buf dspec, doff, dout;
+    ensure(c, dspec, nspec * sizeof(Spec));
+    ensure(c, doff, nspec * sizeof(int64_t));
+    ensure(c, dout, total * sizeof(double));
+    try {
+        cuda_check(cudaMemcpyAsync(dspec.ptr, specs.data(), nspec * sizeof(Spec), cudaMemcpyHostToDevice, s), "specs");
+        cuda_check(cudaMemcpyAsync(doff.ptr, off.data(), nspec * sizeof(int64_t), cudaMemcpyHostToDevice, s), "offs");
+        k_build_ops<<<nspec, 256, 0, s>>>(p, dspec.as<Spec>(), dout.as<double>(), doff.as<int64_t>());
+        count_launch(c);
+        check_launch("build operators");
+        auto cast = [&](Buf& dst, int64_t beg, int64_t end) {
+            ensure(c, dst, (end - beg) * sizeof(T));
+            k_cast<T><<<grid_for(end - beg, 256), 256, 0, s>>>(end - beg, dout.as<double>() + beg, dst.as<T>());
+            count_launch(c);
+        };
+        cast(ops.m2l, 0, m2l_end);
+        cast(ops.m2m, m2l_end, m2m_end);
+        cast(ops.l2l, m2m_end, l2l_end);
+        cast(ops.l2p, l2l_end, l2p_end);
+        cast(ops.p2m, l2p_end, p2m_end);
+        check_launch("cast operators");
+        ensure(c, ops.offsets, offs.size() * sizeof(int));
+        ensure(c, ops.slot_of, slot_of.size() * sizeof(int));
+        cuda_check(cudaMemcpyAsync(ops.offsets.ptr, offs.data(), offs.size() * sizeof(int), cudaMemcpyHostToDevice, s),
+                   "offsets");
+        cuda_check(cudaMemcpyAsync(ops.slot_of.ptr, slot_of.data(), slot_of.size() * sizeof(int),
+                                   cudaMemcpyHostToDevice, s),
+                   "slots");
+        cuda_check(cudaStreamSynchronize(s), "operators");
+    } catch (...) {
+        cudaFree(dspec.ptr);
+        cudaFree(doff.ptr);
+        cudaFree(dout.ptr);
+        throw;
+    }
+    cudaFree(dspec.ptr);
+    cudaFree(doff.ptr);
+    cudaFree(dout.ptr);
+}
+
+template void build_operators<float>(Ctx*, int, OpTables&);
+template void build_operators<double>(Ctx*, int, OpTables&);
+
+}  // namespace lhv

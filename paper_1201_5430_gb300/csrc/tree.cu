@@ -1,0 +1,622 @@
+// Octree construction on the GPU: cube, Morton keys, stable LSD radix sort,
+// boxes per level, parent/child ranges, colleague lists and P2P work items.
+//
+// The paper fixes the data structure only as "octree, neighbor lists" (Sec. 4,
+// table of FMM stages) with the standard 189-box M2L stencil (Sec. 5).  The
+// construction here is: cube origin = per-axis minimum, side = the smallest
+// power of two >= the largest extent; q = floor((x - x0) 2^21 / side) in FP64,
+// clamped to [0, 2^21 - 1]; key = 63-bit interleave with x in bit 0 of each
+// triple; stable sort by key (ties keep the caller's order); leaf level
+// L = min(L_leaf, L_K, max_level) where L_leaf is the shallowest level with at
+// most leaf_max elements per box and L_K the deepest level whose box side is
+// >= r_K, the radius beyond which the Gaussian core of Eq. vem1 equals 1 to
+// eps/10 (so every far-field pair sees the singular kernel of Eq. 1).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "lhv_internal.cuh"
+
+namespace lhv {
+
+// ---------------------------------------------------------------------------
+// Bit interleave helpers (21 bits per axis into 63 bits)
+// ---------------------------------------------------------------------------
+__host__ __device__ inline uint64_t spread3(uint64_t v) {
+    v &= 0x1fffffull;
+    v = (v | (v << 32)) & 0x1f00000000ffffull;
+    v = (v | (v << 16)) & 0x1f0000ff0000ffull;
+    v = (v | (v << 8)) & 0x100f00f00f00f00full;
+    v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+    v = (v | (v << 2)) & 0x1249249249249249ull;
+    return v;
+}
+
+__host__ __device__ inline uint64_t compact3(uint64_t v) {
+    v &= 0x1249249249249249ull;
+    v = (v ^ (v >> 2)) & 0x10c30c30c30c30c3ull;
+    v = (v ^ (v >> 4)) & 0x100f00f00f00f00full;
+    v = (v ^ (v >> 8)) & 0x1f0000ff0000ffull;
+    v = (v ^ (v >> 16)) & 0x1f00000000ffffull;
+    v = (v ^ (v >> 32)) & 0x1fffffull;
+    return v;
+}
+
+__host__ __device__ inline uint64_t morton3(uint64_t qx, uint64_t qy, uint64_t qz) {
+    return spread3(qx) | (spread3(qy) << 1) | (spread3(qz) << 2);
+}
+
+// ---------------------------------------------------------------------------
+// Cube
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_bbox_partial(int64_t n, const vec4_t<T>* __restrict__ x4, const vec4_t<T>* __restrict__ w4,
+                               double* __restrict__ part, int* __restrict__ nonfinite) {
+    __shared__ double s[6][256];
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    int bad = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        vec4_t<T> p = x4[i];
+        vec4_t<T> q = w4 ? w4[i] : p;
+        double c[3] = {(double)p.x, (double)p.y, (double)p.z};
+        bad |= !(isfinite(c[0]) && isfinite(c[1]) && isfinite(c[2]));
+        bad |= !(isfinite((double)q.x) && isfinite((double)q.y) && isfinite((double)q.z));
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = fmin(lo[k], c[k]);
+            hi[k] = fmax(hi[k], c[k]);
+        }
+    }
+    if (bad) atomicOr(nonfinite, 1);
+    for (int k = 0; k < 3; ++k) {
+        s[k][threadIdx.x] = lo[k];
+        s[3 + k][threadIdx.x] = hi[k];
+    }
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            for (int k = 0; k < 3; ++k) {
+                s[k][threadIdx.x] = fmin(s[k][threadIdx.x], s[k][threadIdx.x + w]);
+                s[3 + k][threadIdx.x] = fmax(s[3 + k][threadIdx.x], s[3 + k][threadIdx.x + w]);
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 6) part[blockIdx.x * 6 + threadIdx.x] = s[threadIdx.x][0];
+}
+
+__global__ void k_bbox_final(int nparts, const double* __restrict__ part, TreeParams* __restrict__ tp) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int b = 0; b < nparts; ++b)
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = fmin(lo[k], part[b * 6 + k]);
+            hi[k] = fmax(hi[k], part[b * 6 + 3 + k]);
+        }
+    double ext = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        tp->x0[k] = lo[k];
+        ext = fmax(ext, hi[k] - lo[k]);
+    }
+    double side = 1.0;
+    if (ext > 0.0) {
+        int e;
+        double mant = frexp(ext, &e);  // ext = mant 2^e, 0.5 <= mant < 1
+        side = (mant == 0.5) ? ldexp(1.0, e - 1) : ldexp(1.0, e);
+    }
+    tp->side = side;
+    tp->deepest_shared = -1;
+}
+
+template <typename T>
+__global__ void k_morton(int64_t n, const vec4_t<T>* __restrict__ x4, const TreeParams* __restrict__ tp,
+                         uint64_t* __restrict__ keys, int* __restrict__ idx) {
+    const double scale = (double)(1 << KEY_BITS) / tp->side;
+    const double x0 = tp->x0[0], y0 = tp->x0[1], z0 = tp->x0[2];
+    const double qmax = (double)((1 << KEY_BITS) - 1);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        vec4_t<T> p = x4[i];
+        double qx = fmin(fmax(floor(((double)p.x - x0) * scale), 0.0), qmax);
+        double qy = fmin(fmax(floor(((double)p.y - y0) * scale), 0.0), qmax);
+        double qz = fmin(fmax(floor(((double)p.z - z0) * scale), 0.0), qmax);
+        keys[i] = morton3((uint64_t)qx, (uint64_t)qy, (uint64_t)qz);
+        idx[i] = (int)i;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Stable LSD radix sort of (key, index), 8-bit digits
+// ---------------------------------------------------------------------------
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_ITEMS = 16;
+constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
+
+__global__ void k_radix_hist(int64_t n, const uint64_t* __restrict__ keys, int shift, int nblocks,
+                             int* __restrict__ hist) {
+    __shared__ int cnt[256];
+    cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * SORT_TILE;
+    for (int j = 0; j < SORT_ITEMS; ++j) {
+        int64_t i = base + j * SORT_THREADS + threadIdx.x;
+        if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 255u], 1);
+    }
+    __syncthreads();
+    hist[threadIdx.x * nblocks + blockIdx.x] = cnt[threadIdx.x];
+}
+
+__global__ void k_radix_scatter(int64_t n, const uint64_t* __restrict__ kin, const int* __restrict__ vin,
+                                uint64_t* __restrict__ kout, int* __restrict__ vout, int shift, int nblocks,
+                                const int* __restrict__ offs) {
+    __shared__ int base[256];
+    __shared__ int wcnt[SORT_THREADS / 32][257];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    base[t] = offs[t * nblocks + blockIdx.x];
+    for (int w = 0; w < SORT_THREADS / 32; ++w) wcnt[w][t] = 0;
+    __syncthreads();
+    const int64_t tile = (int64_t)blockIdx.x * SORT_TILE;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int j = 0; j < SORT_ITEMS; ++j) {
+        int64_t i = tile + j * SORT_THREADS + t;
+        bool valid = i < n;
+        uint64_t key = valid ? kin[i] : 0ull;
+        int val = valid ? vin[i] : 0;
+        int d = valid ? (int)((key >> shift) & 255u) : 256;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        int rank = __popc(peers & lt);
+        if (valid && rank == 0) wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        if (valid) {
+            int pos = base[d] + rank;
+            for (int w = 0; w < warp; ++w) pos += wcnt[w][d];
+            kout[pos] = key;
+            vout[pos] = val;
+        }
+        __syncthreads();
+        int add = 0;
+        for (int w = 0; w < SORT_THREADS / 32; ++w) {
+            add += wcnt[w][t];
+            wcnt[w][t] = 0;
+        }
+        base[t] += add;
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan of int32 (three passes)
+// ---------------------------------------------------------------------------
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 16;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+__device__ inline int block_exclusive_scan(int v, int* total) {
+    __shared__ int warp_sums[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int nw = blockDim.x >> 5;
+        int s = lane < nw ? warp_sums[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < nw) warp_sums[lane] = s;
+    }
+    __syncthreads();
+    int excl = x - v + (warp > 0 ? warp_sums[warp - 1] : 0);
+    if (total) *total = warp_sums[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return excl;
+}
+
+__global__ void k_scan_reduce(int64_t n, const int* __restrict__ in, int* __restrict__ sums) {
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    int s = 0;
+    for (int j = 0; j < SCAN_ITEMS; ++j)
+        if (base + j < n) s += in[base + j];
+    int total;
+    block_exclusive_scan(s, &total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+// Single block: exclusive scan of the block sums; writes the grand total.
+__global__ void k_scan_sums(int nb, int* __restrict__ sums, int* __restrict__ total_out) {
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < nb; b0 += blockDim.x) {
+        int i = b0 + threadIdx.x;
+        int v = i < nb ? sums[i] : 0;
+        int tot;
+        int ex = block_exclusive_scan(v, &tot);
+        if (i < nb) sums[i] = carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && total_out) *total_out = carry;
+}
+
+__global__ void k_scan_apply(int64_t n, const int* __restrict__ in, const int* __restrict__ sums,
+                             int* __restrict__ out) {
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    int v[SCAN_ITEMS];
+    int s = 0;
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        v[j] = (base + j < n) ? in[base + j] : 0;
+        s += v[j];
+    }
+    int ex = block_exclusive_scan(s, nullptr) + sums[blockIdx.x];
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        if (base + j < n) out[base + j] = ex;
+        ex += v[j];
+    }
+}
+
+void exclusive_scan(Ctx* c, int64_t n, const int* in, int* out, int* sums_tmp, int* total_out) {
+    cudaStream_t s = stream_of(c);
+    int nb = (int)((n + SCAN_TILE - 1) / SCAN_TILE);
+    if (nb < 1) nb = 1;
+    k_scan_reduce<<<nb, SCAN_THREADS, 0, s>>>(n, in, sums_tmp);
+    count_launch(c);
+    k_scan_sums<<<1, 1024, 0, s>>>(nb, sums_tmp, total_out);
+    count_launch(c);
+    k_scan_apply<<<nb, SCAN_THREADS, 0, s>>>(n, in, sums_tmp, out);
+    count_launch(c);
+    check_launch("exclusive_scan");
+}
+
+int64_t scan_tmp_ints(int64_t n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 1; }
+
+// ---------------------------------------------------------------------------
+// Leaf level
+// ---------------------------------------------------------------------------
+__global__ void k_shared_level(int64_t n, int leaf_max, const uint64_t* __restrict__ keys,
+                               TreeParams* __restrict__ tp) {
+    int best = -1;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i + leaf_max < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t x = keys[i] ^ keys[i + leaf_max];
+        int lvl;
+        if (x == 0) {
+            lvl = KEY_BITS;
+        } else {
+            int msb = 63 - __clzll((long long)x);
+            lvl = KEY_BITS - (msb + 3) / 3;  // deepest level at which both keys share a box
+        }
+        best = max(best, lvl);
+    }
+    for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if ((threadIdx.x & 31) == 0 && best >= 0) atomicMax(&tp->deepest_shared, best);
+}
+
+__global__ void k_leaf_level(TreeParams* __restrict__ tp, double rK, int max_level) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int L_leaf = min(tp->deepest_shared + 1, KEY_BITS);
+    int L_K = KEY_BITS;
+    if (rK > 0.0) {
+        L_K = 0;
+        for (int l = 0; l <= KEY_BITS; ++l)
+            if (ldexp(tp->side, -l) >= rK) L_K = l;
+    }
+    int L = min(L_leaf, L_K);
+    if (max_level > 0) L = min(L, max_level);
+    tp->L = L;
+}
+
+// ---------------------------------------------------------------------------
+// Boxes per level (temporary layout: capacity offsets)
+// ---------------------------------------------------------------------------
+__global__ void k_level_flags(int64_t n, const uint64_t* __restrict__ keys, int shift, int* __restrict__ flags) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        flags[i] = (i == 0) || ((keys[i] >> shift) != (keys[i - 1] >> shift));
+}
+
+// box_of[i] = exclusive[i] + flag[i] - 1; records box starts and keys.
+__global__ void k_level_boxes(int64_t n, const uint64_t* __restrict__ keys, int shift, const int* __restrict__ flags,
+                              int* __restrict__ boxof, uint64_t* __restrict__ bkey, int* __restrict__ bbeg,
+                              int* __restrict__ bend) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int f = flags[i];
+        int b = boxof[i] + f - 1;
+        boxof[i] = b;
+        if (f) {
+            bkey[b] = keys[i] >> shift;
+            bbeg[b] = (int)i;
+            if (b > 0) bend[b - 1] = (int)i;
+        }
+        if (i == n - 1) bend[b] = (int)n;
+    }
+}
+
+// Parent index (level l-1) of every box at level l, from the element ranges.
+__global__ void k_level_parent(const int* __restrict__ nb_dev, const int* __restrict__ bbeg,
+                               const int* __restrict__ boxof_up, int* __restrict__ bparent) {
+    int nb = *nb_dev;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x)
+        bparent[b] = boxof_up[bbeg[b]];
+}
+
+__global__ void k_level_children(const int* __restrict__ nb_dev, const int* __restrict__ bparent,
+                                 int* __restrict__ cbeg_up, int* __restrict__ cend_up) {
+    int nb = *nb_dev;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+        int p = bparent[b];
+        if (b == 0 || bparent[b - 1] != p) cbeg_up[p] = b;
+        if (b == nb - 1 || bparent[b + 1] != p) cend_up[p] = b + 1;
+    }
+}
+
+// Copy one level from the capacity layout to the compact layout.
+__global__ void k_compact_level(int nb, int level, int L, const uint64_t* __restrict__ tkey,
+                                const int* __restrict__ tbeg, const int* __restrict__ tend,
+                                const int* __restrict__ tpar, const int* __restrict__ tcb, const int* __restrict__ tce,
+                                uint64_t* __restrict__ bkey, int* __restrict__ bbeg, int* __restrict__ bend,
+                                int* __restrict__ bpar, int* __restrict__ bcb, int* __restrict__ bce) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+        bkey[b] = tkey[b];
+        bbeg[b] = tbeg[b];
+        bend[b] = tend[b];
+        bpar[b] = level > 0 ? tpar[b] : -1;
+        bcb[b] = level < L ? tcb[b] : 0;
+        bce[b] = level < L ? tce[b] : 0;
+    }
+}
+
+// 27 colleagues of every box of one level (binary search among the level's keys).
+__global__ void k_colleagues(int nb, int level, const uint64_t* __restrict__ bkey, int* __restrict__ col) {
+    const int64_t dim = 1ll << level;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+        uint64_t key = bkey[b];
+        int64_t cx = (int64_t)compact3(key), cy = (int64_t)compact3(key >> 1), cz = (int64_t)compact3(key >> 2);
+        int slot = 0;
+        for (int dx = -1; dx <= 1; ++dx)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dz = -1; dz <= 1; ++dz, ++slot) {
+                    int64_t x = cx + dx, y = cy + dy, z = cz + dz;
+                    int found = -1;
+                    if (x >= 0 && y >= 0 && z >= 0 && x < dim && y < dim && z < dim) {
+                        uint64_t k2 = morton3((uint64_t)x, (uint64_t)y, (uint64_t)z);
+                        int lo = 0, hi = nb - 1;
+                        while (lo <= hi) {
+                            int mid = (lo + hi) >> 1;
+                            uint64_t km = bkey[mid];
+                            if (km == k2) {
+                                found = mid;
+                                break;
+                            }
+                            if (km < k2) lo = mid + 1; else hi = mid - 1;
+                        }
+                    }
+                    col[(int64_t)b * 27 + slot] = found;
+                }
+    }
+}
+
+// P2P work items: leaf b is split into ceil(count / P2P_TILE) tiles.
+__global__ void k_tile_counts(int nb, const int* __restrict__ bbeg, const int* __restrict__ bend,
+                              int* __restrict__ cnt) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x)
+        cnt[b] = (bend[b] - bbeg[b] + P2P_TILE - 1) / P2P_TILE;
+}
+
+__global__ void k_tile_fill(int nb, const int* __restrict__ bbeg, const int* __restrict__ bend,
+                            const int* __restrict__ first, int2* __restrict__ tiles) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+        int nt = (bend[b] - bbeg[b] + P2P_TILE - 1) / P2P_TILE;
+        for (int j = 0; j < nt; ++j) tiles[first[b] + j] = make_int2(b, bbeg[b] + j * P2P_TILE);
+    }
+}
+
+template <typename T>
+__global__ void k_gather(int64_t n, const int* __restrict__ perm, const vec4_t<T>* __restrict__ x4,
+                         const vec4_t<T>* __restrict__ w4, vec4_t<T>* __restrict__ xs, vec4_t<T>* __restrict__ ws) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int j = perm[i];
+        vec4_t<T> a = x4[j], b = w4[j];
+        a.w = 0;
+        b.w = 0;
+        xs[i] = a;
+        ws[i] = b;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host orchestration
+// ---------------------------------------------------------------------------
+template <typename T>
+void gather_sorted(Ctx* c, int64_t n, const int* perm, const vec4_t<T>* x4, const vec4_t<T>* w4, vec4_t<T>* xs,
+                   vec4_t<T>* ws) {
+    if (n <= 0) return;
+    k_gather<T><<<grid_for(n, 256), 256, 0, stream_of(c)>>>(n, perm, x4, w4, xs, ws);
+    count_launch(c);
+    check_launch("gather");
+}
+
+template <typename T>
+int build_tree(Ctx* c, int64_t n, const vec4_t<T>* x4, const vec4_t<T>* w4, TreeBufs& tb, Levels& lv,
+               TreeParams& hp, Error& err) {
+    cudaStream_t s = stream_of(c);
+    const int leaf_max = ctx_leaf_max(c);
+    const int64_t nn = n;
+
+    // capacities that depend on n only
+    const int nsort = (int)((nn + SORT_TILE - 1) / SORT_TILE);
+    ensure(c, tb.keys_a, nn * 8);
+    ensure(c, tb.keys_b, nn * 8);
+    ensure(c, tb.idx_a, nn * 4);
+    ensure(c, tb.idx_b, nn * 4);
+    ensure(c, tb.hist, (int64_t)nsort * 256 * 4 + 64);
+    ensure(c, tb.flags, nn * 4);
+    ensure(c, tb.boxof_a, nn * 4);
+    ensure(c, tb.boxof_b, nn * 4);
+    ensure(c, tb.scan_tmp, (scan_tmp_ints(std::max<int64_t>(nn, 256 * (int64_t)nsort)) + 64) * 4);
+    ensure(c, tb.params, sizeof(TreeParams));
+    ensure(c, tb.counts, 64 * 4);
+
+    TreeParams* tp = tb.params.as<TreeParams>();
+    int* counts = tb.counts.as<int>();
+    cuda_check(cudaMemsetAsync(tp, 0, sizeof(TreeParams), s), "memset params");
+    cuda_check(cudaMemsetAsync(counts, 0, 64 * 4, s), "memset counts");
+
+    // cube and keys (the radix histogram buffer holds the bounding-box partials first)
+    const int nparts = grid_for(nn, 256, 1024);
+    ensure(c, tb.hist, std::max<int64_t>((int64_t)nsort * 256 * 4 + 64, (int64_t)nparts * 6 * 8));
+    double* part = reinterpret_cast<double*>(tb.hist.ptr);
+    k_bbox_partial<T><<<nparts, 256, 0, s>>>(nn, x4, w4, part, &tp->nonfinite);
+    count_launch(c);
+    k_bbox_final<<<1, 32, 0, s>>>(nparts, part, tp);
+    count_launch(c);
+    k_morton<T><<<grid_for(nn, 256), 256, 0, s>>>(nn, x4, tp, tb.keys_a.as<uint64_t>(), tb.idx_a.as<int>());
+    count_launch(c);
+    check_launch("keys");
+
+    // stable radix sort, 8 passes of 8 bits
+    uint64_t* kin = tb.keys_a.as<uint64_t>();
+    uint64_t* kout = tb.keys_b.as<uint64_t>();
+    int* vin = tb.idx_a.as<int>();
+    int* vout = tb.idx_b.as<int>();
+    int* hist = tb.hist.as<int>();
+    for (int pass = 0; pass < 8; ++pass) {
+        int shift = pass * 8;
+        k_radix_hist<<<nsort, SORT_THREADS, 0, s>>>(nn, kin, shift, nsort, hist);
+        count_launch(c);
+        exclusive_scan(c, (int64_t)nsort * 256, hist, hist, tb.scan_tmp.as<int>(), nullptr);
+        k_radix_scatter<<<nsort, SORT_THREADS, 0, s>>>(nn, kin, vin, kout, vout, shift, nsort, hist);
+        count_launch(c);
+        std::swap(kin, kout);
+        std::swap(vin, vout);
+    }
+    check_launch("sort");
+    // after an even number of passes the result is back in keys_a / idx_a
+    uint64_t* keys = kin;
+    int* perm = vin;
+
+    k_shared_level<<<grid_for(nn, 256), 256, 0, s>>>(nn, leaf_max, keys, tp);
+    count_launch(c);
+    k_leaf_level<<<1, 32, 0, s>>>(tp, ctx_rK(c), ctx_max_level(c));
+    count_launch(c);
+    check_launch("leaf level");
+    cuda_check(cudaMemcpyAsync(&hp, tp, sizeof(TreeParams), cudaMemcpyDeviceToHost, s), "read params");
+    cuda_check(cudaStreamSynchronize(s), "sync params");
+    if (hp.nonfinite) {
+        err = {LHV_ENONFINITE, "non-finite position or strength"};
+        return LHV_ENONFINITE;
+    }
+    const int L = hp.L;
+    lv.L = L;
+
+    // temporary per-level arrays in capacity layout
+    lv.cap_off[0] = 0;
+    for (int l = 0; l <= L; ++l) {
+        int64_t cap = std::min<int64_t>(nn, (l >= 21) ? nn : (1ll << (3 * l)));
+        lv.cap_off[l + 1] = lv.cap_off[l] + (int)cap;
+    }
+    const int64_t tot_cap = lv.cap_off[L + 1];
+    Buf& tkey = ctx_tmp(c, 0);
+    Buf& tbeg = ctx_tmp(c, 1);
+    Buf& tend = ctx_tmp(c, 2);
+    Buf& tpar = ctx_tmp(c, 3);
+    Buf& tcb = ctx_tmp(c, 4);
+    Buf& tce = ctx_tmp(c, 5);
+    ensure(c, tkey, tot_cap * 8);
+    ensure(c, tbeg, tot_cap * 4);
+    ensure(c, tend, tot_cap * 4);
+    ensure(c, tpar, tot_cap * 4);
+    ensure(c, tcb, tot_cap * 4);
+    ensure(c, tce, tot_cap * 4);
+
+    int* boxof_prev = tb.boxof_a.as<int>();
+    int* boxof_cur = tb.boxof_b.as<int>();
+    for (int l = 0; l <= L; ++l) {
+        int shift = 3 * (KEY_BITS - l);
+        int off = lv.cap_off[l];
+        int* flags = tb.flags.as<int>();
+        k_level_flags<<<grid_for(nn, 256), 256, 0, s>>>(nn, keys, shift, flags);
+        count_launch(c);
+        exclusive_scan(c, nn, flags, boxof_cur, tb.scan_tmp.as<int>(), counts + l);
+        // the scan total is the number of boxes of the level
+        k_level_boxes<<<grid_for(nn, 256), 256, 0, s>>>(nn, keys, shift, flags, boxof_cur, tkey.as<uint64_t>() + off,
+                                                        tbeg.as<int>() + off, tend.as<int>() + off);
+        count_launch(c);
+        if (l > 0) {
+            int offu = lv.cap_off[l - 1];
+            int capl = lv.cap_off[l + 1] - off;
+            k_level_parent<<<grid_for(capl, 256), 256, 0, s>>>(counts + l, tbeg.as<int>() + off, boxof_prev,
+                                                                tpar.as<int>() + off);
+            count_launch(c);
+            k_level_children<<<grid_for(capl, 256), 256, 0, s>>>(counts + l, tpar.as<int>() + off,
+                                                                  tcb.as<int>() + offu, tce.as<int>() + offu);
+            count_launch(c);
+        }
+        std::swap(boxof_prev, boxof_cur);
+        check_launch("levels");
+    }
+    int hcounts[64];
+    cuda_check(cudaMemcpyAsync(hcounts, counts, 64 * 4, cudaMemcpyDeviceToHost, s), "read counts");
+    cuda_check(cudaStreamSynchronize(s), "sync counts");
+    lv.off[0] = 0;
+    for (int l = 0; l < MAX_LEVELS; ++l) {
+        lv.nbox[l] = (l <= L) ? hcounts[l] : 0;
+        lv.off[l + 1] = lv.off[l] + lv.nbox[l];
+    }
+    const int64_t nbt = lv.off[L + 1];
+
+    // compact layout
+    ensure(c, tb.bkey, nbt * 8);
+    ensure(c, tb.bbeg, nbt * 4);
+    ensure(c, tb.bend, nbt * 4);
+    ensure(c, tb.bparent, nbt * 4);
+    ensure(c, tb.bcbeg, nbt * 4);
+    ensure(c, tb.bcend, nbt * 4);
+    ensure(c, tb.bcol, nbt * 27 * 4);
+    for (int l = 0; l <= L; ++l) {
+        int nb = lv.nbox[l], o = lv.off[l], co = lv.cap_off[l];
+        k_compact_level<<<grid_for(nb, 256), 256, 0, s>>>(
+            nb, l, L, tkey.as<uint64_t>() + co, tbeg.as<int>() + co, tend.as<int>() + co, tpar.as<int>() + co,
+            tcb.as<int>() + co, tce.as<int>() + co, tb.bkey.as<uint64_t>() + o, tb.bbeg.as<int>() + o,
+            tb.bend.as<int>() + o, tb.bparent.as<int>() + o, tb.bcbeg.as<int>() + o, tb.bcend.as<int>() + o);
+        count_launch(c);
+        k_colleagues<<<grid_for(nb, 128), 128, 0, s>>>(nb, l, tb.bkey.as<uint64_t>() + o,
+                                                       tb.bcol.as<int>() + (int64_t)o * 27);
+        count_launch(c);
+    }
+    check_launch("compact");
+
+    // P2P work items over the leaves
+    {
+        int nl = lv.nbox[L], o = lv.off[L];
+        int* cnt = tb.flags.as<int>();
+        int* first = tb.boxof_a.as<int>();
+        k_tile_counts<<<grid_for(nl, 256), 256, 0, s>>>(nl, tb.bbeg.as<int>() + o, tb.bend.as<int>() + o, cnt);
+        count_launch(c);
+        ensure(c, tb.tile_count, 16);
+        exclusive_scan(c, nl, cnt, first, tb.scan_tmp.as<int>(), tb.tile_count.as<int>());
+        int64_t max_tiles = nl + nn / P2P_TILE + 1;
+        ensure(c, tb.tiles, max_tiles * 8);
+        k_tile_fill<<<grid_for(nl, 256), 256, 0, s>>>(nl, tb.bbeg.as<int>() + o, tb.bend.as<int>() + o, first,
+                                                      tb.tiles.as<int2>());
+        count_launch(c);
+        check_launch("tiles");
+    }
+    // the sorted permutation
+    ensure(c, tb.perm, nn * 4);
+    cuda_check(cudaMemcpyAsync(tb.perm.ptr, perm, nn * 4, cudaMemcpyDeviceToDevice, s), "perm");
+    if (keys != tb.keys_a.as<uint64_t>())
+        cuda_check(cudaMemcpyAsync(tb.keys_a.ptr, keys, nn * 8, cudaMemcpyDeviceToDevice, s), "keys");
+    return LHV_OK;
+}
+
+template int build_tree<float>(Ctx*, int64_t, const float4*, const float4*, TreeBufs&, Levels&, TreeParams&, Error&);
+template int build_tree<double>(Ctx*, int64_t, const dbl4*, const dbl4*, TreeBufs&, Levels&, TreeParams&, Error&);
+template void gather_sorted<float>(Ctx*, int64_t, const int*, const float4*, const float4*, float4*, float4*);
+template void gather_sorted<double>(Ctx*, int64_t, const int*, const dbl4*, const dbl4*, dbl4*, dbl4*);
+
+}  // namespace lhv

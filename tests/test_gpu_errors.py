@@ -1,0 +1,54 @@
+"""Status codes of the C ABI on a GPU: bad arguments, non-finite input, empty input."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import workloads
+from tests.gpu_util import dev
+
+pytestmark = pytest.mark.gpu
+
+
+def test_errors_and_recovery():
+    import torch
+    from paper_1201_5430_gb300 import LHV, LHVError
+    from paper_1201_5430_gb300 import _lib
+    ctx = LHV(p=6, leaf_max=16, core_a=0.01)
+    lib = ctx.lib
+    x, w = workloads.cube(500, 1)
+    x4, w4 = dev(x, "fp32"), dev(w, "fp32")
+    v4, s4 = torch.empty_like(x4), torch.empty_like(x4)
+    p = lambda t: ctypes.c_void_p(t.data_ptr())
+    assert lib.lhv_evaluate_velocity_stretching(ctx.h, -1, p(x4), p(w4), p(v4), p(s4)) == _lib.LHV_EINVAL
+    assert lib.lhv_evaluate_velocity_stretching(ctx.h, 500, None, p(w4), p(v4), p(s4)) == _lib.LHV_EINVAL
+    mis = ctypes.c_void_p(x4.data_ptr() + 4)
+    assert lib.lhv_evaluate_velocity_stretching(ctx.h, 499, mis, p(w4), p(v4), p(s4)) == _lib.LHV_EINVAL
+    assert lib.lhv_evaluate_velocity_stretching_f64(ctx.h, 500, p(x4), p(w4), p(v4), p(s4)) == _lib.LHV_EINVAL
+    assert lib.lhv_evaluate_velocity_stretching(ctx.h, 0, None, None, None, None) == 0
+    bad = x4.clone()
+    bad[17, 1] = float("nan")
+    with pytest.raises(LHVError) as e:
+        ctx.evaluate_velocity_stretching(bad, w4)
+    assert e.value.status == _lib.LHV_ENONFINITE
+    badw = w4.clone()
+    badw[3, 0] = float("inf")
+    with pytest.raises(LHVError):
+        ctx.evaluate_velocity_stretching(x4, badw)
+    v, s = ctx.evaluate_velocity_stretching(x4, w4)      # the context is still usable
+    assert torch.isfinite(v).all() and torch.isfinite(s).all()
+    ctx.close()
+
+
+def test_identical_points_and_single_element():
+    from paper_1201_5430_gb300 import LHV
+    ctx = LHV(p=6, leaf_max=4, core_a=0.05, precision="fp64")
+    x = np.zeros((10, 3), np.float32) + np.float32(0.25)
+    w = np.random.default_rng(0).normal(size=(10, 3)).astype(np.float32)
+    v, s = ctx.evaluate_velocity_stretching(dev(x, "fp64"), dev(w, "fp64"))
+    from oracle import direct
+    v0, _, s0 = direct.direct(x, w, 0.05)
+    np.testing.assert_allclose(v[:, :3].cpu().numpy(), v0, atol=1e-12)
+    np.testing.assert_allclose(s[:, :3].cpu().numpy(), s0, atol=1e-10)
+    v1, s1 = ctx.evaluate_velocity_stretching(dev(x[:1], "fp64"), dev(w[:1], "fp64"))
+    assert float(v1.abs().max()) == 0.0 and float(s1.abs().max()) == 0.0

@@ -84,3 +84,13 @@ def test_coincident_distinct_elements_are_regular():
     w = np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
     v, u, s = direct.direct(x, w, 0.01)
     assert np.all(np.isfinite(v)) and np.all(np.isfinite(u))
+
+
+def test_coincident_limit_is_continuous():
+    """f = K/r^3 and f'/r at r = 0 (Eq. vem1 limits) continue the values at tiny r."""
+    a = 0.05
+    w = np.array([[0.3, -0.2, 0.9]])
+    v0, u0 = direct.pair_terms(np.zeros((1, 3)), w, a)
+    v1, u1 = direct.pair_terms(np.array([[1e-4 * a, 0.0, 0.0]]), w, a)
+    assert np.all(v0 == 0)
+    np.testing.assert_allclose(u0, u1, rtol=1e-6, atol=1e-9 * np.abs(u1).max())
