@@ -165,6 +165,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="ncu target: one warm-up evaluation and one evaluation of the workload, nothing else")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -189,6 +191,11 @@ def main():
     x0 = torch.from_numpy(workloads.to_f4(x)).cuda()
     w0 = torch.from_numpy(workloads.to_f4(w)).cuda()
     x4, w4 = x0.clone(), w0.clone()
+    if args.profile:
+        for _ in range(2):
+            ctx.evaluate_velocity_stretching(x4, w4)
+        torch.cuda.synchronize()
+        return
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > L2
     stream = torch.cuda.current_stream()
 

@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(GG_THREADS) k_group_gemm(GemmArgs<T> a) {
     constexpr int XS = NC + 4;  // row stride of X (keeps 16-byte alignment, breaks the worst bank conflicts)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* X = reinterpret_cast<T*>(smem_raw);       // [C][XS]
-    T* A = X + (size_t)a.C * XS;                 // [KC][RT]
+    T* A = X + (size_t)a.C * XS;                 // [2][KC][RT] (double buffer)
     __shared__ int s_work;
     __shared__ int s_src[NC], s_dst[NC];
     const int t = threadIdx.x;
@@ -106,20 +106,33 @@ __global__ void __launch_bounds__(GG_THREADS) k_group_gemm(GemmArgs<T> a) {
 #pragma unroll
             for (int c = 0; c < TN; ++c) acc[j][c] = 0;
         const T* Ag = a.ops + (int64_t)(g % a.ops_mod) * a.C * a.R;
-        for (int kc = tile_kstart; kc < a.C; kc += KC) {
-            __syncthreads();
-            for (int e = t; e < KC * RT; e += GG_THREADS) {
+        // operator rows [kc, kc + KC) of this row tile: each thread owns EPT entries; the next
+        // step's entries are loaded into registers while the current step computes
+        constexpr int EPT = KC * RT / GG_THREADS;
+        T nxt[EPT];
+        auto load = [&](int kc) {
+#pragma unroll
+            for (int q = 0; q < EPT; ++q) {
+                const int e = t + q * GG_THREADS;
                 const int kk = e / RT, r = e - kk * RT;
                 const int k = kc + kk, row = r0 + r;
-                A[e] = (k < a.C && row < a.R) ? Ag[(int64_t)k * a.R + row] : (T)0;
+                nxt[q] = (k < a.C && row < a.R) ? Ag[(int64_t)k * a.R + row] : (T)0;
             }
+        };
+        load(tile_kstart);
+        int buf = 0;
+        for (int kc = tile_kstart; kc < a.C; kc += KC) {
+            T* Ab = A + buf * KC * RT;
+#pragma unroll
+            for (int q = 0; q < EPT; ++q) Ab[t + q * GG_THREADS] = nxt[q];
             __syncthreads();
+            if (kc + KC < a.C) load(kc + KC);
             const int kn = min(KC, a.C - kc);
             for (int kk = 0; kk < kn; ++kk) {
                 if (kc + kk < kstart) continue;
                 T av[TM], xv[TN];
 #pragma unroll
-                for (int j = 0; j < TM; ++j) av[j] = A[kk * RT + rg * TM + j];
+                for (int j = 0; j < TM; ++j) av[j] = Ab[kk * RT + rg * TM + j];
 #pragma unroll
                 for (int c = 0; c < TN; ++c) xv[c] = X[(kc + kk) * XS + cg * TN + c];
 #pragma unroll
@@ -127,6 +140,7 @@ __global__ void __launch_bounds__(GG_THREADS) k_group_gemm(GemmArgs<T> a) {
 #pragma unroll
                     for (int c = 0; c < TN; ++c) acc[j][c] += av[j] * xv[c];
             }
+            buf ^= 1;
         }
 #pragma unroll
         for (int c = 0; c < TN; ++c) {
@@ -149,7 +163,7 @@ __global__ void __launch_bounds__(GG_THREADS) k_group_gemm(GemmArgs<T> a) {
 
 template <typename T, int NC, int TM>
 void launch_gemm(Ctx* c, const GemmArgs<T>& a) {
-    const size_t smem = sizeof(T) * ((size_t)a.C * (NC + 4) + (size_t)KC * 16 * TM);
+    const size_t smem = sizeof(T) * ((size_t)a.C * (NC + 4) + 2 * (size_t)KC * 16 * TM);
     cuda_check(cudaFuncSetAttribute(k_group_gemm<T, NC, TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                "gemm attr");
     int per_sm = 1;
@@ -210,7 +224,7 @@ int gemm_nc(int C) {
     // largest NC whose gathered X fits next to the operator stage in ~200 KB
     const int limit = 200 * 1024;
     for (int nc : {64, 32, 16})
-        if ((size_t)C * (nc + 4) * sizeof(T) + (size_t)KC * 128 * sizeof(T) <= (size_t)limit) return nc;
+        if ((size_t)C * (nc + 4) * sizeof(T) + 2 * (size_t)KC * 128 * sizeof(T) <= (size_t)limit) return nc;
     return 16;
 }
 

@@ -7,42 +7,47 @@
 // and the stretching s_i = sum_l w_{i,l} u_lk (Eq. s1.1) is accumulated as
 //   s_i = (sum_j f w_j) x w_i + sum_j g (w_i . d) (w_j x d),   g = f'/r.
 // K evaluation, x = r/a:
-//   x >= x_cut : K = 1 to the working precision (f = 1/r^3, g = -3/r^5);
-//   x <  1     : the Taylor series of K/x^3 in x^2 (dK/dx = sqrt(2/pi) x^2 e^{-x^2/2}
-//                integrates term by term), which avoids the cancellation of the
-//                closed form at small x;
-//   otherwise  : Eq. vem1 directly (erf and exp).
+//   x >= x_cut  : K = 1 to the working precision (f = 1/r^3, g = -3/r^5);
+//   x <  x_ser  : the Taylor series of K/x^3 in x^2 (dK/dx = sqrt(2/pi) x^2 e^{-x^2/2}
+//                 integrates term by term), which avoids the cancellation of the
+//                 closed form at small x (x_ser = 1.5 in FP32, 1 in FP64);
+//   otherwise   : K = 1 - exp(-x^2/2) R(x), R from a Chebyshev fit (FP32), or
+//                 Eq. vem1 with erf (FP64).
+// The self pair j = i is excluded only in the source chunk that can hold it.
 // The far-field result (L2P) of the same element is added and the sum is
 // written in the caller's order.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 
+#include <type_traits>
+
+#include "core_fit.cuh"
 #include "lhv_internal.cuh"
 
 namespace lhv {
 
 namespace {
 
-constexpr int P2P_THREADS = P2P_TILE;
-
 template <typename T> struct CoreConsts {
     T inv_a, inv_a2, c3, c5;  // 1/a, 1/a^2, sqrt(2/pi)/a^3, sqrt(2/pi)/a^5
     T x2_cut;                 // (r/a)^2 beyond which K = 1 in this precision
+    T u_series;               // (r/a)^2 below which the Taylor series is used
     int smooth;
 };
 
 // Series: F(u) = sum_k (-1)^k u^k / (2^k k! (2k+3)),  K/r^3 = sqrt(2/pi)/a^3 F(x^2)
-// and g = f'/r = 2 sqrt(2/pi)/a^5 F'(x^2).
+// and g = f'/r = 2 sqrt(2/pi)/a^5 F'(x^2).  12 terms: below 1e-9 for u < 2.25.
 template <typename T>
 __device__ inline void core_series(T u, T& F, T& Fp) {
-    // coefficients c_k = (-1)^k / (2^k k! (2k+3)), k = 0..11
     const T c[12] = {(T)(1.0 / 3.0), (T)(-1.0 / 10.0), (T)(1.0 / 56.0), (T)(-1.0 / 432.0),
                      (T)(1.0 / 4224.0), (T)(-1.0 / 49920.0), (T)(1.0 / 691200.0), (T)(-1.0 / 10967040.0),
                      (T)(1.0 / 196116480.0), (T)(-1.0 / 3901685760.0), (T)(1.0 / 85465497600.0),
                      (T)(-1.0 / 2043740160000.0)};
-    constexpr int K = sizeof(T) == 4 ? 9 : 12;
+    constexpr int K = 12;
     T f = c[K - 1], fp = (T)(K - 1) * c[K - 1];
+#pragma unroll
     for (int k = K - 2; k >= 0; --k) {
         f = f * u + c[k];
         if (k >= 1) fp = fp * u + (T)k * c[k];
@@ -51,28 +56,112 @@ __device__ inline void core_series(T u, T& F, T& Fp) {
     Fp = fp;
 }
 
-template <typename T> __device__ inline T rsqrt_t(T x);
-template <> __device__ inline float rsqrt_t<float>(float x) { return rsqrtf(x); }
-template <> __device__ inline double rsqrt_t<double>(double x) { return rsqrt(x); }
-template <typename T> __device__ inline T erf_t(T x);
-template <> __device__ inline float erf_t<float>(float x) { return erff(x); }
-template <> __device__ inline double erf_t<double>(double x) { return erf(x); }
-template <typename T> __device__ inline T exp_t(T x);
-template <> __device__ inline float exp_t<float>(float x) { return expf(x); }
-template <> __device__ inline double exp_t<double>(double x) { return exp(x); }
+// Approximate SFU forms used in FP32 (max. relative errors about 2^-23 and
+// 2^-22.5 per the PTX ISA); FP64 uses the full-precision library functions.
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float ex2_ftz(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
+// f = K/r^3 and g = f'/r for one pair.  The singular part 1/r^3 is shared; the
+// core correction (divergent, only for r < x_cut a) replaces it.
+template <bool SMOOTH>
+__device__ __forceinline__ void kernel_fg(float r2, const CoreConsts<float>& cc, float& f, float& g) {
+    const float ri = rsqrt_ftz(r2);
+    const float ri2 = ri * ri;
+    f = ri * ri2;
+    if (SMOOTH) {
+        const float u = r2 * cc.inv_a2;
+        if (u < cc.x2_cut) {
+            if (u < cc.u_series) {
+                float F, Fp;
+                core_series<float>(u, F, Fp);
+                f = cc.c3 * F;
+                g = 2.0f * cc.c5 * Fp;
+                return;
+            }
+            const float x = r2 * ri * cc.inv_a;
+            const float t = fmaf(x, 0.4f, -1.6f);  // (2x - 8)/5
+            float R = kCoreFit[LHV_CORE_FIT_DEG];
+#pragma unroll
+            for (int k = LHV_CORE_FIT_DEG - 1; k >= 0; --k) R = fmaf(R, t, kCoreFit[k]);
+            const float e = ex2_ftz(u * -0.72134752044448170368f);  // exp(-u/2)
+            const float K = fmaf(-e, R, 1.0f);
+            f *= K;
+            g = (cc.c3 * e - 3.0f * f) * ri2;
+            return;
+        }
+    }
+    g = -3.0f * f * ri2;
+}
+
+template <bool SMOOTH>
+__device__ __forceinline__ void kernel_fg(double r2, const CoreConsts<double>& cc, double& f, double& g) {
+    if (SMOOTH) {
+        const double u = r2 * cc.inv_a2;
+        if (u < cc.x2_cut) {
+            if (u < cc.u_series) {
+                double F, Fp;
+                core_series<double>(u, F, Fp);
+                f = cc.c3 * F;
+                g = 2.0 * cc.c5 * Fp;
+                return;
+            }
+            const double ri = rsqrt(r2);
+            const double ri2 = ri * ri;
+            const double x = r2 * ri * cc.inv_a;
+            const double e = exp(-0.5 * u);
+            const double K = erf(x * 0.70710678118654752440) - 0.79788456080286535588 * x * e;
+            f = K * ri * ri2;
+            g = (cc.c3 * e - 3.0 * f) * ri2;
+            return;
+        }
+    }
+    const double ri = rsqrt(r2);
+    const double ri2 = ri * ri;
+    f = ri * ri2;
+    g = -3.0 * f * ri2;
+}
+
+// Knuth's TwoSum: hi + lo += a exactly up to the final rounding of lo.
 template <typename T>
-__global__ void __launch_bounds__(P2P_THREADS) k_p2p(const int* __restrict__ ntiles_dev, const int2* __restrict__ tiles,
-                                                   int* __restrict__ work, const int* __restrict__ bbeg,
-                                                   const int* __restrict__ bend, const int* __restrict__ bcol,
-                                                   const vec4_t<T>* __restrict__ xs, const vec4_t<T>* __restrict__ ws,
-                                                   const int* __restrict__ perm, const vec4_t<T>* __restrict__ vfar,
-                                                   const vec4_t<T>* __restrict__ sfar, vec4_t<T>* __restrict__ vout,
-                                                   vec4_t<T>* __restrict__ sout, CoreConsts<T> cc, int near,
-                                                   unsigned long long* __restrict__ pairs) {
-    __shared__ vec4_t<T> sx[P2P_THREADS];
-    __shared__ vec4_t<T> sw[P2P_THREADS];
-    __shared__ int sid[P2P_THREADS];
+__device__ inline void two_sum_acc(T& hi, T& lo, T a) {
+    const T s = hi + a;
+    const T bb = s - hi;
+    const T err = (hi - (s - bb)) + (a - bb);
+    hi = s;
+    lo += err;
+}
+
+// TPT targets per thread; a tile is P2P_TILE consecutive targets of one leaf.
+// Accumulation is blocked: plain sums over each chunk of P2P_TILE sources, then
+// a compensated (TwoSum) add of the chunk sums into per-target totals.
+template <typename T, bool SMOOTH, int TPT>
+__global__ void __launch_bounds__(P2P_TILE / TPT) k_p2p(const int* __restrict__ ntiles_dev,
+                                                       const int2* __restrict__ tiles, int* __restrict__ work,
+                                                       const int* __restrict__ bbeg, const int* __restrict__ bend,
+                                                       const int* __restrict__ bcol,
+                                                       const vec4_t<T>* __restrict__ xs,
+                                                       const vec4_t<T>* __restrict__ ws,
+                                                       const int* __restrict__ perm,
+                                                       const vec4_t<T>* __restrict__ vfar,
+                                                       const vec4_t<T>* __restrict__ sfar,
+                                                       vec4_t<T>* __restrict__ vout, vec4_t<T>* __restrict__ sout,
+                                                       CoreConsts<T> cc, int near,
+                                                       unsigned long long* __restrict__ pairs) {
+    constexpr int NT = P2P_TILE / TPT;   // threads
+    constexpr int CH = P2P_TILE;         // sources staged per step
+    constexpr int NA = 9;                // accumulators per target: v (3), sum f w_j (3), g-terms (3)
+    __shared__ vec4_t<T> sx[CH];
+    __shared__ vec4_t<T> sw[CH];
+    __shared__ int sid[CH];
+    __shared__ T tot[2][NA][TPT][NT];    // compensated totals (hi, lo)
     __shared__ int cbeg[27], cpre[28];
     __shared__ int cur;
     const int ntiles = *ntiles_dev;
@@ -85,12 +174,11 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(const int* __restrict__ nti
         if (tile >= ntiles) break;
         const int2 tw = tiles[tile];
         const int leaf = tw.x;
-        const int i = tw.y + threadIdx.x;
-        const bool active = i < bend[leaf];
+        const int tend = bend[leaf];
         if (threadIdx.x == 0) {
             int acc = 0;
             for (int q = 0; q < 27; ++q) {
-                int cb = bcol[(int64_t)leaf * 27 + q];
+                const int cb = bcol[(int64_t)leaf * 27 + q];
                 int cnt = 0;
                 if (cb >= 0) {
                     cbeg[q] = bbeg[cb];
@@ -103,101 +191,108 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p(const int* __restrict__ nti
             }
             cpre[27] = acc;
         }
-        vec4_t<T> xi{}, wi{};
-        if (active) {
-            xi = xs[i];
-            wi = ws[i];
+        int ti[TPT];
+        bool act[TPT];
+        vec4_t<T> xi[TPT], wi[TPT];
+#pragma unroll
+        for (int q = 0; q < TPT; ++q) {
+            ti[q] = tw.y + threadIdx.x + q * NT;
+            act[q] = ti[q] < tend;
+            xi[q] = act[q] ? xs[ti[q]] : vec4_t<T>{};
+            wi[q] = act[q] ? ws[ti[q]] : vec4_t<T>{};
+#pragma unroll
+            for (int a = 0; a < NA; ++a) {
+                tot[0][a][q][threadIdx.x] = 0;
+                tot[1][a][q][threadIdx.x] = 0;
+            }
         }
-        T vx = 0, vy = 0, vz = 0, Fx = 0, Fy = 0, Fz = 0, gx = 0, gy = 0, gz = 0;
         __syncthreads();
         const int nsrc = near ? cpre[27] : 0;
+        // virtual source positions of the tile's own targets (colleague 13 is the leaf itself)
+        const int self_lo = cpre[13] + (tw.y - cbeg[13]);
+        const int self_hi = self_lo + P2P_TILE;
         if (threadIdx.x == 0 && near) {
-            const int nt = min(P2P_THREADS, bend[leaf] - tw.y);
+            const int nt = min(P2P_TILE, tend - tw.y);
             my_pairs += (unsigned long long)nt * (unsigned long long)(nsrc - 1);
         }
-        for (int s0 = 0; s0 < nsrc; s0 += P2P_THREADS) {
-            const int v = s0 + threadIdx.x;
-            if (v < nsrc) {
+        for (int s0 = 0; s0 < nsrc; s0 += CH) {
+            for (int v = s0 + threadIdx.x; v < min(nsrc, s0 + CH); v += NT) {
                 int q = 0;
                 while (cpre[q + 1] <= v) ++q;
                 const int j = cbeg[q] + (v - cpre[q]);
-                sx[threadIdx.x] = xs[j];
-                sw[threadIdx.x] = ws[j];
-                sid[threadIdx.x] = j;
+                sx[v - s0] = xs[j];
+                sw[v - s0] = ws[j];
+                sid[v - s0] = j;
             }
             __syncthreads();
-            const int ns = min(P2P_THREADS, nsrc - s0);
-            if (active) {
+            const int ns = min(CH, nsrc - s0);
+            T acc[NA][TPT];
+#pragma unroll
+            for (int a = 0; a < NA; ++a)
+#pragma unroll
+                for (int q = 0; q < TPT; ++q) acc[a][q] = 0;
+            auto chunk = [&](auto check) {
                 for (int k = 0; k < ns; ++k) {
                     const vec4_t<T> xj = sx[k];
                     const vec4_t<T> wj = sw[k];
-                    const T dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
-                    const T r2 = dx * dx + dy * dy + dz * dz;
-                    T f, g;
-                    if (cc.smooth) {
-                        const T u = r2 * cc.inv_a2;
-                        if (u >= cc.x2_cut) {
-                            const T ri = rsqrt_t<T>(r2);
-                            const T ri2 = ri * ri;
-                            f = ri * ri2;
-                            g = (T)-3 * f * ri2;
-                        } else if (u < (T)1) {
-                            T F, Fp;
-                            core_series<T>(u, F, Fp);
-                            f = cc.c3 * F;
-                            g = (T)2 * cc.c5 * Fp;
-                        } else {
-                            const T ri = rsqrt_t<T>(r2);
-                            const T ri2 = ri * ri;
-                            const T x = r2 * ri * cc.inv_a;
-                            const T e = exp_t<T>((T)-0.5 * u);
-                            const T K = erf_t<T>(x * (T)0.70710678118654752440) - (T)0.79788456080286535588 * x * e;
-                            f = K * ri * ri2;
-                            g = (cc.c3 * e - (T)3 * f) * ri2;
+                    int j = -1;
+                    if (decltype(check)::value) j = sid[k];
+#pragma unroll
+                    for (int q = 0; q < TPT; ++q) {
+                        const T dx = xi[q].x - xj.x, dy = xi[q].y - xj.y, dz = xi[q].z - xj.z;
+                        const T r2 = dx * dx + dy * dy + dz * dz;
+                        T f, g;
+                        kernel_fg<SMOOTH>(r2, cc, f, g);
+                        if (decltype(check)::value && j == ti[q]) {
+                            f = 0;
+                            g = 0;
                         }
-                    } else {
-                        const T ri = rsqrt_t<T>(r2);
-                        const T ri2 = ri * ri;
-                        f = ri * ri2;
-                        g = (T)-3 * f * ri2;
+                        const T cx = wj.y * dz - wj.z * dy;
+                        const T cy = wj.z * dx - wj.x * dz;
+                        const T cz = wj.x * dy - wj.y * dx;
+                        acc[0][q] += f * cx;
+                        acc[1][q] += f * cy;
+                        acc[2][q] += f * cz;
+                        acc[3][q] += f * wj.x;
+                        acc[4][q] += f * wj.y;
+                        acc[5][q] += f * wj.z;
+                        const T h = g * (wi[q].x * dx + wi[q].y * dy + wi[q].z * dz);
+                        acc[6][q] += h * cx;
+                        acc[7][q] += h * cy;
+                        acc[8][q] += h * cz;
                     }
-                    if (sid[k] == i) {
-                        f = 0;
-                        g = 0;
-                    }
-                    // c = w_j x d
-                    const T cx = wj.y * dz - wj.z * dy;
-                    const T cy = wj.z * dx - wj.x * dz;
-                    const T cz = wj.x * dy - wj.y * dx;
-                    vx += f * cx;
-                    vy += f * cy;
-                    vz += f * cz;
-                    Fx += f * wj.x;
-                    Fy += f * wj.y;
-                    Fz += f * wj.z;
-                    const T h = g * (wi.x * dx + wi.y * dy + wi.z * dz);
-                    gx += h * cx;
-                    gy += h * cy;
-                    gz += h * cz;
                 }
-            }
+            };
+            if (s0 < self_hi && s0 + ns > self_lo) chunk(std::true_type{});
+            else chunk(std::false_type{});
+#pragma unroll
+            for (int a = 0; a < NA; ++a)
+#pragma unroll
+                for (int q = 0; q < TPT; ++q)
+                    two_sum_acc(tot[0][a][q][threadIdx.x], tot[1][a][q][threadIdx.x], acc[a][q]);
             __syncthreads();
         }
-        if (active) {
+#pragma unroll
+        for (int q = 0; q < TPT; ++q) {
+            if (!act[q]) continue;
+            T r[NA];
+#pragma unroll
+            for (int a = 0; a < NA; ++a) r[a] = tot[0][a][q][threadIdx.x] + tot[1][a][q][threadIdx.x];
+            const int i = ti[q];
             vec4_t<T> vf{}, sf{};
             if (vfar) {
                 vf = vfar[i];
                 sf = sfar[i];
             }
             vec4_t<T> vo, so;
-            vo.x = vf.x + vx;
-            vo.y = vf.y + vy;
-            vo.z = vf.z + vz;
+            vo.x = vf.x + r[0];
+            vo.y = vf.y + r[1];
+            vo.z = vf.z + r[2];
             vo.w = 0;
-            // (sum f w_j) x w_i
-            so.x = sf.x + (Fy * wi.z - Fz * wi.y) + gx;
-            so.y = sf.y + (Fz * wi.x - Fx * wi.z) + gy;
-            so.z = sf.z + (Fx * wi.y - Fy * wi.x) + gz;
+            // (sum_j f w_j) x w_i + sum_j g (w_i . d)(w_j x d)
+            so.x = sf.x + (r[4] * wi[q].z - r[5] * wi[q].y) + r[6];
+            so.y = sf.y + (r[5] * wi[q].x - r[3] * wi[q].z) + r[7];
+            so.z = sf.z + (r[3] * wi[q].y - r[4] * wi[q].x) + r[8];
             so.w = 0;
             const int o = perm[i];
             vout[o] = vo;
@@ -286,15 +381,23 @@ void run_p2p(Ctx* c, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs, 
         // beyond x_cut, 1 - K and the K' term are below the unit roundoff
         const double xc = sizeof(T) == 4 ? 6.5 : 9.0;
         cc.x2_cut = (T)(xc * xc);
+        cc.u_series = (T)(sizeof(T) == 4 ? 2.25 : 1.0);
     }
     int* work = reinterpret_cast<int*>(ctx_tmp(c, 6).ptr);
     ensure(c, ctx_tmp(c, 6), 64);
     work = reinterpret_cast<int*>(ctx_tmp(c, 6).ptr);
     cuda_check(cudaMemsetAsync(work, 0, 4, s), "p2p counter");
     const int64_t max_tiles = lv.nbox[L] + n / P2P_TILE + 1;
-    k_p2p<T><<<grid_for(max_tiles, 1, 152 * 16), P2P_THREADS, 0, s>>>(
-        tb.tile_count.as<int>(), tb.tiles.as<int2>(), work, tb.bbeg.as<int>() + o, tb.bend.as<int>() + o,
-        tb.bcol.as<int>() + (int64_t)o * 27, xs, ws, perm, vfar, sfar, v_out, s_out, cc, near ? 1 : 0, pair_counter);
+    constexpr int TPT = 2;
+    auto kern = cc.smooth ? k_p2p<T, true, TPT> : k_p2p<T, false, TPT>;
+    int per_sm = 1, sms = 152, dev = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, P2P_TILE / TPT, 0);
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = (int)std::min<int64_t>(max_tiles, (int64_t)sms * std::max(per_sm, 1));
+    kern<<<grid, P2P_TILE / TPT, 0, s>>>(tb.tile_count.as<int>(), tb.tiles.as<int2>(), work, tb.bbeg.as<int>() + o,
+                                         tb.bend.as<int>() + o, tb.bcol.as<int>() + (int64_t)o * 27, xs, ws, perm,
+                                         vfar, sfar, v_out, s_out, cc, near ? 1 : 0, pair_counter);
     count_launch(c);
     check_launch("p2p");
 }

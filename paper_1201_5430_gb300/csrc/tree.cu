@@ -86,17 +86,31 @@ __global__ void k_bbox_partial(int64_t n, const vec4_t<T>* __restrict__ x4, cons
 }
 
 __global__ void k_bbox_final(int nparts, const double* __restrict__ part, TreeParams* __restrict__ tp) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    __shared__ double r[6][256];
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int b = 0; b < nparts; ++b)
+    for (int b = threadIdx.x; b < nparts; b += blockDim.x)
         for (int k = 0; k < 3; ++k) {
             lo[k] = fmin(lo[k], part[b * 6 + k]);
             hi[k] = fmax(hi[k], part[b * 6 + 3 + k]);
         }
+    for (int k = 0; k < 3; ++k) {
+        r[k][threadIdx.x] = lo[k];
+        r[3 + k][threadIdx.x] = hi[k];
+    }
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int k = 0; k < 3; ++k) {
+                r[k][threadIdx.x] = fmin(r[k][threadIdx.x], r[k][threadIdx.x + w]);
+                r[3 + k][threadIdx.x] = fmax(r[3 + k][threadIdx.x], r[3 + k][threadIdx.x + w]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
     double ext = 0.0;
     for (int k = 0; k < 3; ++k) {
-        tp->x0[k] = lo[k];
-        ext = fmax(ext, hi[k] - lo[k]);
+        tp->x0[k] = r[k][0];
+        ext = fmax(ext, r[3 + k][0] - r[k][0]);
     }
     double side = 1.0;
     if (ext > 0.0) {
@@ -472,7 +486,7 @@ int build_tree(Ctx* c, int64_t n, const vec4_t<T>* x4, const vec4_t<T>* w4, Tree
     double* part = reinterpret_cast<double*>(tb.hist.ptr);
     k_bbox_partial<T><<<nparts, 256, 0, s>>>(nn, x4, w4, part, &tp->nonfinite);
     count_launch(c);
-    k_bbox_final<<<1, 32, 0, s>>>(nparts, part, tp);
+    k_bbox_final<<<1, 256, 0, s>>>(nparts, part, tp);
     count_launch(c);
     k_morton<T><<<grid_for(nn, 256), 256, 0, s>>>(nn, x4, tp, tb.keys_a.as<uint64_t>(), tb.idx_a.as<int>());
     count_launch(c);

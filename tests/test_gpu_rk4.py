@@ -23,7 +23,11 @@ def test_rk4_step_parity():
     x4, w4 = dev(x, "fp32"), dev(w, "fp32")
     ctx.step(x4, w4, dt)
     gx, gw = host3(x4), host3(w4)
-    assert rel(gx - x, x1 - x) < 1e-5, rel(gx - x, x1 - x)
+    # the state is stored in FP32: |x| ~ 1 carries 6e-8 of rounding on a
+    # displacement of ~1e-3, so the displacement is compared at 1e-4 and the
+    # positions within a few units in the last place
+    assert rel(gx - x, x1 - x) < 1e-4, rel(gx - x, x1 - x)
+    assert np.abs(gx - x1).max() <= 4 * np.finfo(np.float32).eps * np.abs(x1).max()
     assert rel(gw - w, w1 - w) < 1e-4, rel(gw - w, w1 - w)
 
 
@@ -36,5 +40,6 @@ def test_step_host_matches_device():
     hx, hw = x4.cpu().clone(), w4.cpu().clone()
     ctx.step(x4, w4, 1e-3)
     ctx.step_host(hx, hw, 1e-3)
-    torch.testing.assert_close(hx, x4.cpu(), rtol=0, atol=0)
-    torch.testing.assert_close(hw, w4.cpu(), rtol=0, atol=0)
+    # M2L and M2M accumulate with atomics, so two runs agree to rounding, not bitwise
+    torch.testing.assert_close(hx, x4.cpu(), rtol=0, atol=4 * 2.0 ** -24 * float(x4.abs().max()))
+    torch.testing.assert_close(hw, w4.cpu(), rtol=0, atol=4 * 2.0 ** -24 * float(w4.abs().max()))
