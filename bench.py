@@ -165,6 +165,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="tf32x3", choices=["tf32x3", "fp32"],
+                    help="tf32x3: translations on the tensor cores (TF32 split products); fp32: plain CUDA-core FMM")
     ap.add_argument("--profile", action="store_true",
                     help="ncu target: one warm-up evaluation and one evaluation of the workload, nothing else")
     args = ap.parse_args()
@@ -187,45 +189,53 @@ def main():
     from paper_1201_5430_gb300 import LHV
     x, w, spec = workloads.make(WORKLOAD)
     n = x.shape[0]
-    ctx = LHV(p=spec["p"], leaf_max=spec["leaf_max"], core_a=spec["a"], eps=spec["eps"], precision="fp32")
     x0 = torch.from_numpy(workloads.to_f4(x)).cuda()
     w0 = torch.from_numpy(workloads.to_f4(w)).cuda()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    def make_ctx(precision):
+        return LHV(p=spec["p"], leaf_max=spec["leaf_max"], core_a=spec["a"], eps=spec["eps"], precision=precision)
+
+    ctx = make_ctx(args.precision)
     x4, w4 = x0.clone(), w0.clone()
     if args.profile:
         for _ in range(2):
             ctx.evaluate_velocity_stretching(x4, w4)
         torch.cuda.synchronize()
         return
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > L2
-    stream = torch.cuda.current_stream()
 
-    for _ in range(max(args.warmup, 3)):
-        x4.copy_(x0)
-        w4.copy_(w0)
-        ctx.step(x4, w4, spec["dt"])
-    torch.cuda.synchronize()
-
-    ctx.set_timing(True)
-    ctx.reset_stats()
-    times = []
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with Clocks(local) as clk:
-        for _ in range(args.steps):
+    def timed_steps(c, steps, warmup, clocks=None):
+        for _ in range(max(warmup, 3)):
+            x4.copy_(x0)
+            w4.copy_(w0)
+            c.step(x4, w4, spec["dt"])
+        torch.cuda.synchronize()
+        c.set_timing(True)
+        c.reset_stats()
+        times = []
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for _ in range(steps):
             x4.copy_(x0)
             w4.copy_(w0)
             flush.zero_()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            ctx.step(x4, w4, spec["dt"])
-            b.record(stream)
-            b.synchronize()
-            times.append(a.elapsed_time(b))
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    st = ctx.stats()
+            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ea.record(stream)
+            c.step(x4, w4, spec["dt"])
+            eb.record(stream)
+            eb.synchronize()
+            times.append(ea.elapsed_time(eb))
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        st = c.stats()
+        c.set_timing(False)
+        return times, st
+
+    with Clocks(local) as clk:
+        times, st = timed_steps(ctx, args.steps, args.warmup)
     total_ms = float(sum(times))
     if dist:
         t = torch.tensor([total_ms], device="cuda")
@@ -233,6 +243,18 @@ def main():
         total_ms = float(t.item())
     evals = 4 * n * args.steps * world
     value = evals / (total_ms / 1e3)
+    plain = None
+    if args.precision != "fp32":
+        pctx = make_ctx("fp32")
+        ptimes, pst = timed_steps(pctx, args.steps, args.warmup)
+        ptotal = float(sum(ptimes))
+        if dist:
+            t = torch.tensor([ptotal], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ptotal = float(t.item())
+        plain = {"value": evals / (ptotal / 1e3), "ms_per_step": ptotal / args.steps,
+                 "stage_ms_per_step": {k: v / args.steps for k, v in pst["stage_ms"].items() if v > 0}}
+        pctx.close()
 
     # roofline of the dominant kernel (P2P): algorithmic FP32 flops per launch / its mean duration
     peaks, peak_kind = _measured_peaks()
@@ -242,6 +264,11 @@ def main():
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     peak = sms * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     traffic = _traffic_record("p2p.cu")
+    # M2L products: useful flops 6 p^4 per box pair (the fused [[T, C12 T], [0, C22 T]] with its
+    # zero block skipped) over the mean duration of the products
+    m2l_ms = st["stage_ms"].get("m2l_products", 0.0) / max(st["stage_launches"].get("m2l_products", 0), 1)
+    m2l_flops = 6.0 * spec["p"] ** 4 * st["m2l_pairs"]
+    tf32_peak = peaks.get("bf16_tflops", 1862.0) * (1.1 / 2.25)
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     hx = x0.cpu().pin_memory()
@@ -267,9 +294,11 @@ def main():
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f32+tf32x3",
+        "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": n, "p": spec["p"], "leaf_max": spec["leaf_max"],
                    "core_a": spec["a"], "eps": spec["eps"], "dt": spec["dt"], "rk4_evals_per_step": 4,
+                   "precision": args.precision,
                    "l2": "flushed between steps (256 MB write)", "parallelism": "replicas" if world > 1 else "1 GPU",
                    "leaf_level": st["leaf_level"], "boxes": st["nbox"]},
         "roofline": {"kernel": "k_p2p (near field)", "bound": "alu", "achieved": achieved, "peak": peak,
@@ -277,7 +306,19 @@ def main():
                      "peak_kind": f"FP32 FMA pipe: {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x "
                                   f"{peaks.get('sm_max_mhz', 2070.0)} MHz ({peak_kind} max clock)",
                      "pairs_per_launch": pairs, "flops_per_pair": P2P_FLOPS_PER_PAIR, "mean_launch_ms": p2p_ms},
+        "roofline_m2l": {"kernel": "grouped GEMM, M2L products" + (" (tcgen05 TF32 x3)" if args.precision == "tf32x3"
+                                                                      else " (FP32 CUDA cores)"),
+                         "bound": "tensor" if args.precision == "tf32x3" else "alu",
+                         "achieved": m2l_flops / (m2l_ms / 1e3) / 1e12 if m2l_ms else None,
+                         "peak": tf32_peak if args.precision == "tf32x3" else peak, "unit": "TFLOP/s",
+                         "frac": (m2l_flops / (m2l_ms / 1e3) / 1e12) / (tf32_peak if args.precision == "tf32x3" else peak)
+                         if m2l_ms else None,
+                         "peak_kind": "TF32 = measured BF16 burst x 1.1/2.25 (nominal ratio)" if args.precision == "tf32x3"
+                         else "FP32 FMA pipe", "box_pairs": st["m2l_pairs"], "flops_per_pair": 6 * spec["p"] ** 4,
+                         "useful_only": "split products issue 3x these flops", "mean_launch_ms": m2l_ms},
         "stage_ms_per_step": {k: v / args.steps for k, v in st["stage_ms"].items() if v > 0},
+        "plain_fp32": plain,
+        "speedup_vs_plain_fp32": (value / plain["value"]) if plain else None,
         "cpu_baseline": cb,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(2 * n * 16),
                 "d2h_bytes_per_step": int(2 * n * 16)},

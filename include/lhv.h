@@ -49,8 +49,11 @@ extern "C" {
 #define LHV_EUNSUPPORTED -6  /* valid request this build does not implement */
 
 /* ---- arithmetic of the evaluation (lhv_config.precision) --------------- */
-#define LHV_FP32 0  /* all kernels in FP32; operator tables built in FP64, stored FP32 */
+#define LHV_FP32 0  /* all kernels in FP32 (CUDA cores); operator tables built in FP64, stored FP32 */
 #define LHV_FP64 1  /* all kernels in FP64 (use the _f64 entry points) */
+#define LHV_TF32X3 2 /* mixed precision: as LHV_FP32, but every translation and coefficient map
+                        (P2M, M2M, M2L, L2L, L2P) runs on the tensor cores in TF32 with split
+                        operands (hi.hi + hi.lo + lo.hi, FP32 accumulation); needs p even */
 
 /* ---- which parts of Eq. fmm1 to evaluate (lhv_config.terms) ------------ */
 #define LHV_TERMS_NEAR 1  /* sparse part only: direct sum over colleague leaves */
@@ -67,13 +70,13 @@ typedef struct {
     double eps;        /* target accuracy in (0, 1): leaf boxes are kept no smaller
                           than r_K = x_K a with 1 - K(x_K a; a) = eps/10, so far pairs
                           see K = 1 to eps/10 (Eq. 2) */
-    int    precision;  /* LHV_FP32 or LHV_FP64 */
+    int    precision;  /* LHV_FP32, LHV_FP64 or LHV_TF32X3 */
     int    terms;      /* LHV_TERMS_* (0 means LHV_TERMS_ALL) */
     int    max_level;  /* cap on the leaf level, 0 = none (21, the key depth) */
 } lhv_config;
 
 #define LHV_MAX_LEVELS 22
-#define LHV_NUM_STAGES 10
+#define LHV_NUM_STAGES 11
 /* stage indices of lhv_stats.stage_ms */
 #define LHV_STAGE_TREE   0  /* Morton keys, sort, boxes, lists */
 #define LHV_STAGE_P2M    1  /* Sec. 4.3 */
@@ -85,6 +88,7 @@ typedef struct {
 #define LHV_STAGE_RK4    7  /* Sec. 5.3 RK4 combine */
 #define LHV_STAGE_OPS    8  /* FP64 operator build (once per context) */
 #define LHV_STAGE_COPY   9  /* host <-> device copies of the _host entry points */
+#define LHV_STAGE_M2L_PRODUCTS 10  /* the operator products of M2L alone (inside LHV_STAGE_M2L) */
 
 typedef struct {
     int     leaf_level;                      /* L of the last tree */
@@ -167,6 +171,14 @@ int lhv_reset_stats(lhv_ctx* ctx);
  * R coefficients as             c_n^m h^n / nu_n^m (phi)    and c_n^m h^(n+1) / nu_n^m (chi),
  * nu_n^m = sqrt((n-|m|)! (n+|m|)!), c_n^m the coefficients of Eq. rsbf6. */
 int lhv_export(lhv_ctx* ctx, int what, int level, void* dst, int64_t capacity_bytes, int64_t* bytes_out);
+
+/* Diagnostic: D = X B^T on the TF32 tensor-core path of this library, one CTA,
+ * operands rounded to TF32 (no splitting).  X: device float [128][K], B: device
+ * float [N][K], D: device float [128][N]; 16 <= N <= 256 with N % 16 == 0 and
+ * K % 32 == 0.  Synchronous on the legacy default stream.  Returns LHV_EINVAL
+ * for other sizes, LHV_ETIMEOUT if the tensor-core work never signalled
+ * completion (the kernel then stops by itself). */
+int lhv_tc_selftest(const float* X, const float* B, float* D, int N, int K);
 
 #ifdef __cplusplus
 }

@@ -6,11 +6,11 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblhv.so")
 
 LHV_OK, LHV_EINVAL, LHV_ENOMEM, LHV_ECUDA, LHV_ETIMEOUT, LHV_ENONFINITE, LHV_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
-LHV_FP32, LHV_FP64 = 0, 1
+LHV_FP32, LHV_FP64, LHV_TF32X3 = 0, 1, 2
 LHV_TERMS_NEAR, LHV_TERMS_FAR, LHV_TERMS_ALL = 1, 2, 3
 LHV_MAX_LEVELS = 22
-LHV_NUM_STAGES = 10
-STAGES = ["tree", "p2m", "m2m", "m2l", "l2l", "l2p", "p2p", "rk4", "ops", "copy"]
+LHV_NUM_STAGES = 11
+STAGES = ["tree", "p2m", "m2m", "m2l", "l2l", "l2p", "p2p", "rk4", "ops", "copy", "m2l_products"]
 EXPORT = {"keys": 1, "perm": 2, "box_keys": 3, "box_range": 4, "colleagues": 5,
           "multipole": 6, "local": 7, "cube": 8}
 
@@ -45,6 +45,7 @@ SIGNATURES = {
     "lhv_set_timing": (_int, [_vp, _int]),
     "lhv_reset_stats": (_int, [_vp]),
     "lhv_export": (_int, [_vp, _int, _int, _vp, _i64, ctypes.POINTER(_i64)]),
+    "lhv_tc_selftest": (_int, [_vp, _vp, _vp, _int, _int]),
 }
 
 _lib = None

@@ -20,14 +20,16 @@ class LHV:
     def __init__(self, p, leaf_max=64, core_a=0.0, eps=1e-6, precision="fp32", terms="all",
                  max_level=0, stream=None, device=None):
         self.lib = L.load()
+        if precision not in ("fp32", "fp64", "tf32x3"):
+            raise ValueError("precision must be fp32, fp64 or tf32x3")
         self.precision = precision
-        self.dtype = torch.float32 if precision == "fp32" else torch.float64
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         if stream is None:
             stream = torch.cuda.current_stream(self.device)
         self.stream = stream
         cfg = L.Config(p=int(p), leaf_max=int(leaf_max), core_a=float(core_a), eps=float(eps),
-                       precision=L.LHV_FP32 if precision == "fp32" else L.LHV_FP64,
+                       precision={"fp32": L.LHV_FP32, "fp64": L.LHV_FP64, "tf32x3": L.LHV_TF32X3}[precision],
                        terms={"near": 1, "far": 2, "all": 3}[terms], max_level=int(max_level))
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
@@ -67,15 +69,15 @@ class LHV:
         n = x4.shape[0]
         v4 = torch.empty_like(x4) if v4 is None else self._elems(v4)
         s4 = torch.empty_like(x4) if s4 is None else self._elems(s4)
-        fn = self.lib.lhv_evaluate_velocity_stretching if self.precision == "fp32" else \
-            self.lib.lhv_evaluate_velocity_stretching_f64
+        fn = self.lib.lhv_evaluate_velocity_stretching_f64 if self.precision == "fp64" else \
+            self.lib.lhv_evaluate_velocity_stretching
         self._check(fn(self.h, n, _ptr(x4), _ptr(w4), _ptr(v4), _ptr(s4)), "evaluate_velocity_stretching")
         return v4, s4
 
     def step(self, x4, w4, dt):
         self._elems(x4)
         self._elems(w4)
-        fn = self.lib.lhv_step if self.precision == "fp32" else self.lib.lhv_step_f64
+        fn = self.lib.lhv_step_f64 if self.precision == "fp64" else self.lib.lhv_step
         self._check(fn(self.h, x4.shape[0], _ptr(x4), _ptr(w4), float(dt)), "step")
 
     def step_host(self, x4_host, w4_host, dt):

@@ -51,6 +51,8 @@ int ctx_leaf_max(Ctx* c) { return c->cfg.leaf_max; }
 int ctx_max_level(Ctx* c) { return c->cfg.max_level; }
 double ctx_rK(Ctx* c) { return c->rK; }
 Buf& ctx_tmp(Ctx* c, int i) { return c->tmp[i]; }
+bool ctx_use_tc(Ctx* c) { return c->cfg.precision == LHV_TF32X3; }
+int* ctx_err_flag(Ctx* c) { return reinterpret_cast<int*>(c->counters.as<unsigned long long>() + 2); }
 
 void cuda_check(cudaError_t e, const char* what) {
     if (e != cudaSuccess) throw Error{LHV_ECUDA, std::string(what) + ": " + cudaGetErrorString(e)};
@@ -130,6 +132,13 @@ static void ensure_ops(Ctx* c) {
     StageScope sc(c, LHV_STAGE_OPS);
     build_operators<T>(c, c->cfg.p, c->ops);
     c->ops_type = (int)sizeof(T);
+    if constexpr (sizeof(T) == 4) {
+        const int P = c->ops.P;
+        if (ctx_use_tc(c) && tc_supported(2 * P, 2 * P, P)) {
+            tc_tiles_build(c, c->ops.m2l.as<float>(), NUM_OFFSETS, 2 * P, 2 * P, P, c->ops.m2l_tiles);
+            cuda_check(cudaStreamSynchronize(c->stream), "tc tiles");
+        }
+    }
 }
 
 template <typename T>
@@ -148,9 +157,12 @@ template <typename T>
 static int evaluate(Ctx* c, int64_t n, const vec4_t<T>* x4, const vec4_t<T>* w4, vec4_t<T>* v4, vec4_t<T>* s4) {
     if (n == 0) return LHV_OK;
     ensure_ops<T>(c);
-    ensure(c, c->counters, 64);
+    if (!c->counters.ptr) {
+        ensure(c, c->counters, 64);
+        cuda_check(cudaMemsetAsync(c->counters.ptr, 0, 64, c->stream), "counters init");
+    }
     unsigned long long* cnt = c->counters.as<unsigned long long>();
-    cuda_check(cudaMemsetAsync(cnt, 0, 16, c->stream), "counters");
+    cuda_check(cudaMemsetAsync(cnt, 0, 16, c->stream), "counters");  // [2] holds the device error flag
     Error err{LHV_OK, ""};
     int st = tree_stage<T>(c, n, x4, w4, err);
     if (st != LHV_OK) throw err;
@@ -189,7 +201,9 @@ static int evaluate(Ctx* c, int64_t n, const vec4_t<T>* x4, const vec4_t<T>* w4,
             cuda_check(cudaMemsetAsync(loc + (int64_t)lv.off[2] * 2 * P, 0,
                                        sizeof(T) * (size_t)(nbt - lv.off[2]) * 2 * P, c->stream),
                        "zero locals");
-            run_m2l<T>(c, c->ops, c->tb, lv, c->table.as<int>(), c->gp_m2l, mult, loc, cnt + 1);
+            m2l_prepare(c, c->ops, c->tb, lv, c->table.as<int>(), c->gp_m2l, gemm_nc<T>(2 * P), cnt + 1);
+            StageScope sg(c, LHV_STAGE_M2L_PRODUCTS);
+            m2l_apply<T>(c, c->ops, c->gp_m2l, mult, loc);
         }
         {
             StageScope sc(c, LHV_STAGE_L2L);
@@ -274,7 +288,8 @@ int check_elems(lhv_ctx* ctx, int64_t n, std::initializer_list<const void*> ptrs
         ctx->c.last_error = "n out of range";
         return LHV_EINVAL;
     }
-    if (ctx->c.cfg.precision != want_prec) {
+    const int prec = ctx->c.cfg.precision == LHV_TF32X3 ? LHV_FP32 : ctx->c.cfg.precision;
+    if (prec != want_prec) {
         ctx->c.last_error = "entry point does not match the context precision";
         return LHV_EINVAL;
     }
@@ -323,7 +338,8 @@ int lhv_create(const lhv_config* cfg, void* cuda_stream, lhv_ctx** out) {
     if (cfg->p < 1 || cfg->p > 24 || cfg->leaf_max < 1 || !(cfg->core_a >= 0.0) || !std::isfinite(cfg->core_a))
         return LHV_EINVAL;
     if (cfg->core_a > 0.0 && !(cfg->eps > 0.0 && cfg->eps < 1.0)) return LHV_EINVAL;
-    if (cfg->precision != LHV_FP32 && cfg->precision != LHV_FP64) return LHV_EINVAL;
+    if (cfg->precision != LHV_FP32 && cfg->precision != LHV_FP64 && cfg->precision != LHV_TF32X3) return LHV_EINVAL;
+    if (cfg->precision == LHV_TF32X3 && (cfg->p % 2) != 0) return LHV_EUNSUPPORTED;
     if (cfg->terms < 0 || cfg->terms > 3 || cfg->max_level < 0 || cfg->max_level > 21) return LHV_EINVAL;
     lhv_ctx* h = new (std::nothrow) lhv_ctx();
     if (!h) return LHV_ENOMEM;
@@ -418,7 +434,7 @@ int lhv_step_f64(lhv_ctx* ctx, int64_t n, double* x4, double* w4, double dt) {
 
 int lhv_step_host(lhv_ctx* ctx, int64_t n, float* x4_host, float* w4_host, double dt) {
     if (!ctx) return LHV_EINVAL;
-    if (ctx->c.cfg.precision != LHV_FP32 || n < 0 || (n > 0 && (!x4_host || !w4_host)) || !std::isfinite(dt))
+    if (ctx->c.cfg.precision == LHV_FP64 || n < 0 || (n > 0 && (!x4_host || !w4_host)) || !std::isfinite(dt))
         return LHV_EINVAL;
     if (n == 0) return LHV_OK;
     return guarded(ctx, [&] {
@@ -471,11 +487,15 @@ int lhv_get_stats(lhv_ctx* ctx, lhv_stats* out) {
         for (int l = 0; l < LHV_MAX_LEVELS; ++l) out->nbox[l] = c.lv.nbox[l];
         out->n = c.tree_n;
         if (c.counters.ptr) {
-            unsigned long long h[2] = {0, 0};
-            lhv::cuda_check(cudaMemcpyAsync(h, c.counters.ptr, 16, cudaMemcpyDeviceToHost, c.stream), "stats");
+            unsigned long long h[3] = {0, 0, 0};
+            lhv::cuda_check(cudaMemcpyAsync(h, c.counters.ptr, 24, cudaMemcpyDeviceToHost, c.stream), "stats");
             lhv::cuda_check(cudaStreamSynchronize(c.stream), "stats sync");
             out->p2p_pairs = (int64_t)h[0];
             out->m2l_pairs = (int64_t)h[1];
+            if (h[2]) {
+                lhv::cuda_check(cudaMemsetAsync(c.counters.as<unsigned long long>() + 2, 0, 8, c.stream), "flag");
+                throw Error{LHV_ETIMEOUT, "a tensor-core wait timed out; results of that evaluation are invalid"};
+            }
         }
         for (int i = 0; i < LHV_NUM_STAGES; ++i) {
             out->stage_ms[i] = c.stage_ms[i];

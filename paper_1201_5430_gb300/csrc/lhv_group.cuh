@@ -83,6 +83,13 @@ int gemm_nc(int C);
 template <typename T>
 void run_group_gemm(Ctx* c, Grouped& gp, GemmArgs<T> a);
 
+// tensor-core form (tc_gemm.cu), FP32 data; shapes with R % 16 == 0, C % 8 == 0.
+// tc_tiles_build re-lays `ngroups` k-major operators into the TF32 hi/lo tiles the
+// kernel copies straight into shared memory.
+bool tc_supported(int R, int C, int psplit);
+void tc_tiles_build(Ctx* c, const float* ops, int ngroups, int R, int C, int psplit, Buf& tiles);
+void run_tc_gemm(Ctx* c, Grouped& gp, GemmArgs<float> a, const float* tiles, int* err);
+
 // Item sources ---------------------------------------------------------------
 
 // Every box b of the global range [b0, b0 + n) to itself shifted: (src_off + i, dst_off + i), group 0.

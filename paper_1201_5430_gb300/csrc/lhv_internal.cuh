@@ -68,6 +68,8 @@ int ctx_leaf_max(Ctx* c);
 int ctx_max_level(Ctx* c);
 double ctx_rK(Ctx* c);
 Buf& ctx_tmp(Ctx* c, int i);                         // scratch buffers 0..7 owned by the context
+bool ctx_use_tc(Ctx* c);                             // LHV_TF32X3: dense maps on the tensor cores
+int* ctx_err_flag(Ctx* c);                           // device word set by a timed-out device wait
 
 inline int grid_for(int64_t n, int block, int cap = 152 * 32) {
     int64_t g = (n + block - 1) / block;
@@ -111,6 +113,7 @@ struct OpTables {
     Buf l2l;                   // [8][2P][2P]   fused (R|R) + Eq. drt10 per child octant
     Buf l2p;                   // [2P][12P]     v_k (Eq. evf3) and u_lk (Eq. dt3) coefficients
     Buf p2m;                   // [3P][2P]      Eq. eve4 for w = i_x, i_y, i_z
+    Buf m2l_tiles;             // TF32 hi/lo tiles of m2l for the tensor-core products (LHV_TF32X3)
     Buf offsets;               // int[316][3] M2L offsets (dx, dy, dz)
     Buf slot_of;               // int[343] offset (dx+3)*49+(dy+3)*7+(dz+3) -> slot or -1
 };
@@ -141,10 +144,12 @@ void run_l2p(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& lv, 
              vec4_t<T>* sfar);
 
 // ---- M2L (m2l.cu) ------------------------------------------------------------
-// table: (off[L+1] - off[2]) * 316 ints.  loc must be zero for levels >= 2.
+// table: (off[L+1] - off[2]) * 316 ints; nc: pairs per GEMM chunk (gemm_nc).
+void m2l_prepare(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& lv, int* table, Grouped& gp,
+                 int nc, unsigned long long* pair_counter);
+// the products; loc must be zero for levels >= 2.
 template <typename T>
-void run_m2l(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& lv, int* table, Grouped& gp,
-             const T* mult, T* loc, unsigned long long* pair_counter);
+void m2l_apply(Ctx* c, const OpTables& ops, Grouped& gp, const T* mult, T* loc);
 
 // ---- P2P (p2p.cu) ------------------------------------------------------------
 template <typename T>

@@ -56,9 +56,8 @@ __global__ void k_m2l_table(int nb, int level, int off_l, const uint64_t* __rest
 
 }  // namespace
 
-template <typename T>
-void run_m2l(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& lv, int* table, Grouped& gp,
-             const T* mult, T* loc, unsigned long long* pair_counter) {
+void m2l_prepare(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& lv, int* table, Grouped& gp,
+                 int nc, unsigned long long* pair_counter) {
     cudaStream_t s = stream_of(c);
     const int P = ops.P, L = lv.L;
     // table rows for the global boxes [off[2], off[L+1])
@@ -73,8 +72,13 @@ void run_m2l(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& lv, 
     }
     check_launch("m2l table");
     const int64_t ntarget = lv.off[L + 1] - t0;
-    const int nc = gemm_nc<T>(2 * P);
     build_grouped(c, gp, NUM_OFFSETS, ntarget * NUM_OFFSETS, ntarget * 189, nc, M2LItems{table, t0});
+    (void)P;
+}
+
+template <typename T>
+void m2l_apply(Ctx* c, const OpTables& ops, Grouped& gp, const T* mult, T* loc) {
+    const int P = ops.P;
     GemmArgs<T> a{};
     a.g0 = 0;
     a.g1 = NUM_OFFSETS;
@@ -89,12 +93,16 @@ void run_m2l(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& lv, 
     a.ldout = 2 * P;
     a.mode = GEMM_ATOMIC;
     a.scale = (T)1;
+    if constexpr (sizeof(T) == 4) {
+        if (ctx_use_tc(c) && ops.m2l_tiles.ptr) {
+            run_tc_gemm(c, gp, a, ops.m2l_tiles.as<float>(), ctx_err_flag(c));
+            return;
+        }
+    }
     run_group_gemm<T>(c, gp, a);
 }
 
-template void run_m2l<float>(Ctx*, const OpTables&, const TreeBufs&, const Levels&, int*, Grouped&, const float*,
-                             float*, unsigned long long*);
-template void run_m2l<double>(Ctx*, const OpTables&, const TreeBufs&, const Levels&, int*, Grouped&, const double*,
-                              double*, unsigned long long*);
+template void m2l_apply<float>(Ctx*, const OpTables&, Grouped&, const float*, float*);
+template void m2l_apply<double>(Ctx*, const OpTables&, Grouped&, const double*, double*);
 
 }  // namespace lhv

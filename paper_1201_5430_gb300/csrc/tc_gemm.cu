@@ -1,0 +1,470 @@
+// Tensor-core (tcgen05, TF32) form of the grouped scatter GEMM.
+//
+// Same contract as group_gemm.cu, Y (R x pairs) = A_g X, computed transposed so
+// that the box pairs are the MMA's M dimension:
+//     D (128 pairs x N outputs) = X^T (128 x K) . A_g^T (K x N)        (N <= 256)
+// with D in tensor memory (TMEM, FP32).  Precision: every operand is split
+// a = hi + lo with hi = tf32(a), lo = tf32(a - hi), and D accumulates
+// hi.hi + hi.lo + lo.hi (the lo.lo product is below FP32 rounding), which keeps
+// FP32-level accuracy on the TF32 tensor pipe.
+//
+// The operator side is re-laid once per context (k_tc_tiles) into TF32 hi/lo
+// tiles in the exact shared-memory order, so staging it is a straight 16-byte
+// copy.  Per work item (a chunk of <= 128 pairs of one operator, one N range),
+// for each K chunk of 32 the 256 threads gather and split X^T into one of two
+// shared stages (canonical no-swizzle K-major layout: 8-row x 16-byte core
+// matrices) and copy the operator tile, fence to the async proxy, and one thread
+// issues 4 k-steps x 3 MMAs and commits them to that stage's mbarrier; the next
+// chunk is staged into the other stage while the tensor cores run.  Then each
+// warp reads 32 TMEM lanes (= pairs) and scatters the rows (vector atomics).
+// Every wait on the mbarrier gives up after a fixed number of polls, records an
+// error flag for the host and ends the kernel cleanly (TMEM freed).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "lhv_group.cuh"
+#include "lhv_internal.cuh"
+
+namespace lhv {
+
+namespace {
+
+constexpr int TC_THREADS = 128;   // 4 warps: warp w owns TMEM lanes [32 w, 32 w + 32)
+constexpr int TC_M = 128;         // pairs per work item (MMA M)
+constexpr int TC_KC = 32;         // K per staged chunk (4 MMA k-steps of 8)
+constexpr int TC_NMAX = 256;      // outputs per work item (MMA N, TMEM columns)
+constexpr uint32_t TMEM_COLS = 256;
+constexpr long long WAIT_LIMIT = 1ll << 26;
+
+// byte offset of element (row, k) of a [rows x TC_KC] K-major tile made of
+// 8 x 16-byte core matrices, the K groups of one 8-row block contiguous
+__device__ __forceinline__ uint32_t tile_off(int row, int k) {
+    return (uint32_t)(((row >> 3) * (TC_KC / 4) + (k >> 2)) * 128 + (row & 7) * 16 + (k & 3) * 4);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// shared-memory matrix descriptor, K-major, no swizzle
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo & 0x3FFFFu) >> 4) << 16;
+    d |= (uint64_t)((sbo & 0x3FFFFu) >> 4) << 32;
+    d |= 1ull << 46;  // descriptor version
+    return d;         // base offset 0, swizzle none
+}
+
+// instruction descriptor: D F32, A/B TF32, both K-major, M x N
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, int acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// bounded wait for the phase `parity` of an mbarrier; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    for (long long it = 0; it < WAIT_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 lanes x 32 columns: thread = lane, 32 consecutive FP32 columns
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float c, float d) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
+                 : "memory");
+}
+
+struct TcArgs {
+    GemmArgs<float> g;
+    const float* tiles;    // operator tiles in shared-memory order (see tc_tiles_build), hi then lo
+    int64_t group_stride;  // floats per group of `tiles`
+    int nranges;
+    int n0[8], nlen[8];    // N ranges (<= 256 wide, multiples of 16)
+    int kbeg[8];           // first K of each range (psplit for the chi outputs)
+    int64_t roff[8];       // float offset of each range inside a group
+    int* err;              // set to 1 if a wait timed out
+};
+
+constexpr int TC2_THREADS = 256;  // 8 warps; warp w drains lanes 32 (w % 4) .. +32, column half w / 4
+constexpr int STAGE_BYTES = 2 * TC_M * TC_KC * 4 + 2 * TC_NMAX * TC_KC * 4;  // Xh, Xl, Bh, Bl
+
+// One work item = (chunk of <= 128 pairs of one operator, one N range).  Two
+// shared stages: the tensor cores read stage s while the threads fill s ^ 1.
+__global__ void __launch_bounds__(TC2_THREADS, 1) k_tc_gemm(TcArgs ta) {
+    const GemmArgs<float>& a = ta.g;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ uint64_t bar[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_src[TC_M], s_dst[TC_M];
+    __shared__ int s_work, s_abort;
+    const int t = threadIdx.x, warp = t >> 5;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (t == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    uint32_t par[2] = {0u, 0u};     // next parity to wait for, per barrier
+    int pending[2] = {0, 0};        // commits not yet waited for, per barrier
+
+    auto wait_bar = [&](int b) {
+        if (!pending[b]) return;
+        if (!mbar_wait(&bar[b], par[b]) && t == 0) {
+            atomicExch(ta.err, 1);
+            s_abort = 1;
+        }
+        par[b] ^= 1u;
+        pending[b] = 0;
+    };
+
+    const int c_beg = a.choff[a.g0], c_end = a.choff[a.g1];
+    const int nwork = (c_end - c_beg) * ta.nranges;
+    for (;;) {
+        __syncthreads();
+        if (t == 0) s_work = atomicAdd(a.work, 1);
+        __syncthreads();
+        const int w = s_work;
+        if (w >= nwork || s_abort) break;
+        const int chunk = c_beg + w / ta.nranges, r = w % ta.nranges;
+        const int4 ch = a.chunks[chunk];
+        const int g = ch.x, p0 = ch.y, np = ch.z;
+        const int n0 = ta.n0[r], nlen = ta.nlen[r], kbeg = ta.kbeg[r];
+        const int nk = (a.C - kbeg + TC_KC - 1) / TC_KC;
+        const float* tg = ta.tiles + (int64_t)(g % a.ops_mod) * ta.group_stride + ta.roff[r];
+        const int tile_floats = nlen * TC_KC;
+        if (t < TC_M) {
+            if (t < np) {
+                const int2 pr = a.pairs[p0 + t];
+                s_src[t] = pr.x;
+                s_dst[t] = pr.y;
+            } else {
+                s_src[t] = -1;
+                s_dst[t] = -1;
+            }
+        }
+        const uint32_t idesc = make_idesc(TC_M, nlen);
+        __syncthreads();
+        for (int i = 0; i < nk; ++i) {
+            const int b = i & 1;
+            wait_bar(b);  // the MMAs of chunk i - 2 read this stage
+            unsigned char* st = smem + b * STAGE_BYTES;
+            unsigned char* Xh = st;
+            unsigned char* Xl = Xh + TC_M * TC_KC * 4;
+            unsigned char* Bh = Xl + TC_M * TC_KC * 4;
+            unsigned char* Bl = Bh + TC_NMAX * TC_KC * 4;
+            const int kc = kbeg + i * TC_KC;
+            const int kn = min(TC_KC, a.C - kc);
+            // X^T: 128 rows x 8 groups of 4, two threads per row
+            for (int e = t; e < TC_M * (TC_KC / 4); e += TC2_THREADS) {
+                const int row = e >> 3, kg = e & 7;
+                const int s = s_src[row];
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (s >= 0 && kg * 4 < kn) v = *reinterpret_cast<const float4*>(a.in + (int64_t)s * a.ldin + kc + kg * 4);
+                float4 h, l;
+                h.x = tf32_rna(v.x); l.x = tf32_rna(v.x - h.x);
+                h.y = tf32_rna(v.y); l.y = tf32_rna(v.y - h.y);
+                h.z = tf32_rna(v.z); l.z = tf32_rna(v.z - h.z);
+                h.w = tf32_rna(v.w); l.w = tf32_rna(v.w - h.w);
+                const uint32_t o = tile_off(row, kg * 4);
+                *reinterpret_cast<float4*>(Xh + o) = h;
+                *reinterpret_cast<float4*>(Xl + o) = l;
+            }
+            // A_g^T tile i of this range, already in shared-memory order: straight copies
+            const float4* src = reinterpret_cast<const float4*>(tg + (int64_t)i * 2 * tile_floats);
+            for (int e = t; e < tile_floats / 4; e += TC2_THREADS) {
+                reinterpret_cast<float4*>(Bh)[e] = src[e];
+                reinterpret_cast<float4*>(Bl)[e] = src[e + tile_floats / 4];
+            }
+            fence_async_smem();
+            __syncthreads();
+            if (s_abort) break;
+            if (t == 0) {
+                tc_fence_after();
+                const uint32_t lbo = 128, sbo = (TC_KC / 4) * 128;
+                for (int ks = 0; ks < kn / 8; ++ks) {
+                    const uint32_t step = ks * 2 * 128;
+                    const uint64_t xh = make_desc(smem_u32(Xh) + step, lbo, sbo);
+                    const uint64_t xl = make_desc(smem_u32(Xl) + step, lbo, sbo);
+                    const uint64_t bh = make_desc(smem_u32(Bh) + step, lbo, sbo);
+                    const uint64_t bl = make_desc(smem_u32(Bl) + step, lbo, sbo);
+                    mma_tf32(tmem, xh, bh, idesc, (i == 0 && ks == 0) ? 0 : 1);
+                    mma_tf32(tmem, xh, bl, idesc, 1);
+                    mma_tf32(tmem, xl, bh, idesc, 1);
+                }
+                mma_commit(&bar[b]);
+            }
+            pending[b] = 1;
+        }
+        wait_bar(0);
+        wait_bar(1);
+        tc_fence_after();
+        __syncthreads();
+        if (s_abort) break;
+        // drain: lanes = pairs; the two warps of a lane quarter split the columns
+        const int quarter = warp & 3, half = warp >> 2;
+        const int pr = quarter * 32 + (t & 31);
+        const int d = s_dst[pr];
+        const int ncol = (nlen + 63) / 64 * 32;  // columns per half, multiple of 32
+        for (int c0 = half * ncol; c0 < min(nlen, (half + 1) * ncol); c0 += 32) {
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
+            if (d < 0) continue;
+            float* o = a.out + (int64_t)d * a.ldout + n0 + c0;
+            const int cn = min(32, nlen - c0);
+            if (a.mode == GEMM_ATOMIC) {
+                for (int c = 0; c < cn; c += 4)
+                    red_add_v4(o + c, v[c] * a.scale, v[c + 1] * a.scale, v[c + 2] * a.scale, v[c + 3] * a.scale);
+            } else if (a.mode == GEMM_ADD) {
+                for (int c = 0; c < cn; ++c) o[c] += v[c] * a.scale;
+            } else {
+                for (int c = 0; c < cn; ++c) o[c] = v[c] * a.scale;
+            }
+        }
+        tc_fence_before();
+    }
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+// tiles[g][range r][k chunk i][hi|lo][tile_off order] from the k-major table A_g[C][R]
+__global__ void k_tc_tiles(int ngroups, const float* __restrict__ ops, int R, int C, TcArgs ta, float* __restrict__ tiles) {
+    for (int g = blockIdx.x; g < ngroups; g += gridDim.x) {
+        const float* Ag = ops + (int64_t)g * C * R;
+        float* tg = tiles + (int64_t)g * ta.group_stride;
+        for (int r = 0; r < ta.nranges; ++r) {
+            const int n0 = ta.n0[r], nlen = ta.nlen[r], kbeg = ta.kbeg[r];
+            const int nk = (C - kbeg + TC_KC - 1) / TC_KC;
+            const int tile_floats = nlen * TC_KC;
+            for (int e = threadIdx.x; e < nk * tile_floats; e += blockDim.x) {
+                const int i = e / tile_floats, q = e - i * tile_floats;
+                const int k = q / nlen, n = q - k * nlen;
+                const int kk = kbeg + i * TC_KC + k;
+                const float v = (kk < C) ? Ag[(int64_t)kk * R + n0 + n] : 0.f;
+                const float h = tf32_rna(v), l = tf32_rna(v - h);
+                float* base = tg + ta.roff[r] + (int64_t)i * 2 * tile_floats;
+                const uint32_t o = tile_off(n, k) / 4;
+                base[o] = h;
+                base[tile_floats + o] = l;
+            }
+        }
+    }
+}
+
+// A self-contained check of the descriptor conventions: D (128 x N) = X (128 x K) B^T (K x N),
+// one CTA, no splitting, plain FP32 inputs rounded to TF32.
+__global__ void __launch_bounds__(TC_THREADS, 1) k_tc_selftest(const float* X, const float* B, float* D, int N, int K,
+                                                             int* err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* Xs = smem;
+    unsigned char* Bs = Xs + TC_M * TC_KC * 4;
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tmem_base;
+    const int t = threadIdx.x, warp = t >> 5;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (t == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int kc = 0; kc < K && ok; kc += TC_KC) {
+        for (int k = 0; k < TC_KC; ++k) *reinterpret_cast<float*>(Xs + tile_off(t, k)) = tf32_rna(X[t * K + kc + k]);
+        for (int e = t; e < N * TC_KC; e += TC_THREADS) {
+            const int n = e / TC_KC, k = e % TC_KC;
+            *reinterpret_cast<float*>(Bs + tile_off(n, k)) = tf32_rna(B[n * K + kc + k]);
+        }
+        fence_async_smem();
+        __syncthreads();
+        if (t == 0) {
+            tc_fence_after();
+            for (int ks = 0; ks < TC_KC / 8; ++ks) {
+                const uint32_t step = ks * 2 * 128;
+                mma_tf32(tmem, make_desc(smem_u32(Xs) + step, 128, (TC_KC / 4) * 128),
+                         make_desc(smem_u32(Bs) + step, 128, (TC_KC / 4) * 128), make_idesc(TC_M, N),
+                         (kc > 0 || ks > 0) ? 1 : 0);
+            }
+            mma_commit(&bar);
+        }
+        if (!mbar_wait(&bar, phase)) {
+            ok = false;
+            if (t == 0) atomicExch(err, 1);
+        }
+        phase ^= 1u;
+        tc_fence_after();
+        __syncthreads();
+    }
+    if (ok) {
+        for (int c0 = 0; c0 < N; c0 += 32) {
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            for (int c = 0; c < 32 && c0 + c < N; ++c) D[t * N + c0 + c] = v[c];
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+constexpr size_t TC_SMEM = (size_t)2 * TC_M * TC_KC * 4 + (size_t)2 * TC_NMAX * TC_KC * 4 + 1024;
+constexpr size_t TC2_SMEM = (size_t)2 * STAGE_BYTES + 1024;
+
+TcArgs tc_layout(int R, int C, int psplit) {
+    TcArgs ta{};
+    auto add = [&](int lo, int hi, int kbeg) {
+        for (int x = lo; x < hi; x += TC_NMAX) {
+            const int r = ta.nranges++;
+            ta.n0[r] = x;
+            ta.nlen[r] = std::min(TC_NMAX, hi - x);
+            ta.kbeg[r] = kbeg;
+        }
+    };
+    if (psplit > 0) {
+        add(0, psplit, 0);
+        add(psplit, R, psplit);
+    } else {
+        add(0, R, 0);
+    }
+    int64_t off = 0;
+    for (int r = 0; r < ta.nranges; ++r) {
+        ta.roff[r] = off;
+        const int nk = (C - ta.kbeg[r] + TC_KC - 1) / TC_KC;
+        off += (int64_t)nk * 2 * ta.nlen[r] * TC_KC;
+    }
+    ta.group_stride = off;
+    return ta;
+}
+
+}  // namespace
+
+bool tc_supported(int R, int C, int psplit) {
+    if (C % 8 != 0 || R % 16 != 0) return false;
+    if (psplit > 0 && (psplit % 16 != 0)) return false;
+    const int ranges = psplit > 0 ? (psplit + TC_NMAX - 1) / TC_NMAX + (R - psplit + TC_NMAX - 1) / TC_NMAX
+                                  : (R + TC_NMAX - 1) / TC_NMAX;
+    return ranges <= 8;
+}
+
+void tc_tiles_build(Ctx* c, const float* ops, int ngroups, int R, int C, int psplit, Buf& tiles) {
+    TcArgs ta = tc_layout(R, C, psplit);
+    ensure(c, tiles, ta.group_stride * ngroups * (int64_t)sizeof(float));
+    k_tc_tiles<<<std::min(ngroups, 152 * 4), 256, 0, stream_of(c)>>>(ngroups, ops, R, C, ta, tiles.as<float>());
+    count_launch(c);
+    check_launch("tc tiles");
+}
+
+void run_tc_gemm(Ctx* c, Grouped& gp, GemmArgs<float> a, const float* tiles, int* err) {
+    a.chunks = gp.chunks.as<int4>();
+    a.pairs = gp.pairs.as<int2>();
+    a.choff = gp.choff.as<int>();
+    a.work = gp.work.as<int>();
+    cudaStream_t s = stream_of(c);
+    cuda_check(cudaMemsetAsync(a.work, 0, 4, s), "tc work");
+    TcArgs ta = tc_layout(a.R, a.C, a.psplit);
+    ta.g = a;
+    ta.tiles = tiles;
+    ta.err = err;
+    cuda_check(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC2_SMEM), "tc attr");
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    k_tc_gemm<<<sms, TC2_THREADS, TC2_SMEM, s>>>(ta);
+    count_launch(c);
+    check_launch("tc gemm");
+}
+
+}  // namespace lhv
+
+// Test entry (declared in include/lhv.h): D (128 x N) = X (128 x K) B^T with
+// the TF32 tensor-core path; device pointers, N in {16..256} multiple of 16,
+// K a multiple of 32.  Synchronous.  Returns LHV_ETIMEOUT if the MMA never
+// completed, LHV_EINVAL for bad sizes.
+extern "C" int lhv_tc_selftest(const float* X, const float* B, float* D, int N, int K) {
+    using namespace lhv;
+    if (!X || !B || !D || N < 16 || N > 256 || N % 16 || K < 32 || K % 32) return LHV_EINVAL;
+    int* err = nullptr;
+    if (cudaMalloc(&err, 4) != cudaSuccess) return LHV_ENOMEM;
+    cudaMemset(err, 0, 4);
+    cudaFuncSetAttribute(k_tc_selftest, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+    k_tc_selftest<<<1, TC_THREADS, TC_SMEM>>>(X, B, D, N, K, err);
+    cudaError_t e = cudaDeviceSynchronize();
+    int h = 0;
+    cudaMemcpy(&h, err, 4, cudaMemcpyDeviceToHost);
+    cudaFree(err);
+    if (e != cudaSuccess) return LHV_ECUDA;
+    return h ? LHV_ETIMEOUT : LHV_OK;
+}
