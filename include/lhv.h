@@ -137,6 +137,18 @@ int lhv_step(lhv_ctx* ctx, int64_t n, float* x4, float* w4, double dt);
  * x4_host and w4_host. */
 int lhv_step_host(lhv_ctx* ctx, int64_t n, float* x4_host, float* w4_host, double dt);
 
+/* Batched form: nsys independent systems in one call.  System k owns the
+ * elements [offsets[k], offsets[k+1]) of x4/w4/v4/s4 (offsets: HOST int64
+ * [nsys+1], offsets[0] = 0, non-decreasing; 1 <= nsys <= 4096).  Systems do not
+ * interact; each gets its own cube and octree, all trees are built, translated
+ * and summed by the same launches.  One leaf level serves the whole batch: the
+ * deepest any system needs, capped by the core rule of the smallest cube.
+ * Morton keys keep the system id in their top bits and use
+ * floor((63 - ceil(log2 nsys)) / 3) bits per axis.  FP32 / TF32X3 contexts. */
+int lhv_evaluate_batched(lhv_ctx* ctx, int nsys, const int64_t* offsets, const float* x4, const float* w4,
+                         float* v4, float* s4);
+int lhv_step_batched(lhv_ctx* ctx, int nsys, const int64_t* offsets, float* x4, float* w4, double dt);
+
 /* FP64 twins (FP64 context; element buffers are double[n][4], 32-byte aligned). */
 int lhv_evaluate_velocity_stretching_f64(lhv_ctx* ctx, int64_t n, const double* x4, const double* w4,
                                          double* v4, double* s4);
@@ -164,7 +176,7 @@ int lhv_reset_stats(lhv_ctx* ctx);
                                      offset (dx,dy,dz) at ((dx+1)*3+(dy+1))*3+(dz+1) */
 #define LHV_EXPORT_MULTIPOLE   6  /* real[nbox(level)][2][p*p] scaled S coefficients (phi, chi) */
 #define LHV_EXPORT_LOCAL       7  /* real[nbox(level)][2][p*p] scaled R coefficients (phi, chi) */
-#define LHV_EXPORT_CUBE        8  /* double[4]: x0, y0, z0 of the cube and its side */
+#define LHV_EXPORT_CUBE        8  /* double[4]: x0, y0, z0 of the (first system's) cube and its side */
 /* Scaled real coefficient layout (both potentials, box side h at that level):
  * real index n*n for Re c_n^0, n*n + 2m - 1 / n*n + 2m for Re / Im c_n^m (m >= 1);
  * S coefficients are stored as  c_n^m nu_n^m / h^(n+1) (phi) and c_n^m nu_n^m / h^n (chi),

@@ -46,6 +46,8 @@ SIGNATURES = {
     "lhv_reset_stats": (_int, [_vp]),
     "lhv_export": (_int, [_vp, _int, _int, _vp, _i64, ctypes.POINTER(_i64)]),
     "lhv_tc_selftest": (_int, [_vp, _vp, _vp, _int, _int]),
+    "lhv_evaluate_batched": (_int, [_vp, _int, ctypes.POINTER(_i64), _vp, _vp, _vp, _vp]),
+    "lhv_step_batched": (_int, [_vp, _int, ctypes.POINTER(_i64), _vp, _vp, _dbl]),
 }
 
 _lib = None

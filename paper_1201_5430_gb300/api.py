@@ -74,6 +74,24 @@ class LHV:
         self._check(fn(self.h, n, _ptr(x4), _ptr(w4), _ptr(v4), _ptr(s4)), "evaluate_velocity_stretching")
         return v4, s4
 
+    def evaluate_batched(self, offsets, x4, w4, v4=None, s4=None):
+        """Independent systems: system k owns rows offsets[k]:offsets[k+1]."""
+        self._elems(x4)
+        self._elems(w4)
+        off = (ctypes.c_int64 * len(offsets))(*[int(o) for o in offsets])
+        v4 = torch.empty_like(x4) if v4 is None else self._elems(v4)
+        s4 = torch.empty_like(x4) if s4 is None else self._elems(s4)
+        self._check(self.lib.lhv_evaluate_batched(self.h, len(offsets) - 1, off, _ptr(x4), _ptr(w4), _ptr(v4),
+                                                  _ptr(s4)), "evaluate_batched")
+        return v4, s4
+
+    def step_batched(self, offsets, x4, w4, dt):
+        self._elems(x4)
+        self._elems(w4)
+        off = (ctypes.c_int64 * len(offsets))(*[int(o) for o in offsets])
+        self._check(self.lib.lhv_step_batched(self.h, len(offsets) - 1, off, _ptr(x4), _ptr(w4), float(dt)),
+                    "step_batched")
+
     def step(self, x4, w4, dt):
         self._elems(x4)
         self._elems(w4)

@@ -142,9 +142,10 @@ static void ensure_ops(Ctx* c) {
 }
 
 template <typename T>
-static int tree_stage(Ctx* c, int64_t n, const vec4_t<T>* x4, const vec4_t<T>* w4, Error& err) {
+static int tree_stage(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const vec4_t<T>* x4, const vec4_t<T>* w4,
+                      Error& err) {
     StageScope sc(c, LHV_STAGE_TREE);
-    int st = build_tree<T>(c, n, x4, w4, c->tb, c->lv, c->hp, err);
+    int st = build_tree<T>(c, n, nsys, sysoff, x4, w4, c->tb, c->lv, c->hp, err);
     if (st != LHV_OK) return st;
     c->tree_n = n;
     ensure(c, c->xs, n * (int64_t)sizeof(vec4_t<T>));
@@ -154,7 +155,8 @@ static int tree_stage(Ctx* c, int64_t n, const vec4_t<T>* x4, const vec4_t<T>* w
 }
 
 template <typename T>
-static int evaluate(Ctx* c, int64_t n, const vec4_t<T>* x4, const vec4_t<T>* w4, vec4_t<T>* v4, vec4_t<T>* s4) {
+static int evaluate(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const vec4_t<T>* x4, const vec4_t<T>* w4,
+                    vec4_t<T>* v4, vec4_t<T>* s4) {
     if (n == 0) return LHV_OK;
     ensure_ops<T>(c);
     if (!c->counters.ptr) {
@@ -164,7 +166,7 @@ static int evaluate(Ctx* c, int64_t n, const vec4_t<T>* x4, const vec4_t<T>* w4,
     unsigned long long* cnt = c->counters.as<unsigned long long>();
     cuda_check(cudaMemsetAsync(cnt, 0, 16, c->stream), "counters");  // [2] holds the device error flag
     Error err{LHV_OK, ""};
-    int st = tree_stage<T>(c, n, x4, w4, err);
+    int st = tree_stage<T>(c, n, nsys, sysoff, x4, w4, err);
     if (st != LHV_OK) throw err;
     const Levels& lv = c->lv;
     const int L = lv.L, P = c->ops.P;
@@ -224,7 +226,7 @@ static int evaluate(Ctx* c, int64_t n, const vec4_t<T>* x4, const vec4_t<T>* w4,
 }
 
 template <typename T>
-static int step(Ctx* c, int64_t n, vec4_t<T>* x4, vec4_t<T>* w4, double dt) {
+static int step(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, vec4_t<T>* x4, vec4_t<T>* w4, double dt) {
     if (n == 0) return LHV_OK;
     const int64_t bytes = n * (int64_t)sizeof(vec4_t<T>);
     for (int i = 0; i < 6; ++i) ensure(c, c->rk[i], bytes);
@@ -240,7 +242,7 @@ static int step(Ctx* c, int64_t n, vec4_t<T>* x4, vec4_t<T>* w4, double dt) {
     for (int k = 0; k < 4; ++k) {
         const vec4_t<T>* xin = (k == 0) ? x4 : sx;
         const vec4_t<T>* win = (k == 0) ? w4 : sw;
-        int st = evaluate<T>(c, n, xin, win, kv, ks);
+        int st = evaluate<T>(c, n, nsys, sysoff, xin, win, kv, ks);
         if (st != LHV_OK) return st;
         StageScope sc(c, LHV_STAGE_RK4);
         run_rk4_stage<T>(c, n, x4, w4, kv, ks, ax, aw, sx, sw, c_acc[k], c_stage[k], k == 0);
@@ -363,7 +365,7 @@ void lhv_destroy(lhv_ctx* ctx) {
     lhv::TreeBufs& t = c.tb;
     lhv::Buf* tree[] = {&t.keys_a, &t.keys_b, &t.idx_a, &t.idx_b, &t.hist, &t.boxof_a, &t.boxof_b, &t.flags,
                         &t.scan_tmp, &t.perm, &t.params, &t.counts, &t.bkey, &t.bbeg, &t.bend, &t.bparent,
-                        &t.bcbeg, &t.bcend, &t.bcol, &t.tiles, &t.tile_count};
+                        &t.bcbeg, &t.bcend, &t.bcol, &t.tiles, &t.tile_count, &t.cubes, &t.sysoff};
     for (auto* b : tree) lhv::release(*b);
     for (auto& b : c.tmp) lhv::release(b);
     lhv::Buf* rest[] = {&c.xs, &c.ws, &c.mult, &c.loc, &c.table, &c.vfar, &c.sfar, &c.counters, &c.hx, &c.hw,
@@ -385,7 +387,8 @@ int lhv_build_tree(lhv_ctx* ctx, int64_t n, const float* x4) {
     if (st != LHV_OK || n == 0) return st;
     return guarded(ctx, [&] {
         Error err{LHV_OK, ""};
-        int s = lhv::tree_stage<float>(&ctx->c, n, reinterpret_cast<const float4*>(x4),
+        const int64_t off[2] = {0, n};
+        int s = lhv::tree_stage<float>(&ctx->c, n, 1, off, reinterpret_cast<const float4*>(x4),
                                        reinterpret_cast<const float4*>(x4), err);
         if (s != LHV_OK) throw err;
         return LHV_OK;
@@ -397,7 +400,8 @@ int lhv_evaluate_velocity_stretching(lhv_ctx* ctx, int64_t n, const float* x4, c
     int st = check_elems(ctx, n, {x4, w4, v4, s4}, 16, LHV_FP32);
     if (st != LHV_OK) return st;
     return guarded(ctx, [&] {
-        return lhv::evaluate<float>(&ctx->c, n, reinterpret_cast<const float4*>(x4),
+        const int64_t off[2] = {0, n};
+        return lhv::evaluate<float>(&ctx->c, n, 1, off, reinterpret_cast<const float4*>(x4),
                                     reinterpret_cast<const float4*>(w4), reinterpret_cast<float4*>(v4),
                                     reinterpret_cast<float4*>(s4));
     });
@@ -408,7 +412,8 @@ int lhv_evaluate_velocity_stretching_f64(lhv_ctx* ctx, int64_t n, const double* 
     int st = check_elems(ctx, n, {x4, w4, v4, s4}, 32, LHV_FP64);
     if (st != LHV_OK) return st;
     return guarded(ctx, [&] {
-        return lhv::evaluate<double>(&ctx->c, n, reinterpret_cast<const lhv::dbl4*>(x4),
+        const int64_t off[2] = {0, n};
+        return lhv::evaluate<double>(&ctx->c, n, 1, off, reinterpret_cast<const lhv::dbl4*>(x4),
                                      reinterpret_cast<const lhv::dbl4*>(w4), reinterpret_cast<lhv::dbl4*>(v4),
                                      reinterpret_cast<lhv::dbl4*>(s4));
     });
@@ -419,7 +424,8 @@ int lhv_step(lhv_ctx* ctx, int64_t n, float* x4, float* w4, double dt) {
     if (st != LHV_OK) return st;
     if (!std::isfinite(dt)) return LHV_EINVAL;
     return guarded(ctx, [&] {
-        return lhv::step<float>(&ctx->c, n, reinterpret_cast<float4*>(x4), reinterpret_cast<float4*>(w4), dt);
+        const int64_t off[2] = {0, n};
+        return lhv::step<float>(&ctx->c, n, 1, off, reinterpret_cast<float4*>(x4), reinterpret_cast<float4*>(w4), dt);
     });
 }
 
@@ -428,7 +434,9 @@ int lhv_step_f64(lhv_ctx* ctx, int64_t n, double* x4, double* w4, double dt) {
     if (st != LHV_OK) return st;
     if (!std::isfinite(dt)) return LHV_EINVAL;
     return guarded(ctx, [&] {
-        return lhv::step<double>(&ctx->c, n, reinterpret_cast<lhv::dbl4*>(x4), reinterpret_cast<lhv::dbl4*>(w4), dt);
+        const int64_t off[2] = {0, n};
+        return lhv::step<double>(&ctx->c, n, 1, off, reinterpret_cast<lhv::dbl4*>(x4), reinterpret_cast<lhv::dbl4*>(w4),
+                                 dt);
     });
 }
 
@@ -447,7 +455,8 @@ int lhv_step_host(lhv_ctx* ctx, int64_t n, float* x4_host, float* w4_host, doubl
             lhv::cuda_check(cudaMemcpyAsync(c.hx.ptr, x4_host, bytes, cudaMemcpyHostToDevice, c.stream), "h2d x");
             lhv::cuda_check(cudaMemcpyAsync(c.hw.ptr, w4_host, bytes, cudaMemcpyHostToDevice, c.stream), "h2d w");
         }
-        int st = lhv::step<float>(&c, n, c.hx.as<float4>(), c.hw.as<float4>(), dt);
+        const int64_t off[2] = {0, n};
+        int st = lhv::step<float>(&c, n, 1, off, c.hx.as<float4>(), c.hw.as<float4>(), dt);
         if (st != LHV_OK) return st;
         {
             lhv::StageScope sc(&c, LHV_STAGE_COPY);
@@ -456,6 +465,40 @@ int lhv_step_host(lhv_ctx* ctx, int64_t n, float* x4_host, float* w4_host, doubl
         }
         lhv::cuda_check(cudaStreamSynchronize(c.stream), "sync step_host");
         return LHV_OK;
+    });
+}
+
+static int check_offsets(lhv_ctx* ctx, int nsys, const int64_t* offsets) {
+    if (!ctx || nsys < 1 || nsys > 4096 || !offsets || offsets[0] != 0) return LHV_EINVAL;
+    for (int i = 0; i < nsys; ++i)
+        if (offsets[i + 1] < offsets[i]) return LHV_EINVAL;
+    return LHV_OK;
+}
+
+int lhv_evaluate_batched(lhv_ctx* ctx, int nsys, const int64_t* offsets, const float* x4, const float* w4, float* v4,
+                         float* s4) {
+    int st = check_offsets(ctx, nsys, offsets);
+    if (st != LHV_OK) return st;
+    const int64_t n = offsets[nsys];
+    st = check_elems(ctx, n, {x4, w4, v4, s4}, 16, LHV_FP32);
+    if (st != LHV_OK) return st;
+    return guarded(ctx, [&] {
+        return lhv::evaluate<float>(&ctx->c, n, nsys, offsets, reinterpret_cast<const float4*>(x4),
+                                    reinterpret_cast<const float4*>(w4), reinterpret_cast<float4*>(v4),
+                                    reinterpret_cast<float4*>(s4));
+    });
+}
+
+int lhv_step_batched(lhv_ctx* ctx, int nsys, const int64_t* offsets, float* x4, float* w4, double dt) {
+    int st = check_offsets(ctx, nsys, offsets);
+    if (st != LHV_OK) return st;
+    const int64_t n = offsets[nsys];
+    st = check_elems(ctx, n, {x4, w4}, 16, LHV_FP32);
+    if (st != LHV_OK) return st;
+    if (!std::isfinite(dt)) return LHV_EINVAL;
+    return guarded(ctx, [&] {
+        return lhv::step<float>(&ctx->c, n, nsys, offsets, reinterpret_cast<float4*>(x4), reinterpret_cast<float4*>(w4),
+                                dt);
     });
 }
 
@@ -554,7 +597,7 @@ int lhv_export(lhv_ctx* ctx, int what, int level, void* dst, int64_t capacity_by
                 if (bytes_out) *bytes_out = bytes;
                 if (!dst) return LHV_OK;
                 if (capacity_bytes < bytes) return LHV_EINVAL;
-                lhv::cuda_check(cudaMemcpyAsync(dst, c.tb.params.ptr, 32, cudaMemcpyDeviceToDevice, c.stream),
+                lhv::cuda_check(cudaMemcpyAsync(dst, c.tb.cubes.ptr, 32, cudaMemcpyDeviceToDevice, c.stream),
                                 "export cube");
                 return LHV_OK;
             }

@@ -17,12 +17,18 @@ namespace lhv {
 
 namespace {
 
-__device__ inline double box_centre(const TreeParams* tp, uint64_t key, int axis, int level, double h) {
-    // key prefix at `level`: bits interleaved x, y, z from bit 0
-    uint64_t v = key >> axis;
-    uint64_t c = 0;
-    for (int b = 0; b < level; ++b) c |= ((v >> (3 * b)) & 1ull) << b;
-    return tp->x0[axis] + ((double)c + 0.5) * h;
+// Centre and side of a box from its key prefix at `level` (Morton bits interleaved
+// x, y, z from bit 0; the system id above bit 3*level selects the cube).
+__device__ inline void box_geom(const SysCube* __restrict__ cubes, uint64_t key, int level, double& cx, double& cy,
+                                double& cz, double& h) {
+    const SysCube cb = cubes[level > 0 ? (key >> (3 * level)) : key];
+    h = ldexp(cb.side, -level);
+    uint64_t c[3] = {0, 0, 0};
+    for (int b = 0; b < level; ++b)
+        for (int ax = 0; ax < 3; ++ax) c[ax] |= ((key >> (3 * b + ax)) & 1ull) << b;
+    cx = cb.x0[0] + ((double)c[0] + 0.5) * h;
+    cy = cb.x0[1] + ((double)c[1] + 0.5) * h;
+    cz = cb.x0[2] + ((double)c[2] + 0.5) * h;
 }
 
 // Walks every (n, m), 0 <= m <= n < p, of the recurrence of Q_n^m at (x, y, z)
@@ -71,7 +77,7 @@ constexpr int P2M_THREADS = 128;
 template <typename T>
 __global__ void __launch_bounds__(P2M_THREADS) k_p2m_w(int nleaf, int level, const uint64_t* __restrict__ bkey,
                                                      const int* __restrict__ bbeg, const int* __restrict__ bend,
-                                                     const TreeParams* __restrict__ tp,
+                                                     const SysCube* __restrict__ cubes,
                                                      const vec4_t<T>* __restrict__ xs,
                                                      const vec4_t<T>* __restrict__ ws, T* __restrict__ Wout, int p,
                                                      int chunk) {
@@ -79,11 +85,10 @@ __global__ void __launch_bounds__(P2M_THREADS) k_p2m_w(int nleaf, int level, con
     const int P = p * p;
     T* gh = reinterpret_cast<T*>(smem_raw);  // [chunk][P]
     T* wk = gh + (size_t)chunk * P;          // [chunk][3]
-    const double h = ldexp(tp->side, -level);
     for (int b = blockIdx.x; b < nleaf; b += gridDim.x) {
-        const uint64_t key = bkey[b];
-        const double cx = box_centre(tp, key, 0, level, h), cy = box_centre(tp, key, 1, level, h),
-                     cz = box_centre(tp, key, 2, level, h);
+        double cx, cy, cz, h;
+        box_geom(cubes, bkey[b], level, cx, cy, cz, h);
+        const T invh = (T)(1.0 / h);
         T* Wb = Wout + (int64_t)b * 3 * P;  // entry i is owned by thread i mod blockDim
         for (int i = threadIdx.x; i < 3 * P; i += blockDim.x) Wb[i] = 0;
         const int e0 = bbeg[b], e1 = bend[b];
@@ -92,9 +97,9 @@ __global__ void __launch_bounds__(P2M_THREADS) k_p2m_w(int nleaf, int level, con
             __syncthreads();
             for (int e = threadIdx.x; e < ne; e += blockDim.x) {
                 vec4_t<T> xv = xs[c0 + e], wv = ws[c0 + e];
-                wk[e * 3 + 0] = wv.x;
-                wk[e * 3 + 1] = wv.y;
-                wk[e * 3 + 2] = wv.z;
+                wk[e * 3 + 0] = wv.x * invh;  // M_hat carries 1/h (P2M scaling)
+                wk[e * 3 + 1] = wv.y * invh;
+                wk[e * 3 + 2] = wv.z * invh;
                 T* g = gh + (size_t)e * P;
                 const T rx = (T)(((double)xv.x - cx) / h), ry = (T)(((double)xv.y - cy) / h),
                         rz = (T)(((double)xv.z - cz) / h);
@@ -139,7 +144,7 @@ constexpr int L2P_THREADS = 128;
 template <typename T>
 __global__ void __launch_bounds__(L2P_THREADS) k_l2p_eval(int nleaf, int level, const uint64_t* __restrict__ bkey,
                                                         const int* __restrict__ bbeg, const int* __restrict__ bend,
-                                                        const TreeParams* __restrict__ tp,
+                                                        const SysCube* __restrict__ cubes,
                                                         const vec4_t<T>* __restrict__ xs,
                                                         const vec4_t<T>* __restrict__ ws, const T* __restrict__ cfg,
                                                         vec4_t<T>* __restrict__ vfar, vec4_t<T>* __restrict__ sfar,
@@ -147,11 +152,9 @@ __global__ void __launch_bounds__(L2P_THREADS) k_l2p_eval(int nleaf, int level, 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int P = p * p;
     T* cf = reinterpret_cast<T*>(smem_raw);  // [P][12]
-    const double h = ldexp(tp->side, -level);
     for (int b = blockIdx.x; b < nleaf; b += gridDim.x) {
-        const uint64_t key = bkey[b];
-        const double cx = box_centre(tp, key, 0, level, h), cy = box_centre(tp, key, 1, level, h),
-                     cz = box_centre(tp, key, 2, level, h);
+        double cx, cy, cz, h;
+        box_geom(cubes, bkey[b], level, cx, cy, cz, h);
         __syncthreads();
         const T* src = cfg + (int64_t)b * 12 * P;
         for (int idx = threadIdx.x; idx < 12 * P; idx += blockDim.x) {
@@ -218,7 +221,7 @@ void run_p2m(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& lv, 
     const size_t smem = sizeof(T) * (size_t)chunk * (P + 3);
     cuda_check(cudaFuncSetAttribute(k_p2m_w<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "p2m attr");
     k_p2m_w<T><<<grid_for(nl, 1, 152 * 16), P2M_THREADS, smem, stream_of(c)>>>(
-        nl, L, tb.bkey.as<uint64_t>() + o, tb.bbeg.as<int>() + o, tb.bend.as<int>() + o, tb.params.as<TreeParams>(), xs,
+        nl, L, tb.bkey.as<uint64_t>() + o, tb.bbeg.as<int>() + o, tb.bend.as<int>() + o, tb.cubes.as<SysCube>(), xs,
         ws, W, ops.p, chunk);
     count_launch(c);
     check_launch("p2m w");
@@ -236,7 +239,7 @@ void run_p2m(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& lv, 
     a.out = mult;
     a.ldout = 2 * P;
     a.mode = GEMM_STORE;
-    a.scale = (T)(1.0 / ldexp(hp.side, -L));
+    a.scale = (T)1;  // the 1/h of each leaf is applied to W
     run_group_gemm<T>(c, gp, a);
 }
 
@@ -330,7 +333,7 @@ void run_l2p(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& lv, 
     const size_t smem = sizeof(T) * 12 * P;
     cuda_check(cudaFuncSetAttribute(k_l2p_eval<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "l2p attr");
     k_l2p_eval<T><<<grid_for(nl, 1, 152 * 16), L2P_THREADS, smem, stream_of(c)>>>(
-        nl, L, tb.bkey.as<uint64_t>() + o, tb.bbeg.as<int>() + o, tb.bend.as<int>() + o, tb.params.as<TreeParams>(), xs,
+        nl, L, tb.bkey.as<uint64_t>() + o, tb.bbeg.as<int>() + o, tb.bend.as<int>() + o, tb.cubes.as<SysCube>(), xs,
         ws, cf, vfar, sfar, ops.p);
     count_launch(c);
     check_launch("l2p");

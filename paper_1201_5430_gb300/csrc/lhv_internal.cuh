@@ -26,14 +26,22 @@ template <> struct Vec4<float> { using type = float4; };
 template <> struct Vec4<double> { using type = dbl4; };
 template <typename T> using vec4_t = typename Vec4<T>::type;
 
-// Cube and level of the current tree, written by the tree kernels.
+// Cube of one system: origin (FP32 minimum per axis) and power-of-two side.
+struct SysCube {
+    double x0[3];
+    double side;
+};
+
+// Leaf level and key layout of the current tree, written by the tree kernels.
+// Keys: system id in the top bits, then the 3 * bits Morton bits of the position
+// in the system's own cube (bits = 21 for one system).
 struct TreeParams {
-    double x0[3];       // cube origin (FP32 minimum per axis)
-    double side;        // power-of-two side
-    int L;              // leaf level
+    int L;              // leaf level (the same for every system of a batch)
     int nonfinite;      // 1 if a position or strength is NaN/Inf
     int deepest_shared; // deepest level at which leaf_max+1 consecutive keys share a box
-    int pad;
+    int bits;           // Morton bits per axis
+    int nsys;
+    int pad[3];
 };
 
 // Growable device allocation.
@@ -83,16 +91,20 @@ struct TreeBufs {
     Buf keys_a, keys_b, idx_a, idx_b, hist, boxof_a, boxof_b, flags, scan_tmp;
     Buf perm;                  // int32[n]
     Buf params;                // TreeParams (device)
+    Buf cubes;                 // SysCube[nsys] (device)
+    Buf sysoff;                // int64[nsys + 1] element offsets of the systems (device)
     Buf counts;                // int32[64] (device)
     Buf bkey, bbeg, bend, bparent, bcbeg, bcend, bcol;  // per box (global index)
     Buf tiles, tile_count;     // P2P work items: int2 (leaf, first element)
 };
 
-// Builds keys, sort, levels and lists for n positions (device [n][4] of T).
-// On return `lv` (host) is filled; one stream synchronisation happens inside.
+// Builds keys, sort, levels and lists for n positions (device [n][4] of T) of
+// nsys systems (host offsets sysoff[0..nsys], sysoff[0] = 0, sysoff[nsys] = n).
+// On return `lv` (host) is filled; two short stream synchronisations happen inside.
 template <typename T>
-int build_tree(Ctx* c, int64_t n, const vec4_t<T>* x4, const vec4_t<T>* w4, TreeBufs& tb, Levels& lv,
-               TreeParams& hp, Error& err);
+int build_tree(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const vec4_t<T>* x4, const vec4_t<T>* w4,
+               TreeBufs& tb, Levels& lv, TreeParams& hp, Error& err);
+int key_bits_for(int nsys);
 
 // Device-wide exclusive scan of int32 (in may equal out); *total_out (device) gets the sum.
 void exclusive_scan(Ctx* c, int64_t n, const int* in, int* out, int* tmp, int* total_out);

@@ -50,18 +50,23 @@ __host__ __device__ inline uint64_t morton3(uint64_t qx, uint64_t qy, uint64_t q
 // ---------------------------------------------------------------------------
 // Cube
 // ---------------------------------------------------------------------------
+// nsys * parts blocks; block b reduces part b % parts of system b / parts.
 template <typename T>
-__global__ void k_bbox_partial(int64_t n, const vec4_t<T>* __restrict__ x4, const vec4_t<T>* __restrict__ w4,
-                               double* __restrict__ part, int* __restrict__ nonfinite) {
+__global__ void k_bbox_partial(int parts, const int64_t* __restrict__ sysoff, const vec4_t<T>* __restrict__ x4,
+                               const vec4_t<T>* __restrict__ w4, double* __restrict__ part,
+                               int* __restrict__ nonfinite) {
     __shared__ double s[6][256];
+    const int sys = blockIdx.x / parts, q = blockIdx.x % parts;
+    const int64_t o0 = sysoff[sys], len = sysoff[sys + 1] - o0;
+    const int64_t beg = o0 + len * q / parts, end = o0 + len * (q + 1) / parts;
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     int bad = 0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
         vec4_t<T> p = x4[i];
-        vec4_t<T> q = w4 ? w4[i] : p;
+        vec4_t<T> qv = w4 ? w4[i] : p;
         double c[3] = {(double)p.x, (double)p.y, (double)p.z};
         bad |= !(isfinite(c[0]) && isfinite(c[1]) && isfinite(c[2]));
-        bad |= !(isfinite((double)q.x) && isfinite((double)q.y) && isfinite((double)q.z));
+        bad |= !(isfinite((double)qv.x) && isfinite((double)qv.y) && isfinite((double)qv.z));
         for (int k = 0; k < 3; ++k) {
             lo[k] = fmin(lo[k], c[k]);
             hi[k] = fmax(hi[k], c[k]);
@@ -85,13 +90,16 @@ __global__ void k_bbox_partial(int64_t n, const vec4_t<T>* __restrict__ x4, cons
     if (threadIdx.x < 6) part[blockIdx.x * 6 + threadIdx.x] = s[threadIdx.x][0];
 }
 
-__global__ void k_bbox_final(int nparts, const double* __restrict__ part, TreeParams* __restrict__ tp) {
+// one block per system: its cube (an empty system gets the unit cube at the origin)
+__global__ void k_bbox_final(int parts, const double* __restrict__ part, SysCube* __restrict__ cubes,
+                             TreeParams* __restrict__ tp) {
     __shared__ double r[6][256];
+    const int sys = blockIdx.x;
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int b = threadIdx.x; b < nparts; b += blockDim.x)
+    for (int b = threadIdx.x; b < parts; b += blockDim.x)
         for (int k = 0; k < 3; ++k) {
-            lo[k] = fmin(lo[k], part[b * 6 + k]);
-            hi[k] = fmax(hi[k], part[b * 6 + 3 + k]);
+            lo[k] = fmin(lo[k], part[(sys * parts + b) * 6 + k]);
+            hi[k] = fmax(hi[k], part[(sys * parts + b) * 6 + 3 + k]);
         }
     for (int k = 0; k < 3; ++k) {
         r[k][threadIdx.x] = lo[k];
@@ -108,9 +116,10 @@ __global__ void k_bbox_final(int nparts, const double* __restrict__ part, TreePa
     }
     if (threadIdx.x != 0) return;
     double ext = 0.0;
+    const bool empty = !(r[0][0] <= r[3][0]);
     for (int k = 0; k < 3; ++k) {
-        tp->x0[k] = r[k][0];
-        ext = fmax(ext, r[3 + k][0] - r[k][0]);
+        cubes[sys].x0[k] = empty ? 0.0 : r[k][0];
+        if (!empty) ext = fmax(ext, r[3 + k][0] - r[k][0]);
     }
     double side = 1.0;
     if (ext > 0.0) {
@@ -118,22 +127,33 @@ __global__ void k_bbox_final(int nparts, const double* __restrict__ part, TreePa
         double mant = frexp(ext, &e);  // ext = mant 2^e, 0.5 <= mant < 1
         side = (mant == 0.5) ? ldexp(1.0, e - 1) : ldexp(1.0, e);
     }
-    tp->side = side;
-    tp->deepest_shared = -1;
+    cubes[sys].side = side;
+    if (sys == 0) tp->deepest_shared = -1;
+}
+
+__device__ inline int system_of(int64_t i, int nsys, const int64_t* __restrict__ sysoff) {
+    int lo = 0, hi = nsys - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sysoff[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
 }
 
 template <typename T>
-__global__ void k_morton(int64_t n, const vec4_t<T>* __restrict__ x4, const TreeParams* __restrict__ tp,
+__global__ void k_morton(int64_t n, int nsys, int bits, const int64_t* __restrict__ sysoff,
+                         const SysCube* __restrict__ cubes, const vec4_t<T>* __restrict__ x4,
                          uint64_t* __restrict__ keys, int* __restrict__ idx) {
-    const double scale = (double)(1 << KEY_BITS) / tp->side;
-    const double x0 = tp->x0[0], y0 = tp->x0[1], z0 = tp->x0[2];
-    const double qmax = (double)((1 << KEY_BITS) - 1);
+    const double qmax = (double)((1 << bits) - 1);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int sys = nsys > 1 ? system_of(i, nsys, sysoff) : 0;
+        const SysCube cb = cubes[sys];
+        const double scale = (double)(1 << bits) / cb.side;
         vec4_t<T> p = x4[i];
-        double qx = fmin(fmax(floor(((double)p.x - x0) * scale), 0.0), qmax);
-        double qy = fmin(fmax(floor(((double)p.y - y0) * scale), 0.0), qmax);
-        double qz = fmin(fmax(floor(((double)p.z - z0) * scale), 0.0), qmax);
-        keys[i] = morton3((uint64_t)qx, (uint64_t)qy, (uint64_t)qz);
+        double qx = fmin(fmax(floor(((double)p.x - cb.x0[0]) * scale), 0.0), qmax);
+        double qy = fmin(fmax(floor(((double)p.y - cb.x0[1]) * scale), 0.0), qmax);
+        double qz = fmin(fmax(floor(((double)p.z - cb.x0[2]) * scale), 0.0), qmax);
+        keys[i] = ((uint64_t)sys << (3 * bits)) | morton3((uint64_t)qx, (uint64_t)qy, (uint64_t)qz);
         idx[i] = (int)i;
     }
 }
@@ -292,7 +312,7 @@ int64_t scan_tmp_ints(int64_t n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 1; }
 // ---------------------------------------------------------------------------
 // Leaf level
 // ---------------------------------------------------------------------------
-__global__ void k_shared_level(int64_t n, int leaf_max, const uint64_t* __restrict__ keys,
+__global__ void k_shared_level(int64_t n, int leaf_max, int bits, const uint64_t* __restrict__ keys,
                                TreeParams* __restrict__ tp) {
     int best = -1;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i + leaf_max < n;
@@ -300,10 +320,10 @@ __global__ void k_shared_level(int64_t n, int leaf_max, const uint64_t* __restri
         uint64_t x = keys[i] ^ keys[i + leaf_max];
         int lvl;
         if (x == 0) {
-            lvl = KEY_BITS;
+            lvl = bits;
         } else {
             int msb = 63 - __clzll((long long)x);
-            lvl = KEY_BITS - (msb + 3) / 3;  // deepest level at which both keys share a box
+            lvl = bits - (msb + 3) / 3;  // deepest level at which both keys share a box (< 0: two systems)
         }
         best = max(best, lvl);
     }
@@ -311,14 +331,19 @@ __global__ void k_shared_level(int64_t n, int leaf_max, const uint64_t* __restri
     if ((threadIdx.x & 31) == 0 && best >= 0) atomicMax(&tp->deepest_shared, best);
 }
 
-__global__ void k_leaf_level(TreeParams* __restrict__ tp, double rK, int max_level) {
+// One leaf level for all systems: the deepest L_leaf any system needs, capped by the
+// core rule of the smallest cube (every far pair of every system sees K = 1).
+__global__ void k_leaf_level(TreeParams* __restrict__ tp, const SysCube* __restrict__ cubes, int nsys, int bits,
+                             double rK, int max_level) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    int L_leaf = min(tp->deepest_shared + 1, KEY_BITS);
-    int L_K = KEY_BITS;
+    int L_leaf = min(tp->deepest_shared + 1, bits);
+    double min_side = INFINITY;
+    for (int s = 0; s < nsys; ++s) min_side = fmin(min_side, cubes[s].side);
+    int L_K = bits;
     if (rK > 0.0) {
         L_K = 0;
-        for (int l = 0; l <= KEY_BITS; ++l)
-            if (ldexp(tp->side, -l) >= rK) L_K = l;
+        for (int l = 0; l <= bits; ++l)
+            if (ldexp(min_side, -l) >= rK) L_K = l;
     }
     int L = min(L_leaf, L_K);
     if (max_level > 0) L = min(L, max_level);
@@ -384,11 +409,15 @@ __global__ void k_compact_level(int nb, int level, int L, const uint64_t* __rest
     }
 }
 
-// 27 colleagues of every box of one level (binary search among the level's keys).
+// 27 colleagues of every box of one level (binary search among the level's keys);
+// the system id above the level's 3*level Morton bits is kept.
 __global__ void k_colleagues(int nb, int level, const uint64_t* __restrict__ bkey, int* __restrict__ col) {
     const int64_t dim = 1ll << level;
+    const uint64_t mask = (level > 0) ? ((~0ull) >> (64 - 3 * level)) : 0ull;
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
-        uint64_t key = bkey[b];
+        const uint64_t full = bkey[b];
+        const uint64_t sysk = (level > 0) ? ((full >> (3 * level)) << (3 * level)) : full;
+        const uint64_t key = full & mask;
         int64_t cx = (int64_t)compact3(key), cy = (int64_t)compact3(key >> 1), cz = (int64_t)compact3(key >> 2);
         int slot = 0;
         for (int dx = -1; dx <= 1; ++dx)
@@ -397,7 +426,7 @@ __global__ void k_colleagues(int nb, int level, const uint64_t* __restrict__ bke
                     int64_t x = cx + dx, y = cy + dy, z = cz + dz;
                     int found = -1;
                     if (x >= 0 && y >= 0 && z >= 0 && x < dim && y < dim && z < dim) {
-                        uint64_t k2 = morton3((uint64_t)x, (uint64_t)y, (uint64_t)z);
+                        uint64_t k2 = sysk | morton3((uint64_t)x, (uint64_t)y, (uint64_t)z);
                         int lo = 0, hi = nb - 1;
                         while (lo <= hi) {
                             int mid = (lo + hi) >> 1;
@@ -454,12 +483,19 @@ void gather_sorted(Ctx* c, int64_t n, const int* perm, const vec4_t<T>* x4, cons
     check_launch("gather");
 }
 
+int key_bits_for(int nsys) {
+    int sysbits = 0;
+    while ((1 << sysbits) < nsys) ++sysbits;
+    return std::min(KEY_BITS, (63 - sysbits) / 3);
+}
+
 template <typename T>
-int build_tree(Ctx* c, int64_t n, const vec4_t<T>* x4, const vec4_t<T>* w4, TreeBufs& tb, Levels& lv,
-               TreeParams& hp, Error& err) {
+int build_tree(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const vec4_t<T>* x4, const vec4_t<T>* w4,
+               TreeBufs& tb, Levels& lv, TreeParams& hp, Error& err) {
     cudaStream_t s = stream_of(c);
     const int leaf_max = ctx_leaf_max(c);
     const int64_t nn = n;
+    const int bits = key_bits_for(nsys);
 
     // capacities that depend on n only
     const int nsort = (int)((nn + SORT_TILE - 1) / SORT_TILE);
@@ -474,21 +510,27 @@ int build_tree(Ctx* c, int64_t n, const vec4_t<T>* x4, const vec4_t<T>* w4, Tree
     ensure(c, tb.scan_tmp, (scan_tmp_ints(std::max<int64_t>(nn, 256 * (int64_t)nsort)) + 64) * 4);
     ensure(c, tb.params, sizeof(TreeParams));
     ensure(c, tb.counts, 64 * 4);
+    ensure(c, tb.cubes, (int64_t)nsys * sizeof(SysCube));
+    ensure(c, tb.sysoff, (int64_t)(nsys + 1) * 8);
+    cuda_check(cudaMemcpyAsync(tb.sysoff.ptr, sysoff, (nsys + 1) * 8, cudaMemcpyHostToDevice, s), "system offsets");
 
     TreeParams* tp = tb.params.as<TreeParams>();
     int* counts = tb.counts.as<int>();
     cuda_check(cudaMemsetAsync(tp, 0, sizeof(TreeParams), s), "memset params");
     cuda_check(cudaMemsetAsync(counts, 0, 64 * 4, s), "memset counts");
 
-    // cube and keys (the radix histogram buffer holds the bounding-box partials first)
-    const int nparts = grid_for(nn, 256, 1024);
-    ensure(c, tb.hist, std::max<int64_t>((int64_t)nsort * 256 * 4 + 64, (int64_t)nparts * 6 * 8));
+    // cubes and keys (the radix histogram buffer holds the bounding-box partials first)
+    const int parts = std::max(1, std::min(1024 / nsys, (int)((nn / nsys + 4095) / 4096)));
+    ensure(c, tb.hist, std::max<int64_t>((int64_t)nsort * 256 * 4 + 64, (int64_t)nsys * parts * 6 * 8));
     double* part = reinterpret_cast<double*>(tb.hist.ptr);
-    k_bbox_partial<T><<<nparts, 256, 0, s>>>(nn, x4, w4, part, &tp->nonfinite);
+    const int64_t* dsysoff = tb.sysoff.as<int64_t>();
+    SysCube* cubes = tb.cubes.as<SysCube>();
+    k_bbox_partial<T><<<nsys * parts, 256, 0, s>>>(parts, dsysoff, x4, w4, part, &tp->nonfinite);
     count_launch(c);
-    k_bbox_final<<<1, 256, 0, s>>>(nparts, part, tp);
+    k_bbox_final<<<nsys, 256, 0, s>>>(parts, part, cubes, tp);
     count_launch(c);
-    k_morton<T><<<grid_for(nn, 256), 256, 0, s>>>(nn, x4, tp, tb.keys_a.as<uint64_t>(), tb.idx_a.as<int>());
+    k_morton<T><<<grid_for(nn, 256), 256, 0, s>>>(nn, nsys, bits, dsysoff, cubes, x4, tb.keys_a.as<uint64_t>(),
+                                                   tb.idx_a.as<int>());
     count_launch(c);
     check_launch("keys");
 
@@ -513,9 +555,9 @@ int build_tree(Ctx* c, int64_t n, const vec4_t<T>* x4, const vec4_t<T>* w4, Tree
     uint64_t* keys = kin;
     int* perm = vin;
 
-    k_shared_level<<<grid_for(nn, 256), 256, 0, s>>>(nn, leaf_max, keys, tp);
+    k_shared_level<<<grid_for(nn, 256), 256, 0, s>>>(nn, leaf_max, bits, keys, tp);
     count_launch(c);
-    k_leaf_level<<<1, 32, 0, s>>>(tp, ctx_rK(c), ctx_max_level(c));
+    k_leaf_level<<<1, 32, 0, s>>>(tp, cubes, nsys, bits, ctx_rK(c), ctx_max_level(c));
     count_launch(c);
     check_launch("leaf level");
     cuda_check(cudaMemcpyAsync(&hp, tp, sizeof(TreeParams), cudaMemcpyDeviceToHost, s), "read params");
@@ -526,11 +568,14 @@ int build_tree(Ctx* c, int64_t n, const vec4_t<T>* x4, const vec4_t<T>* w4, Tree
     }
     const int L = hp.L;
     lv.L = L;
+    hp.bits = bits;
+    hp.nsys = nsys;
 
     // temporary per-level arrays in capacity layout
     lv.cap_off[0] = 0;
     for (int l = 0; l <= L; ++l) {
-        int64_t cap = std::min<int64_t>(nn, (l >= 21) ? nn : (1ll << (3 * l)));
+        int64_t cap = nn;
+        if (3 * l < 40) cap = std::min<int64_t>(nn, (int64_t)nsys << (3 * l));  // boxes per level <= nsys 8^l
         lv.cap_off[l + 1] = lv.cap_off[l] + (int)cap;
     }
     const int64_t tot_cap = lv.cap_off[L + 1];
@@ -550,7 +595,7 @@ int build_tree(Ctx* c, int64_t n, const vec4_t<T>* x4, const vec4_t<T>* w4, Tree
     int* boxof_prev = tb.boxof_a.as<int>();
     int* boxof_cur = tb.boxof_b.as<int>();
     for (int l = 0; l <= L; ++l) {
-        int shift = 3 * (KEY_BITS - l);
+        int shift = 3 * (bits - l);
         int off = lv.cap_off[l];
         int* flags = tb.flags.as<int>();
         k_level_flags<<<grid_for(nn, 256), 256, 0, s>>>(nn, keys, shift, flags);
@@ -628,8 +673,10 @@ int build_tree(Ctx* c, int64_t n, const vec4_t<T>* x4, const vec4_t<T>* w4, Tree
     return LHV_OK;
 }
 
-template int build_tree<float>(Ctx*, int64_t, const float4*, const float4*, TreeBufs&, Levels&, TreeParams&, Error&);
-template int build_tree<double>(Ctx*, int64_t, const dbl4*, const dbl4*, TreeBufs&, Levels&, TreeParams&, Error&);
+template int build_tree<float>(Ctx*, int64_t, int, const int64_t*, const float4*, const float4*, TreeBufs&, Levels&,
+                               TreeParams&, Error&);
+template int build_tree<double>(Ctx*, int64_t, int, const int64_t*, const dbl4*, const dbl4*, TreeBufs&, Levels&,
+                                TreeParams&, Error&);
 template void gather_sorted<float>(Ctx*, int64_t, const int*, const float4*, const float4*, float4*, float4*);
 template void gather_sorted<double>(Ctx*, int64_t, const int*, const dbl4*, const dbl4*, dbl4*, dbl4*);
 

@@ -15,7 +15,8 @@ Workloads (shapes follow the paper's test problems, Sec. 5):
                 1/(4 pi), Eq. 7 puts it into the strengths).
 * ``ring_pair`` -- two rings (Sec. 5.3.2): coaxial leapfrogging pair, or an
                 offset pair whose second ring is tilted and reversed.
-* ``blob_systems`` -- independent systems of Gaussian blob clouds of uneven size.
+* ``blob_systems`` -- independent systems of Gaussian blob clouds of uneven size,
+                strengths xi / (4 pi N_s) with xi ~ N(0, 1) (quadrature weight 1/N_s).
 """
 import math
 
@@ -80,8 +81,10 @@ def ring_pair(n_per_ring, seed, kind="leapfrog"):
 
 def blob_systems(nsys=64, seed=4, n_lo=1e4, n_hi=5e5, blobs=8, sigma=0.05):
     """List of (x, w) per system: sizes log-uniform in [n_lo, n_hi]; each system
-    is ``blobs`` Gaussian clouds (centres ~ U[0.2, 0.8]^3, std ``sigma``) with
-    w ~ N(0, 1) per component."""
+    is ``blobs`` Gaussian clouds (centres ~ U[0.2, 0.8]^3, std ``sigma``).
+    Strengths w = xi / (4 pi N_s), xi ~ N(0, 1) per component: a unit-strength
+    random vorticity field sampled with quadrature weight 1/N_s, the weight and
+    the 1/(4 pi) entering w as in Eq. 7."""
     rng = np.random.default_rng(seed)
     sizes = np.rint(np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), nsys))).astype(np.int64)
     out = []
@@ -92,7 +95,7 @@ def blob_systems(nsys=64, seed=4, n_lo=1e4, n_hi=5e5, blobs=8, sigma=0.05):
         for c in counts:
             centre = rng.uniform(0.2, 0.8, 3)
             xs.append(centre + sigma * rng.standard_normal((c, 3)))
-            ws.append(rng.standard_normal((c, 3)))
+            ws.append(rng.standard_normal((c, 3)) / (4.0 * math.pi * ns))
         out.append((_f32(np.concatenate(xs)), _f32(np.concatenate(ws))))
     return out
 
