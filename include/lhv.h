@@ -47,6 +47,7 @@ extern "C" {
 #define LHV_ETIMEOUT     -4  /* a device-side bounded wait gave up */
 #define LHV_ENONFINITE   -5  /* NaN or Inf in the positions or strengths */
 #define LHV_EUNSUPPORTED -6  /* valid request this build does not implement */
+#define LHV_ETOOBIG      -7  /* input larger than the fixed scratch of a no-allocation entry point */
 
 /* ---- arithmetic of the evaluation (lhv_config.precision) --------------- */
 #define LHV_FP32 0  /* all kernels in FP32 (CUDA cores); operator tables built in FP64, stored FP32 */
@@ -183,6 +184,41 @@ int lhv_reset_stats(lhv_ctx* ctx);
  * R coefficients as             c_n^m h^n / nu_n^m (phi)    and c_n^m h^(n+1) / nu_n^m (chi),
  * nu_n^m = sqrt((n-|m|)! (n+|m|)!), c_n^m the coefficients of Eq. rsbf6. */
 int lhv_export(lhv_ctx* ctx, int what, int level, void* dst, int64_t capacity_bytes, int64_t* bytes_out);
+
+/* ---- no-allocation entry point ------------------------------------------
+ * The paper has no counterpart to this call: it is an engineering variant of the
+ * first step of lhv_build_tree (cube, Morton keys and stable sort of one system,
+ * Sec. 4, "Create data structure") for callers that must not allocate device
+ * memory, because cudaFree synchronises the whole device (cudaMalloc may too)
+ * and both can fail or stall when a caching allocator already holds the device
+ * memory: a real-time loop that shares the GPU with other streams, a host
+ * callback, or an application that owns a fixed memory budget.  It allocates nothing (no
+ * cudaMalloc/cudaFree, no allocating library routine): every temporary lives in
+ * one file-scope device array of fixed size (about 12.3 MiB, present once the
+ * library's module is loaded on a device), whose address the first call on each
+ * device looks up (cudaGetSymbolAddress).  That first call also loads the
+ * library's kernels on the device; make it before any stream capture begins and
+ * outside any region that cannot tolerate that one-time setup.
+ *
+ * Inputs: n <= LHV_NOALLOC_MAX_N positions x4 (device float [n][4], 16-byte
+ * aligned) and optional strengths w4 (same layout, or NULL; only checked for
+ * NaN/Inf).  Outputs (caller-owned device memory, also used as one side of the
+ * sort's ping-pong): keys (uint64 [n]) the sorted Morton keys and perm (int32
+ * [n]) sorted position -> caller index, identical to LHV_EXPORT_KEYS and
+ * LHV_EXPORT_PERM after lhv_build_tree of the same positions (21 bits per axis,
+ * stable order of equal keys).  Work is enqueued on cuda_stream (a cudaStream_t,
+ * NULL = legacy default stream); the call returns after that stream has
+ * finished it (one device-to-host read of the non-finite flag).  The only
+ * scratch state that must start at zero (the non-finite flag) is cleared by the
+ * call's first kernel.  Returns LHV_ETOOBIG for n > LHV_NOALLOC_MAX_N,
+ * LHV_EINVAL for n < 0, null or misaligned pointers, LHV_ENONFINITE for NaN/Inf,
+ * LHV_ECUDA if a CUDA call failed, LHV_OK for n = 0 (nothing done).
+ * Calls that overlap in time on one device (from several host threads, or on
+ * several streams without ordering between them) share the one scratch array
+ * and race: the caller serialises them. */
+#define LHV_NOALLOC_MAX_N (1 << 20)
+int lhv_morton_sort_noalloc(int64_t n, const float* x4, const float* w4, uint64_t* keys, int32_t* perm,
+                            void* cuda_stream);
 
 /* Diagnostic: D = X B^T on the TF32 tensor-core path of this library, one CTA,
  * operands rounded to TF32 (no splitting).  X: device float [128][K], B: device

@@ -48,7 +48,10 @@ SIGNATURES = {
     "lhv_tc_selftest": (_int, [_vp, _vp, _vp, _int, _int]),
     "lhv_evaluate_batched": (_int, [_vp, _int, ctypes.POINTER(_i64), _vp, _vp, _vp, _vp]),
     "lhv_step_batched": (_int, [_vp, _int, ctypes.POINTER(_i64), _vp, _vp, _dbl]),
+    "lhv_morton_sort_noalloc": (_int, [_i64, _vp, _vp, _vp, _vp, _vp]),
 }
+
+NOALLOC_MAX_N = 1 << 20  # LHV_NOALLOC_MAX_N
 
 _lib = None
 

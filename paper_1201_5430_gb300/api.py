@@ -141,3 +141,25 @@ class LHV:
         if what == "cube":
             return buf.view(torch.float64)
         return buf.view(self.dtype)
+
+
+def morton_sort_noalloc(x4, keys, perm, w4=None):
+    """lhv_morton_sort_noalloc: sorted Morton keys and permutation of one system
+    without any device allocation, written into the caller's CUDA tensors
+    ``keys`` (int64 [n]) and ``perm`` (int32 [n]); x4 (and w4) float32 [n][4].
+    Runs on the current CUDA stream and returns when it has finished.  Calls
+    that overlap in time on one device race on the library's fixed scratch."""
+    lib = L.load()
+    n = x4.shape[0]
+    for t, dt, shape in ((x4, torch.float32, (n, 4)), (keys, torch.int64, (n,)), (perm, torch.int32, (n,))):
+        if not (t.is_cuda and t.dtype == dt and tuple(t.shape) == shape and t.is_contiguous()):
+            raise ValueError(f"expected a contiguous CUDA {dt} tensor of shape {shape}")
+    if w4 is not None and not (w4.is_cuda and w4.dtype == torch.float32 and w4.shape == x4.shape
+                               and w4.is_contiguous()):
+        raise ValueError("w4 must match x4")
+    with torch.cuda.device(x4.device):
+        stream = ctypes.c_void_p(torch.cuda.current_stream(x4.device).cuda_stream)
+        st = lib.lhv_morton_sort_noalloc(n, _ptr(x4), _ptr(w4) if w4 is not None else None, _ptr(keys),
+                                         _ptr(perm), stream)
+    if st != 0:
+        raise L.LHVError(st, "morton_sort_noalloc: " + lib.lhv_status_string(st).decode())

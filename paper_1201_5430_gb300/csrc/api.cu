@@ -330,6 +330,7 @@ const char* lhv_status_string(int status) {
         case LHV_ETIMEOUT: return "device wait timed out";
         case LHV_ENONFINITE: return "non-finite input";
         case LHV_EUNSUPPORTED: return "unsupported";
+        case LHV_ETOOBIG: return "input exceeds the fixed scratch of a no-allocation entry point";
         default: return "unknown status";
     }
 }

@@ -681,3 +681,115 @@ template void gather_sorted<float>(Ctx*, int64_t, const int*, const float4*, con
 template void gather_sorted<double>(Ctx*, int64_t, const int*, const dbl4*, const dbl4*, dbl4*, dbl4*);
 
 }  // namespace lhv
+
+// ---------------------------------------------------------------------------
+// Cube, Morton keys and sort without allocation (lhv_morton_sort_noalloc)
+// ---------------------------------------------------------------------------
+// The same kernels as the first part of build_tree for one system, with every
+// temporary array in one fixed file-scope device array instead of context
+// buffers.  The caller's output arrays are one side of the sort's ping-pong.
+namespace lhv {
+namespace {
+
+constexpr int64_t NOALLOC_MAX_N = LHV_NOALLOC_MAX_N;
+constexpr int NOALLOC_NSORT = (int)((NOALLOC_MAX_N + SORT_TILE - 1) / SORT_TILE);
+constexpr int NOALLOC_MAX_PARTS = 1024;
+
+constexpr int64_t align256(int64_t b) { return (b + 255) / 256 * 256; }
+// scratch regions (byte offsets)
+constexpr int64_t NA_KEYS = 0;                                                   // uint64[max n]
+constexpr int64_t NA_IDX = NA_KEYS + align256(NOALLOC_MAX_N * 8);                // int32[max n]
+constexpr int64_t NA_HIST = NA_IDX + align256(NOALLOC_MAX_N * 4);                // int32[256 * nsort]
+constexpr int64_t NA_SCAN = NA_HIST + align256((int64_t)NOALLOC_NSORT * 256 * 4);  // int32 block sums
+constexpr int64_t NA_SCAN_INTS = ((int64_t)NOALLOC_NSORT * 256 + SCAN_TILE - 1) / SCAN_TILE + 1 + 64;
+constexpr int64_t NA_PART = NA_SCAN + align256(NA_SCAN_INTS * 4);                // double[parts][6]
+constexpr int64_t NA_SYSOFF = NA_PART + align256((int64_t)NOALLOC_MAX_PARTS * 6 * 8);  // int64[2]
+constexpr int64_t NA_CUBE = NA_SYSOFF + 256;                                     // SysCube
+constexpr int64_t NA_PARAMS = NA_CUBE + align256(sizeof(SysCube));               // TreeParams
+constexpr int64_t NA_BYTES = NA_PARAMS + align256(sizeof(TreeParams));
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
+
+// Address of g_noalloc_scratch per device, looked up by the first call on that device.
+constexpr int NOALLOC_MAX_DEVICES = 64;
+unsigned char* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+// The only state that must start at zero: the non-finite flag (all of
+// TreeParams is cleared); also writes the system offsets {0, n}.
+__global__ void k_noalloc_init(int64_t n, int64_t* __restrict__ sysoff, TreeParams* __restrict__ tp) {
+    if (threadIdx.x == 0) {
+        sysoff[0] = 0;
+        sysoff[1] = n;
+        *tp = TreeParams{};
+    }
+}
+
+}  // namespace
+}  // namespace lhv
+
+extern "C" int lhv_morton_sort_noalloc(int64_t n, const float* x4, const float* w4, uint64_t* keys, int32_t* perm,
+                                       void* cuda_stream) {
+    using namespace lhv;
+    if (n < 0) return LHV_EINVAL;
+    if (n > NOALLOC_MAX_N) return LHV_ETOOBIG;
+    if (n == 0) return LHV_OK;
+    if (!x4 || !keys || !perm) return LHV_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(x4) | reinterpret_cast<uintptr_t>(w4)) % 16 != 0 ||
+        reinterpret_cast<uintptr_t>(keys) % 8 != 0 || reinterpret_cast<uintptr_t>(perm) % 4 != 0)
+        return LHV_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LHV_ECUDA;
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return LHV_EUNSUPPORTED;
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return LHV_ECUDA;
+        }
+        g_noalloc_ptr[dev] = static_cast<unsigned char*>(p);
+    }
+    unsigned char* base = g_noalloc_ptr[dev];
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    int64_t* sysoff = reinterpret_cast<int64_t*>(base + NA_SYSOFF);
+    SysCube* cube = reinterpret_cast<SysCube*>(base + NA_CUBE);
+    TreeParams* tp = reinterpret_cast<TreeParams*>(base + NA_PARAMS);
+    double* part = reinterpret_cast<double*>(base + NA_PART);
+    int* hist = reinterpret_cast<int*>(base + NA_HIST);
+    int* sums = reinterpret_cast<int*>(base + NA_SCAN);
+    const float4* x = reinterpret_cast<const float4*>(x4);
+    const float4* w = reinterpret_cast<const float4*>(w4);
+
+    const int bits = key_bits_for(1);
+    const int nsort = (int)((n + SORT_TILE - 1) / SORT_TILE);
+    const int parts = std::max(1, std::min(NOALLOC_MAX_PARTS, (int)((n + 4095) / 4096)));
+    k_noalloc_init<<<1, 32, 0, s>>>(n, sysoff, tp);
+    k_bbox_partial<float><<<parts, 256, 0, s>>>(parts, sysoff, x, w, part, &tp->nonfinite);
+    k_bbox_final<<<1, 256, 0, s>>>(parts, part, cube, tp);
+    k_morton<float><<<grid_for(n, 256), 256, 0, s>>>(n, 1, bits, sysoff, cube, x, keys, perm);
+
+    // 8 passes of 8 bits; the even count leaves the result in the caller's arrays
+    uint64_t* kin = keys;
+    uint64_t* kout = reinterpret_cast<uint64_t*>(base + NA_KEYS);
+    int* vin = perm;
+    int* vout = reinterpret_cast<int*>(base + NA_IDX);
+    const int64_t nh = (int64_t)nsort * 256;
+    const int nb = (int)((nh + SCAN_TILE - 1) / SCAN_TILE);
+    for (int pass = 0; pass < 8; ++pass) {
+        const int shift = pass * 8;
+        k_radix_hist<<<nsort, SORT_THREADS, 0, s>>>(n, kin, shift, nsort, hist);
+        k_scan_reduce<<<nb, SCAN_THREADS, 0, s>>>(nh, hist, sums);
+        k_scan_sums<<<1, 1024, 0, s>>>(nb, sums, nullptr);
+        k_scan_apply<<<nb, SCAN_THREADS, 0, s>>>(nh, hist, sums, hist);
+        k_radix_scatter<<<nsort, SORT_THREADS, 0, s>>>(n, kin, vin, kout, vout, shift, nsort, hist);
+        std::swap(kin, kout);
+        std::swap(vin, vout);
+    }
+    if (cudaGetLastError() != cudaSuccess) return LHV_ECUDA;
+    TreeParams hp{};
+    if (cudaMemcpyAsync(&hp, tp, sizeof(TreeParams), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return LHV_ECUDA;
+    }
+    return hp.nonfinite ? LHV_ENONFINITE : LHV_OK;
+}
