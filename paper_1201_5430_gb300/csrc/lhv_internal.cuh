@@ -133,6 +133,12 @@ struct OpTables {
 // Builds every table in FP64 on the GPU and stores it in T.
 template <typename T>
 void build_operators(Ctx* c, int p, OpTables& ops);
+// One operator family in FP64 -> T: M2L (316 x [2Pin][2Pout], pout == pin), M2M (8 x
+// [2Pin][2Pout], child pin -> parent pout), L2L (8 x [2Pin][2Pout], parent pin ->
+// child pout), L2P ([2P][12P]), P2M ([3P][2P]); P = p*p.
+enum OpKind : int { OP_M2L = 0, OP_M2M = 1, OP_L2L = 2, OP_L2P = 3, OP_P2M = 4 };
+template <typename T>
+void build_op(Ctx* c, int kind, int pout, int pin, Buf& dst);
 void free_operators(OpTables& ops);
 int m2l_slot_host(int dx, int dy, int dz);   // same mapping as slot_of, on the host
 

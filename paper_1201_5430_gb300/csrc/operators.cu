@@ -68,6 +68,8 @@ struct Spec {
     int row0;        // first row of this block in the destination matrix
     int64_t ld;      // rows of the destination matrix (k-major: element (col, row) at col * ld + row)
     double t[3];
+    int pout, pin;   // truncation numbers of the output and input expansions
+    int pad[2];
 };
 
 constexpr int MAXD = 48;             // highest degree of a solid harmonic needed (2p - 2 <= 46)
@@ -79,7 +81,7 @@ struct Ctx2 {
     const cplx* Q;       // Q_n^m, m >= 0
     double rho;
     const double* fact;  // k!
-    int p;
+    int pout, pin;       // output (n', m') < pout, input (n, m) < pin
     double t[3];
 };
 
@@ -108,7 +110,7 @@ __device__ inline bool valid_nm(int n, int m, int p) { return n >= 0 && n < p &&
 
 // Translation map entries, Eqs. mr2/mr3.  tk: 0 = (R|R), 1 = (S|R), 2 = (S|S).
 __device__ cplx T_entry(const Ctx2& g, int tk, int n2, int m2, int n, int m) {
-    if (!valid_nm(n2, m2, g.p) || !valid_nm(n, m, g.p)) return C(0);
+    if (!valid_nm(n2, m2, g.pout) || !valid_nm(n, m, g.pin)) return C(0);
     if (tk == 0) return R_at(g, n - n2, m - m2);
     if (tk == 1) return S_at(g, n + n2, m - m2);
     return R_at(g, n2 - n, m - m2);
@@ -230,14 +232,14 @@ __device__ cplx terms_T(const Ctx2& g, const Terms& tr, int tk, int n2, int m2, 
     cplx s = C(0);
     for (int i = 0; i < tr.k; ++i) {
         int a = n2 + tr.dn[i], b = m2 + tr.dm[i];
-        if (valid_nm(a, b, g.p)) s = s + tr.co[i] * T_entry(g, tk, a, b, n, m);
+        if (valid_nm(a, b, g.pout)) s = s + tr.co[i] * T_entry(g, tk, a, b, n, m);
     }
     return s;
 }
 
 // Complex entry of the unscaled map of one operator block.
 __device__ cplx op_entry(const Ctx2& g, const Spec& sp, int pot_out, int pot_in, int n2, int m2, int n, int m) {
-    const int p = g.p;
+    const int p = g.pin;  // the sparse maps (L2P, P2M) are square: pin == pout
     switch (sp.kind) {
         case K_M2L: {
             if (pot_out == 0 && pot_in == 0) return T_entry(g, 1, n2, m2, n, m);
@@ -321,16 +323,16 @@ __device__ void dims(int kind, int P, int& pots_out, int& pots_in) {
     }
 }
 
-__global__ void k_build_ops(int p, const Spec* __restrict__ specs, double* __restrict__ out,
+__global__ void k_build_ops(const Spec* __restrict__ specs, double* __restrict__ out,
                             const int64_t* __restrict__ out_off) {
     __shared__ cplx Q[MAXTRI];
     __shared__ double fact[2 * MAXD + 2];
     const Spec sp = specs[blockIdx.x];
-    const int P = p * p;
+    const int Pout = sp.pout * sp.pout, Pin = sp.pin * sp.pin;
     int D;
     switch (sp.kind) {
-        case K_M2L: D = 2 * p - 2; break;
-        case K_M2M: case K_L2L: D = p - 1; break;
+        case K_M2L: D = sp.pout + sp.pin - 2; break;
+        case K_M2M: case K_L2L: D = max(sp.pout, sp.pin) - 1; break;
         default: D = 0; break;
     }
     for (int k = threadIdx.x; k < 2 * MAXD + 2; k += blockDim.x) {
@@ -358,17 +360,17 @@ __global__ void k_build_ops(int p, const Spec* __restrict__ specs, double* __res
         }
     }
     __syncthreads();
-    Ctx2 g{Q, sqrt(r2), fact, p, {x, y, z}};
+    Ctx2 g{Q, sqrt(r2), fact, sp.pout, sp.pin, {x, y, z}};
     int po, pi;
-    dims(sp.kind, P, po, pi);
-    const int rows = po * P, cols = pi * P;
+    dims(sp.kind, 0, po, pi);
+    const int rows = po * Pout, cols = pi * Pin;
     double* dst = out + out_off[blockIdx.x] + sp.row0;
     for (int64_t e = threadIdx.x; e < (int64_t)rows * cols; e += blockDim.x) {
         int row = (int)(e % rows), col = (int)(e / rows);  // k-major: element (col, row) at col*rows + row
-        int pot_out = row / P, pot_in = col / P;
+        int pot_out = row / Pout, pot_in = col / Pin;
         int n2, m2, pt2, n, m, q;
-        decode(row % P, n2, m2, pt2);
-        decode(col % P, n, m, q);
+        decode(row % Pout, n2, m2, pt2);
+        decode(col % Pin, n, m, q);
         // realify: the input unit vector sets c_n^m = 1 or i, and c_n^{-m} by symmetry
         cplx cin = q ? C(0, 1) : C(1, 0);
         cplx yv = op_entry(g, sp, pot_out, pot_in, n2, m2, n, m) * cin;
@@ -411,33 +413,9 @@ void free_operators(OpTables& ops) {
     ops.p = 0;
 }
 
-template <typename T>
-void build_operators(Ctx* c, int p, OpTables& ops) {
-    cudaStream_t s = stream_of(c);
-    const int P = p * p;
-    ops.p = p;
-    ops.P = P;
-    std::vector<Spec> specs;
-    std::vector<int64_t> off;
-    int64_t total = 0;
-    // size: entries of the block; ld / row0: placement inside a wider destination (0 = own block)
-    auto push = [&](int kind, int aux, int aux2, double tx, double ty, double tz, int64_t rows, int64_t size,
-                    int64_t ld = 0, int row0 = 0, int64_t at = -1) {
-        Spec sp{};
-        sp.kind = kind;
-        sp.aux = aux;
-        sp.aux2 = aux2;
-        sp.row0 = row0;
-        sp.ld = ld ? ld : rows;
-        sp.t[0] = tx;
-        sp.t[1] = ty;
-        sp.t[2] = tz;
-        specs.push_back(sp);
-        off.push_back(at >= 0 ? at : total);
-        if (at < 0) total += size;
-    };
-    // M2L: offset d = source - target (box units), t = target - source = -d
-    std::vector<int> offs, slot_of(343, -1);
+void m2l_offsets(std::vector<int>& offs, std::vector<int>& slot_of) {
+    offs.clear();
+    slot_of.assign(343, -1);
     int slot = 0;
     for (int a = -3; a <= 3; ++a)
         for (int b = -3; b <= 3; ++b)
@@ -447,72 +425,109 @@ void build_operators(Ctx* c, int p, OpTables& ops) {
                 offs.push_back(b);
                 offs.push_back(cc);
                 slot_of[(a + 3) * 49 + (b + 3) * 7 + (cc + 3)] = slot++;
-                push(K_M2L, 0, 0, -a, -b, -cc, 2 * P, 4ll * P * P);
             }
-    const int64_t m2l_end = total;
-    // child octant o = (ox, oy, oz): child = 2 parent + o; in child units t(M2M) = 0.5 - o, t(L2L) = o - 0.5
-    for (int o = 0; o < 8; ++o) {
-        int ox = o & 1, oy = (o >> 1) & 1, oz = (o >> 2) & 1;
-        push(K_M2M, 0, 0, 0.5 - ox, 0.5 - oy, 0.5 - oz, 2 * P, 4ll * P * P);
-    }
-    const int64_t m2m_end = total;
-    for (int o = 0; o < 8; ++o) {
-        int ox = o & 1, oy = (o >> 1) & 1, oz = (o >> 2) & 1;
-        push(K_L2L, 0, 0, ox - 0.5, oy - 0.5, oz - 0.5, 2 * P, 4ll * P * P);
-    }
-    const int64_t l2l_end = total;
-    // L2P: one [2P][12P] matrix; block j (v_x, v_y, v_z, u_xx, u_xy, ..., u_zz) at rows j*P
-    const int64_t l2p_beg = total;
-    total += 24ll * P * P;
-    for (int k = 0; k < 3; ++k) push(K_L2P_V, k, 0, 0, 0, 0, P, 0, 12ll * P, k * P, l2p_beg);
-    for (int l = 0; l < 3; ++l)
-        for (int k = 0; k < 3; ++k) push(K_L2P_U, l, k, 0, 0, 0, P, 0, 12ll * P, (3 + 3 * l + k) * P, l2p_beg);
-    const int64_t l2p_end = total;
-    // P2M: [3P][2P], the three strength components stacked along the input
-    for (int k = 0; k < 3; ++k) push(K_P2M, k, 0, 0, 0, 0, 2 * P, 2ll * P * P);
-    const int64_t p2m_end = total;
+}
 
+template <typename T>
+void build_op(Ctx* c, int kind, int pout, int pin, Buf& dst) {
+    cudaStream_t s = stream_of(c);
+    const int64_t Pout = (int64_t)pout * pout, Pin = (int64_t)pin * pin;
+    std::vector<Spec> specs;
+    std::vector<int64_t> off;
+    int64_t total = 0;
+    auto push = [&](int k, int aux, int aux2, double tx, double ty, double tz, int64_t rows, int64_t size,
+                    int64_t ld = 0, int row0 = 0, int64_t at = -1) {
+        Spec sp{};
+        sp.kind = k;
+        sp.aux = aux;
+        sp.aux2 = aux2;
+        sp.row0 = row0;
+        sp.ld = ld ? ld : rows;
+        sp.t[0] = tx;
+        sp.t[1] = ty;
+        sp.t[2] = tz;
+        sp.pout = pout;
+        sp.pin = pin;
+        specs.push_back(sp);
+        off.push_back(at >= 0 ? at : total);
+        if (at < 0) total += size;
+    };
+    if (kind == OP_M2L) {
+        // offset d = source - target (box units), t = target - source = -d
+        std::vector<int> offs, slot_of;
+        m2l_offsets(offs, slot_of);
+        for (size_t i = 0; i < offs.size(); i += 3)
+            push(K_M2L, 0, 0, -offs[i], -offs[i + 1], -offs[i + 2], 2 * Pout, 4 * Pout * Pin);
+    } else if (kind == OP_M2M || kind == OP_L2L) {
+        // child octant o: child = 2 parent + o; in child units t(M2M) = 0.5 - o, t(L2L) = o - 0.5
+        for (int o = 0; o < 8; ++o) {
+            const int ox = o & 1, oy = (o >> 1) & 1, oz = (o >> 2) & 1;
+            if (kind == OP_M2M) push(K_M2M, 0, 0, 0.5 - ox, 0.5 - oy, 0.5 - oz, 2 * Pout, 4 * Pout * Pin);
+            else push(K_L2L, 0, 0, ox - 0.5, oy - 0.5, oz - 0.5, 2 * Pout, 4 * Pout * Pin);
+        }
+    } else if (kind == OP_L2P) {
+        // one [2P][12P] matrix; block j (v_x, v_y, v_z, u_xx, u_xy, ..., u_zz) at rows j*P
+        total = 24 * Pout * Pin;
+        for (int k = 0; k < 3; ++k) push(K_L2P_V, k, 0, 0, 0, 0, Pout, 0, 12 * Pout, k * (int)Pout, 0);
+        for (int l = 0; l < 3; ++l)
+            for (int k = 0; k < 3; ++k)
+                push(K_L2P_U, l, k, 0, 0, 0, Pout, 0, 12 * Pout, (3 + 3 * l + k) * (int)Pout, 0);
+    } else {
+        // P2M: [3P][2P], the three strength components stacked along the input
+        for (int k = 0; k < 3; ++k) push(K_P2M, k, 0, 0, 0, 0, 2 * Pout, 2 * Pout * Pin);
+    }
     const int nspec = (int)specs.size();
     Buf dspec, doff, dout;
-    ensure(c, dspec, nspec * sizeof(Spec));
-    ensure(c, doff, nspec * sizeof(int64_t));
-    ensure(c, dout, total * sizeof(double));
-    try {
-        cuda_check(cudaMemcpyAsync(dspec.ptr, specs.data(), nspec * sizeof(Spec), cudaMemcpyHostToDevice, s), "specs");
-        cuda_check(cudaMemcpyAsync(doff.ptr, off.data(), nspec * sizeof(int64_t), cudaMemcpyHostToDevice, s), "offs");
-        k_build_ops<<<nspec, 256, 0, s>>>(p, dspec.as<Spec>(), dout.as<double>(), doff.as<int64_t>());
-        count_launch(c);
-        check_launch("build operators");
-        auto cast = [&](Buf& dst, int64_t beg, int64_t end) {
-            ensure(c, dst, (end - beg) * sizeof(T));
-            k_cast<T><<<grid_for(end - beg, 256), 256, 0, s>>>(end - beg, dout.as<double>() + beg, dst.as<T>());
-            count_launch(c);
-        };
-        cast(ops.m2l, 0, m2l_end);
-        cast(ops.m2m, m2l_end, m2m_end);
-        cast(ops.l2l, m2m_end, l2l_end);
-        cast(ops.l2p, l2l_end, l2p_end);
-        cast(ops.p2m, l2p_end, p2m_end);
-        check_launch("cast operators");
-        ensure(c, ops.offsets, offs.size() * sizeof(int));
-        ensure(c, ops.slot_of, slot_of.size() * sizeof(int));
-        cuda_check(cudaMemcpyAsync(ops.offsets.ptr, offs.data(), offs.size() * sizeof(int), cudaMemcpyHostToDevice, s),
-                   "offsets");
-        cuda_check(cudaMemcpyAsync(ops.slot_of.ptr, slot_of.data(), slot_of.size() * sizeof(int),
-                                   cudaMemcpyHostToDevice, s),
-                   "slots");
-        cuda_check(cudaStreamSynchronize(s), "operators");
-    } catch (...) {
+    auto cleanup = [&] {
         cudaFree(dspec.ptr);
         cudaFree(doff.ptr);
         cudaFree(dout.ptr);
+    };
+    try {
+        ensure(c, dspec, nspec * sizeof(Spec));
+        ensure(c, doff, nspec * sizeof(int64_t));
+        ensure(c, dout, total * sizeof(double));
+        cuda_check(cudaMemsetAsync(dout.ptr, 0, total * sizeof(double), s), "zero ops");
+        cuda_check(cudaMemcpyAsync(dspec.ptr, specs.data(), nspec * sizeof(Spec), cudaMemcpyHostToDevice, s), "specs");
+        cuda_check(cudaMemcpyAsync(doff.ptr, off.data(), nspec * sizeof(int64_t), cudaMemcpyHostToDevice, s), "offs");
+        k_build_ops<<<nspec, 256, 0, s>>>(dspec.as<Spec>(), dout.as<double>(), doff.as<int64_t>());
+        count_launch(c);
+        check_launch("build operators");
+        ensure(c, dst, total * sizeof(T));
+        k_cast<T><<<grid_for(total, 256), 256, 0, s>>>(total, dout.as<double>(), dst.as<T>());
+        count_launch(c);
+        check_launch("cast operators");
+        cuda_check(cudaStreamSynchronize(s), "operators");
+    } catch (...) {
+        cleanup();
         throw;
     }
-    cudaFree(dspec.ptr);
-    cudaFree(doff.ptr);
-    cudaFree(dout.ptr);
+    cleanup();
 }
 
+template <typename T>
+void build_operators(Ctx* c, int p, OpTables& ops) {
+    cudaStream_t s = stream_of(c);
+    ops.p = p;
+    ops.P = p * p;
+    build_op<T>(c, OP_M2L, p, p, ops.m2l);
+    build_op<T>(c, OP_M2M, p, p, ops.m2m);
+    build_op<T>(c, OP_L2L, p, p, ops.l2l);
+    build_op<T>(c, OP_L2P, p, p, ops.l2p);
+    build_op<T>(c, OP_P2M, p, p, ops.p2m);
+    std::vector<int> offs, slot_of;
+    m2l_offsets(offs, slot_of);
+    ensure(c, ops.offsets, offs.size() * sizeof(int));
+    ensure(c, ops.slot_of, slot_of.size() * sizeof(int));
+    cuda_check(cudaMemcpyAsync(ops.offsets.ptr, offs.data(), offs.size() * sizeof(int), cudaMemcpyHostToDevice, s),
+               "offsets");
+    cuda_check(cudaMemcpyAsync(ops.slot_of.ptr, slot_of.data(), slot_of.size() * sizeof(int), cudaMemcpyHostToDevice, s),
+               "slots");
+    cuda_check(cudaStreamSynchronize(s), "operators");
+}
+
+template void build_op<float>(Ctx*, int, int, int, Buf&);
+template void build_op<double>(Ctx*, int, int, int, Buf&);
 template void build_operators<float>(Ctx*, int, OpTables&);
 template void build_operators<double>(Ctx*, int, OpTables&);
 
