@@ -52,9 +52,10 @@ extern "C" {
 /* ---- arithmetic of the evaluation (lhv_config.precision) --------------- */
 #define LHV_FP32 0  /* all kernels in FP32 (CUDA cores); operator tables built in FP64, stored FP32 */
 #define LHV_FP64 1  /* all kernels in FP64 (use the _f64 entry points) */
-#define LHV_TF32X3 2 /* mixed precision: as LHV_FP32, but every translation and coefficient map
-                        (P2M, M2M, M2L, L2L, L2P) runs on the tensor cores in TF32 with split
-                        operands (hi.hi + hi.lo + lo.hi, FP32 accumulation); needs p even */
+#define LHV_TF32X3 2 /* mixed precision: as LHV_FP32, but the M2L products (the dominant dense
+                        map) run on the tensor cores in TF32 with split operands (hi.hi + hi.lo +
+                        lo.hi, FP32 accumulation) where p is a multiple of 4; other p, and the
+                        other maps, run as in LHV_FP32 */
 
 /* ---- which parts of Eq. fmm1 to evaluate (lhv_config.terms) ------------ */
 #define LHV_TERMS_NEAR 1  /* sparse part only: direct sum over colleague leaves */
@@ -102,6 +103,8 @@ typedef struct {
                                                 reset (only while timing is enabled) */
     int64_t stage_launches[LHV_NUM_STAGES];  /* timed stage executions since the last reset */
     int64_t kernel_launches;                 /* kernels launched since the last reset */
+    int     level_p[LHV_MAX_LEVELS];         /* truncation number of each level's expansions in
+                                                the last evaluation with a far field (0: none) */
 } lhv_stats;
 
 /* Create a context for one configuration on one CUDA stream (a cudaStream_t,
@@ -155,6 +158,18 @@ int lhv_evaluate_velocity_stretching_f64(lhv_ctx* ctx, int64_t n, const double* 
                                          double* v4, double* s4);
 int lhv_step_f64(lhv_ctx* ctx, int64_t n, double* x4, double* w4, double dt);
 
+/* Truncation number per octree level (variable truncation, which the paper
+ * mentions but does not use, Sec. 5).  p[l] for the levels l < nlevels (host
+ * array; 1 <= p[l] <= 24, or 0 for lhv_config.p); levels >= nlevels, and every
+ * level after nlevels = 0, use lhv_config.p.  The expansions of level l (S at the
+ * leaves and above, R from level 2 down) then have p[l] terms: P2M and L2P use
+ * p[L], M2L at level l maps p[l] -> p[l], M2M level l+1 -> l maps p[l+1] ->
+ * p[l] and L2L level l -> l+1 maps p[l] -> p[l+1] (each result truncated to
+ * its level's p before the conversion of Eqs. drt10/drt11).  Tables of other
+ * (p_out, p_in) pairs are built in FP64 on first use and kept by the context.
+ * Takes effect at the next evaluation.  LHV_EINVAL for values out of range. */
+int lhv_set_level_p(lhv_ctx* ctx, const int* p, int nlevels);
+
 /* Statistics of the last tree/evaluation and the accumulated stage timings. */
 int lhv_get_stats(lhv_ctx* ctx, lhv_stats* out);
 
@@ -175,7 +190,8 @@ int lhv_reset_stats(lhv_ctx* ctx);
 #define LHV_EXPORT_BOX_RANGE   4  /* int32[nbox(level)][2] sorted element range [begin, end) */
 #define LHV_EXPORT_COLLEAGUES  5  /* int32[nbox(level)][27] colleague box index or -1,
                                      offset (dx,dy,dz) at ((dx+1)*3+(dy+1))*3+(dz+1) */
-#define LHV_EXPORT_MULTIPOLE   6  /* real[nbox(level)][2][p*p] scaled S coefficients (phi, chi) */
+#define LHV_EXPORT_MULTIPOLE   6  /* real[nbox(level)][2][p*p] scaled S coefficients (phi, chi),
+                                     p = the level's truncation number (lhv_stats.level_p) */
 #define LHV_EXPORT_LOCAL       7  /* real[nbox(level)][2][p*p] scaled R coefficients (phi, chi) */
 #define LHV_EXPORT_CUBE        8  /* double[4]: x0, y0, z0 of the (first system's) cube and its side */
 /* Scaled real coefficient layout (both potentials, box side h at that level):

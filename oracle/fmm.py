@@ -21,7 +21,7 @@ import numpy as np
 
 from .direct import pair_terms
 from .expansions import l2p, p2m_method2
-from .operators import convert_R, convert_S, empty, flatten, translation_matrix, unflatten
+from .operators import convert_R, convert_S, empty, flatten, resize, translation_matrix, unflatten
 from .tree import build_tree
 
 __all__ = ["fmm", "FMMResult"]
@@ -32,24 +32,30 @@ class FMMResult:
 
 
 class _Ops:
-    """Memoised dense translation matrices, keyed by (kind, level, integer offset)."""
+    """Memoised dense translation matrices, keyed by (kind, level, integer offset, size)."""
 
-    def __init__(self, p):
-        self.p = p
+    def __init__(self):
         self.cache = {}
 
-    def apply(self, kind, key, t, c):
-        T = self.cache.get((kind,) + key)
+    def apply(self, kind, key, t, c, p_out):
+        """Translate c (c.shape[0] terms) and keep p_out terms.  The square map at
+        max(p_in, p_out) restricted to n' < p_out, n < p_in is the rectangular map."""
+        pm = max(c.shape[0], p_out)
+        T = self.cache.get((kind, pm) + key)
         if T is None:
-            T = translation_matrix(kind, t, self.p)
-            self.cache[(kind,) + key] = T
-        return unflatten(T @ flatten(c), self.p)
+            T = translation_matrix(kind, t, pm)
+            self.cache[(kind, pm) + key] = T
+        return resize(unflatten(T @ flatten(resize(c, pm)), pm), p_out)
 
 
-def fmm(x, w, p, leaf_max=64, a=0.0, eps=1e-6, tree=None, far=True, near=True):
+def fmm(x, w, p, leaf_max=64, a=0.0, eps=1e-6, tree=None, far=True, near=True, level_p=None):
     """v, grad v ([i, l, k] = d_l v_k) and s at every element, in input order.
 
-    x, w: (N, 3) FP32 (or any float) arrays; they are widened to FP64."""
+    x, w: (N, 3) FP32 (or any float) arrays; they are widened to FP64.
+    level_p: optional truncation number per level (entry l for level l; 0 or a
+    missing entry means p).  The expansions of level l then carry level_p[l]
+    terms; every translation result is truncated to its level's p before its
+    conversion, as in the uniform case."""
     x32 = np.asarray(x, dtype=np.float32).reshape(-1, 3)
     x = x32.astype(np.float64)
     w = np.asarray(w, dtype=np.float32).reshape(-1, 3).astype(np.float64)
@@ -58,8 +64,11 @@ def fmm(x, w, p, leaf_max=64, a=0.0, eps=1e-6, tree=None, far=True, near=True):
     n = x.shape[0]
     xs, ws = x[tree.perm], w[tree.perm]
     L = tree.L
-    ops = _Ops(p)
+    ops = _Ops()
+    pl = [int(level_p[l]) if level_p is not None and l < len(level_p) and level_p[l] > 0 else int(p)
+          for l in range(L + 1)]
     res = FMMResult()
+    res.level_p = pl
     res.tree = tree
     res.multipole = [None] * (L + 1)
     res.local = [None] * (L + 1)
@@ -71,20 +80,20 @@ def fmm(x, w, p, leaf_max=64, a=0.0, eps=1e-6, tree=None, far=True, near=True):
         lv = tree.levels[L]
         nb = lv["keys"].shape[0]
         res.multipole[L] = [p2m_method2(xs[lv["begin"][b]:lv["end"][b]], ws[lv["begin"][b]:lv["end"][b]],
-                                        tree.centre(L, b), p) for b in range(nb)]
+                                        tree.centre(L, b), pl[L]) for b in range(nb)]
         # 2. upward pass: M2M + S conversion
         for lev in range(L - 1, 1, -1):
             d = tree.levels[lev]
             out = []
             for b in range(d["keys"].shape[0]):
-                phi, chi = empty(p), empty(p)
+                phi, chi = empty(pl[lev]), empty(pl[lev])
                 cb = tree.centre(lev, b)
                 for ch in d["children"][b]:
                     t = cb - tree.centre(lev + 1, ch)
                     key = (lev, tuple(2 * d["coords"][b] - tree.levels[lev + 1]["coords"][ch]))
                     mp, mc = res.multipole[lev + 1][ch]
-                    ph = ops.apply("SS", key, t, mp)
-                    cc = ops.apply("SS", key, t, mc)
+                    ph = ops.apply("SS", key, t, mp, pl[lev])
+                    cc = ops.apply("SS", key, t, mc, pl[lev])
                     ph, cc = convert_S(ph, cc, t)
                     phi += ph
                     chi += cc
@@ -95,15 +104,15 @@ def fmm(x, w, p, leaf_max=64, a=0.0, eps=1e-6, tree=None, far=True, near=True):
             d = tree.levels[lev]
             out = []
             for b in range(d["keys"].shape[0]):
-                phi, chi = empty(p), empty(p)
+                phi, chi = empty(pl[lev]), empty(pl[lev])
                 cb = tree.centre(lev, b)
                 if lev > 2:
                     par = d["parent"][b]
                     t = cb - tree.centre(lev - 1, par)
                     key = (lev, tuple(d["coords"][b] - 2 * tree.levels[lev - 1]["coords"][par]))
                     lp, lc = res.local[lev - 1][par]
-                    ph = ops.apply("RR", key, t, lp)
-                    cc = ops.apply("RR", key, t, lc)
+                    ph = ops.apply("RR", key, t, lp, pl[lev])
+                    cc = ops.apply("RR", key, t, lc, pl[lev])
                     ph, cc = convert_R(ph, cc, t)
                     phi += ph
                     chi += cc
@@ -111,8 +120,8 @@ def fmm(x, w, p, leaf_max=64, a=0.0, eps=1e-6, tree=None, far=True, near=True):
                     t = cb - tree.centre(lev, s)
                     key = (lev, tuple(d["coords"][b] - d["coords"][s]))
                     mp, mc = res.multipole[lev][s]
-                    ph = ops.apply("SR", key, t, mp)
-                    cc = ops.apply("SR", key, t, mc)
+                    ph = ops.apply("SR", key, t, mp, pl[lev])
+                    cc = ops.apply("SR", key, t, mc, pl[lev])
                     ph, cc = convert_R(ph, cc, t)
                     phi += ph
                     chi += cc

@@ -23,12 +23,21 @@ from .basis import R_table, S_table
 __all__ = [
     "get", "empty", "translation_matrix", "translate", "C",
     "apply_Dr", "apply_Dt", "apply_Drxt", "convert_R", "convert_S",
-    "flatten", "unflatten",
+    "flatten", "unflatten", "resize",
 ]
 
 
 def empty(p):
     return np.zeros((p, 2 * p - 1), dtype=np.complex128)
+
+
+def resize(c, p):
+    """The same expansion with p terms (n < p): truncated, or padded with zeros."""
+    q = c.shape[0]
+    out = empty(p)
+    k = min(p, q)
+    out[:k, p - 1 - (k - 1): p - 1 + k] = c[:k, q - 1 - (k - 1): q - 1 + k]
+    return out
 
 
 def get(c, n, m):

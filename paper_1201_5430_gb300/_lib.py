@@ -25,7 +25,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("leaf_level", ctypes.c_int), ("nbox", ctypes.c_int * LHV_MAX_LEVELS), ("n", ctypes.c_int64),
                 ("p2p_pairs", ctypes.c_int64), ("m2l_pairs", ctypes.c_int64),
                 ("stage_ms", ctypes.c_double * LHV_NUM_STAGES),
-                ("stage_launches", ctypes.c_int64 * LHV_NUM_STAGES), ("kernel_launches", ctypes.c_int64)]
+                ("stage_launches", ctypes.c_int64 * LHV_NUM_STAGES), ("kernel_launches", ctypes.c_int64),
+                ("level_p", ctypes.c_int * LHV_MAX_LEVELS)]
 
 
 # exported function -> (restype, argtypes); every name here is declared in include/lhv.h
@@ -42,6 +43,7 @@ SIGNATURES = {
     "lhv_evaluate_velocity_stretching_f64": (_int, [_vp, _i64, _vp, _vp, _vp, _vp]),
     "lhv_step_f64": (_int, [_vp, _i64, _vp, _vp, _dbl]),
     "lhv_get_stats": (_int, [_vp, ctypes.POINTER(Stats)]),
+    "lhv_set_level_p": (_int, [_vp, ctypes.POINTER(_int), _int]),
     "lhv_set_timing": (_int, [_vp, _int]),
     "lhv_reset_stats": (_int, [_vp]),
     "lhv_export": (_int, [_vp, _int, _int, _vp, _i64, ctypes.POINTER(_i64)]),

@@ -121,7 +121,14 @@ class LHV:
             "stage_ms": dict(zip(L.STAGES, list(s.stage_ms))),
             "stage_launches": dict(zip(L.STAGES, list(s.stage_launches))),
             "kernel_launches": s.kernel_launches,
+            "level_p": list(s.level_p)[: s.leaf_level + 1],
         }
+
+    def set_level_p(self, p_per_level=None):
+        """Truncation number per octree level (lhv_set_level_p); None restores config p."""
+        vals = [int(v) for v in (p_per_level or [])]
+        arr = (ctypes.c_int * max(len(vals), 1))(*vals)
+        self._check(self.lib.lhv_set_level_p(self.h, arr, len(vals)), "set_level_p")
 
     def export(self, what, level=0):
         """Copy an internal array (see lhv_export) into a new CUDA tensor."""

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -42,6 +43,11 @@ struct Ctx {
     Buf rk[6];         // kv, ks, ax, aw, sx, sw
     Buf hx, hw;        // device copies for lhv_step_host
     bool have_far = false;
+    int level_p[MAX_LEVELS + 1] = {};   // lhv_set_level_p (0: cfg.p)
+    std::map<int, Buf> opcache;         // tables of other (kind, p_out, p_in) than ops, type opcache_type
+    int opcache_type = 0;
+    int eval_p[MAX_LEVELS + 1] = {};    // truncation numbers of the last evaluation's expansions
+    int eval_ld = 0;                    // their stride (reals per box)
 };
 
 // ---- helpers used by every translation unit ------------------------------
@@ -141,6 +147,72 @@ static void ensure_ops(Ctx* c) {
     }
 }
 
+// Operator table (kind, p_out, p_in) in T from the cache, built on first use.
+// kind 5 is the tensor-core tile set of M2L(p, p).
+template <typename T>
+static const T* cached_op(Ctx* c, int kind, int pout, int pin) {
+    if (c->opcache_type != (int)sizeof(T)) {
+        for (auto& kv : c->opcache) release(kv.second);
+        c->opcache.clear();
+        c->opcache_type = (int)sizeof(T);
+    }
+    const int key = kind | (pout << 8) | (pin << 16);
+    auto it = c->opcache.find(key);
+    if (it != c->opcache.end()) return it->second.as<T>();
+    Buf& b = c->opcache[key];
+    StageScope sc(c, LHV_STAGE_OPS);
+    if (kind == 5) {
+        if constexpr (sizeof(T) == 4) {
+            const int P = pout * pout;
+            const float* m2l = cached_op<float>(c, OP_M2L, pout, pout);
+            tc_tiles_build(c, m2l, NUM_OFFSETS, 2 * P, 2 * P, P, c->opcache[key]);
+            cuda_check(cudaStreamSynchronize(c->stream), "tc tiles");
+        }
+    } else {
+        build_op<T>(c, kind, pout, pin, b);
+    }
+    return c->opcache[key].as<T>();
+}
+
+// Truncation numbers and tables of an evaluation over levels 0..L.
+template <typename T>
+static Plan<T> make_plan(Ctx* c, int L) {
+    Plan<T> pl;
+    pl.L = L;
+    for (int l = 0; l <= L; ++l) pl.p[l] = c->level_p[l] > 0 ? c->level_p[l] : c->cfg.p;
+    int pmax = 1;
+    pl.uniform = true;
+    for (int l = 2; l <= L; ++l) {
+        pmax = std::max(pmax, pl.p[l]);
+        if (pl.p[l] != pl.p[2]) pl.uniform = false;
+    }
+    if (L < 2) pmax = pl.p[L];
+    pl.ld = (2 * pmax * pmax + 7) / 8 * 8;  // 32-byte rows for the vector loads of the tensor-core path
+    const bool base = pl.uniform && pl.p[L] == c->cfg.p;
+    const bool tc = sizeof(T) == 4 && ctx_use_tc(c);
+    if (base) {
+        pl.p2m = c->ops.p2m.as<T>();
+        pl.l2p = c->ops.l2p.as<T>();
+        for (int l = 0; l <= L; ++l) {
+            pl.m2m[l] = c->ops.m2m.as<T>();
+            pl.l2l[l] = c->ops.l2l.as<T>();
+            pl.m2l[l] = c->ops.m2l.as<T>();
+            pl.m2l_tiles[l] = c->ops.m2l_tiles.ptr ? c->ops.m2l_tiles.as<float>() : nullptr;
+        }
+        return pl;
+    }
+    pl.p2m = cached_op<T>(c, OP_P2M, pl.p[L], pl.p[L]);
+    pl.l2p = cached_op<T>(c, OP_L2P, pl.p[L], pl.p[L]);
+    for (int l = 2; l <= L; ++l) {
+        const int P = pl.p[l] * pl.p[l];
+        pl.m2l[l] = cached_op<T>(c, OP_M2L, pl.p[l], pl.p[l]);
+        if (tc && tc_supported(2 * P, 2 * P, P)) pl.m2l_tiles[l] = cached_op<float>(c, 5, pl.p[l], pl.p[l]);
+        if (l < L) pl.m2m[l] = cached_op<T>(c, OP_M2M, pl.p[l], pl.p[l + 1]);
+        if (l > 2) pl.l2l[l] = cached_op<T>(c, OP_L2L, pl.p[l], pl.p[l - 1]);
+    }
+    return pl;
+}
+
 template <typename T>
 static int tree_stage(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const vec4_t<T>* x4, const vec4_t<T>* w4,
                       Error& err) {
@@ -169,7 +241,7 @@ static int evaluate(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const ve
     int st = tree_stage<T>(c, n, nsys, sysoff, x4, w4, err);
     if (st != LHV_OK) throw err;
     const Levels& lv = c->lv;
-    const int L = lv.L, P = c->ops.P;
+    const int L = lv.L;
     const int terms = c->cfg.terms ? c->cfg.terms : LHV_TERMS_ALL;
     const bool far = (terms & LHV_TERMS_FAR) && L >= 2;
     const bool near = (terms & LHV_TERMS_NEAR) != 0;
@@ -179,43 +251,50 @@ static int evaluate(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const ve
     vec4_t<T>* sfar = nullptr;
     c->have_far = far;
     if (far) {
+        const Plan<T> pl = make_plan<T>(c, L);
+        for (int l = 0; l <= MAX_LEVELS; ++l) c->eval_p[l] = l <= L ? pl.p[l] : 0;
+        c->eval_ld = pl.ld;
+        const int PL = pl.p[L] * pl.p[L];
         const int64_t nbt = lv.off[L + 1];
         const int64_t nleaf = lv.nbox[L];
-        ensure(c, c->mult, nbt * 2 * P * (int64_t)sizeof(T));
-        ensure(c, c->loc, nbt * 2 * P * (int64_t)sizeof(T));
+        ensure(c, c->mult, nbt * pl.ld * (int64_t)sizeof(T));
+        ensure(c, c->loc, nbt * pl.ld * (int64_t)sizeof(T));
         ensure(c, c->table, (nbt - lv.off[2]) * (int64_t)NUM_OFFSETS * 4);
-        ensure(c, c->W, nleaf * 3 * P * (int64_t)sizeof(T));
-        ensure(c, c->cf, nleaf * 12 * P * (int64_t)sizeof(T));
+        ensure(c, c->W, nleaf * 3 * PL * (int64_t)sizeof(T));
+        ensure(c, c->cf, nleaf * 12 * PL * (int64_t)sizeof(T));
         ensure(c, c->vfar, n * (int64_t)sizeof(vec4_t<T>));
         ensure(c, c->sfar, n * (int64_t)sizeof(vec4_t<T>));
         T* mult = c->mult.as<T>();
         T* loc = c->loc.as<T>();
         {
             StageScope sc(c, LHV_STAGE_P2M);
-            run_p2m<T>(c, c->ops, c->tb, lv, c->hp, xs, ws, c->W.as<T>(), c->gp_leaf, mult);
+            run_p2m<T>(c, pl, c->tb, lv, xs, ws, c->W.as<T>(), c->gp_leaf, mult);
         }
         {
             StageScope sc(c, LHV_STAGE_M2M);
-            run_m2m<T>(c, c->ops, c->tb, lv, c->gp_m2m, mult);
+            run_m2m<T>(c, pl, c->tb, lv, c->gp_m2m, mult);
         }
         {
             StageScope sc(c, LHV_STAGE_M2L);
-            cuda_check(cudaMemsetAsync(loc + (int64_t)lv.off[2] * 2 * P, 0,
-                                       sizeof(T) * (size_t)(nbt - lv.off[2]) * 2 * P, c->stream),
+            cuda_check(cudaMemsetAsync(loc + (int64_t)lv.off[2] * pl.ld, 0,
+                                       sizeof(T) * (size_t)(nbt - lv.off[2]) * pl.ld, c->stream),
                        "zero locals");
-            m2l_prepare(c, c->ops, c->tb, lv, c->table.as<int>(), c->gp_m2l, gemm_nc<T>(2 * P), cnt + 1);
+            int pmax = 1;
+            for (int l = 2; l <= L; ++l) pmax = std::max(pmax, pl.p[l]);
+            m2l_prepare(c, c->ops, c->tb, lv, c->table.as<int>(), c->gp_m2l, gemm_nc<T>(2 * pmax * pmax), pl.uniform,
+                        cnt + 1);
             StageScope sg(c, LHV_STAGE_M2L_PRODUCTS);
-            m2l_apply<T>(c, c->ops, c->gp_m2l, mult, loc);
+            m2l_apply<T>(c, pl, lv, c->gp_m2l, mult, loc);
         }
         {
             StageScope sc(c, LHV_STAGE_L2L);
-            run_l2l<T>(c, c->ops, c->tb, lv, c->gp_l2l, loc);
+            run_l2l<T>(c, pl, c->tb, lv, c->gp_l2l, loc);
         }
         vfar = c->vfar.as<vec4_t<T>>();
         sfar = c->sfar.as<vec4_t<T>>();
         {
             StageScope sc(c, LHV_STAGE_L2P);
-            run_l2p<T>(c, c->ops, c->tb, lv, c->hp, xs, ws, loc, c->cf.as<T>(), c->gp_leaf, vfar, sfar);
+            run_l2p<T>(c, pl, c->tb, lv, xs, ws, loc, c->cf.as<T>(), c->gp_leaf, vfar, sfar);
         }
     }
     {
@@ -363,6 +442,8 @@ void lhv_destroy(lhv_ctx* ctx) {
     }
     for (auto e : c.pool) cudaEventDestroy(e);
     lhv::free_operators(c.ops);
+    for (auto& kv : c.opcache) lhv::release(kv.second);
+    c.opcache.clear();
     lhv::TreeBufs& t = c.tb;
     lhv::Buf* tree[] = {&t.keys_a, &t.keys_b, &t.idx_a, &t.idx_b, &t.hist, &t.boxof_a, &t.boxof_b, &t.flags,
                         &t.scan_tmp, &t.perm, &t.params, &t.counts, &t.bkey, &t.bbeg, &t.bend, &t.bparent,
@@ -529,6 +610,7 @@ int lhv_get_stats(lhv_ctx* ctx, lhv_stats* out) {
         std::memset(out, 0, sizeof(*out));
         out->leaf_level = c.lv.L;
         for (int l = 0; l < LHV_MAX_LEVELS; ++l) out->nbox[l] = c.lv.nbox[l];
+        for (int l = 0; l < LHV_MAX_LEVELS; ++l) out->level_p[l] = c.eval_p[l];
         out->n = c.tree_n;
         if (c.counters.ptr) {
             unsigned long long h[3] = {0, 0, 0};
@@ -550,6 +632,15 @@ int lhv_get_stats(lhv_ctx* ctx, lhv_stats* out) {
     });
 }
 
+int lhv_set_level_p(lhv_ctx* ctx, const int* p, int nlevels) {
+    if (!ctx || nlevels < 0 || nlevels > LHV_MAX_LEVELS || (nlevels > 0 && !p)) return LHV_EINVAL;
+    for (int l = 0; l < nlevels; ++l)
+        if (p[l] < 0 || p[l] > 24) return LHV_EINVAL;
+    Ctx& c = ctx->c;
+    for (int l = 0; l <= lhv::MAX_LEVELS; ++l) c.level_p[l] = l < nlevels ? p[l] : 0;
+    return LHV_OK;
+}
+
 int lhv_export(lhv_ctx* ctx, int what, int level, void* dst, int64_t capacity_bytes, int64_t* bytes_out) {
     return guarded(ctx, [&]() -> int {
         Ctx& c = ctx->c;
@@ -560,7 +651,6 @@ int lhv_export(lhv_ctx* ctx, int what, int level, void* dst, int64_t capacity_by
         const bool lvl_ok = level >= 0 && level <= lv.L;
         const int nb = lvl_ok ? lv.nbox[level] : 0;
         const int off = lvl_ok ? lv.off[level] : 0;
-        const int64_t coef = (int64_t)2 * c.ops.P * c.ops_type;
         std::vector<double> cube;
         switch (what) {
             case LHV_EXPORT_KEYS: src = c.tb.keys_a.ptr; bytes = n * 8; break;
@@ -588,11 +678,21 @@ int lhv_export(lhv_ctx* ctx, int what, int level, void* dst, int64_t capacity_by
                 bytes = (int64_t)nb * 27 * 4;
                 break;
             case LHV_EXPORT_MULTIPOLE:
-            case LHV_EXPORT_LOCAL:
+            case LHV_EXPORT_LOCAL: {
                 if (!lvl_ok || !c.have_far || level < 2) return LHV_EINVAL;
-                src = static_cast<const char*>(what == LHV_EXPORT_MULTIPOLE ? c.mult.ptr : c.loc.ptr) + off * coef;
-                bytes = nb * coef;
-                break;
+                const int64_t row = (int64_t)2 * c.eval_p[level] * c.eval_p[level] * c.ops_type;
+                const int64_t pitch = (int64_t)c.eval_ld * c.ops_type;
+                bytes = nb * row;
+                if (bytes_out) *bytes_out = bytes;
+                if (!dst) return LHV_OK;
+                if (capacity_bytes < bytes) return LHV_EINVAL;
+                const char* base = static_cast<const char*>(what == LHV_EXPORT_MULTIPOLE ? c.mult.ptr : c.loc.ptr);
+                if (nb > 0)
+                    lhv::cuda_check(cudaMemcpy2DAsync(dst, row, base + off * pitch, pitch, row, nb,
+                                                      cudaMemcpyDeviceToDevice, c.stream),
+                                    "export coefficients");
+                return LHV_OK;
+            }
             case LHV_EXPORT_CUBE: {
                 bytes = 32;
                 if (bytes_out) *bytes_out = bytes;

@@ -213,23 +213,23 @@ __global__ void __launch_bounds__(L2P_THREADS) k_l2p_eval(int nleaf, int level, 
 }  // namespace
 
 template <typename T>
-void run_p2m(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& lv, const TreeParams& hp,
-             const vec4_t<T>* xs, const vec4_t<T>* ws, T* W, Grouped& gp, T* mult) {
-    const int L = lv.L, nl = lv.nbox[L], o = lv.off[L], P = ops.P;
+void run_p2m(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs,
+             const vec4_t<T>* ws, T* W, Grouped& gp, T* mult) {
+    const int L = lv.L, nl = lv.nbox[L], o = lv.off[L], p = pl.p[L], P = p * p;
     int chunk = (int)std::min<size_t>(128, (160 * 1024) / (sizeof(T) * (P + 3)));
     chunk = std::max(32, chunk / 32 * 32);
     const size_t smem = sizeof(T) * (size_t)chunk * (P + 3);
     cuda_check(cudaFuncSetAttribute(k_p2m_w<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "p2m attr");
     k_p2m_w<T><<<grid_for(nl, 1, 152 * 16), P2M_THREADS, smem, stream_of(c)>>>(
         nl, L, tb.bkey.as<uint64_t>() + o, tb.bbeg.as<int>() + o, tb.bend.as<int>() + o, tb.cubes.as<SysCube>(), xs,
-        ws, W, ops.p, chunk);
+        ws, W, p, chunk);
     count_launch(c);
     check_launch("p2m w");
     build_grouped(c, gp, 1, nl, nl, gemm_nc<T>(3 * P), IdentItems{0, o});
     GemmArgs<T> a{};
     a.g0 = 0;
     a.g1 = 1;
-    a.ops = ops.p2m.as<T>();
+    a.ops = pl.p2m;
     a.ops_mod = 1;
     a.R = 2 * P;
     a.C = 3 * P;
@@ -237,7 +237,7 @@ void run_p2m(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& lv, 
     a.in = W;
     a.ldin = 3 * P;
     a.out = mult;
-    a.ldout = 2 * P;
+    a.ldout = pl.ld;
     a.mode = GEMM_STORE;
     a.scale = (T)1;  // the 1/h of each leaf is applied to W
     run_group_gemm<T>(c, gp, a);
@@ -255,29 +255,39 @@ static OctItems oct_items(const TreeBufs& tb, const Levels& lv, bool up) {
     return it;
 }
 
+// chunk width for the translations between levels: set by the widest input
 template <typename T>
-void run_m2m(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& lv, Grouped& gp, T* mult) {
-    const int L = lv.L, P = ops.P;
+static int oct_nc(const Plan<T>& pl) {
+    int pmax = 1;
+    for (int l = 2; l <= pl.L; ++l) pmax = std::max(pmax, pl.p[l]);
+    return gemm_nc<T>(2 * pmax * pmax);
+}
+
+template <typename T>
+void run_m2m(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, Grouped& gp, T* mult) {
+    const int L = lv.L;
     if (L < 3) return;
     // parents of the levels 2 .. L-1 accumulate atomically
-    cuda_check(cudaMemsetAsync(mult + (int64_t)lv.off[2] * 2 * P, 0,
-                               sizeof(T) * (size_t)(lv.off[L] - lv.off[2]) * 2 * P, stream_of(c)),
+    cuda_check(cudaMemsetAsync(mult + (int64_t)lv.off[2] * pl.ld, 0,
+                               sizeof(T) * (size_t)(lv.off[L] - lv.off[2]) * pl.ld, stream_of(c)),
                "m2m zero");
     const int nitems = lv.off[L + 1] - lv.off[3];
-    build_grouped(c, gp, (L - 2) * 8, nitems, nitems, gemm_nc<T>(2 * P), oct_items<T>(tb, lv, true));
+    build_grouped(c, gp, (L - 2) * 8, nitems, nitems, oct_nc(pl), oct_items<T>(tb, lv, true));
     for (int l = L - 1; l >= 2; --l) {
+        const int Pout = pl.p[l] * pl.p[l], Pin = pl.p[l + 1] * pl.p[l + 1];
         GemmArgs<T> a{};
         a.g0 = (l + 1 - 3) * 8;
         a.g1 = a.g0 + 8;
-        a.ops = ops.m2m.as<T>();
+        a.ops = pl.m2m[l];
         a.ops_mod = 8;
-        a.R = 2 * P;
-        a.C = 2 * P;
-        a.psplit = P;
+        a.R = 2 * Pout;
+        a.C = 2 * Pin;
+        a.psplit = Pout;
+        a.psplit_c = Pin;
         a.in = mult;
-        a.ldin = 2 * P;
+        a.ldin = pl.ld;
         a.out = mult;
-        a.ldout = 2 * P;
+        a.ldout = pl.ld;
         a.mode = GEMM_ATOMIC;
         a.scale = (T)1;
         run_group_gemm<T>(c, gp, a);
@@ -285,24 +295,26 @@ void run_m2m(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& lv, 
 }
 
 template <typename T>
-void run_l2l(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& lv, Grouped& gp, T* loc) {
-    const int L = lv.L, P = ops.P;
+void run_l2l(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, Grouped& gp, T* loc) {
+    const int L = lv.L;
     if (L < 3) return;
     const int nitems = lv.off[L + 1] - lv.off[3];
-    build_grouped(c, gp, (L - 2) * 8, nitems, nitems, gemm_nc<T>(2 * P), oct_items<T>(tb, lv, false));
+    build_grouped(c, gp, (L - 2) * 8, nitems, nitems, oct_nc(pl), oct_items<T>(tb, lv, false));
     for (int l = 2; l < L; ++l) {
+        const int Pout = pl.p[l + 1] * pl.p[l + 1], Pin = pl.p[l] * pl.p[l];
         GemmArgs<T> a{};
         a.g0 = (l + 1 - 3) * 8;
         a.g1 = a.g0 + 8;
-        a.ops = ops.l2l.as<T>();
+        a.ops = pl.l2l[l + 1];
         a.ops_mod = 8;
-        a.R = 2 * P;
-        a.C = 2 * P;
-        a.psplit = P;
+        a.R = 2 * Pout;
+        a.C = 2 * Pin;
+        a.psplit = Pout;
+        a.psplit_c = Pin;
         a.in = loc;
-        a.ldin = 2 * P;
+        a.ldin = pl.ld;
         a.out = loc;
-        a.ldout = 2 * P;
+        a.ldout = pl.ld;
         a.mode = GEMM_ADD;
         a.scale = (T)1;
         run_group_gemm<T>(c, gp, a);
@@ -310,21 +322,20 @@ void run_l2l(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& lv, 
 }
 
 template <typename T>
-void run_l2p(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& lv, const TreeParams& hp,
-             const vec4_t<T>* xs, const vec4_t<T>* ws, const T* loc, T* cf, Grouped& gp, vec4_t<T>* vfar,
-             vec4_t<T>* sfar) {
-    const int L = lv.L, nl = lv.nbox[L], o = lv.off[L], P = ops.P;
+void run_l2p(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs,
+             const vec4_t<T>* ws, const T* loc, T* cf, Grouped& gp, vec4_t<T>* vfar, vec4_t<T>* sfar) {
+    const int L = lv.L, nl = lv.nbox[L], o = lv.off[L], p = pl.p[L], P = p * p;
     build_grouped(c, gp, 1, nl, nl, gemm_nc<T>(2 * P), IdentItems{o, 0});
     GemmArgs<T> a{};
     a.g0 = 0;
     a.g1 = 1;
-    a.ops = ops.l2p.as<T>();
+    a.ops = pl.l2p;
     a.ops_mod = 1;
     a.R = 12 * P;
     a.C = 2 * P;
     a.psplit = 0;
     a.in = loc;
-    a.ldin = 2 * P;
+    a.ldin = pl.ld;
     a.out = cf;
     a.ldout = 12 * P;
     a.mode = GEMM_STORE;
@@ -334,18 +345,18 @@ void run_l2p(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& lv, 
     cuda_check(cudaFuncSetAttribute(k_l2p_eval<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "l2p attr");
     k_l2p_eval<T><<<grid_for(nl, 1, 152 * 16), L2P_THREADS, smem, stream_of(c)>>>(
         nl, L, tb.bkey.as<uint64_t>() + o, tb.bbeg.as<int>() + o, tb.bend.as<int>() + o, tb.cubes.as<SysCube>(), xs,
-        ws, cf, vfar, sfar, ops.p);
+        ws, cf, vfar, sfar, p);
     count_launch(c);
     check_launch("l2p");
 }
 
-#define LHV_INST(T)                                                                                             \
-    template void run_p2m<T>(Ctx*, const OpTables&, const TreeBufs&, const Levels&, const TreeParams&,         \
-                             const vec4_t<T>*, const vec4_t<T>*, T*, Grouped&, T*);                            \
-    template void run_m2m<T>(Ctx*, const OpTables&, const TreeBufs&, const Levels&, Grouped&, T*);            \
-    template void run_l2l<T>(Ctx*, const OpTables&, const TreeBufs&, const Levels&, Grouped&, T*);            \
-    template void run_l2p<T>(Ctx*, const OpTables&, const TreeBufs&, const Levels&, const TreeParams&,         \
-                             const vec4_t<T>*, const vec4_t<T>*, const T*, T*, Grouped&, vec4_t<T>*, vec4_t<T>*);
+#define LHV_INST(T)                                                                                              \
+    template void run_p2m<T>(Ctx*, const Plan<T>&, const TreeBufs&, const Levels&, const vec4_t<T>*,            \
+                             const vec4_t<T>*, T*, Grouped&, T*);                                               \
+    template void run_m2m<T>(Ctx*, const Plan<T>&, const TreeBufs&, const Levels&, Grouped&, T*);              \
+    template void run_l2l<T>(Ctx*, const Plan<T>&, const TreeBufs&, const Levels&, Grouped&, T*);              \
+    template void run_l2p<T>(Ctx*, const Plan<T>&, const TreeBufs&, const Levels&, const vec4_t<T>*,            \
+                             const vec4_t<T>*, const T*, T*, Grouped&, vec4_t<T>*, vec4_t<T>*);
 LHV_INST(float)
 LHV_INST(double)
 #undef LHV_INST

@@ -98,8 +98,9 @@ __global__ void __launch_bounds__(GG_THREADS) k_group_gemm(GemmArgs<T> a) {
         }
         // rows of this thread: r0 + rg*TM + j; skip the zero block (rows >= psplit read inputs >= psplit only)
         const int myrow0 = r0 + rg * TM;
-        const int kstart = (a.psplit > 0 && myrow0 >= a.psplit) ? a.psplit : 0;
-        const int tile_kstart = (a.psplit > 0 && r0 >= a.psplit) ? a.psplit : 0;
+        const int pcol = a.psplit_c > 0 ? a.psplit_c : a.psplit;
+        const int kstart = (a.psplit > 0 && myrow0 >= a.psplit) ? pcol : 0;
+        const int tile_kstart = (a.psplit > 0 && r0 >= a.psplit) ? pcol : 0;
         T acc[TM][TN];
 #pragma unroll
         for (int j = 0; j < TM; ++j)

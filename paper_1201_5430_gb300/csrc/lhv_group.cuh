@@ -28,7 +28,8 @@ struct GemmArgs {
     const T* ops;         // operator of group g at ops + (g % ops_mod) * C * R, k-major [C][R]
     int ops_mod;
     int R, C;
-    int psplit;           // > 0: rows >= psplit use inputs >= psplit only (zero lower-left block)
+    int psplit;           // > 0: rows >= psplit use inputs >= psplit_c only (zero lower-left block)
+    int psplit_c;         // column of that split (0: the same as psplit)
     const T* in;          // source vectors: in + src * ldin, C entries
     int64_t ldin;
     T* out;               // destination vectors: out + dst * ldout, R entries
@@ -130,15 +131,25 @@ struct OctItems {
 };
 
 // M2L: rows of the interaction table (global target box, 316 slots -> global source box or -1).
+// by_level = false: group = offset slot (pairs of all levels share the operator);
+// by_level = true : group = (level - 2) * 316 + slot (each level has its own p).
 struct M2LItems {
     const int* table;  // rows for the targets [t0, ...)
     int t0;
+    bool by_level;
+    int L;
+    int off[MAX_LEVELS + 2];  // global box offsets of the levels
     __device__ bool operator()(int64_t i, int& g, int& s, int& d) const {
         const int src = table[i];
         if (src < 0) return false;
         g = (int)(i % NUM_OFFSETS);
         s = src;
         d = t0 + (int)(i / NUM_OFFSETS);
+        if (by_level) {
+            int l = 2;
+            while (l < L && d >= off[l + 1]) ++l;
+            g += (l - 2) * NUM_OFFSETS;
+        }
         return true;
     }
 };

@@ -144,30 +144,48 @@ int m2l_slot_host(int dx, int dy, int dz);   // same mapping as slot_of, on the 
 
 struct Grouped;
 
+// ---- per-level plan of one evaluation (api.cu) ---------------------------------
+// Truncation number of every level and the operator tables that go with it.
+// With one p for all levels the tables are those of OpTables; otherwise
+// rectangular M2M / L2L tables connect levels of different p.
+template <typename T>
+struct Plan {
+    int L = 0;
+    int p[MAX_LEVELS + 1] = {};            // truncation number of the expansions of level l
+    int ld = 0;                            // reals per box in mult / loc: 2 max_l p[l]^2 (l = 2..L)
+    const T* p2m = nullptr;                // P2M(p[L])          [3P][2P]
+    const T* l2p = nullptr;                // L2P(p[L])          [2P][12P]
+    const T* m2m[MAX_LEVELS + 1] = {};     // [l]: level l+1 -> l, 8 x [2P(l+1)][2P(l)]
+    const T* l2l[MAX_LEVELS + 1] = {};     // [l]: level l-1 -> l, 8 x [2P(l-1)][2P(l)]
+    const T* m2l[MAX_LEVELS + 1] = {};     // [l]: 316 x [2P(l)][2P(l)]
+    const float* m2l_tiles[MAX_LEVELS + 1] = {};  // tensor-core tiles of m2l[l] (LHV_TF32X3), or null
+    bool uniform = true;                   // p[l] equal over l = 2..L
+};
+
 // ---- expansions (expansions.cu) ----------------------------------------------
 // P2M into mult (leaf level), work buffer W: nleaf * 3P reals.
 template <typename T>
-void run_p2m(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& lv, const TreeParams& hp,
-             const vec4_t<T>* xs, const vec4_t<T>* ws, T* W, Grouped& gp, T* mult);
+void run_p2m(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs,
+             const vec4_t<T>* ws, T* W, Grouped& gp, T* mult);
 // M2M for all levels L-1 .. 2 (mult of the levels < L is overwritten).
 template <typename T>
-void run_m2m(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& lv, Grouped& gp, T* mult);
+void run_m2m(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, Grouped& gp, T* mult);
 // L2L for all levels 2 -> 3 .. L-1 -> L (adds into loc).
 template <typename T>
-void run_l2l(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& lv, Grouped& gp, T* loc);
+void run_l2l(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, Grouped& gp, T* loc);
 // L2P at the leaves; work buffer cf: nleaf * 12P reals.
 template <typename T>
-void run_l2p(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& lv, const TreeParams& hp,
-             const vec4_t<T>* xs, const vec4_t<T>* ws, const T* loc, T* cf, Grouped& gp, vec4_t<T>* vfar,
-             vec4_t<T>* sfar);
+void run_l2p(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs,
+             const vec4_t<T>* ws, const T* loc, T* cf, Grouped& gp, vec4_t<T>* vfar, vec4_t<T>* sfar);
 
 // ---- M2L (m2l.cu) ------------------------------------------------------------
 // table: (off[L+1] - off[2]) * 316 ints; nc: pairs per GEMM chunk (gemm_nc).
+// uniform: pairs of all levels bucketed by offset; else by (level, offset).
 void m2l_prepare(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& lv, int* table, Grouped& gp,
-                 int nc, unsigned long long* pair_counter);
+                 int nc, bool uniform, unsigned long long* pair_counter);
 // the products; loc must be zero for levels >= 2.
 template <typename T>
-void m2l_apply(Ctx* c, const OpTables& ops, Grouped& gp, const T* mult, T* loc);
+void m2l_apply(Ctx* c, const Plan<T>& pl, const Levels& lv, Grouped& gp, const T* mult, T* loc);
 
 // ---- P2P (p2p.cu) ------------------------------------------------------------
 template <typename T>

@@ -57,9 +57,9 @@ __global__ void k_m2l_table(int nb, int level, int off_l, const uint64_t* __rest
 }  // namespace
 
 void m2l_prepare(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& lv, int* table, Grouped& gp,
-                 int nc, unsigned long long* pair_counter) {
+                 int nc, bool uniform, unsigned long long* pair_counter) {
     cudaStream_t s = stream_of(c);
-    const int P = ops.P, L = lv.L;
+    const int L = lv.L;
     // table rows for the global boxes [off[2], off[L+1])
     const int t0 = lv.off[2];
     for (int l = 2; l <= L; ++l) {
@@ -72,37 +72,53 @@ void m2l_prepare(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& 
     }
     check_launch("m2l table");
     const int64_t ntarget = lv.off[L + 1] - t0;
-    build_grouped(c, gp, NUM_OFFSETS, ntarget * NUM_OFFSETS, ntarget * 189, nc, M2LItems{table, t0});
-    (void)P;
+    M2LItems it{};
+    it.table = table;
+    it.t0 = t0;
+    it.by_level = !uniform;
+    it.L = L;
+    for (int l = 0; l <= MAX_LEVELS; ++l) it.off[l] = lv.off[l];
+    const int ngroups = uniform ? NUM_OFFSETS : NUM_OFFSETS * (L - 1);
+    build_grouped(c, gp, ngroups, ntarget * NUM_OFFSETS, ntarget * 189, nc, it);
 }
 
 template <typename T>
-void m2l_apply(Ctx* c, const OpTables& ops, Grouped& gp, const T* mult, T* loc) {
-    const int P = ops.P;
-    GemmArgs<T> a{};
-    a.g0 = 0;
-    a.g1 = NUM_OFFSETS;
-    a.ops = ops.m2l.as<T>();
-    a.ops_mod = NUM_OFFSETS;
-    a.R = 2 * P;
-    a.C = 2 * P;
-    a.psplit = P;
-    a.in = mult;
-    a.ldin = 2 * P;
-    a.out = loc;
-    a.ldout = 2 * P;
-    a.mode = GEMM_ATOMIC;
-    a.scale = (T)1;
-    if constexpr (sizeof(T) == 4) {
-        if (ctx_use_tc(c) && ops.m2l_tiles.ptr) {
-            run_tc_gemm(c, gp, a, ops.m2l_tiles.as<float>(), ctx_err_flag(c));
-            return;
+void m2l_apply(Ctx* c, const Plan<T>& pl, const Levels& lv, Grouped& gp, const T* mult, T* loc) {
+    const int L = lv.L;
+    // one launch per run of levels with the same p (one launch in all when uniform)
+    for (int l0 = 2; l0 <= L;) {
+        int l1 = l0 + 1;
+        if (pl.uniform) l1 = L + 1;
+        else
+            while (l1 <= L && pl.p[l1] == pl.p[l0]) ++l1;
+        const int P = pl.p[l0] * pl.p[l0];
+        GemmArgs<T> a{};
+        a.g0 = pl.uniform ? 0 : (l0 - 2) * NUM_OFFSETS;
+        a.g1 = pl.uniform ? NUM_OFFSETS : (l1 - 2) * NUM_OFFSETS;
+        a.ops = pl.m2l[l0];
+        a.ops_mod = NUM_OFFSETS;
+        a.R = 2 * P;
+        a.C = 2 * P;
+        a.psplit = P;
+        a.in = mult;
+        a.ldin = pl.ld;
+        a.out = loc;
+        a.ldout = pl.ld;
+        a.mode = GEMM_ATOMIC;
+        a.scale = (T)1;
+        bool done = false;
+        if constexpr (sizeof(T) == 4) {
+            if (ctx_use_tc(c) && pl.m2l_tiles[l0]) {
+                run_tc_gemm(c, gp, a, pl.m2l_tiles[l0], ctx_err_flag(c));
+                done = true;
+            }
         }
+        if (!done) run_group_gemm<T>(c, gp, a);
+        l0 = l1;
     }
-    run_group_gemm<T>(c, gp, a);
 }
 
-template void m2l_apply<float>(Ctx*, const OpTables&, Grouped&, const float*, float*);
-template void m2l_apply<double>(Ctx*, const OpTables&, Grouped&, const double*, double*);
+template void m2l_apply<float>(Ctx*, const Plan<float>&, const Levels&, Grouped&, const float*, float*);
+template void m2l_apply<double>(Ctx*, const Plan<double>&, const Levels&, Grouped&, const double*, double*);
 
 }  // namespace lhv
