@@ -158,6 +158,21 @@ int lhv_evaluate_velocity_stretching_f64(lhv_ctx* ctx, int64_t n, const double* 
                                          double* v4, double* s4);
 int lhv_step_f64(lhv_ctx* ctx, int64_t n, double* x4, double* w4, double dt);
 
+/* The exact sum the FMM approximates, at m sampled targets: v and s of Eq.
+ * s1.1 with the kernel of Eqs. 2/vem1 (the context's core_a) summed over every
+ * element j != idx[k] (excluded by index), in FP64 arithmetic.  This is the
+ * measure of the FMM error on a sample of targets (Sec. 5.1 uses 1000 points).
+ * x4, w4: the n elements (device [n][4], FP32 for lhv_direct_sampled, FP64 for
+ * the _f64 twin on an FP64 context); idx: device int32 [m] caller indices;
+ * v4, s4: device double [m][4] (32-byte aligned) outputs.  With core_a = 0
+ * coincident distinct elements contribute nothing (the singular kernel has no
+ * value there).  Synchronous on the context stream; O(m n) work.  Returns
+ * LHV_EINVAL for an index outside [0, n). */
+int lhv_direct_sampled(lhv_ctx* ctx, int64_t n, const float* x4, const float* w4, int m, const int32_t* idx,
+                       double* v4, double* s4);
+int lhv_direct_sampled_f64(lhv_ctx* ctx, int64_t n, const double* x4, const double* w4, int m, const int32_t* idx,
+                           double* v4, double* s4);
+
 /* Truncation number per octree level (variable truncation, which the paper
  * mentions but does not use, Sec. 5).  p[l] for the levels l < nlevels (host
  * array; 1 <= p[l] <= 24, or 0 for lhv_config.p); levels >= nlevels, and every
@@ -235,6 +250,41 @@ int lhv_export(lhv_ctx* ctx, int what, int level, void* dst, int64_t capacity_by
 #define LHV_NOALLOC_MAX_N (1 << 20)
 int lhv_morton_sort_noalloc(int64_t n, const float* x4, const float* w4, uint64_t* keys, int32_t* perm,
                             void* cuda_stream);
+
+/* ---- selector network of the learned form -------------------------------
+ * The paper uses one truncation number for the whole tree (Sec. 5 names a
+ * variable truncation number among the optimisations it left out).  The learned
+ * form picks one per level with a multilayer perceptron over 12 features of the
+ * level: h1 = relu(W1 x + b1) (12 -> 64), h2 = relu(W2 h1 + b2) (64 -> 64),
+ * h3 = relu(W3 h2 + b3) (64 -> 64), z = W4 h3 + b4 (64 -> 21); z[0..16] score
+ * p = 4 .. 20, z[17..20] score the leaf caps 16, 32, 64, 128.  Weights are
+ * bfloat16 (W: uint16 bit patterns, W1, W2, W3, W4 row-major (out x in) one
+ * after the other, LHV_MLP_NW values), biases FP32 (b1..b4, LHV_MLP_NB values);
+ * all arithmetic and accumulation is FP32.  These three calls are stateless:
+ * every pointer is caller-owned DEVICE memory, work is enqueued on cuda_stream
+ * (a cudaStream_t, NULL = legacy default stream); LHV_EINVAL for rows < 0 or a
+ * null pointer, LHV_ECUDA if a launch failed. */
+#define LHV_MLP_IN     12
+#define LHV_MLP_HIDDEN 64
+#define LHV_MLP_OUT    21
+#define LHV_MLP_NP     17
+#define LHV_MLP_NW     10304
+#define LHV_MLP_NB     213
+/* Z [rows][21] = logits of the feature rows X [rows][12]. */
+int lhv_mlp_forward(int rows, const float* X, const uint16_t* W, const float* b, float* Z, void* cuda_stream);
+/* Loss of a batch and its gradient: yp [rows] (p label 0..16, or -1 for none),
+ * yl [rows] (leaf label 0..3 or -1); loss = mean cross-entropy over the rows
+ * with a p label + mean cross-entropy over the rows with a leaf label.  gW
+ * (float [LHV_MLP_NW]), gb (float [LHV_MLP_NB]) and loss (float [1]) are
+ * overwritten with the gradient with respect to the weights (taken at their
+ * bfloat16 values) and biases; work: device int [2] scratch. */
+int lhv_mlp_loss_grad(int rows, const float* X, const int32_t* yp, const int32_t* yl, const uint16_t* W,
+                      const float* b, float* gW, float* gb, float* loss, int32_t* work, void* cuda_stream);
+/* One Adam step (Kingma & Ba 2015; beta1 0.9, beta2 0.999, eps 1e-8) of step
+ * number t >= 1 on the FP32 master weights W32 and biases b with moments
+ * (mW, vW), (mb, vb); W receives the bfloat16 rounding (to nearest even) of W32. */
+int lhv_mlp_adam(float* W32, uint16_t* W, const float* gW, float* mW, float* vW, float* b, const float* gb,
+                 float* mb, float* vb, int t, float lr, void* cuda_stream);
 
 /* Diagnostic: D = X B^T on the TF32 tensor-core path of this library, one CTA,
  * operands rounded to TF32 (no splitting).  X: device float [128][K], B: device

@@ -44,6 +44,11 @@ SIGNATURES = {
     "lhv_step_f64": (_int, [_vp, _i64, _vp, _vp, _dbl]),
     "lhv_get_stats": (_int, [_vp, ctypes.POINTER(Stats)]),
     "lhv_set_level_p": (_int, [_vp, ctypes.POINTER(_int), _int]),
+    "lhv_mlp_forward": (_int, [_int, _vp, _vp, _vp, _vp, _vp]),
+    "lhv_mlp_loss_grad": (_int, [_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "lhv_mlp_adam": (_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _int, ctypes.c_float, _vp]),
+    "lhv_direct_sampled": (_int, [_vp, _i64, _vp, _vp, _int, _vp, _vp, _vp]),
+    "lhv_direct_sampled_f64": (_int, [_vp, _i64, _vp, _vp, _int, _vp, _vp, _vp]),
     "lhv_set_timing": (_int, [_vp, _int]),
     "lhv_reset_stats": (_int, [_vp]),
     "lhv_export": (_int, [_vp, _int, _int, _vp, _i64, ctypes.POINTER(_i64)]),
@@ -54,6 +59,7 @@ SIGNATURES = {
 }
 
 NOALLOC_MAX_N = 1 << 20  # LHV_NOALLOC_MAX_N
+MLP_IN, MLP_OUT, MLP_NP, MLP_NW, MLP_NB = 12, 21, 17, 10304, 213  # LHV_MLP_*
 
 _lib = None
 

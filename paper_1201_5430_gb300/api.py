@@ -124,6 +124,20 @@ class LHV:
             "level_p": list(s.level_p)[: s.leaf_level + 1],
         }
 
+    def direct_sampled(self, x4, w4, idx):
+        """FP64 direct sums (lhv_direct_sampled) at the elements idx (CUDA int32 [m]):
+        returns (v, s) as CUDA float64 [m, 4] tensors."""
+        self._elems(x4)
+        self._elems(w4)
+        if not (idx.is_cuda and idx.dtype == torch.int32 and idx.dim() == 1 and idx.is_contiguous()):
+            raise ValueError("idx must be a contiguous CUDA int32 vector")
+        m = idx.shape[0]
+        v = torch.empty((m, 4), dtype=torch.float64, device=self.device)
+        s = torch.empty((m, 4), dtype=torch.float64, device=self.device)
+        fn = self.lib.lhv_direct_sampled_f64 if self.precision == "fp64" else self.lib.lhv_direct_sampled
+        self._check(fn(self.h, x4.shape[0], _ptr(x4), _ptr(w4), m, _ptr(idx), _ptr(v), _ptr(s)), "direct_sampled")
+        return v, s
+
     def set_level_p(self, p_per_level=None):
         """Truncation number per octree level (lhv_set_level_p); None restores config p."""
         vals = [int(v) for v in (p_per_level or [])]
@@ -170,3 +184,65 @@ def morton_sort_noalloc(x4, keys, perm, w4=None):
                                          _ptr(perm), stream)
     if st != 0:
         raise L.LHVError(st, "morton_sort_noalloc: " + lib.lhv_status_string(st).decode())
+
+
+# ---- selector network (lhv_mlp_*): stateless calls on caller tensors ------------
+
+def _stream(t):
+    return ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
+
+
+def _need(t, dtype, numel=None):
+    if not (t.is_cuda and t.dtype == dtype and t.is_contiguous() and (numel is None or t.numel() == numel)):
+        raise ValueError(f"expected a contiguous CUDA {dtype} tensor" + (f" of {numel} values" if numel else ""))
+
+
+def mlp_forward(X, W, b):
+    """Logits [rows, 21] of feature rows X (float32 [rows, 12]); W: bfloat16 [LHV_MLP_NW], b: float32."""
+    lib = L.load()
+    _need(X, torch.float32)
+    _need(W, torch.bfloat16, L.MLP_NW)
+    _need(b, torch.float32, L.MLP_NB)
+    rows = X.shape[0]
+    Z = torch.empty((rows, L.MLP_OUT), dtype=torch.float32, device=X.device)
+    with torch.cuda.device(X.device):
+        st = lib.lhv_mlp_forward(rows, _ptr(X), _ptr(W), _ptr(b), _ptr(Z), _stream(X))
+    if st:
+        raise L.LHVError(st, "mlp_forward")
+    return Z
+
+
+def mlp_loss_grad(X, yp, yl, W, b):
+    """(loss, gW, gb) of lhv_mlp_loss_grad; yp, yl int32 [rows] (-1 = no label)."""
+    lib = L.load()
+    _need(X, torch.float32)
+    _need(yp, torch.int32, X.shape[0])
+    _need(yl, torch.int32, X.shape[0])
+    _need(W, torch.bfloat16, L.MLP_NW)
+    _need(b, torch.float32, L.MLP_NB)
+    dev = X.device
+    gW = torch.empty(L.MLP_NW, dtype=torch.float32, device=dev)
+    gb = torch.empty(L.MLP_NB, dtype=torch.float32, device=dev)
+    loss = torch.empty(1, dtype=torch.float32, device=dev)
+    work = torch.empty(2, dtype=torch.int32, device=dev)
+    with torch.cuda.device(dev):
+        st = lib.lhv_mlp_loss_grad(X.shape[0], _ptr(X), _ptr(yp), _ptr(yl), _ptr(W), _ptr(b), _ptr(gW), _ptr(gb),
+                                   _ptr(loss), _ptr(work), _stream(X))
+    if st:
+        raise L.LHVError(st, "mlp_loss_grad")
+    return loss, gW, gb
+
+
+def mlp_adam(W32, W, gW, mW, vW, b, gb, mb, vb, t, lr):
+    """One lhv_mlp_adam step in place (all CUDA tensors; W bfloat16, the rest float32)."""
+    lib = L.load()
+    for x in (W32, gW, mW, vW):
+        _need(x, torch.float32, L.MLP_NW)
+    for x in (b, gb, mb, vb):
+        _need(x, torch.float32, L.MLP_NB)
+    _need(W, torch.bfloat16, L.MLP_NW)
+    with torch.cuda.device(W32.device):
+        st = lib.lhv_mlp_adam(_ptr(W32), _ptr(W), _ptr(gW), _ptr(mW), _ptr(vW), _ptr(b), _ptr(gb), _ptr(mb),
+                              _ptr(vb), int(t), float(lr), _stream(W32))
+    if st:
+        raise L.LHVError(st, "mlp_adam")

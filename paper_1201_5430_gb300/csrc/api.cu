@@ -37,7 +37,7 @@ struct Ctx {
     int64_t tree_n = 0;
     OpTables ops;
     int ops_type = 0;  // sizeof(T) of the built tables
-    Buf tmp[8];
+    Buf tmp[12];
     Buf xs, ws, mult, loc, table, vfar, sfar, counters, W, cf;
     Grouped gp_leaf, gp_m2m, gp_m2l, gp_l2l;
     Buf rk[6];         // kv, ks, ax, aw, sx, sw
@@ -396,6 +396,22 @@ double core_cutoff(double a, double eps) {
     return 0.5 * (lo + hi) * a;
 }
 
+template <typename T>
+int direct_entry(lhv_ctx* ctx, int64_t n, const T* x4, const T* w4, int m, const int32_t* idx, double* v4,
+                        double* s4, int want_prec) {
+    int st = check_elems(ctx, n, {x4, w4}, 4 * sizeof(T), want_prec);
+    if (st != LHV_OK) return st;
+    if (m < 0 || (m > 0 && (!idx || !v4 || !s4)) || (m > 0 && n == 0)) return LHV_EINVAL;
+    if (m == 0) return LHV_OK;
+    if (!aligned(v4, 32) || !aligned(s4, 32) || !aligned(idx, 4)) return LHV_EINVAL;
+    return guarded(ctx, [&] {
+        int r = lhv::direct_sampled<T>(&ctx->c, n, reinterpret_cast<const lhv::vec4_t<T>*>(x4),
+                                       reinterpret_cast<const lhv::vec4_t<T>*>(w4), m, idx, ctx->c.cfg.core_a, v4, s4);
+        if (r != LHV_OK) ctx->c.last_error = "sample index out of range";
+        return r;
+    });
+}
+
 }  // namespace
 
 extern "C" {
@@ -520,6 +536,41 @@ int lhv_step_f64(lhv_ctx* ctx, int64_t n, double* x4, double* w4, double dt) {
         return lhv::step<double>(&ctx->c, n, 1, off, reinterpret_cast<lhv::dbl4*>(x4), reinterpret_cast<lhv::dbl4*>(w4),
                                  dt);
     });
+}
+
+int lhv_mlp_forward(int rows, const float* X, const uint16_t* W, const float* b, float* Z, void* cuda_stream) {
+    if (rows < 0 || (rows > 0 && (!X || !W || !b || !Z))) return LHV_EINVAL;
+    if (rows == 0) return LHV_OK;
+    return lhv::mlp_forward(static_cast<cudaStream_t>(cuda_stream), rows, X, W, b, Z) == cudaSuccess ? LHV_OK
+                                                                                                    : LHV_ECUDA;
+}
+
+int lhv_mlp_loss_grad(int rows, const float* X, const int32_t* yp, const int32_t* yl, const uint16_t* W,
+                      const float* b, float* gW, float* gb, float* loss, int32_t* work, void* cuda_stream) {
+    if (rows < 0 || !W || !b || !gW || !gb || !loss || !work || (rows > 0 && (!X || !yp || !yl))) return LHV_EINVAL;
+    return lhv::mlp_grad(static_cast<cudaStream_t>(cuda_stream), rows, X, yp, yl, W, b, gW, gb, loss, work) ==
+                   cudaSuccess
+               ? LHV_OK
+               : LHV_ECUDA;
+}
+
+int lhv_mlp_adam(float* W32, uint16_t* W, const float* gW, float* mW, float* vW, float* b, const float* gb,
+                 float* mb, float* vb, int t, float lr, void* cuda_stream) {
+    if (!W32 || !W || !gW || !mW || !vW || !b || !gb || !mb || !vb || t < 1) return LHV_EINVAL;
+    return lhv::mlp_adam(static_cast<cudaStream_t>(cuda_stream), W32, W, gW, mW, vW, b, gb, mb, vb, t, lr) ==
+                   cudaSuccess
+               ? LHV_OK
+               : LHV_ECUDA;
+}
+
+int lhv_direct_sampled(lhv_ctx* ctx, int64_t n, const float* x4, const float* w4, int m, const int32_t* idx,
+                       double* v4, double* s4) {
+    return direct_entry<float>(ctx, n, x4, w4, m, idx, v4, s4, LHV_FP32);
+}
+
+int lhv_direct_sampled_f64(lhv_ctx* ctx, int64_t n, const double* x4, const double* w4, int m, const int32_t* idx,
+                           double* v4, double* s4) {
+    return direct_entry<double>(ctx, n, x4, w4, m, idx, v4, s4, LHV_FP64);
 }
 
 int lhv_step_host(lhv_ctx* ctx, int64_t n, float* x4_host, float* w4_host, double dt) {

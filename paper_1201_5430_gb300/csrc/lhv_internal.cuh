@@ -75,7 +75,7 @@ void ensure(Ctx* c, Buf& b, int64_t bytes);          // grow b to >= bytes (thro
 int ctx_leaf_max(Ctx* c);
 int ctx_max_level(Ctx* c);
 double ctx_rK(Ctx* c);
-Buf& ctx_tmp(Ctx* c, int i);                         // scratch buffers 0..7 owned by the context
+Buf& ctx_tmp(Ctx* c, int i);                         // scratch buffers 0..11 owned by the context
 bool ctx_use_tc(Ctx* c);                             // LHV_TF32X3: dense maps on the tensor cores
 int* ctx_err_flag(Ctx* c);                           // device word set by a timed-out device wait
 
@@ -192,6 +192,19 @@ template <typename T>
 void run_p2p(Ctx* c, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs, const vec4_t<T>* ws,
              const int* perm, const vec4_t<T>* vfar, const vec4_t<T>* sfar, vec4_t<T>* v_out, vec4_t<T>* s_out,
              double a, bool near, int64_t n, unsigned long long* pair_counter);
+
+// ---- direct sums at sampled targets (direct.cu) ---------------------------------
+// v4, s4: device double [m][4]; synchronous; LHV_EINVAL if an index is out of range.
+template <typename T>
+int direct_sampled(Ctx* c, int64_t n, const vec4_t<T>* x4, const vec4_t<T>* w4, int m, const int* idx, double a,
+                   double* v4, double* s4);
+
+// ---- selector network (mlp.cu) ------------------------------------------------
+cudaError_t mlp_forward(cudaStream_t s, int rows, const float* X, const uint16_t* W, const float* b, float* Z);
+cudaError_t mlp_grad(cudaStream_t s, int rows, const float* X, const int* yp, const int* yl, const uint16_t* W,
+                     const float* b, float* gW, float* gb, float* loss, int* cnt);
+cudaError_t mlp_adam(cudaStream_t s, float* W32, uint16_t* W, const float* gW, float* mW, float* vW, float* b,
+                     const float* gb, float* mb, float* vb, int t, float lr);
 
 // ---- RK4 (p2p.cu) ------------------------------------------------------------
 template <typename T>
