@@ -105,6 +105,12 @@ typedef struct {
     int64_t kernel_launches;                 /* kernels launched since the last reset */
     int     level_p[LHV_MAX_LEVELS];         /* truncation number of each level's expansions in
                                                 the last evaluation with a far field (0: none) */
+    int     selector_leaf_max;               /* leaf cap of the last selection (0: none yet) */
+    int64_t selector_selections;             /* selections since lhv_set_selector */
+    int64_t selector_checks;                 /* sampled direct-sum checks since then */
+    int64_t selector_fallbacks;              /* checks that failed (fixed p used instead) */
+    double  selector_err_v, selector_err_s;  /* relative L2 error of v and s on the sample at the
+                                                last check (-1: none) */
 } lhv_stats;
 
 /* Create a context for one configuration on one CUDA stream (a cudaStream_t,
@@ -285,6 +291,38 @@ int lhv_mlp_loss_grad(int rows, const float* X, const int32_t* yp, const int32_t
  * (mW, vW), (mb, vb); W receives the bfloat16 rounding (to nearest even) of W32. */
 int lhv_mlp_adam(float* W32, uint16_t* W, const float* gW, float* mW, float* vW, float* b, const float* gb,
                  float* mb, float* vb, int t, float lr, void* cuda_stream);
+
+/* Learned form on a context (FP32 or TF32X3; single-system entry points).
+ * lhv_set_selector copies the network (HOST arrays W: LHV_MLP_NW bfloat16
+ * bit patterns, b: LHV_MLP_NB floats; W = NULL switches the form off) and sets
+ * the target eps: the relative L2 error of v against the direct sum on a sample
+ * of check_samples elements (Sec. 5.1 uses 1000).  Then every
+ * lhv_evaluate_velocity_stretching, and every lhv_step / lhv_step_host from its
+ * initial state, first builds the tree at lhv_config.leaf_max, scores levels
+ * 2..L with the network, and evaluates with p[l] = 4 + argmax of the p scores of
+ * level l and leaf cap = {16, 32, 64, 128}[argmax of the leaf scores of level L]
+ * (an lhv_step keeps that choice for its four stages).  The first selection
+ * and every check_every-th after it (0: never) is checked: the FP64 direct sums
+ * of lhv_direct_sampled at the sample against the evaluation; if the error of v
+ * exceeds eps the evaluation is redone with lhv_config.p at every level and
+ * lhv_config.leaf_max (the fixed-p fallback).  lhv_get_stats reports the
+ * choices, checks and fallbacks.  While the form is on, the selector replaces
+ * any lhv_set_level_p values.  LHV_EINVAL for eps outside (0, 1), check_samples
+ * < 1, or an FP64 context. */
+int lhv_set_selector(lhv_ctx* ctx, const uint16_t* W, const float* b, double eps, int check_every,
+                     int check_samples);
+/* The network's input for n FP32 elements: builds their tree (x4, w4 device
+ * [n][4]) and writes one row of LHV_MLP_IN features per level l = 2..L (row
+ * l - 2) into X (device float [capacity_rows][LHV_MLP_IN]); *rows_out = L - 1
+ * (0 when the tree has no far field; X may be NULL to query it).  eps is the
+ * target that enters the features.  Feature list (each scaled to about
+ * [-1, 1]): l/10, (L-l)/10, log2(boxes at l)/20, log2(boxes(l)/boxes(l-1))/3,
+ * log2(n/boxes at l)/20, -log10(eps)/10, log2(a/h_l)/10 (-3 when a = 0),
+ * mean interaction-list size/189, mean colleague count/27,
+ * log10(sum_b |sum_{j in b} w_j| / sum_j |w_j|)/3, log2(n)/24, and 0 / 0.5
+ * for FP32 / TF32X3. */
+int lhv_selector_features(lhv_ctx* ctx, int64_t n, const float* x4, const float* w4, double eps, float* X,
+                          int capacity_rows, int* rows_out);
 
 /* Diagnostic: D = X B^T on the TF32 tensor-core path of this library, one CTA,
  * operands rounded to TF32 (no splitting).  X: device float [128][K], B: device

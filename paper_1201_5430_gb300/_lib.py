@@ -26,7 +26,10 @@ class Stats(ctypes.Structure):
                 ("p2p_pairs", ctypes.c_int64), ("m2l_pairs", ctypes.c_int64),
                 ("stage_ms", ctypes.c_double * LHV_NUM_STAGES),
                 ("stage_launches", ctypes.c_int64 * LHV_NUM_STAGES), ("kernel_launches", ctypes.c_int64),
-                ("level_p", ctypes.c_int * LHV_MAX_LEVELS)]
+                ("level_p", ctypes.c_int * LHV_MAX_LEVELS), ("selector_leaf_max", ctypes.c_int),
+                ("selector_selections", ctypes.c_int64), ("selector_checks", ctypes.c_int64),
+                ("selector_fallbacks", ctypes.c_int64), ("selector_err_v", ctypes.c_double),
+                ("selector_err_s", ctypes.c_double)]
 
 
 # exported function -> (restype, argtypes); every name here is declared in include/lhv.h
@@ -44,6 +47,8 @@ SIGNATURES = {
     "lhv_step_f64": (_int, [_vp, _i64, _vp, _vp, _dbl]),
     "lhv_get_stats": (_int, [_vp, ctypes.POINTER(Stats)]),
     "lhv_set_level_p": (_int, [_vp, ctypes.POINTER(_int), _int]),
+    "lhv_set_selector": (_int, [_vp, _vp, _vp, _dbl, _int, _int]),
+    "lhv_selector_features": (_int, [_vp, _i64, _vp, _vp, _dbl, _vp, _int, ctypes.POINTER(_int)]),
     "lhv_mlp_forward": (_int, [_int, _vp, _vp, _vp, _vp, _vp]),
     "lhv_mlp_loss_grad": (_int, [_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "lhv_mlp_adam": (_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _int, ctypes.c_float, _vp]),

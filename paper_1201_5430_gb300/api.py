@@ -122,7 +122,35 @@ class LHV:
             "stage_launches": dict(zip(L.STAGES, list(s.stage_launches))),
             "kernel_launches": s.kernel_launches,
             "level_p": list(s.level_p)[: s.leaf_level + 1],
+            "selector": {"leaf_max": s.selector_leaf_max, "selections": s.selector_selections,
+                         "checks": s.selector_checks, "fallbacks": s.selector_fallbacks,
+                         "err_v": s.selector_err_v, "err_s": s.selector_err_s},
         }
+
+    def set_selector(self, W=None, b=None, eps=1e-6, check_every=1, check_samples=1000):
+        """Switch the learned form on with network weights W (bfloat16 [LHV_MLP_NW]) and
+        biases b (float32 [LHV_MLP_NB]), host or device tensors; W = None switches it off."""
+        if W is None:
+            self._check(self.lib.lhv_set_selector(self.h, None, None, float(eps), 0, 1), "set_selector")
+            return
+        Wh = W.detach().to("cpu", torch.bfloat16).contiguous()
+        bh = b.detach().to("cpu", torch.float32).contiguous()
+        if Wh.numel() != L.MLP_NW or bh.numel() != L.MLP_NB:
+            raise ValueError("selector weights have the wrong size")
+        self._check(self.lib.lhv_set_selector(self.h, _ptr(Wh), _ptr(bh), float(eps), int(check_every),
+                                              int(check_samples)), "set_selector")
+
+    def selector_features(self, x4, w4, eps=1e-6):
+        """Feature rows (CUDA float32 [L-1, 12]) of the levels 2..L of the tree of x4."""
+        self._elems(x4)
+        self._elems(w4)
+        rows = ctypes.c_int(0)
+        self._check(self.lib.lhv_selector_features(self.h, x4.shape[0], _ptr(x4), _ptr(w4), float(eps), None, 0,
+                                                   ctypes.byref(rows)), "selector_features")
+        X = torch.empty((max(rows.value, 1), L.MLP_IN), dtype=torch.float32, device=self.device)
+        self._check(self.lib.lhv_selector_features(self.h, x4.shape[0], _ptr(x4), _ptr(w4), float(eps), _ptr(X),
+                                                   X.shape[0], ctypes.byref(rows)), "selector_features")
+        return X[: rows.value]
 
     def direct_sampled(self, x4, w4, idx):
         """FP64 direct sums (lhv_direct_sampled) at the elements idx (CUDA int32 [m]):

@@ -7,6 +7,8 @@
 #include <cstring>
 #include <new>
 #include <map>
+#include <random>
+#include <unordered_set>
 #include <string>
 #include <vector>
 
@@ -48,12 +50,23 @@ struct Ctx {
     int opcache_type = 0;
     int eval_p[MAX_LEVELS + 1] = {};    // truncation numbers of the last evaluation's expansions
     int eval_ld = 0;                    // their stride (reals per box)
+    int leaf_override = 0;              // leaf cap chosen by the selector (0: cfg.leaf_max)
+    bool tree_reuse = false;            // the next evaluation may use the tree just built for its inputs
+    // learned form (lhv_set_selector)
+    bool sel_active = false;
+    double sel_eps = 1e-6;
+    int sel_check_every = 1, sel_check_samples = 1000;
+    int64_t sel_selections = 0, sel_checks = 0, sel_fallbacks = 0;
+    double sel_err_v = -1.0, sel_err_s = -1.0;
+    int sel_leaf = 0;
+    int64_t sel_idx_n = -1;
+    Buf sel_W, sel_b, sel_X, sel_Z, sel_choice, sel_idx, sel_dv, sel_ds, sel_err;
 };
 
 // ---- helpers used by every translation unit ------------------------------
 void count_launch(Ctx* c) { ++c->launches; }
 cudaStream_t stream_of(Ctx* c) { return c->stream; }
-int ctx_leaf_max(Ctx* c) { return c->cfg.leaf_max; }
+int ctx_leaf_max(Ctx* c) { return c->leaf_override > 0 ? c->leaf_override : c->cfg.leaf_max; }
 int ctx_max_level(Ctx* c) { return c->cfg.max_level; }
 double ctx_rK(Ctx* c) { return c->rK; }
 Buf& ctx_tmp(Ctx* c, int i) { return c->tmp[i]; }
@@ -238,8 +251,11 @@ static int evaluate(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const ve
     unsigned long long* cnt = c->counters.as<unsigned long long>();
     cuda_check(cudaMemsetAsync(cnt, 0, 16, c->stream), "counters");  // [2] holds the device error flag
     Error err{LHV_OK, ""};
-    int st = tree_stage<T>(c, n, nsys, sysoff, x4, w4, err);
-    if (st != LHV_OK) throw err;
+    if (!c->tree_reuse) {
+        int st = tree_stage<T>(c, n, nsys, sysoff, x4, w4, err);
+        if (st != LHV_OK) throw err;
+    }
+    c->tree_reuse = false;
     const Levels& lv = c->lv;
     const int L = lv.L;
     const int terms = c->cfg.terms ? c->cfg.terms : LHV_TERMS_ALL;
@@ -304,9 +320,109 @@ static int evaluate(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const ve
     return LHV_OK;
 }
 
+// ---- learned form: per-level p and leaf cap from the selector network ----------
+static const int kLeafCaps[4] = {16, 32, 64, 128};
+
+static void clear_schedule(Ctx* c) {
+    c->leaf_override = 0;
+    c->tree_reuse = false;
+    for (int l = 0; l <= MAX_LEVELS; ++l) c->level_p[l] = 0;
+}
+
+// Builds the tree of (x4, w4) at the configured leaf cap, scores its levels with
+// the network and sets level_p / leaf_override for the evaluations that follow.
+template <typename T>
+static void select_schedule(Ctx* c, int64_t n, const vec4_t<T>* x4, const vec4_t<T>* w4) {
+    clear_schedule(c);
+    Error err{LHV_OK, ""};
+    const int64_t off[2] = {0, n};
+    if (tree_stage<T>(c, n, 1, off, x4, w4, err) != LHV_OK) throw err;
+    ++c->sel_selections;
+    const int L = c->lv.L;
+    if (L < 2) return;  // no far field: nothing to choose
+    const int rows = L - 1;
+    ensure(c, c->sel_X, (int64_t)rows * LHV_MLP_IN * 4);
+    ensure(c, c->sel_Z, (int64_t)rows * LHV_MLP_OUT * 4);
+    ensure(c, c->sel_choice, (int64_t)rows * 2 * 4);
+    const double prec = c->cfg.precision == LHV_FP64 ? 1.0 : (c->cfg.precision == LHV_TF32X3 ? 0.5 : 0.0);
+    level_features<T>(c, c->tb, c->lv, n, c->ws.as<vec4_t<T>>(), c->sel_eps, c->cfg.core_a, prec,
+                      c->sel_X.as<float>());
+    cuda_check(mlp_forward(c->stream, rows, c->sel_X.as<float>(), c->sel_W.as<uint16_t>(), c->sel_b.as<float>(),
+                           c->sel_Z.as<float>()),
+               "selector network");
+    count_launch(c);
+    std::vector<int> ch((size_t)rows * 2);
+    select_from_scores(c, rows, c->sel_Z.as<float>(), c->sel_choice.as<int>(), ch.data());
+    for (int l = 2; l <= L; ++l) c->level_p[l] = 4 + ch[2 * (l - 2)];
+    for (int l = 0; l < 2; ++l) c->level_p[l] = c->level_p[2];
+    for (int l = L + 1; l <= MAX_LEVELS; ++l) c->level_p[l] = c->level_p[L];  // a deeper tree at the new cap
+    c->sel_leaf = kLeafCaps[ch[2 * (L - 2) + 1]];
+    c->leaf_override = c->sel_leaf;
+    // the tree just built serves the evaluation when the cap is the one it was built with
+    c->tree_reuse = c->sel_leaf == c->cfg.leaf_max;
+}
+
+// Error of an evaluation (v4, s4 of the elements x4, w4) on the sample against
+// FP64 direct sums; true when the velocity error is within the target.
+template <typename T>
+static bool check_schedule(Ctx* c, int64_t n, const vec4_t<T>* x4, const vec4_t<T>* w4, const vec4_t<T>* v4,
+                           const vec4_t<T>* s4) {
+    const int m = (int)std::min<int64_t>(c->sel_check_samples, n);
+    if (c->sel_idx_n != n) {
+        // m distinct indices, uniform without replacement (Floyd's method), fixed seed
+        std::vector<int> idx;
+        std::mt19937_64 rng(0);
+        std::unordered_set<int64_t> seen;
+        for (int64_t j = n - m; j < n; ++j) {
+            std::uniform_int_distribution<int64_t> u(0, j);
+            int64_t t = u(rng);
+            if (seen.count(t)) t = j;
+            seen.insert(t);
+            idx.push_back((int)t);
+        }
+        ensure(c, c->sel_idx, (int64_t)m * 4);
+        cuda_check(cudaMemcpyAsync(c->sel_idx.ptr, idx.data(), (size_t)m * 4, cudaMemcpyHostToDevice, c->stream),
+                   "sample");
+        cuda_check(cudaStreamSynchronize(c->stream), "sample");
+        c->sel_idx_n = n;
+    }
+    ensure(c, c->sel_dv, (int64_t)m * 32);
+    ensure(c, c->sel_ds, (int64_t)m * 32);
+    ensure(c, c->sel_err, 64);
+    if (direct_sampled<T>(c, n, x4, w4, m, c->sel_idx.as<int>(), c->cfg.core_a, c->sel_dv.as<double>(),
+                          c->sel_ds.as<double>()) != LHV_OK)
+        throw Error{LHV_ECUDA, "sample check"};
+    double e[4];
+    sample_error<T>(c, m, c->sel_idx.as<int>(), v4, s4, c->sel_dv.as<double>(), c->sel_ds.as<double>(),
+                    c->sel_err.as<double>(), e);
+    ++c->sel_checks;
+    c->sel_err_v = e[1] > 0 ? std::sqrt(e[0] / e[1]) : 0.0;
+    c->sel_err_s = e[3] > 0 ? std::sqrt(e[2] / e[3]) : 0.0;
+    return c->sel_err_v <= c->sel_eps;
+}
+
+static bool check_due(Ctx* c) {
+    return c->sel_check_every > 0 && (c->sel_selections - 1) % c->sel_check_every == 0;
+}
+
+// One evaluation through the selector: choose, evaluate, check on schedule,
+// and fall back to the fixed p of the configuration when the check fails.
+template <typename T>
+static int evaluate_selected(Ctx* c, int64_t n, const vec4_t<T>* x4, const vec4_t<T>* w4, vec4_t<T>* v4,
+                             vec4_t<T>* s4) {
+    const int64_t off[2] = {0, n};
+    select_schedule<T>(c, n, x4, w4);
+    int st = evaluate<T>(c, n, 1, off, x4, w4, v4, s4);
+    if (st != LHV_OK || !check_due(c) || check_schedule<T>(c, n, x4, w4, v4, s4)) return st;
+    ++c->sel_fallbacks;
+    clear_schedule(c);
+    return evaluate<T>(c, n, 1, off, x4, w4, v4, s4);
+}
+
 template <typename T>
 static int step(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, vec4_t<T>* x4, vec4_t<T>* w4, double dt) {
     if (n == 0) return LHV_OK;
+    const bool learned = c->sel_active && nsys == 1;
     const int64_t bytes = n * (int64_t)sizeof(vec4_t<T>);
     for (int i = 0; i < 6; ++i) ensure(c, c->rk[i], bytes);
     vec4_t<T>* kv = c->rk[0].as<vec4_t<T>>();
@@ -321,7 +437,9 @@ static int step(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, vec4_t<T>* x
     for (int k = 0; k < 4; ++k) {
         const vec4_t<T>* xin = (k == 0) ? x4 : sx;
         const vec4_t<T>* win = (k == 0) ? w4 : sw;
-        int st = evaluate<T>(c, n, nsys, sysoff, xin, win, kv, ks);
+        // the learned form picks p per level and the leaf cap once per step, from y0
+        int st = (learned && k == 0) ? evaluate_selected<T>(c, n, xin, win, kv, ks)
+                                     : evaluate<T>(c, n, nsys, sysoff, xin, win, kv, ks);
         if (st != LHV_OK) return st;
         StageScope sc(c, LHV_STAGE_RK4);
         run_rk4_stage<T>(c, n, x4, w4, kv, ks, ax, aw, sx, sw, c_acc[k], c_stage[k], k == 0);
@@ -437,7 +555,6 @@ int lhv_create(const lhv_config* cfg, void* cuda_stream, lhv_ctx** out) {
         return LHV_EINVAL;
     if (cfg->core_a > 0.0 && !(cfg->eps > 0.0 && cfg->eps < 1.0)) return LHV_EINVAL;
     if (cfg->precision != LHV_FP32 && cfg->precision != LHV_FP64 && cfg->precision != LHV_TF32X3) return LHV_EINVAL;
-    if (cfg->precision == LHV_TF32X3 && (cfg->p % 2) != 0) return LHV_EUNSUPPORTED;
     if (cfg->terms < 0 || cfg->terms > 3 || cfg->max_level < 0 || cfg->max_level > 21) return LHV_EINVAL;
     lhv_ctx* h = new (std::nothrow) lhv_ctx();
     if (!h) return LHV_ENOMEM;
@@ -460,6 +577,8 @@ void lhv_destroy(lhv_ctx* ctx) {
     lhv::free_operators(c.ops);
     for (auto& kv : c.opcache) lhv::release(kv.second);
     c.opcache.clear();
+    for (auto* b : {&c.sel_W, &c.sel_b, &c.sel_X, &c.sel_Z, &c.sel_choice, &c.sel_idx, &c.sel_dv, &c.sel_ds, &c.sel_err})
+        lhv::release(*b);
     lhv::TreeBufs& t = c.tb;
     lhv::Buf* tree[] = {&t.keys_a, &t.keys_b, &t.idx_a, &t.idx_b, &t.hist, &t.boxof_a, &t.boxof_b, &t.flags,
                         &t.scan_tmp, &t.perm, &t.params, &t.counts, &t.bkey, &t.bbeg, &t.bend, &t.bparent,
@@ -499,6 +618,10 @@ int lhv_evaluate_velocity_stretching(lhv_ctx* ctx, int64_t n, const float* x4, c
     if (st != LHV_OK) return st;
     return guarded(ctx, [&] {
         const int64_t off[2] = {0, n};
+        if (ctx->c.sel_active)
+            return lhv::evaluate_selected<float>(&ctx->c, n, reinterpret_cast<const float4*>(x4),
+                                                 reinterpret_cast<const float4*>(w4), reinterpret_cast<float4*>(v4),
+                                                 reinterpret_cast<float4*>(s4));
         return lhv::evaluate<float>(&ctx->c, n, 1, off, reinterpret_cast<const float4*>(x4),
                                     reinterpret_cast<const float4*>(w4), reinterpret_cast<float4*>(v4),
                                     reinterpret_cast<float4*>(s4));
@@ -662,6 +785,12 @@ int lhv_get_stats(lhv_ctx* ctx, lhv_stats* out) {
         out->leaf_level = c.lv.L;
         for (int l = 0; l < LHV_MAX_LEVELS; ++l) out->nbox[l] = c.lv.nbox[l];
         for (int l = 0; l < LHV_MAX_LEVELS; ++l) out->level_p[l] = c.eval_p[l];
+        out->selector_leaf_max = c.sel_leaf;
+        out->selector_selections = c.sel_selections;
+        out->selector_checks = c.sel_checks;
+        out->selector_fallbacks = c.sel_fallbacks;
+        out->selector_err_v = c.sel_err_v;
+        out->selector_err_s = c.sel_err_s;
         out->n = c.tree_n;
         if (c.counters.ptr) {
             unsigned long long h[3] = {0, 0, 0};
@@ -679,6 +808,57 @@ int lhv_get_stats(lhv_ctx* ctx, lhv_stats* out) {
             out->stage_launches[i] = c.stage_launches[i];
         }
         out->kernel_launches = c.launches;
+        return LHV_OK;
+    });
+}
+
+int lhv_set_selector(lhv_ctx* ctx, const uint16_t* W, const float* b, double eps, int check_every,
+                     int check_samples) {
+    if (!ctx) return LHV_EINVAL;
+    Ctx& c = ctx->c;
+    if (!W) {
+        c.sel_active = false;
+        lhv::clear_schedule(&c);
+        return LHV_OK;
+    }
+    if (!b || !(eps > 0.0 && eps < 1.0) || check_every < 0 || check_samples < 1 || c.cfg.precision == LHV_FP64)
+        return LHV_EINVAL;
+    return guarded(ctx, [&] {
+        lhv::ensure(&c, c.sel_W, LHV_MLP_NW * 2);
+        lhv::ensure(&c, c.sel_b, LHV_MLP_NB * 4);
+        lhv::cuda_check(cudaMemcpyAsync(c.sel_W.ptr, W, LHV_MLP_NW * 2, cudaMemcpyHostToDevice, c.stream), "weights");
+        lhv::cuda_check(cudaMemcpyAsync(c.sel_b.ptr, b, LHV_MLP_NB * 4, cudaMemcpyHostToDevice, c.stream), "biases");
+        lhv::cuda_check(cudaStreamSynchronize(c.stream), "selector");
+        c.sel_active = true;
+        c.sel_eps = eps;
+        c.sel_check_every = check_every;
+        c.sel_check_samples = check_samples;
+        c.sel_selections = c.sel_checks = c.sel_fallbacks = 0;
+        c.sel_err_v = c.sel_err_s = -1.0;
+        return LHV_OK;
+    });
+}
+
+int lhv_selector_features(lhv_ctx* ctx, int64_t n, const float* x4, const float* w4, double eps, float* X,
+                          int capacity_rows, int* rows_out) {
+    int st = check_elems(ctx, n, {x4, w4}, 16, LHV_FP32);
+    if (st != LHV_OK) return st;
+    if (!rows_out || !(eps > 0.0 && eps < 1.0) || capacity_rows < 0) return LHV_EINVAL;
+    *rows_out = 0;
+    if (n == 0) return LHV_OK;
+    return guarded(ctx, [&] {
+        Ctx& c = ctx->c;
+        Error err{LHV_OK, ""};
+        const int64_t off[2] = {0, n};
+        int s2 = lhv::tree_stage<float>(&c, n, 1, off, reinterpret_cast<const float4*>(x4),
+                                        reinterpret_cast<const float4*>(w4), err);
+        if (s2 != LHV_OK) throw err;
+        const int rows = c.lv.L >= 2 ? c.lv.L - 1 : 0;
+        *rows_out = rows;
+        if (!X || rows == 0) return LHV_OK;
+        if (capacity_rows < rows) return LHV_EINVAL;
+        const double prec = c.cfg.precision == LHV_TF32X3 ? 0.5 : 0.0;
+        lhv::level_features<float>(&c, c.tb, c.lv, n, c.ws.as<float4>(), eps, c.cfg.core_a, prec, X);
         return LHV_OK;
     });
 }

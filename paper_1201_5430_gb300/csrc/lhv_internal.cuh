@@ -206,6 +206,18 @@ cudaError_t mlp_grad(cudaStream_t s, int rows, const float* X, const int* yp, co
 cudaError_t mlp_adam(cudaStream_t s, float* W32, uint16_t* W, const float* gW, float* mW, float* vW, float* b,
                      const float* gb, float* mb, float* vb, int t, float lr);
 
+// ---- learned form (selector.cu) ---------------------------------------------------
+// Feature rows of the levels 2..L (LHV_MLP_IN floats each) into X (device); returns the row count.
+template <typename T>
+int level_features(Ctx* c, const TreeBufs& tb, const Levels& lv, int64_t n, const vec4_t<T>* ws, double eps,
+                   double a, double prec, float* X);
+// argmax of the p and leaf scores of each row; choice_host receives rows x (p index, leaf index).
+void select_from_scores(Ctx* c, int rows, const float* Z, int* choice_dev, int* choice_host);
+// sums over the sample of |dv|^2, |v|^2, |ds|^2, |s|^2 (out_host[4]); synchronous.
+template <typename T>
+void sample_error(Ctx* c, int m, const int* idx, const vec4_t<T>* v4, const vec4_t<T>* s4, const double* dv,
+                  const double* ds, double* out_dev, double* out_host);
+
 // ---- RK4 (p2p.cu) ------------------------------------------------------------
 template <typename T>
 void run_rk4_stage(Ctx* c, int64_t n, const vec4_t<T>* x0, const vec4_t<T>* w0, const vec4_t<T>* kv,
