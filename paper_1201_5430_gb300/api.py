@@ -122,10 +122,30 @@ class LHV:
             "stage_launches": dict(zip(L.STAGES, list(s.stage_launches))),
             "kernel_launches": s.kernel_launches,
             "level_p": list(s.level_p)[: s.leaf_level + 1],
+            "launch_shape": {"p2p_targets_per_thread": s.tuned_p2p_targets_per_thread,
+                             "m2l_pairs_per_chunk": s.tuned_m2l_pairs_per_chunk,
+                             "m2l_tensor_cores": s.tuned_m2l_tensor_cores, "tune_ms": list(s.tune_ms)},
             "selector": {"leaf_max": s.selector_leaf_max, "selections": s.selector_selections,
                          "checks": s.selector_checks, "fallbacks": s.selector_fallbacks,
                          "err_v": s.selector_err_v, "err_s": s.selector_err_s},
         }
+
+    def autotune(self, x4, w4, offsets=None):
+        """lhv_autotune (or lhv_autotune_batched with host offsets): keeps the fastest launch shapes."""
+        self._elems(x4)
+        self._elems(w4)
+        v4, s4 = torch.empty_like(x4), torch.empty_like(x4)
+        if offsets is None:
+            self._check(self.lib.lhv_autotune(self.h, x4.shape[0], _ptr(x4), _ptr(w4), _ptr(v4), _ptr(s4)), "autotune")
+        else:
+            off = (ctypes.c_int64 * len(offsets))(*[int(o) for o in offsets])
+            self._check(self.lib.lhv_autotune_batched(self.h, len(offsets) - 1, off, _ptr(x4), _ptr(w4), _ptr(v4),
+                                                      _ptr(s4)), "autotune_batched")
+        return self.stats()["launch_shape"]
+
+    def set_launch_shape(self, p2p_targets_per_thread=1, m2l_pairs_per_chunk=0, m2l_tensor_cores=1):
+        self._check(self.lib.lhv_set_launch_shape(self.h, int(p2p_targets_per_thread), int(m2l_pairs_per_chunk),
+                                                  int(m2l_tensor_cores)), "set_launch_shape")
 
     def set_selector(self, W=None, b=None, eps=1e-6, check_every=1, check_samples=1000):
         """Switch the learned form on with network weights W (bfloat16 [LHV_MLP_NW]) and

@@ -52,6 +52,11 @@ struct Ctx {
     int eval_ld = 0;                    // their stride (reals per box)
     int leaf_override = 0;              // leaf cap chosen by the selector (0: cfg.leaf_max)
     bool tree_reuse = false;            // the next evaluation may use the tree just built for its inputs
+    // launch shapes chosen by lhv_autotune
+    int tune_tpt = 1;                   // P2P targets per thread
+    int tune_nc = 0;                    // M2L pairs per SIMT GEMM chunk (0: the largest that fits)
+    int tune_tc = 1;                    // TF32x3: M2L products on the tensor cores (1) or CUDA cores (0)
+    double tune_ms[8] = {0};            // measured stage times of the candidates
     // learned form (lhv_set_selector)
     bool sel_active = false;
     double sel_eps = 1e-6;
@@ -72,6 +77,9 @@ double ctx_rK(Ctx* c) { return c->rK; }
 Buf& ctx_tmp(Ctx* c, int i) { return c->tmp[i]; }
 bool ctx_use_tc(Ctx* c) { return c->cfg.precision == LHV_TF32X3; }
 int* ctx_err_flag(Ctx* c) { return reinterpret_cast<int*>(c->counters.as<unsigned long long>() + 2); }
+int ctx_p2p_tpt(Ctx* c) { return c->tune_tpt; }
+int ctx_m2l_nc(Ctx* c, int dflt) { return c->tune_nc > 0 && c->tune_nc < dflt ? c->tune_nc : dflt; }
+bool ctx_m2l_tc(Ctx* c) { return ctx_use_tc(c) && c->tune_tc != 0; }
 
 void cuda_check(cudaError_t e, const char* what) {
     if (e != cudaSuccess) throw Error{LHV_ECUDA, std::string(what) + ": " + cudaGetErrorString(e)};
@@ -296,9 +304,14 @@ static int evaluate(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const ve
                                        sizeof(T) * (size_t)(nbt - lv.off[2]) * pl.ld, c->stream),
                        "zero locals");
             int pmax = 1;
-            for (int l = 2; l <= L; ++l) pmax = std::max(pmax, pl.p[l]);
-            m2l_prepare(c, c->ops, c->tb, lv, c->table.as<int>(), c->gp_m2l, gemm_nc<T>(2 * pmax * pmax), pl.uniform,
-                        cnt + 1);
+            bool all_tc = sizeof(T) == 4 && ctx_m2l_tc(c);
+            for (int l = 2; l <= L; ++l) {
+                pmax = std::max(pmax, pl.p[l]);
+                all_tc = all_tc && pl.m2l_tiles[l];
+            }
+            // the tensor-core kernel takes 128 pairs per MMA; the CUDA-core kernel at most 64
+            const int nc = all_tc && c->tune_nc == 0 ? TC_PAIRS : ctx_m2l_nc(c, gemm_nc<T>(2 * pmax * pmax));
+            m2l_prepare(c, c->ops, c->tb, lv, c->table.as<int>(), c->gp_m2l, nc, pl.uniform, cnt + 1);
             StageScope sg(c, LHV_STAGE_M2L_PRODUCTS);
             m2l_apply<T>(c, pl, lv, c->gp_m2l, mult, loc);
         }
@@ -417,6 +430,79 @@ static int evaluate_selected(Ctx* c, int64_t n, const vec4_t<T>* x4, const vec4_
     ++c->sel_fallbacks;
     clear_schedule(c);
     return evaluate<T>(c, n, 1, off, x4, w4, v4, s4);
+}
+
+// ---- autotuner ---------------------------------------------------------------------
+// Times the launch-shape candidates on the caller's workload (stage times from CUDA
+// events, best of `reps` evaluations after one warm-up) and keeps the fastest:
+//   P2P: 1, 2 or 4 targets per thread (128, 64 or 32 threads per tile of 128 targets);
+//   M2L: 64, 32 or 16 pairs per CUDA-core GEMM chunk, and under TF32x3 the tensor-core
+//        kernel with 128 or 64 pairs per chunk.
+template <typename T, typename F>
+static void autotune(Ctx* c, F&& eval) {
+    const bool timing = c->timing;
+    const int reps = 3;
+    harvest(c);
+    double saved_ms[LHV_NUM_STAGES];
+    int64_t saved_n[LHV_NUM_STAGES];
+    for (int i = 0; i < LHV_NUM_STAGES; ++i) {
+        saved_ms[i] = c->stage_ms[i];
+        saved_n[i] = c->stage_launches[i];
+    }
+    c->timing = true;
+    auto measure = [&](int stage) {
+        eval();
+        harvest(c);
+        double best = 1e30;
+        for (int r = 0; r < reps; ++r) {
+            c->stage_ms[stage] = 0;
+            eval();
+            harvest(c);
+            best = std::min(best, c->stage_ms[stage]);
+        }
+        return best;
+    };
+    int k = 0;
+    double best = 1e30;
+    int best_tpt = 2;
+    for (int tpt : {1, 2, 4}) {
+        c->tune_tpt = tpt;
+        const double ms = measure(LHV_STAGE_P2P);
+        c->tune_ms[k++] = ms;
+        if (ms < best) {
+            best = ms;
+            best_tpt = tpt;
+        }
+    }
+    c->tune_tpt = best_tpt;
+    struct Cand {
+        int tc, nc;
+    };
+    std::vector<Cand> cands;
+    if (sizeof(T) == 4 && ctx_use_tc(c)) {
+        cands.push_back({1, 0});
+        cands.push_back({1, 64});
+    }
+    for (int nc : {64, 32, 16}) cands.push_back({0, nc});
+    best = 1e30;
+    Cand pick = cands.front();
+    for (const Cand& cd : cands) {
+        c->tune_tc = cd.tc;
+        c->tune_nc = cd.nc;
+        const double ms = measure(LHV_STAGE_M2L_PRODUCTS);
+        if (k < 8) c->tune_ms[k++] = ms;
+        if (ms < best) {
+            best = ms;
+            pick = cd;
+        }
+    }
+    c->tune_tc = pick.tc;
+    c->tune_nc = pick.nc;
+    for (int i = 0; i < LHV_NUM_STAGES; ++i) {
+        c->stage_ms[i] = saved_ms[i];
+        c->stage_launches[i] = saved_n[i];
+    }
+    c->timing = timing;
 }
 
 template <typename T>
@@ -791,6 +877,10 @@ int lhv_get_stats(lhv_ctx* ctx, lhv_stats* out) {
         out->selector_fallbacks = c.sel_fallbacks;
         out->selector_err_v = c.sel_err_v;
         out->selector_err_s = c.sel_err_s;
+        out->tuned_p2p_targets_per_thread = c.tune_tpt;
+        out->tuned_m2l_pairs_per_chunk = c.tune_nc;
+        out->tuned_m2l_tensor_cores = lhv::ctx_m2l_tc(&c) ? 1 : 0;
+        for (int i = 0; i < 8; ++i) out->tune_ms[i] = c.tune_ms[i];
         out->n = c.tree_n;
         if (c.counters.ptr) {
             unsigned long long h[3] = {0, 0, 0};
@@ -859,6 +949,54 @@ int lhv_selector_features(lhv_ctx* ctx, int64_t n, const float* x4, const float*
         if (capacity_rows < rows) return LHV_EINVAL;
         const double prec = c.cfg.precision == LHV_TF32X3 ? 0.5 : 0.0;
         lhv::level_features<float>(&c, c.tb, c.lv, n, c.ws.as<float4>(), eps, c.cfg.core_a, prec, X);
+        return LHV_OK;
+    });
+}
+
+int lhv_set_launch_shape(lhv_ctx* ctx, int p2p_targets_per_thread, int m2l_pairs_per_chunk, int m2l_tensor_cores) {
+    if (!ctx) return LHV_EINVAL;
+    const int t = p2p_targets_per_thread, nc = m2l_pairs_per_chunk;
+    if ((t != 1 && t != 2 && t != 4) || (nc != 0 && nc != 16 && nc != 32 && nc != 64) ||
+        (m2l_tensor_cores != 0 && m2l_tensor_cores != 1))
+        return LHV_EINVAL;
+    ctx->c.tune_tpt = t;
+    ctx->c.tune_nc = nc;
+    ctx->c.tune_tc = m2l_tensor_cores;
+    return LHV_OK;
+}
+
+int lhv_autotune(lhv_ctx* ctx, int64_t n, const float* x4, const float* w4, float* v4, float* s4) {
+    int st = check_elems(ctx, n, {x4, w4, v4, s4}, 16, LHV_FP32);
+    if (st != LHV_OK) return st;
+    if (n == 0) return LHV_OK;
+    return guarded(ctx, [&] {
+        Ctx& c = ctx->c;
+        const int64_t off[2] = {0, n};
+        lhv::autotune<float>(&c, [&] {
+            int r = lhv::evaluate<float>(&c, n, 1, off, reinterpret_cast<const float4*>(x4),
+                                         reinterpret_cast<const float4*>(w4), reinterpret_cast<float4*>(v4),
+                                         reinterpret_cast<float4*>(s4));
+            if (r != LHV_OK) throw Error{r, "autotune evaluation"};
+        });
+        return LHV_OK;
+    });
+}
+
+int lhv_autotune_batched(lhv_ctx* ctx, int nsys, const int64_t* offsets, const float* x4, const float* w4,
+                         float* v4, float* s4) {
+    int st = check_offsets(ctx, nsys, offsets);
+    if (st != LHV_OK) return st;
+    const int64_t n = offsets[nsys];
+    st = check_elems(ctx, n, {x4, w4, v4, s4}, 16, LHV_FP32);
+    if (st != LHV_OK || n == 0) return st;
+    return guarded(ctx, [&] {
+        Ctx& c = ctx->c;
+        lhv::autotune<float>(&c, [&] {
+            int r = lhv::evaluate<float>(&c, n, nsys, offsets, reinterpret_cast<const float4*>(x4),
+                                         reinterpret_cast<const float4*>(w4), reinterpret_cast<float4*>(v4),
+                                         reinterpret_cast<float4*>(s4));
+            if (r != LHV_OK) throw Error{r, "autotune evaluation"};
+        });
         return LHV_OK;
     });
 }

@@ -15,6 +15,7 @@ constexpr int KEY_BITS = 21;           // bits per axis of a Morton key
 constexpr int MAX_LEVELS = LHV_MAX_LEVELS;
 constexpr int NUM_OFFSETS = 316;       // M2L offsets: [-3,3]^3 minus [-1,1]^3
 constexpr int P2P_TILE = 128;          // targets per P2P work item
+constexpr int TC_PAIRS = 128;          // box pairs per tensor-core M2L chunk (the MMA's M)
 
 // 32-byte aligned four-double element (the _f64 element layout).
 struct alignas(32) dbl4 {
@@ -78,6 +79,9 @@ double ctx_rK(Ctx* c);
 Buf& ctx_tmp(Ctx* c, int i);                         // scratch buffers 0..11 owned by the context
 bool ctx_use_tc(Ctx* c);                             // LHV_TF32X3: dense maps on the tensor cores
 int* ctx_err_flag(Ctx* c);                           // device word set by a timed-out device wait
+int ctx_p2p_tpt(Ctx* c);                             // P2P targets per thread (autotuned; 1, 2 or 4)
+int ctx_m2l_nc(Ctx* c, int dflt);                    // M2L pairs per SIMT GEMM chunk (autotuned, <= dflt)
+bool ctx_m2l_tc(Ctx* c);                             // M2L products on the tensor cores (TF32x3, autotuned)
 
 inline int grid_for(int64_t n, int block, int cap = 152 * 32) {
     int64_t g = (n + block - 1) / block;

@@ -108,7 +108,7 @@ void m2l_apply(Ctx* c, const Plan<T>& pl, const Levels& lv, Grouped& gp, const T
         a.scale = (T)1;
         bool done = false;
         if constexpr (sizeof(T) == 4) {
-            if (ctx_use_tc(c) && pl.m2l_tiles[l0]) {
+            if (ctx_m2l_tc(c) && pl.m2l_tiles[l0]) {
                 run_tc_gemm(c, gp, a, pl.m2l_tiles[l0], ctx_err_flag(c));
                 done = true;
             }

@@ -388,16 +388,25 @@ void run_p2p(Ctx* c, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs, 
     work = reinterpret_cast<int*>(ctx_tmp(c, 6).ptr);
     cuda_check(cudaMemsetAsync(work, 0, 4, s), "p2p counter");
     const int64_t max_tiles = lv.nbox[L] + n / P2P_TILE + 1;
-    constexpr int TPT = 2;
-    auto kern = cc.smooth ? k_p2p<T, true, TPT> : k_p2p<T, false, TPT>;
-    int per_sm = 1, sms = 152, dev = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, P2P_TILE / TPT, 0);
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = (int)std::min<int64_t>(max_tiles, (int64_t)sms * std::max(per_sm, 1));
-    kern<<<grid, P2P_TILE / TPT, 0, s>>>(tb.tile_count.as<int>(), tb.tiles.as<int2>(), work, tb.bbeg.as<int>() + o,
-                                         tb.bend.as<int>() + o, tb.bcol.as<int>() + (int64_t)o * 27, xs, ws, perm,
-                                         vfar, sfar, v_out, s_out, cc, near ? 1 : 0, pair_counter);
+    // targets per thread: 1, 2 or 4 (128, 64 or 32 threads per tile of P2P_TILE targets)
+    auto launch = [&](auto tpt) {
+        constexpr int TPT = decltype(tpt)::value;
+        auto kern = cc.smooth ? k_p2p<T, true, TPT> : k_p2p<T, false, TPT>;
+        int per_sm = 1, sms = 152, dev = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, P2P_TILE / TPT, 0);
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int grid = (int)std::min<int64_t>(max_tiles, (int64_t)sms * std::max(per_sm, 1));
+        kern<<<grid, P2P_TILE / TPT, 0, s>>>(tb.tile_count.as<int>(), tb.tiles.as<int2>(), work,
+                                             tb.bbeg.as<int>() + o, tb.bend.as<int>() + o,
+                                             tb.bcol.as<int>() + (int64_t)o * 27, xs, ws, perm, vfar, sfar, v_out,
+                                             s_out, cc, near ? 1 : 0, pair_counter);
+    };
+    switch (ctx_p2p_tpt(c)) {
+        case 1: launch(std::integral_constant<int, 1>{}); break;
+        case 4: launch(std::integral_constant<int, 4>{}); break;
+        default: launch(std::integral_constant<int, 2>{}); break;
+    }
     count_launch(c);
     check_launch("p2p");
 }
