@@ -74,9 +74,13 @@ __device__ inline void for_each_Q(int p, T x, T y, T z, F&& f) {
 // ---------------------------------------------------------------------------
 constexpr int P2M_THREADS = 128;
 
+// Work items are the tiles of at most P2P_TILE consecutive elements of one leaf
+// (the near-field tiles), so a crowded leaf is spread over several blocks; each
+// block adds its partial W into the leaf's (zeroed) W with atomics.
 template <typename T>
-__global__ void __launch_bounds__(P2M_THREADS) k_p2m_w(int nleaf, int level, const uint64_t* __restrict__ bkey,
-                                                     const int* __restrict__ bbeg, const int* __restrict__ bend,
+__global__ void __launch_bounds__(P2M_THREADS) k_p2m_w(const int* __restrict__ ntiles_dev,
+                                                     const int2* __restrict__ tiles, int level,
+                                                     const uint64_t* __restrict__ bkey, const int* __restrict__ bend,
                                                      const SysCube* __restrict__ cubes,
                                                      const vec4_t<T>* __restrict__ xs,
                                                      const vec4_t<T>* __restrict__ ws, T* __restrict__ Wout, int p,
@@ -85,13 +89,15 @@ __global__ void __launch_bounds__(P2M_THREADS) k_p2m_w(int nleaf, int level, con
     const int P = p * p;
     T* gh = reinterpret_cast<T*>(smem_raw);  // [chunk][P]
     T* wk = gh + (size_t)chunk * P;          // [chunk][3]
-    for (int b = blockIdx.x; b < nleaf; b += gridDim.x) {
+    const int ntiles = *ntiles_dev;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int2 tw = tiles[t];
+        const int b = tw.x;
         double cx, cy, cz, h;
         box_geom(cubes, bkey[b], level, cx, cy, cz, h);
         const T invh = (T)(1.0 / h);
-        T* Wb = Wout + (int64_t)b * 3 * P;  // entry i is owned by thread i mod blockDim
-        for (int i = threadIdx.x; i < 3 * P; i += blockDim.x) Wb[i] = 0;
-        const int e0 = bbeg[b], e1 = bend[b];
+        T* Wb = Wout + (int64_t)b * 3 * P;
+        const int e0 = tw.y, e1 = min(bend[b], tw.y + P2P_TILE);
         for (int c0 = e0; c0 < e1; c0 += chunk) {
             const int ne = min(chunk, e1 - c0);
             __syncthreads();
@@ -124,7 +130,7 @@ __global__ void __launch_bounds__(P2M_THREADS) k_p2m_w(int nleaf, int level, con
                 const int k = i / P, j = i - k * P;
                 T s = 0;
                 for (int e = 0; e < ne; ++e) s += wk[e * 3 + k] * gh[(size_t)e * P + j];
-                Wb[i] += s;
+                atomicAdd(Wb + i, s);
             }
         }
         __syncthreads();
@@ -142,8 +148,10 @@ __global__ void __launch_bounds__(P2M_THREADS) k_p2m_w(int nleaf, int level, con
 constexpr int L2P_THREADS = 128;
 
 template <typename T>
-__global__ void __launch_bounds__(L2P_THREADS) k_l2p_eval(int nleaf, int level, const uint64_t* __restrict__ bkey,
-                                                        const int* __restrict__ bbeg, const int* __restrict__ bend,
+__global__ void __launch_bounds__(L2P_THREADS) k_l2p_eval(const int* __restrict__ ntiles_dev,
+                                                        const int2* __restrict__ tiles, int level,
+                                                        const uint64_t* __restrict__ bkey,
+                                                        const int* __restrict__ bend,
                                                         const SysCube* __restrict__ cubes,
                                                         const vec4_t<T>* __restrict__ xs,
                                                         const vec4_t<T>* __restrict__ ws, const T* __restrict__ cfg,
@@ -152,7 +160,10 @@ __global__ void __launch_bounds__(L2P_THREADS) k_l2p_eval(int nleaf, int level, 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int P = p * p;
     T* cf = reinterpret_cast<T*>(smem_raw);  // [P][12]
-    for (int b = blockIdx.x; b < nleaf; b += gridDim.x) {
+    const int ntiles = *ntiles_dev;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int2 tw = tiles[t];
+        const int b = tw.x;
         double cx, cy, cz, h;
         box_geom(cubes, bkey[b], level, cx, cy, cz, h);
         __syncthreads();
@@ -163,7 +174,8 @@ __global__ void __launch_bounds__(L2P_THREADS) k_l2p_eval(int nleaf, int level, 
         }
         __syncthreads();
         const T invh = (T)(1.0 / h);
-        for (int e = bbeg[b] + threadIdx.x; e < bend[b]; e += blockDim.x) {
+        const int e1 = min(bend[b], tw.y + P2P_TILE);
+        for (int e = tw.y + threadIdx.x; e < e1; e += blockDim.x) {
             vec4_t<T> xv = xs[e], wv = ws[e];
             const T rx = (T)(((double)xv.x - cx) / h), ry = (T)(((double)xv.y - cy) / h),
                     rz = (T)(((double)xv.z - cz) / h);
@@ -220,9 +232,11 @@ void run_p2m(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, co
     chunk = std::max(32, chunk / 32 * 32);
     const size_t smem = sizeof(T) * (size_t)chunk * (P + 3);
     cuda_check(cudaFuncSetAttribute(k_p2m_w<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "p2m attr");
-    k_p2m_w<T><<<grid_for(nl, 1, 152 * 16), P2M_THREADS, smem, stream_of(c)>>>(
-        nl, L, tb.bkey.as<uint64_t>() + o, tb.bbeg.as<int>() + o, tb.bend.as<int>() + o, tb.cubes.as<SysCube>(), xs,
-        ws, W, p, chunk);
+    cuda_check(cudaMemsetAsync(W, 0, sizeof(T) * (size_t)nl * 3 * P, stream_of(c)), "p2m zero");
+    const int64_t max_tiles = nl + lv.n / P2P_TILE + 1;
+    k_p2m_w<T><<<grid_for(max_tiles, 1, 152 * 16), P2M_THREADS, smem, stream_of(c)>>>(
+        tb.tile_count.as<int>(), tb.tiles.as<int2>(), L, tb.bkey.as<uint64_t>() + o, tb.bend.as<int>() + o,
+        tb.cubes.as<SysCube>(), xs, ws, W, p, chunk);
     count_launch(c);
     check_launch("p2m w");
     build_grouped(c, gp, 1, nl, nl, gemm_nc<T>(3 * P), IdentItems{0, o});
@@ -343,9 +357,10 @@ void run_l2p(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, co
     run_group_gemm<T>(c, gp, a);
     const size_t smem = sizeof(T) * 12 * P;
     cuda_check(cudaFuncSetAttribute(k_l2p_eval<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "l2p attr");
-    k_l2p_eval<T><<<grid_for(nl, 1, 152 * 16), L2P_THREADS, smem, stream_of(c)>>>(
-        nl, L, tb.bkey.as<uint64_t>() + o, tb.bbeg.as<int>() + o, tb.bend.as<int>() + o, tb.cubes.as<SysCube>(), xs,
-        ws, cf, vfar, sfar, p);
+    const int64_t max_tiles = nl + lv.n / P2P_TILE + 1;
+    k_l2p_eval<T><<<grid_for(max_tiles, 1, 152 * 16), L2P_THREADS, smem, stream_of(c)>>>(
+        tb.tile_count.as<int>(), tb.tiles.as<int2>(), L, tb.bkey.as<uint64_t>() + o, tb.bend.as<int>() + o,
+        tb.cubes.as<SysCube>(), xs, ws, cf, vfar, sfar, p);
     count_launch(c);
     check_launch("l2p");
 }

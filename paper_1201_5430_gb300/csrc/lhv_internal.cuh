@@ -63,6 +63,7 @@ struct Levels {
     int nbox[MAX_LEVELS] = {0};
     int off[MAX_LEVELS + 1] = {0};   // global box index of the first box of each level
     int cap_off[MAX_LEVELS + 1] = {0};
+    int64_t n = 0;                   // elements of the tree
 };
 
 struct Ctx;

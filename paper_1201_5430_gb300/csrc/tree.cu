@@ -568,6 +568,7 @@ int build_tree(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const vec4_t<
     }
     const int L = hp.L;
     lv.L = L;
+    lv.n = nn;
     hp.bits = bits;
     hp.nsys = nsys;
 
