@@ -239,7 +239,7 @@ void run_p2m(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, co
         tb.cubes.as<SysCube>(), xs, ws, W, p, chunk);
     count_launch(c);
     check_launch("p2m w");
-    build_grouped(c, gp, 1, nl, nl, gemm_nc<T>(3 * P), IdentItems{0, o});
+    build_grouped(c, gp, 1, nl, nl, gemm_nc_for<T>(3 * P, 2 * P, nl), IdentItems{0, o});
     GemmArgs<T> a{};
     a.g0 = 0;
     a.g1 = 1;
@@ -254,6 +254,7 @@ void run_p2m(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, co
     a.ldout = pl.ld;
     a.mode = GEMM_STORE;
     a.scale = (T)1;  // the 1/h of each leaf is applied to W
+    a.pairs_hint = nl;
     run_group_gemm<T>(c, gp, a);
 }
 
@@ -274,7 +275,7 @@ template <typename T>
 static int oct_nc(const Plan<T>& pl) {
     int pmax = 1;
     for (int l = 2; l <= pl.L; ++l) pmax = std::max(pmax, pl.p[l]);
-    return gemm_nc<T>(2 * pmax * pmax);
+    return std::min(16, gemm_nc<T>(2 * pmax * pmax));  // levels hold few boxes: many short items
 }
 
 template <typename T>
@@ -304,6 +305,7 @@ void run_m2m(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, Gr
         a.ldout = pl.ld;
         a.mode = GEMM_ATOMIC;
         a.scale = (T)1;
+        a.pairs_hint = lv.nbox[l + 1];
         run_group_gemm<T>(c, gp, a);
     }
 }
@@ -331,6 +333,7 @@ void run_l2l(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, Gr
         a.ldout = pl.ld;
         a.mode = GEMM_ADD;
         a.scale = (T)1;
+        a.pairs_hint = lv.nbox[l + 1];
         run_group_gemm<T>(c, gp, a);
     }
 }
@@ -339,7 +342,7 @@ template <typename T>
 void run_l2p(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs,
              const vec4_t<T>* ws, const T* loc, T* cf, Grouped& gp, vec4_t<T>* vfar, vec4_t<T>* sfar) {
     const int L = lv.L, nl = lv.nbox[L], o = lv.off[L], p = pl.p[L], P = p * p;
-    build_grouped(c, gp, 1, nl, nl, gemm_nc<T>(2 * P), IdentItems{o, 0});
+    build_grouped(c, gp, 1, nl, nl, gemm_nc_for<T>(2 * P, 12 * P, nl), IdentItems{o, 0});
     GemmArgs<T> a{};
     a.g0 = 0;
     a.g1 = 1;
@@ -354,6 +357,7 @@ void run_l2p(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, co
     a.ldout = 12 * P;
     a.mode = GEMM_STORE;
     a.scale = (T)1;
+    a.pairs_hint = nl;
     run_group_gemm<T>(c, gp, a);
     const size_t smem = sizeof(T) * 12 * P;
     cuda_check(cudaFuncSetAttribute(k_l2p_eval<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "l2p attr");

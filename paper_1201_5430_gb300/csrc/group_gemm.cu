@@ -230,6 +230,23 @@ int gemm_nc(int C) {
 }
 
 template <typename T>
+int gemm_nc_for(int C, int R, int64_t pairs) {
+    // the widest chunk that still gives every SM a few (chunk, 32-row tile) items
+    const int64_t row_tiles = (R + 31) / 32;
+    const int fit = gemm_nc<T>(C);
+    for (int nc : {64, 32})
+        if (nc <= fit && (pairs / nc) * row_tiles >= 4 * 152) return nc;
+    return 16;
+}
+
+template <int NC, typename T>
+static void launch_tm(Ctx* c, const GemmArgs<T>& a, int tm) {
+    if (tm == 8) launch_gemm<T, NC, 8>(c, a);
+    else if (tm == 4) launch_gemm<T, NC, 4>(c, a);
+    else launch_gemm<T, NC, 2>(c, a);
+}
+
+template <typename T>
 void run_group_gemm(Ctx* c, Grouped& gp, GemmArgs<T> a) {
     a.chunks = gp.chunks.as<int4>();
     a.pairs = gp.pairs.as<int2>();
@@ -237,13 +254,22 @@ void run_group_gemm(Ctx* c, Grouped& gp, GemmArgs<T> a) {
     a.work = gp.work.as<int>();
     cuda_check(cudaMemsetAsync(a.work, 0, 4, stream_of(c)), "gemm work");
     const int nc = gp.nc;
-    if (nc == 64) launch_gemm<T, 64, 8>(c, a);
-    else if (nc == 32) launch_gemm<T, 32, 8>(c, a);
-    else launch_gemm<T, 16, 8>(c, a);
+    // rows per tile 16 TM: the tallest tile that still leaves every SM a few work items
+    // (a small level's few chunks would otherwise run as a handful of long serial tiles)
+    int tm = 8;
+    if (a.pairs_hint > 0) {
+        const int64_t chunks = a.pairs_hint / nc + (a.g1 - a.g0);
+        while (tm > 2 && chunks * ((a.R + 16 * tm - 1) / (16 * tm)) < 4 * 152) tm /= 2;
+    }
+    if (nc == 64) launch_tm<64>(c, a, tm);
+    else if (nc == 32) launch_tm<32>(c, a, tm);
+    else launch_tm<16>(c, a, tm);
 }
 
 template int gemm_nc<float>(int);
 template int gemm_nc<double>(int);
+template int gemm_nc_for<float>(int, int, int64_t);
+template int gemm_nc_for<double>(int, int, int64_t);
 template void run_group_gemm<float>(Ctx*, Grouped&, GemmArgs<float>);
 template void run_group_gemm<double>(Ctx*, Grouped&, GemmArgs<double>);
 

@@ -36,6 +36,7 @@ struct GemmArgs {
     int64_t ldout;
     int mode;             // GemmMode
     T scale;
+    int64_t pairs_hint;   // about how many pairs this launch covers (0: unknown); picks the tile height
 };
 
 // Items -> bucketed pairs.  An item functor `it(i, g, src, dst)` returns false
@@ -80,6 +81,9 @@ void build_grouped(Ctx* c, Grouped& gp, int ngroups, int64_t nitems, int64_t max
 
 template <typename T>
 int gemm_nc(int C);
+// chunk width for about `pairs` pairs of an R x C map: narrower chunks when there are few
+template <typename T>
+int gemm_nc_for(int C, int R, int64_t pairs);
 
 template <typename T>
 void run_group_gemm(Ctx* c, Grouped& gp, GemmArgs<T> a);

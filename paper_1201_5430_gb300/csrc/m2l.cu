@@ -15,43 +15,43 @@ namespace lhv {
 
 namespace {
 
-// table[t][slot] = GLOBAL index of the source box at offset `slot`, or -1.
+__device__ inline void key_coords(uint64_t key, int level, int& x, int& y, int& z) {
+    x = y = z = 0;
+    for (int k = 0; k < level; ++k) {
+        x |= (int)((key >> (3 * k)) & 1ull) << k;
+        y |= (int)((key >> (3 * k + 1)) & 1ull) << k;
+        z |= (int)((key >> (3 * k + 2)) & 1ull) << k;
+    }
+}
+
+// table[t][slot] = GLOBAL index of the source box at offset `slot`, or -1 (the
+// table is cleared to -1 before).  One thread per (target box, colleague q of its
+// parent): the children of that colleague that are not colleagues of the target.
 __global__ void k_m2l_table(int nb, int level, int off_l, const uint64_t* __restrict__ bkey,
                             const int* __restrict__ bparent, const int* __restrict__ pcol,
                             const int* __restrict__ pcbeg, const int* __restrict__ pcend,
                             const int* __restrict__ slot_of, int* __restrict__ table,
                             unsigned long long* __restrict__ pairs) {
     unsigned long long cnt = 0;
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+    for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < (int64_t)nb * 27;
+         it += (int64_t)gridDim.x * blockDim.x) {
+        const int b = (int)(it / 27), q = (int)(it - (int64_t)b * 27);
+        const int pc = pcol[(int64_t)bparent[b] * 27 + q];
+        if (pc < 0) continue;
+        int tx, ty, tz;
+        key_coords(bkey[b], level, tx, ty, tz);
         int* row = table + (int64_t)b * NUM_OFFSETS;
-        for (int s = 0; s < NUM_OFFSETS; ++s) row[s] = -1;
-        const uint64_t key = bkey[b];
-        int tx = 0, ty = 0, tz = 0;
-        for (int k = 0; k < level; ++k) {
-            tx |= (int)((key >> (3 * k)) & 1ull) << k;
-            ty |= (int)((key >> (3 * k + 1)) & 1ull) << k;
-            tz |= (int)((key >> (3 * k + 2)) & 1ull) << k;
-        }
-        const int par = bparent[b];
-        for (int q = 0; q < 27; ++q) {
-            const int pc = pcol[(int64_t)par * 27 + q];
-            if (pc < 0) continue;
-            for (int s = pcbeg[pc]; s < pcend[pc]; ++s) {
-                const uint64_t sk = bkey[s];
-                int sx = 0, sy = 0, sz = 0;
-                for (int k = 0; k < level; ++k) {
-                    sx |= (int)((sk >> (3 * k)) & 1ull) << k;
-                    sy |= (int)((sk >> (3 * k + 1)) & 1ull) << k;
-                    sz |= (int)((sk >> (3 * k + 2)) & 1ull) << k;
-                }
-                const int dx = sx - tx, dy = sy - ty, dz = sz - tz;
-                if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1) continue;
-                row[slot_of[(dx + 3) * 49 + (dy + 3) * 7 + (dz + 3)]] = off_l + s;
-                ++cnt;
-            }
+        for (int s = pcbeg[pc]; s < pcend[pc]; ++s) {
+            int sx, sy, sz;
+            key_coords(bkey[s], level, sx, sy, sz);
+            const int dx = sx - tx, dy = sy - ty, dz = sz - tz;
+            if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1) continue;
+            row[slot_of[(dx + 3) * 49 + (dy + 3) * 7 + (dz + 3)]] = off_l + s;
+            ++cnt;
         }
     }
-    if (cnt) atomicAdd(pairs, cnt);
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(pairs, cnt);
 }
 
 }  // namespace
@@ -62,9 +62,11 @@ void m2l_prepare(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& 
     const int L = lv.L;
     // table rows for the global boxes [off[2], off[L+1])
     const int t0 = lv.off[2];
+    cuda_check(cudaMemsetAsync(table, 0xff, sizeof(int) * (size_t)(lv.off[L + 1] - t0) * NUM_OFFSETS, s),
+               "m2l table clear");
     for (int l = 2; l <= L; ++l) {
         const int nb = lv.nbox[l], o = lv.off[l], po = lv.off[l - 1];
-        k_m2l_table<<<grid_for(nb, 128), 128, 0, s>>>(
+        k_m2l_table<<<grid_for((int64_t)nb * 27, 128), 128, 0, s>>>(
             nb, l, o, tb.bkey.as<uint64_t>() + o, tb.bparent.as<int>() + o, tb.bcol.as<int>() + (int64_t)po * 27,
             tb.bcbeg.as<int>() + po, tb.bcend.as<int>() + po, ops.slot_of.as<int>(),
             table + (int64_t)(o - t0) * NUM_OFFSETS, pair_counter);
