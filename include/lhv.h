@@ -112,13 +112,15 @@ typedef struct {
     double  selector_err_v, selector_err_s;  /* relative L2 error of v and s on the sample at the
                                                 last check (-1: none) */
     int     tuned_p2p_targets_per_thread;    /* launch shapes in use (lhv_autotune) */
+    int     tuned_p2p_sources_per_stage;
     int     tuned_m2l_pairs_per_chunk;       /* 0: the default (128 on the tensor cores, else
                                                 the largest CUDA-core chunk that fits) */
     int     tuned_m2l_tensor_cores;          /* 1 when M2L runs on the tensor cores */
-    double  tune_ms[8];                      /* stage times of the candidates, in the order
-                                                P2P 1/2/4 targets per thread, then M2L: (TF32x3
-                                                only: tensor cores 128, 64 pairs,) CUDA cores
-                                                64, 32, 16 pairs */
+    double  tune_ms[12];                     /* stage times of the candidates, in the order
+                                                P2P 1/2/4 targets per thread at 128 sources per
+                                                stage, the same at 256, then M2L: (TF32x3 only:
+                                                tensor cores 128, 64 pairs,) CUDA cores 64, 32,
+                                                16 pairs */
 } lhv_stats;
 
 /* Create a context for one configuration on one CUDA stream (a cudaStream_t,
@@ -188,21 +190,24 @@ int lhv_direct_sampled_f64(lhv_ctx* ctx, int64_t n, const double* x4, const doub
                            double* v4, double* s4);
 
 /* Autotuner (launch shapes, not in the paper): runs the evaluation of the given
- * elements once per candidate and keeps, for this context, the fastest P2P
- * work split (1, 2 or 4 targets per thread over tiles of 128 targets; the
- * sources are staged 128 at a time) and the fastest M2L grouping (box pairs of
- * one offset per GEMM chunk: 64, 32 or 16 on the CUDA cores; under TF32X3 also
- * the tensor-core kernel with 128 or 64 pairs per chunk), judged by CUDA-event
- * stage times (best of 3 after a warm-up).  v4 and s4 receive the last
- * evaluation.  The batched twin tunes on a batch (offsets as for
- * lhv_evaluate_batched).  Results do not depend on the choice beyond rounding. */
+ * elements once per candidate and keeps, for this context, the fastest P2P tile
+ * shape (1, 2 or 4 targets per thread over tiles of 128 targets, i.e. 128, 64 or
+ * 32 threads, times 128 or 256 sources staged in shared memory per step) and the
+ * fastest M2L grouping (box pairs of one offset per GEMM chunk: 64, 32 or 16 on
+ * the CUDA cores; under TF32X3 also the tensor-core kernel with 128 or 64 pairs
+ * per chunk), judged by CUDA-event stage times (best of 3 after a warm-up).  v4
+ * and s4 receive the last evaluation.  The batched twin tunes on a batch
+ * (offsets as for lhv_evaluate_batched).  Results do not depend on the choice
+ * beyond rounding. */
 int lhv_autotune(lhv_ctx* ctx, int64_t n, const float* x4, const float* w4, float* v4, float* s4);
-/* Set the launch shapes directly: P2P targets per thread (1, 2, 4), M2L pairs per
- * CUDA-core chunk (16, 32, 64, or 0 for the default), M2L on the tensor cores
- * (1) or not (0; only TF32X3 contexts use them).  LHV_EINVAL otherwise. */
-int lhv_set_launch_shape(lhv_ctx* ctx, int p2p_targets_per_thread, int m2l_pairs_per_chunk, int m2l_tensor_cores);
 int lhv_autotune_batched(lhv_ctx* ctx, int nsys, const int64_t* offsets, const float* x4, const float* w4,
                          float* v4, float* s4);
+/* Set the launch shapes directly: P2P targets per thread (1, 2, 4) and sources per
+ * stage (128, 256), M2L pairs per CUDA-core chunk (16, 32, 64, or 0 for the
+ * default), M2L on the tensor cores (1) or not (0; only TF32X3 contexts use
+ * them).  LHV_EINVAL otherwise. */
+int lhv_set_launch_shape(lhv_ctx* ctx, int p2p_targets_per_thread, int p2p_sources_per_stage,
+                         int m2l_pairs_per_chunk, int m2l_tensor_cores);
 
 /* Truncation number per octree level (variable truncation, which the paper
  * mentions but does not use, Sec. 5).  p[l] for the levels l < nlevels (host

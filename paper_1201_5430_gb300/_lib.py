@@ -30,8 +30,9 @@ class Stats(ctypes.Structure):
                 ("selector_selections", ctypes.c_int64), ("selector_checks", ctypes.c_int64),
                 ("selector_fallbacks", ctypes.c_int64), ("selector_err_v", ctypes.c_double),
                 ("selector_err_s", ctypes.c_double), ("tuned_p2p_targets_per_thread", ctypes.c_int),
+                ("tuned_p2p_sources_per_stage", ctypes.c_int),
                 ("tuned_m2l_pairs_per_chunk", ctypes.c_int), ("tuned_m2l_tensor_cores", ctypes.c_int),
-                ("tune_ms", ctypes.c_double * 8)]
+                ("tune_ms", ctypes.c_double * 12)]
 
 
 # exported function -> (restype, argtypes); every name here is declared in include/lhv.h
@@ -51,7 +52,7 @@ SIGNATURES = {
     "lhv_set_level_p": (_int, [_vp, ctypes.POINTER(_int), _int]),
     "lhv_autotune": (_int, [_vp, _i64, _vp, _vp, _vp, _vp]),
     "lhv_autotune_batched": (_int, [_vp, _int, ctypes.POINTER(_i64), _vp, _vp, _vp, _vp]),
-    "lhv_set_launch_shape": (_int, [_vp, _int, _int, _int]),
+    "lhv_set_launch_shape": (_int, [_vp, _int, _int, _int, _int]),
     "lhv_set_selector": (_int, [_vp, _vp, _vp, _dbl, _int, _int]),
     "lhv_selector_features": (_int, [_vp, _i64, _vp, _vp, _dbl, _vp, _int, ctypes.POINTER(_int)]),
     "lhv_mlp_forward": (_int, [_int, _vp, _vp, _vp, _vp, _vp]),

@@ -123,6 +123,7 @@ class LHV:
             "kernel_launches": s.kernel_launches,
             "level_p": list(s.level_p)[: s.leaf_level + 1],
             "launch_shape": {"p2p_targets_per_thread": s.tuned_p2p_targets_per_thread,
+                             "p2p_sources_per_stage": s.tuned_p2p_sources_per_stage,
                              "m2l_pairs_per_chunk": s.tuned_m2l_pairs_per_chunk,
                              "m2l_tensor_cores": s.tuned_m2l_tensor_cores, "tune_ms": list(s.tune_ms)},
             "selector": {"leaf_max": s.selector_leaf_max, "selections": s.selector_selections,
@@ -143,9 +144,11 @@ class LHV:
                                                       _ptr(s4)), "autotune_batched")
         return self.stats()["launch_shape"]
 
-    def set_launch_shape(self, p2p_targets_per_thread=1, m2l_pairs_per_chunk=0, m2l_tensor_cores=1):
-        self._check(self.lib.lhv_set_launch_shape(self.h, int(p2p_targets_per_thread), int(m2l_pairs_per_chunk),
-                                                  int(m2l_tensor_cores)), "set_launch_shape")
+    def set_launch_shape(self, p2p_targets_per_thread=1, m2l_pairs_per_chunk=0, m2l_tensor_cores=1,
+                         p2p_sources_per_stage=128):
+        self._check(self.lib.lhv_set_launch_shape(self.h, int(p2p_targets_per_thread), int(p2p_sources_per_stage),
+                                                  int(m2l_pairs_per_chunk), int(m2l_tensor_cores)),
+                    "set_launch_shape")
 
     def set_selector(self, W=None, b=None, eps=1e-6, check_every=1, check_samples=1000):
         """Switch the learned form on with network weights W (bfloat16 [LHV_MLP_NW]) and

@@ -54,9 +54,10 @@ struct Ctx {
     bool tree_reuse = false;            // the next evaluation may use the tree just built for its inputs
     // launch shapes chosen by lhv_autotune
     int tune_tpt = 1;                   // P2P targets per thread
+    int tune_ch = 128;                  // P2P sources per shared-memory stage
     int tune_nc = 0;                    // M2L pairs per SIMT GEMM chunk (0: the largest that fits)
     int tune_tc = 1;                    // TF32x3: M2L products on the tensor cores (1) or CUDA cores (0)
-    double tune_ms[8] = {0};            // measured stage times of the candidates
+    double tune_ms[12] = {0};           // measured stage times of the candidates
     // learned form (lhv_set_selector)
     bool sel_active = false;
     double sel_eps = 1e-6;
@@ -78,6 +79,7 @@ Buf& ctx_tmp(Ctx* c, int i) { return c->tmp[i]; }
 bool ctx_use_tc(Ctx* c) { return c->cfg.precision == LHV_TF32X3; }
 int* ctx_err_flag(Ctx* c) { return reinterpret_cast<int*>(c->counters.as<unsigned long long>() + 2); }
 int ctx_p2p_tpt(Ctx* c) { return c->tune_tpt; }
+int ctx_p2p_sources(Ctx* c) { return c->tune_ch; }
 int ctx_m2l_nc(Ctx* c, int dflt) { return c->tune_nc > 0 && c->tune_nc < dflt ? c->tune_nc : dflt; }
 bool ctx_m2l_tc(Ctx* c) { return ctx_use_tc(c) && c->tune_tc != 0; }
 
@@ -464,17 +466,21 @@ static void autotune(Ctx* c, F&& eval) {
     };
     int k = 0;
     double best = 1e30;
-    int best_tpt = 2;
-    for (int tpt : {1, 2, 4}) {
-        c->tune_tpt = tpt;
-        const double ms = measure(LHV_STAGE_P2P);
-        c->tune_ms[k++] = ms;
-        if (ms < best) {
-            best = ms;
-            best_tpt = tpt;
+    int best_tpt = 1, best_ch = 128;
+    for (int ch : {128, 256})
+        for (int tpt : {1, 2, 4}) {
+            c->tune_tpt = tpt;
+            c->tune_ch = ch;
+            const double ms = measure(LHV_STAGE_P2P);
+            c->tune_ms[k++] = ms;
+            if (ms < best) {
+                best = ms;
+                best_tpt = tpt;
+                best_ch = ch;
+            }
         }
-    }
     c->tune_tpt = best_tpt;
+    c->tune_ch = best_ch;
     struct Cand {
         int tc, nc;
     };
@@ -490,7 +496,7 @@ static void autotune(Ctx* c, F&& eval) {
         c->tune_tc = cd.tc;
         c->tune_nc = cd.nc;
         const double ms = measure(LHV_STAGE_M2L_PRODUCTS);
-        if (k < 8) c->tune_ms[k++] = ms;
+        if (k < 12) c->tune_ms[k++] = ms;
         if (ms < best) {
             best = ms;
             pick = cd;
@@ -878,9 +884,10 @@ int lhv_get_stats(lhv_ctx* ctx, lhv_stats* out) {
         out->selector_err_v = c.sel_err_v;
         out->selector_err_s = c.sel_err_s;
         out->tuned_p2p_targets_per_thread = c.tune_tpt;
+        out->tuned_p2p_sources_per_stage = c.tune_ch;
         out->tuned_m2l_pairs_per_chunk = c.tune_nc;
         out->tuned_m2l_tensor_cores = lhv::ctx_m2l_tc(&c) ? 1 : 0;
-        for (int i = 0; i < 8; ++i) out->tune_ms[i] = c.tune_ms[i];
+        for (int i = 0; i < 12; ++i) out->tune_ms[i] = c.tune_ms[i];
         out->n = c.tree_n;
         if (c.counters.ptr) {
             unsigned long long h[3] = {0, 0, 0};
@@ -953,13 +960,15 @@ int lhv_selector_features(lhv_ctx* ctx, int64_t n, const float* x4, const float*
     });
 }
 
-int lhv_set_launch_shape(lhv_ctx* ctx, int p2p_targets_per_thread, int m2l_pairs_per_chunk, int m2l_tensor_cores) {
+int lhv_set_launch_shape(lhv_ctx* ctx, int p2p_targets_per_thread, int p2p_sources_per_stage,
+                         int m2l_pairs_per_chunk, int m2l_tensor_cores) {
     if (!ctx) return LHV_EINVAL;
     const int t = p2p_targets_per_thread, nc = m2l_pairs_per_chunk;
-    if ((t != 1 && t != 2 && t != 4) || (nc != 0 && nc != 16 && nc != 32 && nc != 64) ||
-        (m2l_tensor_cores != 0 && m2l_tensor_cores != 1))
+    if ((t != 1 && t != 2 && t != 4) || (p2p_sources_per_stage != 128 && p2p_sources_per_stage != 256) ||
+        (nc != 0 && nc != 16 && nc != 32 && nc != 64) || (m2l_tensor_cores != 0 && m2l_tensor_cores != 1))
         return LHV_EINVAL;
     ctx->c.tune_tpt = t;
+    ctx->c.tune_ch = p2p_sources_per_stage;
     ctx->c.tune_nc = nc;
     ctx->c.tune_tc = m2l_tensor_cores;
     return LHV_OK;

@@ -81,6 +81,7 @@ Buf& ctx_tmp(Ctx* c, int i);                         // scratch buffers 0..11 ow
 bool ctx_use_tc(Ctx* c);                             // LHV_TF32X3: dense maps on the tensor cores
 int* ctx_err_flag(Ctx* c);                           // device word set by a timed-out device wait
 int ctx_p2p_tpt(Ctx* c);                             // P2P targets per thread (autotuned; 1, 2 or 4)
+int ctx_p2p_sources(Ctx* c);                         // P2P sources per shared-memory stage (128 or 256)
 int ctx_m2l_nc(Ctx* c, int dflt);                    // M2L pairs per SIMT GEMM chunk (autotuned, <= dflt)
 bool ctx_m2l_tc(Ctx* c);                             // M2L products on the tensor cores (TF32x3, autotuned)
 

@@ -139,10 +139,11 @@ __device__ inline void two_sum_acc(T& hi, T& lo, T a) {
     lo += err;
 }
 
-// TPT targets per thread; a tile is P2P_TILE consecutive targets of one leaf.
-// Accumulation is blocked: plain sums over each chunk of P2P_TILE sources, then
-// a compensated (TwoSum) add of the chunk sums into per-target totals.
-template <typename T, bool SMOOTH, int TPT>
+// TPT targets per thread; a tile is P2P_TILE consecutive targets of one leaf;
+// CH sources are staged in shared memory per step.  Accumulation is blocked:
+// plain sums over each chunk of CH sources, then a compensated (TwoSum) add of
+// the chunk sums into per-target totals.
+template <typename T, bool SMOOTH, int TPT, int CH>
 __global__ void __launch_bounds__(P2P_TILE / TPT) k_p2p(const int* __restrict__ ntiles_dev,
                                                        const int2* __restrict__ tiles, int* __restrict__ work,
                                                        const int* __restrict__ bbeg, const int* __restrict__ bend,
@@ -156,7 +157,6 @@ __global__ void __launch_bounds__(P2P_TILE / TPT) k_p2p(const int* __restrict__ 
                                                        CoreConsts<T> cc, int near,
                                                        unsigned long long* __restrict__ pairs) {
     constexpr int NT = P2P_TILE / TPT;   // threads
-    constexpr int CH = P2P_TILE;         // sources staged per step
     constexpr int NA = 9;                // accumulators per target: v (3), sum f w_j (3), g-terms (3)
     __shared__ vec4_t<T> sx[CH];
     __shared__ vec4_t<T> sw[CH];
@@ -388,10 +388,12 @@ void run_p2p(Ctx* c, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs, 
     work = reinterpret_cast<int*>(ctx_tmp(c, 6).ptr);
     cuda_check(cudaMemsetAsync(work, 0, 4, s), "p2p counter");
     const int64_t max_tiles = lv.nbox[L] + n / P2P_TILE + 1;
-    // targets per thread: 1, 2 or 4 (128, 64 or 32 threads per tile of P2P_TILE targets)
-    auto launch = [&](auto tpt) {
+    // targets per thread: 1, 2 or 4 (128, 64 or 32 threads per tile of P2P_TILE targets);
+    // sources per shared-memory stage: 128 or 256
+    auto launch = [&](auto tpt, auto ch) {
         constexpr int TPT = decltype(tpt)::value;
-        auto kern = cc.smooth ? k_p2p<T, true, TPT> : k_p2p<T, false, TPT>;
+        constexpr int CH = decltype(ch)::value;
+        auto kern = cc.smooth ? k_p2p<T, true, TPT, CH> : k_p2p<T, false, TPT, CH>;
         int per_sm = 1, sms = 152, dev = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, P2P_TILE / TPT, 0);
         cudaGetDevice(&dev);
@@ -402,10 +404,16 @@ void run_p2p(Ctx* c, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs, 
                                              tb.bcol.as<int>() + (int64_t)o * 27, xs, ws, perm, vfar, sfar, v_out,
                                              s_out, cc, near ? 1 : 0, pair_counter);
     };
+    using I1 = std::integral_constant<int, 1>;
+    using I2 = std::integral_constant<int, 2>;
+    using I4 = std::integral_constant<int, 4>;
+    using C128 = std::integral_constant<int, 128>;
+    using C256 = std::integral_constant<int, 256>;
+    const bool wide = ctx_p2p_sources(c) == 256;
     switch (ctx_p2p_tpt(c)) {
-        case 1: launch(std::integral_constant<int, 1>{}); break;
-        case 4: launch(std::integral_constant<int, 4>{}); break;
-        default: launch(std::integral_constant<int, 2>{}); break;
+        case 2: wide ? launch(I2{}, C256{}) : launch(I2{}, C128{}); break;
+        case 4: wide ? launch(I4{}, C256{}) : launch(I4{}, C128{}); break;
+        default: wide ? launch(I1{}, C256{}) : launch(I1{}, C128{}); break;
     }
     count_launch(c);
     check_launch("p2p");

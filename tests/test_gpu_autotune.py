@@ -19,17 +19,19 @@ def ring():
 
 
 @pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
-@pytest.mark.parametrize("tpt,nc,tc", [(1, 0, 1), (2, 16, 0), (4, 32, 0), (2, 64, 1), (4, 0, 0)])
-def test_every_launch_shape_matches_the_oracle(ring, prec, tpt, nc, tc):
+@pytest.mark.parametrize("tpt,ch,nc,tc", [(1, 128, 0, 1), (2, 256, 16, 0), (4, 128, 32, 0), (2, 128, 64, 1),
+                                          (4, 256, 0, 0), (1, 256, 0, 1)])
+def test_every_launch_shape_matches_the_oracle(ring, prec, tpt, ch, nc, tc):
     from paper_1201_5430_gb300 import LHV
     x, w, a, ref = ring
     ctx = LHV(p=12, leaf_max=64, core_a=a, precision=prec)
-    ctx.set_launch_shape(tpt, nc, tc)
+    ctx.set_launch_shape(tpt, nc, tc, p2p_sources_per_stage=ch)
     v, s = ctx.evaluate_velocity_stretching(dev(x, "fp32"), dev(w, "fp32"))
     ev, es = rel(host3(v), ref.v), rel(host3(s), ref.s)
     assert ev < 1e-6 and es < 1e-6, (ev, es)
     ls = ctx.stats()["launch_shape"]
-    assert ls["p2p_targets_per_thread"] == tpt and ls["m2l_tensor_cores"] == (1 if (tc and prec == "tf32x3") else 0)
+    assert ls["p2p_targets_per_thread"] == tpt and ls["p2p_sources_per_stage"] == ch
+    assert ls["m2l_tensor_cores"] == (1 if (tc and prec == "tf32x3") else 0)
 
 
 @pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
@@ -44,11 +46,15 @@ def test_autotune_keeps_the_fastest_measured_shape(prec):
     ms = ls["tune_ms"]
     print(prec, ls)
     assert ls["p2p_targets_per_thread"] in (1, 2, 4)
-    assert ms[[1, 2, 4].index(ls["p2p_targets_per_thread"])] == min(ms[:3]) and min(ms[:3]) > 0
+    pick = [1, 2, 4].index(ls["p2p_targets_per_thread"]) + (3 if ls["p2p_sources_per_stage"] == 256 else 0)
+    assert ms[pick] == min(ms[:6]) and min(ms[:6]) > 0
     n_m2l = 5 if prec == "tf32x3" else 3
-    assert min(ms[3:3 + n_m2l]) > 0
+    assert min(ms[6:6 + n_m2l]) > 0
     v, s = ctx.evaluate_velocity_stretching(x4, w4)
-    assert rel(host3(v), v0) < 1e-6 and rel(host3(s), s0) < 1e-6
+    # two FP32 sums over ~7,400 sources per target in different blockings: s (a difference of
+    # large, nearly cancelling terms) agrees to FP32 summation accuracy, as in the sampled
+    # full-size parity test
+    assert rel(host3(v), v0) < 1e-6 and rel(host3(s), s0) < 1e-5
     st = ctx.stats()
     assert st["stage_launches"]["p2p"] == 0 or st["stage_ms"]["p2p"] >= 0  # tuning leaves the stage totals as they were
 
