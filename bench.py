@@ -287,9 +287,10 @@ def forms_at_eps(torch, LHV, spec, x0, w0, x4, w4, timed_steps, args, eps=1e-6):
         for p, e in cands:
             c = LHV(p=p, leaf_max=spec["leaf_max"], core_a=spec["a"], eps=spec["eps"], precision=prec)
             c.autotune(x0, w0)
-            t, _ = timed_steps(c, args.steps, 1)
+            t, stf = timed_steps(c, args.steps, 1)
             c.close()
-            r = {"p": p, "err_v": e, "ms_per_step": float(np.mean(t))}
+            r = {"p": p, "err_v": e, "ms_per_step": float(np.mean(t)),
+                 "stage_ms_per_step": {k: v / args.steps for k, v in stf["stage_ms"].items() if v > 0}}
             if best is None or r["ms_per_step"] < best["ms_per_step"]:
                 best = r
         if best:
@@ -305,7 +306,8 @@ def forms_at_eps(torch, LHV, spec, x0, w0, x4, w4, timed_steps, args, eps=1e-6):
     c.set_selector(W, b, eps=eps, check_every=0)
     t, st2 = timed_steps(c, args.steps, 1)
     out["learned_tf32x3"] = {"level_p": st["level_p"], "err_v_checked": st["selector"]["err_v"],
-                             "fallbacks": st["selector"]["fallbacks"], "ms_per_step": float(np.mean(t))}
+                             "fallbacks": st["selector"]["fallbacks"], "ms_per_step": float(np.mean(t)),
+                             "stage_ms_per_step": {k: v / args.steps for k, v in st2["stage_ms"].items() if v > 0}}
     c.close()
     if "fp32" in out:
         base = out["fp32"]["ms_per_step"]

@@ -78,7 +78,7 @@ typedef struct {
 } lhv_config;
 
 #define LHV_MAX_LEVELS 22
-#define LHV_NUM_STAGES 11
+#define LHV_NUM_STAGES 12
 /* stage indices of lhv_stats.stage_ms */
 #define LHV_STAGE_TREE   0  /* Morton keys, sort, boxes, lists */
 #define LHV_STAGE_P2M    1  /* Sec. 4.3 */
@@ -91,6 +91,7 @@ typedef struct {
 #define LHV_STAGE_OPS    8  /* FP64 operator build (once per context) */
 #define LHV_STAGE_COPY   9  /* host <-> device copies of the _host entry points */
 #define LHV_STAGE_M2L_PRODUCTS 10  /* the operator products of M2L alone (inside LHV_STAGE_M2L) */
+#define LHV_STAGE_SELECT 11  /* learned form: features, network and choice (tree excluded) */
 
 typedef struct {
     int     leaf_level;                      /* L of the last tree */

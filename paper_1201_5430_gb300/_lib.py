@@ -9,8 +9,8 @@ LHV_OK, LHV_EINVAL, LHV_ENOMEM, LHV_ECUDA, LHV_ETIMEOUT, LHV_ENONFINITE, LHV_EUN
 LHV_FP32, LHV_FP64, LHV_TF32X3 = 0, 1, 2
 LHV_TERMS_NEAR, LHV_TERMS_FAR, LHV_TERMS_ALL = 1, 2, 3
 LHV_MAX_LEVELS = 22
-LHV_NUM_STAGES = 11
-STAGES = ["tree", "p2m", "m2m", "m2l", "l2l", "l2p", "p2p", "rk4", "ops", "copy", "m2l_products"]
+LHV_NUM_STAGES = 12
+STAGES = ["tree", "p2m", "m2m", "m2l", "l2l", "l2p", "p2p", "rk4", "ops", "copy", "m2l_products", "select"]
 EXPORT = {"keys": 1, "perm": 2, "box_keys": 3, "box_range": 4, "colleagues": 5,
           "multipole": 6, "local": 7, "cube": 8}
 

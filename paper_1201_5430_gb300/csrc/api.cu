@@ -356,6 +356,7 @@ static void select_schedule(Ctx* c, int64_t n, const vec4_t<T>* x4, const vec4_t
     const int L = c->lv.L;
     if (L < 2) return;  // no far field: nothing to choose
     const int rows = L - 1;
+    StageScope sc(c, LHV_STAGE_SELECT);
     ensure(c, c->sel_X, (int64_t)rows * LHV_MLP_IN * 4);
     ensure(c, c->sel_Z, (int64_t)rows * LHV_MLP_OUT * 4);
     ensure(c, c->sel_choice, (int64_t)rows * 2 * 4);

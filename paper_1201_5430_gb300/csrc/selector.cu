@@ -23,24 +23,31 @@ namespace lhv {
 
 namespace {
 
-// sum of w over the elements of each leaf; sum of |w| over all elements into tot[0]
+// sum of w over the elements of each leaf (one warp per leaf); sum of |w| over all
+// elements into tot[0]
 template <typename T>
 __global__ void k_wsum_leaf(int nb, const int* __restrict__ bbeg, const int* __restrict__ bend,
                             const vec4_t<T>* __restrict__ ws, double* __restrict__ wsum, double* __restrict__ tot) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
     double mag = 0.0;
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+    for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nb; b += warps) {
         double s[3] = {0.0, 0.0, 0.0};
-        for (int j = bbeg[b]; j < bend[b]; ++j) {
+        for (int j = bbeg[b] + lane; j < bend[b]; j += 32) {
             const vec4_t<T> w = ws[j];
             s[0] += (double)w.x;
             s[1] += (double)w.y;
             s[2] += (double)w.z;
             mag += sqrt((double)w.x * w.x + (double)w.y * w.y + (double)w.z * w.z);
         }
-        for (int k = 0; k < 3; ++k) wsum[(int64_t)b * 3 + k] = s[k];
+        for (int k = 0; k < 3; ++k) {
+            double v = s[k];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) wsum[(int64_t)b * 3 + k] = v;
+        }
     }
     for (int o = 16; o > 0; o >>= 1) mag += __shfl_down_sync(0xffffffffu, mag, o);
-    if ((threadIdx.x & 31) == 0 && mag != 0.0) atomicAdd(tot, mag);
+    if (lane == 0 && mag != 0.0) atomicAdd(tot, mag);
 }
 
 // box sums of level l from those of its children (level l + 1)
@@ -177,7 +184,7 @@ int level_features(Ctx* c, const TreeBufs& tb, const Levels& lv, int64_t n, cons
     cuda_check(cudaMemsetAsync(st, 0, (MAX_LEVELS + 2) * 4 * 8, s), "feature stats");
     {
         const int nb = lv.nbox[L], o = lv.off[L];
-        k_wsum_leaf<T><<<grid_for(nb, 128), 128, 0, s>>>(nb, tb.bbeg.as<int>() + o, tb.bend.as<int>() + o, ws,
+        k_wsum_leaf<T><<<grid_for((int64_t)nb * 32, 128), 128, 0, s>>>(nb, tb.bbeg.as<int>() + o, tb.bend.as<int>() + o, ws,
                                                           W + (int64_t)o * 3, tot);
         count_launch(c);
     }

@@ -11,12 +11,15 @@
 // The operator side is re-laid once per context (k_tc_tiles) into TF32 hi/lo
 // tiles in the exact shared-memory order, so staging it is a straight 16-byte
 // copy.  Per work item (a chunk of <= 128 pairs of one operator, one N range),
-// for each K chunk of 32 the 256 threads gather and split X^T into one of two
+// for each K chunk of 16 the 256 threads gather and split X^T into one of two
 // shared stages (canonical no-swizzle K-major layout: 8-row x 16-byte core
 // matrices) and copy the operator tile, fence to the async proxy, and one thread
-// issues 4 k-steps x 3 MMAs and commits them to that stage's mbarrier; the next
+// issues 2 k-steps x 3 MMAs and commits them to that stage's mbarrier; the next
 // chunk is staged into the other stage while the tensor cores run.  Then each
 // warp reads 32 TMEM lanes (= pairs) and scatters the rows (vector atomics).
+// The stages are sized for the widest N range of the launch, so two CTAs share
+// an SM (each holds 256 of its 512 TMEM columns) and one gathers while the
+// other's MMAs run.
 // Every wait on the mbarrier gives up after a fixed number of polls, records an
 // error flag for the host and ends the kernel cleanly (TMEM freed).
 #include <cuda_runtime.h>
@@ -32,7 +35,7 @@ namespace {
 
 constexpr int TC_THREADS = 128;   // 4 warps: warp w owns TMEM lanes [32 w, 32 w + 32)
 constexpr int TC_M = 128;         // pairs per work item (MMA M)
-constexpr int TC_KC = 32;         // K per staged chunk (4 MMA k-steps of 8)
+constexpr int TC_KC = 16;         // K per staged chunk (2 MMA k-steps of 8)
 constexpr int TC_NMAX = 256;      // outputs per work item (MMA N, TMEM columns)
 constexpr uint32_t TMEM_COLS = 256;
 constexpr long long WAIT_LIMIT = 1ll << 26;
@@ -133,15 +136,17 @@ struct TcArgs {
     int n0[8], nlen[8];    // N ranges (<= 256 wide, multiples of 16)
     int kbeg[8];           // first K of each range (psplit for the chi outputs)
     int64_t roff[8];       // float offset of each range inside a group
+    int nmax;              // widest range (rows of the operator tile in a stage)
+    int stage_bytes;       // bytes of one shared stage (Xh, Xl, Bh, Bl), 1024-aligned
     int* err;              // set to 1 if a wait timed out
 };
 
 constexpr int TC2_THREADS = 256;  // 8 warps; warp w drains lanes 32 (w % 4) .. +32, column half w / 4
-constexpr int STAGE_BYTES = 2 * TC_M * TC_KC * 4 + 2 * TC_NMAX * TC_KC * 4;  // Xh, Xl, Bh, Bl
+constexpr int TC2_PER_SM = 2;     // CTAs per SM (2 x 256 TMEM columns)
 
 // One work item = (chunk of <= 128 pairs of one operator, one N range).  Two
 // shared stages: the tensor cores read stage s while the threads fill s ^ 1.
-__global__ void __launch_bounds__(TC2_THREADS, 1) k_tc_gemm(TcArgs ta) {
+__global__ void __launch_bounds__(TC2_THREADS, TC2_PER_SM) k_tc_gemm(TcArgs ta) {
     const GemmArgs<float>& a = ta.g;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint64_t bar[2];
@@ -209,16 +214,16 @@ __global__ void __launch_bounds__(TC2_THREADS, 1) k_tc_gemm(TcArgs ta) {
         for (int i = 0; i < nk; ++i) {
             const int b = i & 1;
             wait_bar(b);  // the MMAs of chunk i - 2 read this stage
-            unsigned char* st = smem + b * STAGE_BYTES;
+            unsigned char* st = smem + b * ta.stage_bytes;
             unsigned char* Xh = st;
             unsigned char* Xl = Xh + TC_M * TC_KC * 4;
             unsigned char* Bh = Xl + TC_M * TC_KC * 4;
-            unsigned char* Bl = Bh + TC_NMAX * TC_KC * 4;
+            unsigned char* Bl = Bh + ta.nmax * TC_KC * 4;
             const int kc = kbeg + i * TC_KC;
             const int kn = min(TC_KC, a.C - kc);
-            // X^T: 128 rows x 8 groups of 4, two threads per row
+            // X^T: 128 rows x (TC_KC / 4) groups of 4
             for (int e = t; e < TC_M * (TC_KC / 4); e += TC2_THREADS) {
-                const int row = e >> 3, kg = e & 7;
+                const int row = e / (TC_KC / 4), kg = e % (TC_KC / 4);
                 const int s = s_src[row];
                 float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (s >= 0 && kg * 4 < kn) v = *reinterpret_cast<const float4*>(a.in + (int64_t)s * a.ldin + kc + kg * 4);
@@ -381,7 +386,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_selftest(const float* X, c
 }
 
 constexpr size_t TC_SMEM = (size_t)2 * TC_M * TC_KC * 4 + (size_t)2 * TC_NMAX * TC_KC * 4 + 1024;
-constexpr size_t TC2_SMEM = (size_t)2 * STAGE_BYTES + 1024;
 
 TcArgs tc_layout(int R, int C, int psplit) {
     TcArgs ta{};
@@ -400,12 +404,15 @@ TcArgs tc_layout(int R, int C, int psplit) {
         add(0, R, 0);
     }
     int64_t off = 0;
+    ta.nmax = 16;
     for (int r = 0; r < ta.nranges; ++r) {
         ta.roff[r] = off;
         const int nk = (C - ta.kbeg[r] + TC_KC - 1) / TC_KC;
         off += (int64_t)nk * 2 * ta.nlen[r] * TC_KC;
+        ta.nmax = std::max(ta.nmax, ta.nlen[r]);
     }
     ta.group_stride = off;
+    ta.stage_bytes = (2 * TC_M * TC_KC * 4 + 2 * ta.nmax * TC_KC * 4 + 1023) / 1024 * 1024;
     return ta;
 }
 
@@ -438,11 +445,13 @@ void run_tc_gemm(Ctx* c, Grouped& gp, GemmArgs<float> a, const float* tiles, int
     ta.g = a;
     ta.tiles = tiles;
     ta.err = err;
-    cuda_check(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC2_SMEM), "tc attr");
+    // two stages; at least 80 KB so that no third CTA (and TMEM request) lands on an SM
+    const size_t smem = std::max<size_t>((size_t)2 * ta.stage_bytes + 1024, 80 * 1024);
+    cuda_check(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "tc attr");
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    k_tc_gemm<<<sms, TC2_THREADS, TC2_SMEM, s>>>(ta);
+    k_tc_gemm<<<sms * TC2_PER_SM, TC2_THREADS, smem, s>>>(ta);
     count_launch(c);
     check_launch("tc gemm");
 }

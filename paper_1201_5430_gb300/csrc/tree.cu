@@ -294,8 +294,34 @@ __global__ void k_scan_apply(int64_t n, const int* __restrict__ in, const int* _
     }
 }
 
+// Small arrays (n <= 1024 * SCAN_ITEMS) in one block and one launch.
+constexpr int SCAN_ONE_THREADS = 1024;
+__global__ void __launch_bounds__(SCAN_ONE_THREADS) k_scan_one(int n, const int* __restrict__ in,
+                                                                int* __restrict__ out, int* __restrict__ total_out) {
+    const int base = threadIdx.x * SCAN_ITEMS;
+    int v[SCAN_ITEMS];
+    int s = 0;
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        v[j] = (base + j < n) ? in[base + j] : 0;
+        s += v[j];
+    }
+    int tot;
+    int ex = block_exclusive_scan(s, &tot);
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        if (base + j < n) out[base + j] = ex;
+        ex += v[j];
+    }
+    if (threadIdx.x == 0 && total_out) *total_out = tot;
+}
+
 void exclusive_scan(Ctx* c, int64_t n, const int* in, int* out, int* sums_tmp, int* total_out) {
     cudaStream_t s = stream_of(c);
+    if (n <= (int64_t)SCAN_ONE_THREADS * SCAN_ITEMS) {
+        k_scan_one<<<1, SCAN_ONE_THREADS, 0, s>>>((int)n, in, out, total_out);
+        count_launch(c);
+        check_launch("exclusive_scan");
+        return;
+    }
     int nb = (int)((n + SCAN_TILE - 1) / SCAN_TILE);
     if (nb < 1) nb = 1;
     k_scan_reduce<<<nb, SCAN_THREADS, 0, s>>>(n, in, sums_tmp);

@@ -53,3 +53,27 @@ def test_create_rejects_bad_config_without_gpu(lib):
         cfg = dict(p=8, leaf_max=64, core_a=0.01, eps=1e-6, precision=0, terms=3, max_level=0)
         cfg.update(kw)
         assert L.lhv_create(ctypes.byref(_lib.Config(**cfg)), None, ctypes.byref(h)) == -1
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """ctypes mirrors of lhv_config / lhv_stats have the C sizes and field offsets
+    (a short struct on the Python side would let lhv_get_stats write past it)."""
+    import shutil
+    import subprocess
+    from paper_1201_5430_gb300 import _lib
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not available")
+    fields = [f[0] for f in _lib.Stats._fields_]
+    src = tmp_path / "sz.c"
+    body = "\n".join(f'    printf("{f} %zu\\n", offsetof(lhv_stats, {f}));' for f in fields)
+    src.write_text("#include <stdio.h>\n#include <stddef.h>\n#include \"lhv.h\"\nint main(void) {\n"
+                   f"    printf(\"sizeof %zu\\n\", sizeof(lhv_stats));\n"
+                   f"    printf(\"config %zu\\n\", sizeof(lhv_config));\n{body}\n    return 0;\n}}\n")
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                       check=True).stdout.splitlines())
+    assert int(out["sizeof"]) == ctypes.sizeof(_lib.Stats)
+    assert int(out["config"]) == ctypes.sizeof(_lib.Config)
+    for f in fields:
+        assert int(out[f]) == getattr(_lib.Stats, f).offset, f
