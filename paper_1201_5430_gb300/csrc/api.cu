@@ -39,7 +39,7 @@ struct Ctx {
     int64_t tree_n = 0;
     OpTables ops;
     int ops_type = 0;  // sizeof(T) of the built tables
-    Buf tmp[12];
+    Buf tmp[14];
     Buf xs, ws, mult, loc, table, vfar, sfar, counters, W, cf;
     Grouped gp_leaf, gp_m2m, gp_m2l, gp_l2l;
     Buf rk[6];         // kv, ks, ax, aw, sx, sw

@@ -93,7 +93,10 @@ void run_group_gemm(Ctx* c, Grouped& gp, GemmArgs<T> a);
 // kernel copies straight into shared memory.
 bool tc_supported(int R, int C, int psplit);
 void tc_tiles_build(Ctx* c, const float* ops, int ngroups, int R, int C, int psplit, Buf& tiles);
-void run_tc_gemm(Ctx* c, Grouped& gp, GemmArgs<float> a, const float* tiles, int* err);
+// in_hi / in_lo: the TF32 split of a.in (same layout), from tc_split.
+void run_tc_gemm(Ctx* c, Grouped& gp, GemmArgs<float> a, const float* tiles, const float* in_hi,
+                 const float* in_lo, int* err);
+void tc_split(Ctx* c, int64_t n, const float* x, float* hi, float* lo);
 
 // Item sources ---------------------------------------------------------------
 

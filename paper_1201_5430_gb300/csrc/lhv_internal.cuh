@@ -77,7 +77,7 @@ void ensure(Ctx* c, Buf& b, int64_t bytes);          // grow b to >= bytes (thro
 int ctx_leaf_max(Ctx* c);
 int ctx_max_level(Ctx* c);
 double ctx_rK(Ctx* c);
-Buf& ctx_tmp(Ctx* c, int i);                         // scratch buffers 0..11 owned by the context
+Buf& ctx_tmp(Ctx* c, int i);                         // scratch buffers 0..13 owned by the context
 bool ctx_use_tc(Ctx* c);                             // LHV_TF32X3: dense maps on the tensor cores
 int* ctx_err_flag(Ctx* c);                           // device word set by a timed-out device wait
 int ctx_p2p_tpt(Ctx* c);                             // P2P targets per thread (autotuned; 1, 2 or 4)

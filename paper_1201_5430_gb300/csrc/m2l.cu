@@ -87,6 +87,23 @@ void m2l_prepare(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& 
 template <typename T>
 void m2l_apply(Ctx* c, const Plan<T>& pl, const Levels& lv, Grouped& gp, const T* mult, T* loc) {
     const int L = lv.L;
+    // the tensor-core products read the multipoles split into TF32 hi/lo once
+    const float* mhi = nullptr;
+    const float* mlo = nullptr;
+    if constexpr (sizeof(T) == 4) {
+        bool any_tc = false;
+        for (int l = 2; l <= L; ++l) any_tc = any_tc || (ctx_m2l_tc(c) && pl.m2l_tiles[l]);
+        if (any_tc) {
+            const int64_t first = (int64_t)lv.off[2] * pl.ld, count = (int64_t)(lv.off[L + 1] - lv.off[2]) * pl.ld;
+            Buf& bh = ctx_tmp(c, 12);
+            Buf& bl = ctx_tmp(c, 13);
+            ensure(c, bh, (first + count) * 4);
+            ensure(c, bl, (first + count) * 4);
+            tc_split(c, count, mult + first, bh.as<float>() + first, bl.as<float>() + first);
+            mhi = bh.as<float>();
+            mlo = bl.as<float>();
+        }
+    }
     // one launch per run of levels with the same p (one launch in all when uniform)
     for (int l0 = 2; l0 <= L;) {
         int l1 = l0 + 1;
@@ -111,7 +128,7 @@ void m2l_apply(Ctx* c, const Plan<T>& pl, const Levels& lv, Grouped& gp, const T
         bool done = false;
         if constexpr (sizeof(T) == 4) {
             if (ctx_m2l_tc(c) && pl.m2l_tiles[l0]) {
-                run_tc_gemm(c, gp, a, pl.m2l_tiles[l0], ctx_err_flag(c));
+                run_tc_gemm(c, gp, a, pl.m2l_tiles[l0], mhi, mlo, ctx_err_flag(c));
                 done = true;
             }
         }

@@ -10,16 +10,18 @@
 //
 // The operator side is re-laid once per context (k_tc_tiles) into TF32 hi/lo
 // tiles in the exact shared-memory order, so staging it is a straight 16-byte
-// copy.  Per work item (a chunk of <= 128 pairs of one operator, one N range),
-// for each K chunk of 16 the 256 threads gather and split X^T into one of two
-// shared stages (canonical no-swizzle K-major layout: 8-row x 16-byte core
-// matrices) and copy the operator tile, fence to the async proxy, and one thread
-// issues 2 k-steps x 3 MMAs and commits them to that stage's mbarrier; the next
-// chunk is staged into the other stage while the tensor cores run.  Then each
-// warp reads 32 TMEM lanes (= pairs) and scatters the rows (vector atomics).
-// The stages are sized for the widest N range of the launch, so two CTAs share
-// an SM (each holds 256 of its 512 TMEM columns) and one gathers while the
-// other's MMAs run.
+// copy; the source vectors are split into TF32 hi/lo once per launch
+// (k_tf32_split) so that the gather is a copy too.  Per work item (a chunk of
+// <= 128 pairs of one operator, one N range) the K dimension is walked in
+// chunks of 16 through a ring of S shared stages (canonical no-swizzle K-major
+// layout: 8-row x 16-byte core matrices): the 256 threads fill stage i + S - 1
+// with 16-byte cp.async copies (X^T hi/lo rows of the pairs, operator hi/lo
+// tile) while the tensor cores work on stage i, whose copies are waited for,
+// fenced to the async proxy, and handed to one thread that issues 2 k-steps x 3
+// MMAs and commits them to the stage's mbarrier.  Then each warp reads 32 TMEM
+// lanes (= pairs) and scatters the rows (vector atomics).  Stages are sized for
+// the widest N range of the launch and S (2 or 3) is chosen so that two CTAs
+// share an SM (each holds 256 of its 512 TMEM columns).
 // Every wait on the mbarrier gives up after a fixed number of polls, records an
 // error flag for the host and ends the kernel cleanly (TMEM freed).
 #include <cuda_runtime.h>
@@ -138,8 +140,23 @@ struct TcArgs {
     int64_t roff[8];       // float offset of each range inside a group
     int nmax;              // widest range (rows of the operator tile in a stage)
     int stage_bytes;       // bytes of one shared stage (Xh, Xl, Bh, Bl), 1024-aligned
+    int nstages;           // S, 2 or 3
+    const float* in_hi;    // TF32 hi / lo parts of the source vectors (layout of g.in)
+    const float* in_lo;
     int* err;              // set to 1 if a wait timed out
 };
+
+constexpr int TC_MAX_STAGES = 3;
+
+// 16-byte asynchronous global -> shared copy; src_bytes = 0 fills zeros
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 constexpr int TC2_THREADS = 256;  // 8 warps; warp w drains lanes 32 (w % 4) .. +32, column half w / 4
 constexpr int TC2_PER_SM = 2;     // CTAs per SM (2 x 256 TMEM columns)
@@ -149,7 +166,7 @@ constexpr int TC2_PER_SM = 2;     // CTAs per SM (2 x 256 TMEM columns)
 __global__ void __launch_bounds__(TC2_THREADS, TC2_PER_SM) k_tc_gemm(TcArgs ta) {
     const GemmArgs<float>& a = ta.g;
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ uint64_t bar[2];
+    __shared__ uint64_t bar[TC_MAX_STAGES];
     __shared__ uint32_t tmem_base;
     __shared__ int s_src[TC_M], s_dst[TC_M];
     __shared__ int s_work, s_abort;
@@ -162,8 +179,7 @@ __global__ void __launch_bounds__(TC2_THREADS, TC2_PER_SM) k_tc_gemm(TcArgs ta) 
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (t == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int b = 0; b < TC_MAX_STAGES; ++b) mbar_init(&bar[b], 1);
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -171,8 +187,9 @@ __global__ void __launch_bounds__(TC2_THREADS, TC2_PER_SM) k_tc_gemm(TcArgs ta) 
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
-    uint32_t par[2] = {0u, 0u};     // next parity to wait for, per barrier
-    int pending[2] = {0, 0};        // commits not yet waited for, per barrier
+    uint32_t par[TC_MAX_STAGES] = {0u, 0u, 0u};  // next parity to wait for, per barrier
+    int pending[TC_MAX_STAGES] = {0, 0, 0};      // commits not yet waited for, per barrier
+    const int S = ta.nstages;
 
     auto wait_bar = [&](int b) {
         if (!pending[b]) return;
@@ -211,40 +228,48 @@ __global__ void __launch_bounds__(TC2_THREADS, TC2_PER_SM) k_tc_gemm(TcArgs ta) 
         }
         const uint32_t idesc = make_idesc(TC_M, nlen);
         __syncthreads();
+        // fill the stage of K chunk i (all threads, asynchronous copies, one commit group)
+        auto issue = [&](int i) {
+            if (i < nk) {
+                unsigned char* st = smem + (i % S) * ta.stage_bytes;
+                unsigned char* Xh = st;
+                unsigned char* Xl = Xh + TC_M * TC_KC * 4;
+                unsigned char* Bh = Xl + TC_M * TC_KC * 4;
+                unsigned char* Bl = Bh + ta.nmax * TC_KC * 4;
+                const int kc = kbeg + i * TC_KC;
+                const int kn = min(TC_KC, a.C - kc);
+                for (int e = t; e < TC_M * (TC_KC / 4); e += TC2_THREADS) {
+                    const int row = e / (TC_KC / 4), kg = e % (TC_KC / 4);
+                    const int s = s_src[row];
+                    const bool ok = s >= 0 && kg * 4 < kn;
+                    const int64_t at = ok ? (int64_t)s * a.ldin + kc + kg * 4 : 0;
+                    const uint32_t o = tile_off(row, kg * 4);
+                    cp_async16(Xh + o, ta.in_hi + at, ok ? 16 : 0);
+                    cp_async16(Xl + o, ta.in_lo + at, ok ? 16 : 0);
+                }
+                const float* src = tg + (int64_t)i * 2 * tile_floats;
+                for (int e = t; e < tile_floats / 4; e += TC2_THREADS) {
+                    cp_async16(Bh + 16 * e, src + 4 * e, 16);
+                    cp_async16(Bl + 16 * e, src + tile_floats + 4 * e, 16);
+                }
+            }
+            cp_async_commit();  // an empty group past the last chunk keeps the counting uniform
+        };
+        for (int i = 0; i < S - 1; ++i) issue(i);
         for (int i = 0; i < nk; ++i) {
-            const int b = i & 1;
-            wait_bar(b);  // the MMAs of chunk i - 2 read this stage
+            const int b = i % S;
+            // chunk i's copies are group i of S - 1 + i committed: S - 2 newer ones may still fly
+            if (S == 3) cp_async_wait<1>();
+            else cp_async_wait<0>();
+            fence_async_smem();
+            __syncthreads();
+            if (s_abort) break;
             unsigned char* st = smem + b * ta.stage_bytes;
             unsigned char* Xh = st;
             unsigned char* Xl = Xh + TC_M * TC_KC * 4;
             unsigned char* Bh = Xl + TC_M * TC_KC * 4;
             unsigned char* Bl = Bh + ta.nmax * TC_KC * 4;
-            const int kc = kbeg + i * TC_KC;
-            const int kn = min(TC_KC, a.C - kc);
-            // X^T: 128 rows x (TC_KC / 4) groups of 4
-            for (int e = t; e < TC_M * (TC_KC / 4); e += TC2_THREADS) {
-                const int row = e / (TC_KC / 4), kg = e % (TC_KC / 4);
-                const int s = s_src[row];
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (s >= 0 && kg * 4 < kn) v = *reinterpret_cast<const float4*>(a.in + (int64_t)s * a.ldin + kc + kg * 4);
-                float4 h, l;
-                h.x = tf32_rna(v.x); l.x = tf32_rna(v.x - h.x);
-                h.y = tf32_rna(v.y); l.y = tf32_rna(v.y - h.y);
-                h.z = tf32_rna(v.z); l.z = tf32_rna(v.z - h.z);
-                h.w = tf32_rna(v.w); l.w = tf32_rna(v.w - h.w);
-                const uint32_t o = tile_off(row, kg * 4);
-                *reinterpret_cast<float4*>(Xh + o) = h;
-                *reinterpret_cast<float4*>(Xl + o) = l;
-            }
-            // A_g^T tile i of this range, already in shared-memory order: straight copies
-            const float4* src = reinterpret_cast<const float4*>(tg + (int64_t)i * 2 * tile_floats);
-            for (int e = t; e < tile_floats / 4; e += TC2_THREADS) {
-                reinterpret_cast<float4*>(Bh)[e] = src[e];
-                reinterpret_cast<float4*>(Bl)[e] = src[e + tile_floats / 4];
-            }
-            fence_async_smem();
-            __syncthreads();
-            if (s_abort) break;
+            const int kn = min(TC_KC, a.C - (kbeg + i * TC_KC));
             if (t == 0) {
                 tc_fence_after();
                 const uint32_t lbo = 128, sbo = (TC_KC / 4) * 128;
@@ -261,9 +286,12 @@ __global__ void __launch_bounds__(TC2_THREADS, TC2_PER_SM) k_tc_gemm(TcArgs ta) 
                 mma_commit(&bar[b]);
             }
             pending[b] = 1;
+            // while chunk i multiplies, refill the stage chunk i - 1 used, once its MMAs are done
+            if (i >= 1) wait_bar((i - 1) % S);
+            issue(i + S - 1);
         }
-        wait_bar(0);
-        wait_bar(1);
+        cp_async_wait_all();  // the trailing (empty or abandoned) groups
+        for (int b = 0; b < S; ++b) wait_bar(b);
         tc_fence_after();
         __syncthreads();
         if (s_abort) break;
@@ -434,7 +462,24 @@ void tc_tiles_build(Ctx* c, const float* ops, int ngroups, int R, int C, int psp
     check_launch("tc tiles");
 }
 
-void run_tc_gemm(Ctx* c, Grouped& gp, GemmArgs<float> a, const float* tiles, int* err) {
+// hi = tf32(x), lo = tf32(x - hi) of n floats (the source vectors of the tensor-core products)
+__global__ void k_tf32_split(int64_t n, const float* __restrict__ x, float* __restrict__ hi,
+                             float* __restrict__ lo) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float v = x[i], h = tf32_rna(v);
+        hi[i] = h;
+        lo[i] = tf32_rna(v - h);
+    }
+}
+
+void tc_split(Ctx* c, int64_t n, const float* x, float* hi, float* lo) {
+    k_tf32_split<<<grid_for(n, 256), 256, 0, stream_of(c)>>>(n, x, hi, lo);
+    count_launch(c);
+    check_launch("tf32 split");
+}
+
+void run_tc_gemm(Ctx* c, Grouped& gp, GemmArgs<float> a, const float* tiles, const float* in_hi,
+                 const float* in_lo, int* err) {
     a.chunks = gp.chunks.as<int4>();
     a.pairs = gp.pairs.as<int2>();
     a.choff = gp.choff.as<int>();
@@ -444,9 +489,13 @@ void run_tc_gemm(Ctx* c, Grouped& gp, GemmArgs<float> a, const float* tiles, int
     TcArgs ta = tc_layout(a.R, a.C, a.psplit);
     ta.g = a;
     ta.tiles = tiles;
+    ta.in_hi = in_hi;
+    ta.in_lo = in_lo;
     ta.err = err;
-    // two stages; at least 80 KB so that no third CTA (and TMEM request) lands on an SM
-    const size_t smem = std::max<size_t>((size_t)2 * ta.stage_bytes + 1024, 80 * 1024);
+    // three stages when two CTAs still fit an SM, else two; at least 80 KB so that no
+    // third CTA (and TMEM request) lands on an SM
+    ta.nstages = (size_t)3 * ta.stage_bytes + 1024 + 4096 <= (size_t)110 * 1024 ? 3 : 2;
+    const size_t smem = std::max<size_t>((size_t)ta.nstages * ta.stage_bytes + 1024, 80 * 1024);
     cuda_check(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "tc attr");
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
