@@ -8,11 +8,14 @@
 //   s_i = (sum_j f w_j) x w_i + sum_j g (w_i . d) (w_j x d),   g = f'/r.
 // K evaluation, x = r/a:
 //   x >= x_cut  : K = 1 to the working precision (f = 1/r^3, g = -3/r^5);
-//   x <  x_ser  : the Taylor series of K/x^3 in x^2 (dK/dx = sqrt(2/pi) x^2 e^{-x^2/2}
-//                 integrates term by term), which avoids the cancellation of the
-//                 closed form at small x (x_ser = 1.5 in FP32, 1 in FP64);
-//   otherwise   : K = 1 - exp(-x^2/2) R(x), R from a Chebyshev fit (FP32), or
-//                 Eq. vem1 with erf (FP64).
+//   x <  x_ser  : K/x^3 as a function of x^2 (dK/dx = sqrt(2/pi) x^2 e^{-x^2/2}
+//                 integrates term by term into a series without the cancellation
+//                 of the closed form at small x): in FP32 a degree-7 Chebyshev
+//                 interpolant of it and of its derivative on x^2 < 2.25, in FP64
+//                 the series itself below x = 1;
+//   otherwise   : K = 1 - exp(-x^2/2) R(x), R(x) = exp(x^2/2) erfc(x/sqrt 2) +
+//                 sqrt(2/pi) x with its first term a degree-7 Chebyshev
+//                 interpolant in 1/x (FP32), or Eq. vem1 with erf (FP64).
 // The self pair j = i is excluded only in the source chunk that can hold it.
 // The far-field result (L2P) of the same element is added and the sum is
 // written in the caller's order.
@@ -31,7 +34,7 @@ namespace lhv {
 namespace {
 
 template <typename T> struct CoreConsts {
-    T inv_a, inv_a2, c3, c5;  // 1/a, 1/a^2, sqrt(2/pi)/a^3, sqrt(2/pi)/a^5
+    T a, inv_a, inv_a2, c3, c5;  // a, 1/a, 1/a^2, sqrt(2/pi)/a^3, sqrt(2/pi)/a^5
     T x2_cut;                 // (r/a)^2 beyond which K = 1 in this precision
     T u_series;               // (r/a)^2 below which the Taylor series is used
     int smooth;
@@ -80,17 +83,23 @@ __device__ __forceinline__ void kernel_fg(float r2, const CoreConsts<float>& cc,
         const float u = r2 * cc.inv_a2;
         if (u < cc.x2_cut) {
             if (u < cc.u_series) {
-                float F, Fp;
-                core_series<float>(u, F, Fp);
+                const float s = fmaf(u, 2.0f / LHV_CORE_U_SER, -1.0f);
+                float F = kSerF[LHV_CORE_SER_DEG], Fp = kSerFp[LHV_CORE_SER_DEG];
+#pragma unroll
+                for (int k = LHV_CORE_SER_DEG - 1; k >= 0; --k) {
+                    F = fmaf(F, s, kSerF[k]);
+                    Fp = fmaf(Fp, s, kSerFp[k]);
+                }
                 f = cc.c3 * F;
                 g = 2.0f * cc.c5 * Fp;
                 return;
             }
-            const float x = r2 * ri * cc.inv_a;
-            const float t = fmaf(x, 0.4f, -1.6f);  // (2x - 8)/5
-            float R = kCoreFit[LHV_CORE_FIT_DEG];
+            const float t = fmaf(cc.a * ri, LHV_CORE_Y_SCALE, LHV_CORE_Y_SHIFT);  // y = 1/x = a/r
+            float E = kCoreFit[LHV_CORE_FIT_DEG];
 #pragma unroll
-            for (int k = LHV_CORE_FIT_DEG - 1; k >= 0; --k) R = fmaf(R, t, kCoreFit[k]);
+            for (int k = LHV_CORE_FIT_DEG - 1; k >= 0; --k) E = fmaf(E, t, kCoreFit[k]);
+            const float x = r2 * ri * cc.inv_a;
+            const float R = fmaf(0.79788456080286535588f, x, E);
             const float e = ex2_ftz(u * -0.72134752044448170368f);  // exp(-u/2)
             const float K = fmaf(-e, R, 1.0f);
             f *= K;
@@ -374,6 +383,7 @@ void run_p2p(Ctx* c, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs, 
     cc.smooth = a > 0.0;
     if (cc.smooth) {
         const double s2pi = 0.79788456080286535588;
+        cc.a = (T)a;
         cc.inv_a = (T)(1.0 / a);
         cc.inv_a2 = (T)(1.0 / (a * a));
         cc.c3 = (T)(s2pi / (a * a * a));
@@ -381,7 +391,7 @@ void run_p2p(Ctx* c, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs, 
         // beyond x_cut, 1 - K and the K' term are below the unit roundoff
         const double xc = sizeof(T) == 4 ? 6.5 : 9.0;
         cc.x2_cut = (T)(xc * xc);
-        cc.u_series = (T)(sizeof(T) == 4 ? 2.25 : 1.0);
+        cc.u_series = (T)(sizeof(T) == 4 ? LHV_CORE_U_SER : 1.0);
     }
     int* work = reinterpret_cast<int*>(ctx_tmp(c, 6).ptr);
     ensure(c, ctx_tmp(c, 6), 64);
