@@ -252,6 +252,78 @@ def run_blobs64(args, torch, LHV, local, world, rank, dist):
                           "speedup_vs_sequential_plain_fp32": val_b / val_s}), flush=True)
 
 
+def run_leapfrog(args, torch, LHV, local, world, rank, dist, eps=1e-6):
+    """Learned form on the leapfrogging ring pair (2 x 2^21 elements, dt = 5e-4): RK4 steps
+    with the network choosing p per level once per step (TF32x3, target eps_2(v) <= 1e-6, the
+    first step checked against FP64 direct sums), against the fixed p = 12 of the workload
+    (its fallback) and a fixed p = 16, each timed over the same steps from the same state."""
+    from paper_1201_5430_gb300 import selector
+    x, w, spec = workloads.make("leapfrog_rings_4194304")
+    n = x.shape[0]
+    x0 = torch.from_numpy(workloads.to_f4(x)).cuda()
+    w0 = torch.from_numpy(workloads.to_f4(w)).cuda()
+    x4, w4 = x0.clone(), w0.clone()
+    stream = torch.cuda.current_stream()
+    idx = torch.from_numpy(np.random.default_rng(0).choice(n, 1000, replace=False).astype(np.int32)).cuda()
+    ref = LHV(p=4, leaf_max=spec["leaf_max"], core_a=spec["a"])
+    v0, _ = ref.direct_sampled(x0, w0, idx)
+    ref.close()
+
+    def err(c):
+        v, _ = c.evaluate_velocity_stretching(x0, w0)
+        return float(torch.linalg.norm(v[idx.long()].double()[:, :3] - v0[:, :3]) / torch.linalg.norm(v0[:, :3]))
+
+    def timed(c):
+        for _ in range(3):
+            x4.copy_(x0)
+            w4.copy_(w0)
+            c.step(x4, w4, spec["dt"])
+        torch.cuda.synchronize()
+        x4.copy_(x0)
+        w4.copy_(w0)
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ea.record(stream)
+        for _ in range(args.steps):
+            c.step(x4, w4, spec["dt"])  # consecutive steps of the trajectory
+        eb.record(stream)
+        eb.synchronize()
+        return max_over_ranks(ea.elapsed_time(eb), dist)
+
+    out = {}
+    for name, p, prec in (("fixed_p12", 12, "tf32x3"), ("fixed_p16", 16, "tf32x3")):
+        c = LHV(p=p, leaf_max=spec["leaf_max"], core_a=spec["a"], eps=spec["eps"], precision=prec)
+        c.autotune(x0, w0)
+        e = err(c)
+        ms = timed(c)
+        out[name] = {"p": p, "err_v": e, "ms_per_step": ms / args.steps}
+        c.close()
+    W, b, _ = selector.load()
+    c = LHV(p=12, leaf_max=spec["leaf_max"], core_a=spec["a"], eps=spec["eps"], precision="tf32x3")
+    c.set_selector(W, b, eps=eps, check_every=1, check_samples=1000)
+    v, _ = c.evaluate_velocity_stretching(x0, w0)
+    e = float(torch.linalg.norm(v[idx.long()].double()[:, :3] - v0[:, :3]) / torch.linalg.norm(v0[:, :3]))
+    st = c.stats()
+    c.autotune(x0, w0)
+    c.set_selector(W, b, eps=eps, check_every=0)  # checked once above, on the initial state
+    ms = timed(c)
+    st2 = c.stats()
+    out["learned"] = {"level_p": st["level_p"], "err_v": e, "ms_per_step": ms / args.steps,
+                      "initial_check": {"err_v": st["selector"]["err_v"], "fallbacks": st["selector"]["fallbacks"]},
+                      "level_p_last_step": st2["level_p"]}
+    c.close()
+    value = 4 * n * args.steps * world / (ms / 1e3)
+    if rank == 0:
+        print(json.dumps({"metric": METRIC + " (learned form)", "value": value, "unit": UNIT, "n_gpus": world,
+                          "steps": args.steps, "warmup": 3, "ms_per_step": ms / args.steps,
+                          "higher_is_better": True, "scaling": "weak", "dtype": "f32+tf32x3", "data": "synthetic",
+                          "config": {"workload": "leapfrog_rings_4194304", "n": n, "dt": spec["dt"],
+                                     "a": spec["a"], "eps_target": eps, "steps": "consecutive RK4 steps"},
+                          "arms": out,
+                          "speedup_vs_fixed_p12": out["fixed_p12"]["ms_per_step"] / out["learned"]["ms_per_step"],
+                          "speedup_vs_fixed_p16": out["fixed_p16"]["ms_per_step"] / out["learned"]["ms_per_step"]}),
+              flush=True)
+
+
 def forms_at_eps(torch, LHV, spec, x0, w0, x4, w4, timed_steps, args, eps=1e-6):
     """Plain FP32 and TF32x3 at their smallest uniform p with eps_2(v) <= eps, and the
     learned form (TF32x3, network choice per step), each timed over RK4 steps."""
@@ -324,7 +396,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "blobs64"],
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "blobs64", "leapfrog"],
                     help="blobs64: the batched form, 64 independent blob systems (not the headline line)")
     ap.add_argument("--precision", default="tf32x3", choices=["tf32x3", "fp32"],
                     help="tf32x3: translations on the tensor cores (TF32 split products); fp32: plain CUDA-core FMM")
@@ -351,6 +423,9 @@ def main():
     from paper_1201_5430_gb300 import LHV
     if args.workload == "blobs64":
         run_blobs64(args, torch, LHV, local, world, rank, dist)
+        return
+    if args.workload == "leapfrog":
+        run_leapfrog(args, torch, LHV, local, world, rank, dist)
         return
     x, w, spec = workloads.make(WORKLOAD)
     n = x.shape[0]
