@@ -33,8 +33,9 @@ import workloads  # noqa: E402
 WORKLOAD = "ring_262144"
 METRIC = "vortex-element v+stretching evals/sec at ε=1e-6 vs plain FP32 GPU FMM; % roofline"
 UNIT = "evals/s"
-# algorithmic FP32 work of one near-field pair ("P2P"): d, r^2, 1/r^3,
-# g = f'/r, w_j x d, v += f (w_j x d), sum f w_j, (w_i . d), s += g (w_i . d)(w_j x d)
+# algorithmic FP32 work of one near-field pair (singular kernel): d (3), r^2 (5), 1/r^3 (3),
+# g = f'/r (2), w_j x d (9), v += f (w_j x d) (6), sum f w_j (6), (w_i . d) and g (w_i . d) (6),
+# s += g (w_i . d)(w_j x d) (6) = 46 flops
 P2P_FLOPS_PER_PAIR = 46
 FP32_LANES_PER_SM = 128
 

@@ -46,7 +46,7 @@ extern "C" {
 #define LHV_ECUDA        -3  /* a CUDA runtime call or kernel launch failed */
 #define LHV_ETIMEOUT     -4  /* a device-side bounded wait gave up */
 #define LHV_ENONFINITE   -5  /* NaN or Inf in the positions or strengths */
-#define LHV_EUNSUPPORTED -6  /* valid request this build does not implement */
+#define LHV_EUNSUPPORTED -6  /* valid request this library does not implement */
 #define LHV_ETOOBIG      -7  /* input larger than the fixed scratch of a no-allocation entry point */
 
 /* ---- arithmetic of the evaluation (lhv_config.precision) --------------- */

@@ -1,5 +1,5 @@
-// Direct smoothed Biot-Savart sums at sampled targets, in FP64 (the judge of
-// the FMM error on a sample of targets, Sec. 5.1).
+// Direct smoothed Biot-Savart sums at sampled targets, in FP64: the reference
+// against which the FMM error is measured on a sample of targets (Sec. 5.1).
 //
 // For target i and every source j != i (excluded by index):
 //   v_i   += f(r) w_j x d,                         d = x_i - x_j, r = |d|   (Eqs. 1, 2)
