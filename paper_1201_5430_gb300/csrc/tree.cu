@@ -377,70 +377,140 @@ __global__ void k_leaf_level(TreeParams* __restrict__ tp, const SysCube* __restr
 }
 
 // ---------------------------------------------------------------------------
-// Boxes per level (temporary layout: capacity offsets)
+// Boxes of all levels in three passes over the sorted keys
 // ---------------------------------------------------------------------------
-__global__ void k_level_flags(int64_t n, const uint64_t* __restrict__ keys, int shift, int* __restrict__ flags) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        flags[i] = (i == 0) || ((keys[i] >> shift) != (keys[i - 1] >> shift));
+// Element i starts a box at level l iff its key and the previous key differ in
+// the level-l prefix key >> 3 (bits - l), i.e. iff l >= start_level(i).
+__device__ inline int start_level(const uint64_t* __restrict__ keys, int64_t i, int bits) {
+    if (i == 0) return 0;
+    const uint64_t x = keys[i] ^ keys[i - 1];
+    if (x == 0) return 1 << 20;  // never: same leaf at every level
+    const int msb = 63 - __clzll((long long)x);
+    return max(0, bits - msb / 3);
 }
 
-// box_of[i] = exclusive[i] + flag[i] - 1; records box starts and keys.
-__global__ void k_level_boxes(int64_t n, const uint64_t* __restrict__ keys, int shift, const int* __restrict__ flags,
-                              int* __restrict__ boxof, uint64_t* __restrict__ bkey, int* __restrict__ bbeg,
-                              int* __restrict__ bend) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        int f = flags[i];
-        int b = boxof[i] + f - 1;
-        boxof[i] = b;
-        if (f) {
-            bkey[b] = keys[i] >> shift;
-            bbeg[b] = (int)i;
-            if (b > 0) bend[b - 1] = (int)i;
+// cnt[l * nblk + block] = starts at level l among the block's SCAN_TILE elements
+__global__ void __launch_bounds__(SCAN_THREADS) k_lvl_count(int64_t n, const uint64_t* __restrict__ keys, int bits,
+                                                            int L, int nblk, int* __restrict__ cnt) {
+    __shared__ int sc[MAX_LEVELS + 1];
+    if (threadIdx.x <= L) sc[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    int sl[SCAN_ITEMS];
+    for (int j = 0; j < SCAN_ITEMS; ++j) sl[j] = base + j < n ? start_level(keys, base + j, bits) : (1 << 20);
+    for (int l = 0; l <= L; ++l) {
+        int c = 0;
+        for (int j = 0; j < SCAN_ITEMS; ++j) c += sl[j] <= l;
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+        if ((threadIdx.x & 31) == 0 && c) atomicAdd(&sc[l], c);
+    }
+    __syncthreads();
+    if (threadIdx.x <= L) cnt[threadIdx.x * nblk + blockIdx.x] = sc[threadIdx.x];
+}
+
+// One block: per level, exclusive scan of the block counts (in place); counts[l]
+// = boxes at level l; off[l] = first global box index of level l (off[L+1] = total).
+__global__ void __launch_bounds__(1024) k_lvl_scan(int L, int nblk, int* __restrict__ cnt, int* __restrict__ counts,
+                                                   int* __restrict__ off) {
+    __shared__ int carry;
+    for (int l = 0; l <= L; ++l) {
+        if (threadIdx.x == 0) carry = 0;
+        __syncthreads();
+        int* row = cnt + (int64_t)l * nblk;
+        for (int b0 = 0; b0 < nblk; b0 += blockDim.x) {
+            const int i = b0 + threadIdx.x;
+            const int v = i < nblk ? row[i] : 0;
+            int tot;
+            const int ex = block_exclusive_scan(v, &tot);
+            if (i < nblk) row[i] = carry + ex;
+            __syncthreads();
+            if (threadIdx.x == 0) carry += tot;
+            __syncthreads();
         }
-        if (i == n - 1) bend[b] = (int)n;
+        if (threadIdx.x == 0) counts[l] = carry;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        off[0] = 0;
+        for (int l = 0; l <= L; ++l) off[l + 1] = off[l] + counts[l];
     }
 }
 
-// Parent index (level l-1) of every box at level l, from the element ranges.
-__global__ void k_level_parent(const int* __restrict__ nb_dev, const int* __restrict__ bbeg,
-                               const int* __restrict__ boxof_up, int* __restrict__ bparent) {
-    int nb = *nb_dev;
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x)
-        bparent[b] = boxof_up[bbeg[b]];
-}
-
-__global__ void k_level_children(const int* __restrict__ nb_dev, const int* __restrict__ bparent,
-                                 int* __restrict__ cbeg_up, int* __restrict__ cend_up) {
-    int nb = *nb_dev;
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
-        int p = bparent[b];
-        if (b == 0 || bparent[b - 1] != p) cbeg_up[p] = b;
-        if (b == nb - 1 || bparent[b + 1] != p) cend_up[p] = b + 1;
+// Box records of every level (global index off[l] + b): key prefix, element range,
+// parent (level-local, -1 at level 0) and the first child of each parent.
+__global__ void __launch_bounds__(SCAN_THREADS) k_lvl_apply(int64_t n, const uint64_t* __restrict__ keys, int bits,
+                                                            int L, int nblk, const int* __restrict__ cnt,
+                                                            const int* __restrict__ off, uint64_t* __restrict__ bkey,
+                                                            int* __restrict__ bbeg, int* __restrict__ bend,
+                                                            int* __restrict__ bpar, int* __restrict__ bcbeg) {
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    int sl[SCAN_ITEMS], prev[SCAN_ITEMS];
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        sl[j] = base + j < n ? start_level(keys, base + j, bits) : (1 << 20);
+        prev[j] = 0;
+    }
+    for (int l = 0; l <= L; ++l) {
+        int t = 0;
+        for (int j = 0; j < SCAN_ITEMS; ++j) t += sl[j] <= l;
+        int run = block_exclusive_scan(t, nullptr) + cnt[(int64_t)l * nblk + blockIdx.x];
+        const int o = off[l], ou = l > 0 ? off[l - 1] : 0;
+        const int shift = 3 * (bits - l);
+        for (int j = 0; j < SCAN_ITEMS; ++j) {
+            const int64_t i = base + j;
+            if (i >= n) break;
+            if (sl[j] <= l) {
+                const int b = run;
+                bkey[o + b] = keys[i] >> shift;
+                bbeg[o + b] = (int)i;
+                if (b > 0) bend[o + b - 1] = (int)i;
+                const int par = l > 0 ? prev[j] - 1 : -1;  // the level l-1 box holding element i
+                bpar[o + b] = par;
+                if (l > 0 && sl[j] <= l - 1) bcbeg[ou + par] = b;  // i starts the parent too: first child
+                ++run;
+            }
+            prev[j] = run;  // inclusive count of level-l starts up to element i
+            if (i == n - 1) bend[o + run - 1] = (int)n;
+        }
     }
 }
 
-// Copy one level from the capacity layout to the compact layout.
-__global__ void k_compact_level(int nb, int level, int L, const uint64_t* __restrict__ tkey,
-                                const int* __restrict__ tbeg, const int* __restrict__ tend,
-                                const int* __restrict__ tpar, const int* __restrict__ tcb, const int* __restrict__ tce,
-                                uint64_t* __restrict__ bkey, int* __restrict__ bbeg, int* __restrict__ bend,
-                                int* __restrict__ bpar, int* __restrict__ bcb, int* __restrict__ bce) {
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
-        bkey[b] = tkey[b];
-        bbeg[b] = tbeg[b];
-        bend[b] = tend[b];
-        bpar[b] = level > 0 ? tpar[b] : -1;
-        bcb[b] = level < L ? tcb[b] : 0;
-        bce[b] = level < L ? tce[b] : 0;
+struct LevelTable {
+    int L;
+    int off[MAX_LEVELS + 2];
+};
+
+__device__ inline int level_of(const LevelTable& lt, int gb) {
+    int l = 0;
+    while (l < lt.L && gb >= lt.off[l + 1]) ++l;
+    return l;
+}
+
+// children ranges: end of parent p = first child of p + 1 (or the level's box count);
+// leaves have none
+__global__ void k_lvl_children(int nbt, LevelTable lt, int* __restrict__ bcbeg, int* __restrict__ bcend) {
+    for (int gb = blockIdx.x * blockDim.x + threadIdx.x; gb < nbt; gb += gridDim.x * blockDim.x) {
+        const int l = level_of(lt, gb);
+        if (l == lt.L) {
+            bcbeg[gb] = 0;
+            bcend[gb] = 0;
+            continue;
+        }
+        const int p = gb - lt.off[l], nb = lt.off[l + 1] - lt.off[l];
+        bcend[gb] = p + 1 < nb ? bcbeg[gb + 1] : lt.off[l + 2] - lt.off[l + 1];
     }
 }
 
-// 27 colleagues of every box of one level (binary search among the level's keys);
+// 27 colleagues of every box of every level (binary search among its level's keys);
 // the system id above the level's 3*level Morton bits is kept.
-__global__ void k_colleagues(int nb, int level, const uint64_t* __restrict__ bkey, int* __restrict__ col) {
-    const int64_t dim = 1ll << level;
-    const uint64_t mask = (level > 0) ? ((~0ull) >> (64 - 3 * level)) : 0ull;
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+__global__ void k_colleagues_all(int nbt, LevelTable lt, const uint64_t* __restrict__ bkey_all,
+                                 int* __restrict__ col_all) {
+    for (int gb = blockIdx.x * blockDim.x + threadIdx.x; gb < nbt; gb += gridDim.x * blockDim.x) {
+        const int level = level_of(lt, gb);
+        const int o = lt.off[level], nb = lt.off[level + 1] - o, b = gb - o;
+        const uint64_t* bkey = bkey_all + o;
+        int* col = col_all + (int64_t)o * 27;
+        const int64_t dim = 1ll << level;
+        const uint64_t mask = (level > 0) ? ((~0ull) >> (64 - 3 * level)) : 0ull;
         const uint64_t full = bkey[b];
         const uint64_t sysk = (level > 0) ? ((full >> (3 * level)) << (3 * level)) : full;
         const uint64_t key = full & mask;
@@ -598,53 +668,35 @@ int build_tree(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const vec4_t<
     hp.bits = bits;
     hp.nsys = nsys;
 
-    // temporary per-level arrays in capacity layout
+    // capacity of every level: boxes per level <= min(n, nsys 8^l)
     lv.cap_off[0] = 0;
     for (int l = 0; l <= L; ++l) {
         int64_t cap = nn;
-        if (3 * l < 40) cap = std::min<int64_t>(nn, (int64_t)nsys << (3 * l));  // boxes per level <= nsys 8^l
+        if (3 * l < 40) cap = std::min<int64_t>(nn, (int64_t)nsys << (3 * l));
         lv.cap_off[l + 1] = lv.cap_off[l] + (int)cap;
     }
     const int64_t tot_cap = lv.cap_off[L + 1];
-    Buf& tkey = ctx_tmp(c, 0);
-    Buf& tbeg = ctx_tmp(c, 1);
-    Buf& tend = ctx_tmp(c, 2);
-    Buf& tpar = ctx_tmp(c, 3);
-    Buf& tcb = ctx_tmp(c, 4);
-    Buf& tce = ctx_tmp(c, 5);
-    ensure(c, tkey, tot_cap * 8);
-    ensure(c, tbeg, tot_cap * 4);
-    ensure(c, tend, tot_cap * 4);
-    ensure(c, tpar, tot_cap * 4);
-    ensure(c, tcb, tot_cap * 4);
-    ensure(c, tce, tot_cap * 4);
+    ensure(c, tb.bkey, tot_cap * 8);
+    ensure(c, tb.bbeg, tot_cap * 4);
+    ensure(c, tb.bend, tot_cap * 4);
+    ensure(c, tb.bparent, tot_cap * 4);
+    ensure(c, tb.bcbeg, tot_cap * 4);
+    ensure(c, tb.bcend, tot_cap * 4);
 
-    int* boxof_prev = tb.boxof_a.as<int>();
-    int* boxof_cur = tb.boxof_b.as<int>();
-    for (int l = 0; l <= L; ++l) {
-        int shift = 3 * (bits - l);
-        int off = lv.cap_off[l];
-        int* flags = tb.flags.as<int>();
-        k_level_flags<<<grid_for(nn, 256), 256, 0, s>>>(nn, keys, shift, flags);
-        count_launch(c);
-        exclusive_scan(c, nn, flags, boxof_cur, tb.scan_tmp.as<int>(), counts + l);
-        // the scan total is the number of boxes of the level
-        k_level_boxes<<<grid_for(nn, 256), 256, 0, s>>>(nn, keys, shift, flags, boxof_cur, tkey.as<uint64_t>() + off,
-                                                        tbeg.as<int>() + off, tend.as<int>() + off);
-        count_launch(c);
-        if (l > 0) {
-            int offu = lv.cap_off[l - 1];
-            int capl = lv.cap_off[l + 1] - off;
-            k_level_parent<<<grid_for(capl, 256), 256, 0, s>>>(counts + l, tbeg.as<int>() + off, boxof_prev,
-                                                                tpar.as<int>() + off);
-            count_launch(c);
-            k_level_children<<<grid_for(capl, 256), 256, 0, s>>>(counts + l, tpar.as<int>() + off,
-                                                                  tcb.as<int>() + offu, tce.as<int>() + offu);
-            count_launch(c);
-        }
-        std::swap(boxof_prev, boxof_cur);
-        check_launch("levels");
-    }
+    // all levels at once: counts per (level, block of elements), their scan, the records
+    const int nblk = (int)((nn + SCAN_TILE - 1) / SCAN_TILE);
+    Buf& lcnt = ctx_tmp(c, 0);
+    ensure(c, lcnt, (int64_t)(L + 1) * nblk * 4);
+    int* loff = counts + 32;  // off[0 .. L+1] on the device
+    k_lvl_count<<<nblk, SCAN_THREADS, 0, s>>>(nn, keys, bits, L, nblk, lcnt.as<int>());
+    count_launch(c);
+    k_lvl_scan<<<1, 1024, 0, s>>>(L, nblk, lcnt.as<int>(), counts, loff);
+    count_launch(c);
+    k_lvl_apply<<<nblk, SCAN_THREADS, 0, s>>>(nn, keys, bits, L, nblk, lcnt.as<int>(), loff,
+                                              tb.bkey.as<uint64_t>(), tb.bbeg.as<int>(), tb.bend.as<int>(),
+                                              tb.bparent.as<int>(), tb.bcbeg.as<int>());
+    count_launch(c);
+    check_launch("levels");
     int hcounts[64];
     cuda_check(cudaMemcpyAsync(hcounts, counts, 64 * 4, cudaMemcpyDeviceToHost, s), "read counts");
     cuda_check(cudaStreamSynchronize(s), "sync counts");
@@ -654,27 +706,16 @@ int build_tree(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const vec4_t<
         lv.off[l + 1] = lv.off[l] + lv.nbox[l];
     }
     const int64_t nbt = lv.off[L + 1];
-
-    // compact layout
-    ensure(c, tb.bkey, nbt * 8);
-    ensure(c, tb.bbeg, nbt * 4);
-    ensure(c, tb.bend, nbt * 4);
-    ensure(c, tb.bparent, nbt * 4);
-    ensure(c, tb.bcbeg, nbt * 4);
-    ensure(c, tb.bcend, nbt * 4);
+    LevelTable lt{};
+    lt.L = L;
+    for (int l = 0; l <= L + 1 && l <= MAX_LEVELS; ++l) lt.off[l] = lv.off[l];
+    lt.off[L + 2 <= MAX_LEVELS + 1 ? L + 2 : MAX_LEVELS + 1] = lv.off[L + 1];
+    k_lvl_children<<<grid_for(nbt, 256), 256, 0, s>>>((int)nbt, lt, tb.bcbeg.as<int>(), tb.bcend.as<int>());
+    count_launch(c);
     ensure(c, tb.bcol, nbt * 27 * 4);
-    for (int l = 0; l <= L; ++l) {
-        int nb = lv.nbox[l], o = lv.off[l], co = lv.cap_off[l];
-        k_compact_level<<<grid_for(nb, 256), 256, 0, s>>>(
-            nb, l, L, tkey.as<uint64_t>() + co, tbeg.as<int>() + co, tend.as<int>() + co, tpar.as<int>() + co,
-            tcb.as<int>() + co, tce.as<int>() + co, tb.bkey.as<uint64_t>() + o, tb.bbeg.as<int>() + o,
-            tb.bend.as<int>() + o, tb.bparent.as<int>() + o, tb.bcbeg.as<int>() + o, tb.bcend.as<int>() + o);
-        count_launch(c);
-        k_colleagues<<<grid_for(nb, 128), 128, 0, s>>>(nb, l, tb.bkey.as<uint64_t>() + o,
-                                                       tb.bcol.as<int>() + (int64_t)o * 27);
-        count_launch(c);
-    }
-    check_launch("compact");
+    k_colleagues_all<<<grid_for(nbt, 128), 128, 0, s>>>((int)nbt, lt, tb.bkey.as<uint64_t>(), tb.bcol.as<int>());
+    count_launch(c);
+    check_launch("children, colleagues");
 
     // P2P work items over the leaves
     {
