@@ -167,6 +167,10 @@ static void ensure_ops(Ctx* c) {
             tc_tiles_build(c, c->ops.m2l.as<float>(), NUM_OFFSETS, 2 * P, 2 * P, P, c->ops.m2l_tiles);
             cuda_check(cudaStreamSynchronize(c->stream), "tc tiles");
         }
+        if (ctx_use_tc(c) && tc_supported(12 * P, 2 * P, 0)) {
+            tc_tiles_build(c, c->ops.l2p.as<float>(), 1, 12 * P, 2 * P, 0, c->ops.l2p_tiles);
+            cuda_check(cudaStreamSynchronize(c->stream), "tc tiles");
+        }
     }
 }
 
@@ -184,11 +188,16 @@ static const T* cached_op(Ctx* c, int kind, int pout, int pin) {
     if (it != c->opcache.end()) return it->second.as<T>();
     Buf& b = c->opcache[key];
     StageScope sc(c, LHV_STAGE_OPS);
-    if (kind == 5) {
+    if (kind >= 5) {
+        // tensor-core tiles: 5 of M2L(p, p), 7 of L2P(p)
         if constexpr (sizeof(T) == 4) {
             const int P = pout * pout;
-            const float* m2l = cached_op<float>(c, OP_M2L, pout, pout);
-            tc_tiles_build(c, m2l, NUM_OFFSETS, 2 * P, 2 * P, P, c->opcache[key]);
+            if (kind == 5) {
+                const float* m2l = cached_op<float>(c, OP_M2L, pout, pout);
+                tc_tiles_build(c, m2l, NUM_OFFSETS, 2 * P, 2 * P, P, c->opcache[key]);
+            } else {
+                tc_tiles_build(c, cached_op<float>(c, OP_L2P, pout, pout), 1, 12 * P, 2 * P, 0, c->opcache[key]);
+            }
             cuda_check(cudaStreamSynchronize(c->stream), "tc tiles");
         }
     } else {
@@ -222,10 +231,15 @@ static Plan<T> make_plan(Ctx* c, int L) {
             pl.m2l[l] = c->ops.m2l.as<T>();
             pl.m2l_tiles[l] = c->ops.m2l_tiles.ptr ? c->ops.m2l_tiles.as<float>() : nullptr;
         }
+        pl.l2p_tiles = c->ops.l2p_tiles.ptr ? c->ops.l2p_tiles.as<float>() : nullptr;
         return pl;
     }
     pl.p2m = cached_op<T>(c, OP_P2M, pl.p[L], pl.p[L]);
     pl.l2p = cached_op<T>(c, OP_L2P, pl.p[L], pl.p[L]);
+    {
+        const int PL = pl.p[L] * pl.p[L];
+        if (tc && tc_supported(12 * PL, 2 * PL, 0)) pl.l2p_tiles = cached_op<float>(c, 7, pl.p[L], pl.p[L]);
+    }
     for (int l = 2; l <= L; ++l) {
         const int P = pl.p[l] * pl.p[l];
         pl.m2l[l] = cached_op<T>(c, OP_M2L, pl.p[l], pl.p[l]);

@@ -342,7 +342,9 @@ template <typename T>
 void run_l2p(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs,
              const vec4_t<T>* ws, const T* loc, T* cf, Grouped& gp, vec4_t<T>* vfar, vec4_t<T>* sfar) {
     const int L = lv.L, nl = lv.nbox[L], o = lv.off[L], p = pl.p[L], P = p * p;
-    build_grouped(c, gp, 1, nl, nl, gemm_nc_for<T>(2 * P, 12 * P, nl), IdentItems{o, 0});
+    bool tc = false;
+    if constexpr (sizeof(T) == 4) tc = ctx_m2l_tc(c) && pl.l2p_tiles;
+    build_grouped(c, gp, 1, nl, nl, tc ? TC_PAIRS : gemm_nc_for<T>(2 * P, 12 * P, nl), IdentItems{o, 0});
     GemmArgs<T> a{};
     a.g0 = 0;
     a.g1 = 1;
@@ -358,7 +360,21 @@ void run_l2p(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, co
     a.mode = GEMM_STORE;
     a.scale = (T)1;
     a.pairs_hint = nl;
-    run_group_gemm<T>(c, gp, a);
+    bool done = false;
+    if constexpr (sizeof(T) == 4) {
+        if (tc) {
+            // the leaf locals, split into TF32 hi/lo at their own offsets
+            Buf& hi = ctx_tmp(c, 12);
+            Buf& lo = ctx_tmp(c, 13);
+            const int64_t first = (int64_t)o * pl.ld, count = (int64_t)nl * pl.ld;
+            ensure(c, hi, (first + count) * 4);
+            ensure(c, lo, (first + count) * 4);
+            tc_split(c, count, loc + first, hi.as<float>() + first, lo.as<float>() + first);
+            run_tc_gemm(c, gp, a, pl.l2p_tiles, hi.as<float>(), lo.as<float>(), ctx_err_flag(c));
+            done = true;
+        }
+    }
+    if (!done) run_group_gemm<T>(c, gp, a);
     const size_t smem = sizeof(T) * 12 * P;
     cuda_check(cudaFuncSetAttribute(k_l2p_eval<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "l2p attr");
     const int64_t max_tiles = nl + lv.n / P2P_TILE + 1;

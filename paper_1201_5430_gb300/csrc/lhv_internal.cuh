@@ -132,6 +132,7 @@ struct OpTables {
     Buf l2p;                   // [2P][12P]     v_k (Eq. evf3) and u_lk (Eq. dt3) coefficients
     Buf p2m;                   // [3P][2P]      Eq. eve4 for w = i_x, i_y, i_z
     Buf m2l_tiles;             // TF32 hi/lo tiles of m2l for the tensor-core products (LHV_TF32X3)
+    Buf l2p_tiles;             // the same for the L2P map
     Buf offsets;               // int[316][3] M2L offsets (dx, dy, dz)
     Buf slot_of;               // int[343] offset (dx+3)*49+(dy+3)*7+(dz+3) -> slot or -1
 };
@@ -165,6 +166,7 @@ struct Plan {
     const T* l2l[MAX_LEVELS + 1] = {};     // [l]: level l-1 -> l, 8 x [2P(l-1)][2P(l)]
     const T* m2l[MAX_LEVELS + 1] = {};     // [l]: 316 x [2P(l)][2P(l)]
     const float* m2l_tiles[MAX_LEVELS + 1] = {};  // tensor-core tiles of m2l[l] (LHV_TF32X3), or null
+    const float* l2p_tiles = nullptr;      // tensor-core tiles of l2p (LHV_TF32X3), or null
     bool uniform = true;                   // p[l] equal over l = 2..L
 };
 

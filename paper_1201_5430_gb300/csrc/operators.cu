@@ -404,7 +404,8 @@ int m2l_slot_host(int dx, int dy, int dz) {
 }
 
 void free_operators(OpTables& ops) {
-    Buf* all[] = {&ops.m2l, &ops.m2m, &ops.l2l, &ops.l2p, &ops.p2m, &ops.offsets, &ops.slot_of, &ops.m2l_tiles};
+    Buf* all[] = {&ops.m2l,     &ops.m2m,     &ops.l2l,       &ops.l2p,      &ops.p2m,
+                  &ops.offsets, &ops.slot_of, &ops.m2l_tiles, &ops.l2p_tiles};
     for (Buf* b : all) {
         if (b->ptr) cudaFree(b->ptr);
         b->ptr = nullptr;

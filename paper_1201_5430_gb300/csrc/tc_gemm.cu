@@ -40,6 +40,7 @@ constexpr int TC_M = 128;         // pairs per work item (MMA M)
 constexpr int TC_KC = 16;         // K per staged chunk (2 MMA k-steps of 8)
 constexpr int TC_NMAX = 256;      // outputs per work item (MMA N, TMEM columns)
 constexpr uint32_t TMEM_COLS = 256;
+constexpr int TC_MAX_RANGES = 16;  // output ranges of 256 rows per operator (L2P at p = 16: 12)
 constexpr long long WAIT_LIMIT = 1ll << 26;
 
 // byte offset of element (row, k) of a [rows x TC_KC] K-major tile made of
@@ -135,9 +136,9 @@ struct TcArgs {
     const float* tiles;    // operator tiles in shared-memory order (see tc_tiles_build), hi then lo
     int64_t group_stride;  // floats per group of `tiles`
     int nranges;
-    int n0[8], nlen[8];    // N ranges (<= 256 wide, multiples of 16)
-    int kbeg[8];           // first K of each range (psplit for the chi outputs)
-    int64_t roff[8];       // float offset of each range inside a group
+    int n0[TC_MAX_RANGES], nlen[TC_MAX_RANGES];  // N ranges (<= 256 wide, multiples of 16)
+    int kbeg[TC_MAX_RANGES];                     // first K of each range (psplit for the chi outputs)
+    int64_t roff[TC_MAX_RANGES];                 // float offset of each range inside a group
     int nmax;              // widest range (rows of the operator tile in a stage)
     int stage_bytes;       // bytes of one shared stage (Xh, Xl, Bh, Bl), 1024-aligned
     int nstages;           // S, 2 or 3
@@ -451,7 +452,7 @@ bool tc_supported(int R, int C, int psplit) {
     if (psplit > 0 && (psplit % 16 != 0)) return false;
     const int ranges = psplit > 0 ? (psplit + TC_NMAX - 1) / TC_NMAX + (R - psplit + TC_NMAX - 1) / TC_NMAX
                                   : (R + TC_NMAX - 1) / TC_NMAX;
-    return ranges <= 8;
+    return ranges <= TC_MAX_RANGES;
 }
 
 void tc_tiles_build(Ctx* c, const float* ops, int ngroups, int R, int C, int psplit, Buf& tiles) {
