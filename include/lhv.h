@@ -52,10 +52,10 @@ extern "C" {
 /* ---- arithmetic of the evaluation (lhv_config.precision) --------------- */
 #define LHV_FP32 0  /* all kernels in FP32 (CUDA cores); operator tables built in FP64, stored FP32 */
 #define LHV_FP64 1  /* all kernels in FP64 (use the _f64 entry points) */
-#define LHV_TF32X3 2 /* mixed precision: as LHV_FP32, but the M2L products and the L2P coefficient
-                        map run on the tensor cores in TF32 with split operands (hi.hi + hi.lo +
-                        lo.hi, FP32 accumulation) where the shapes allow (M2L: p a multiple of
-                        4); other p, P2M, M2M and L2L run as in LHV_FP32 */
+#define LHV_TF32X3 2 /* mixed precision: as LHV_FP32, but the M2L products run on the tensor cores
+                        in TF32 with split operands (hi.hi + hi.lo + lo.hi, FP32 accumulation)
+                        where p is a multiple of 4; other p and the other maps run as in
+                        LHV_FP32 */
 
 /* ---- which parts of Eq. fmm1 to evaluate (lhv_config.terms) ------------ */
 #define LHV_TERMS_NEAR 1  /* sparse part only: direct sum over colleague leaves */

@@ -48,6 +48,8 @@ struct Ctx {
     int level_p[MAX_LEVELS + 1] = {};   // lhv_set_level_p (0: cfg.p)
     std::map<int, Buf> opcache;         // tables of other (kind, p_out, p_in) than ops, type opcache_type
     int opcache_type = 0;
+    std::map<int, Csr> spcache;         // sparse P2M / L2P of other p than ops, type spcache_type
+    int spcache_type = 0;
     int eval_p[MAX_LEVELS + 1] = {};    // truncation numbers of the last evaluation's expansions
     int eval_ld = 0;                    // their stride (reals per box)
     int leaf_override = 0;              // leaf cap chosen by the selector (0: cfg.leaf_max)
@@ -160,6 +162,8 @@ static void ensure_ops(Ctx* c) {
     free_operators(c->ops);
     StageScope sc(c, LHV_STAGE_OPS);
     build_operators<T>(c, c->cfg.p, c->ops);
+    build_sparse<T>(c, OP_P2M, c->cfg.p, c->ops.p2m_sp);
+    build_sparse<T>(c, OP_L2P, c->cfg.p, c->ops.l2p_sp);
     c->ops_type = (int)sizeof(T);
     if constexpr (sizeof(T) == 4) {
         const int P = c->ops.P;
@@ -167,10 +171,7 @@ static void ensure_ops(Ctx* c) {
             tc_tiles_build(c, c->ops.m2l.as<float>(), NUM_OFFSETS, 2 * P, 2 * P, P, c->ops.m2l_tiles);
             cuda_check(cudaStreamSynchronize(c->stream), "tc tiles");
         }
-        if (ctx_use_tc(c) && tc_supported(12 * P, 2 * P, 0)) {
-            tc_tiles_build(c, c->ops.l2p.as<float>(), 1, 12 * P, 2 * P, 0, c->ops.l2p_tiles);
-            cuda_check(cudaStreamSynchronize(c->stream), "tc tiles");
-        }
+
     }
 }
 
@@ -188,22 +189,46 @@ static const T* cached_op(Ctx* c, int kind, int pout, int pin) {
     if (it != c->opcache.end()) return it->second.as<T>();
     Buf& b = c->opcache[key];
     StageScope sc(c, LHV_STAGE_OPS);
-    if (kind >= 5) {
-        // tensor-core tiles: 5 of M2L(p, p), 7 of L2P(p)
+    if (kind == 5) {
+        // tensor-core tiles of M2L(p, p)
         if constexpr (sizeof(T) == 4) {
             const int P = pout * pout;
-            if (kind == 5) {
-                const float* m2l = cached_op<float>(c, OP_M2L, pout, pout);
-                tc_tiles_build(c, m2l, NUM_OFFSETS, 2 * P, 2 * P, P, c->opcache[key]);
-            } else {
-                tc_tiles_build(c, cached_op<float>(c, OP_L2P, pout, pout), 1, 12 * P, 2 * P, 0, c->opcache[key]);
-            }
+            const float* m2l = cached_op<float>(c, OP_M2L, pout, pout);
+            tc_tiles_build(c, m2l, NUM_OFFSETS, 2 * P, 2 * P, P, c->opcache[key]);
             cuda_check(cudaStreamSynchronize(c->stream), "tc tiles");
         }
     } else {
         build_op<T>(c, kind, pout, pin, b);
     }
     return c->opcache[key].as<T>();
+}
+
+template <typename T>
+static CsrView<T> view(const Csr& m) {
+    CsrView<T> v;
+    v.rowptr = m.rowptr.as<int>();
+    v.col = m.col.as<int>();
+    v.val = m.val.as<T>();
+    v.rows = m.rows;
+    return v;
+}
+
+// P2M / L2P of truncation number p in row-compressed form, from the cache.
+template <typename T>
+static CsrView<T> cached_sparse(Ctx* c, int kind, int p) {
+    if (c->spcache_type != (int)sizeof(T)) {
+        for (auto& kv : c->spcache) free_csr(kv.second);
+        c->spcache.clear();
+        c->spcache_type = (int)sizeof(T);
+    }
+    const int key = kind | (p << 8);
+    auto it = c->spcache.find(key);
+    if (it == c->spcache.end()) {
+        StageScope sc(c, LHV_STAGE_OPS);
+        build_sparse<T>(c, kind, p, c->spcache[key]);
+        it = c->spcache.find(key);
+    }
+    return view<T>(it->second);
 }
 
 // Truncation numbers and tables of an evaluation over levels 0..L.
@@ -231,15 +256,14 @@ static Plan<T> make_plan(Ctx* c, int L) {
             pl.m2l[l] = c->ops.m2l.as<T>();
             pl.m2l_tiles[l] = c->ops.m2l_tiles.ptr ? c->ops.m2l_tiles.as<float>() : nullptr;
         }
-        pl.l2p_tiles = c->ops.l2p_tiles.ptr ? c->ops.l2p_tiles.as<float>() : nullptr;
+        pl.p2m_sp = view<T>(c->ops.p2m_sp);
+        pl.l2p_sp = view<T>(c->ops.l2p_sp);
         return pl;
     }
     pl.p2m = cached_op<T>(c, OP_P2M, pl.p[L], pl.p[L]);
     pl.l2p = cached_op<T>(c, OP_L2P, pl.p[L], pl.p[L]);
-    {
-        const int PL = pl.p[L] * pl.p[L];
-        if (tc && tc_supported(12 * PL, 2 * PL, 0)) pl.l2p_tiles = cached_op<float>(c, 7, pl.p[L], pl.p[L]);
-    }
+    pl.p2m_sp = cached_sparse<T>(c, OP_P2M, pl.p[L]);
+    pl.l2p_sp = cached_sparse<T>(c, OP_L2P, pl.p[L]);
     for (int l = 2; l <= L; ++l) {
         const int P = pl.p[l] * pl.p[l];
         pl.m2l[l] = cached_op<T>(c, OP_M2L, pl.p[l], pl.p[l]);
@@ -301,7 +325,6 @@ static int evaluate(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const ve
         ensure(c, c->loc, nbt * pl.ld * (int64_t)sizeof(T));
         ensure(c, c->table, (nbt - lv.off[2]) * (int64_t)NUM_OFFSETS * 4);
         ensure(c, c->W, nleaf * 3 * PL * (int64_t)sizeof(T));
-        ensure(c, c->cf, nleaf * 12 * PL * (int64_t)sizeof(T));
         ensure(c, c->vfar, n * (int64_t)sizeof(vec4_t<T>));
         ensure(c, c->sfar, n * (int64_t)sizeof(vec4_t<T>));
         T* mult = c->mult.as<T>();
@@ -339,7 +362,7 @@ static int evaluate(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const ve
         sfar = c->sfar.as<vec4_t<T>>();
         {
             StageScope sc(c, LHV_STAGE_L2P);
-            run_l2p<T>(c, pl, c->tb, lv, xs, ws, loc, c->cf.as<T>(), c->gp_leaf, vfar, sfar);
+            run_l2p<T>(c, pl, c->tb, lv, xs, ws, loc, vfar, sfar);
         }
     }
     {
@@ -684,6 +707,8 @@ void lhv_destroy(lhv_ctx* ctx) {
     lhv::free_operators(c.ops);
     for (auto& kv : c.opcache) lhv::release(kv.second);
     c.opcache.clear();
+    for (auto& kv : c.spcache) lhv::free_csr(kv.second);
+    c.spcache.clear();
     for (auto* b : {&c.sel_W, &c.sel_b, &c.sel_X, &c.sel_Z, &c.sel_choice, &c.sel_idx, &c.sel_dv, &c.sel_ds, &c.sel_err})
         lhv::release(*b);
     lhv::TreeBufs& t = c.tb;

@@ -73,6 +73,7 @@ __device__ inline void for_each_Q(int p, T x, T y, T z, F&& f) {
 // with G_k the scaled real form of Eq. eve4 for w = i_k.
 // ---------------------------------------------------------------------------
 constexpr int P2M_THREADS = 128;
+constexpr int P2M_MAX_OUT = (3 * 24 * 24 + P2M_THREADS - 1) / P2M_THREADS;  // W entries per thread, p <= 24
 
 // Work items are the tiles of at most P2P_TILE consecutive elements of one leaf
 // (the near-field tiles), so a crowded leaf is spread over several blocks; each
@@ -98,6 +99,9 @@ __global__ void __launch_bounds__(P2M_THREADS) k_p2m_w(const int* __restrict__ n
         const T invh = (T)(1.0 / h);
         T* Wb = Wout + (int64_t)b * 3 * P;
         const int e0 = tw.y, e1 = min(bend[b], tw.y + P2P_TILE);
+        T acc[P2M_MAX_OUT];  // outputs i = threadIdx.x + q blockDim.x of this tile, summed over its chunks
+#pragma unroll
+        for (int q = 0; q < P2M_MAX_OUT; ++q) acc[q] = 0;
         for (int c0 = e0; c0 < e1; c0 += chunk) {
             const int ne = min(chunk, e1 - c0);
             __syncthreads();
@@ -126,20 +130,50 @@ __global__ void __launch_bounds__(P2M_THREADS) k_p2m_w(const int* __restrict__ n
                 });
             }
             __syncthreads();
-            for (int i = threadIdx.x; i < 3 * P; i += blockDim.x) {
+#pragma unroll
+            for (int q = 0; q < P2M_MAX_OUT; ++q) {
+                const int i = threadIdx.x + q * blockDim.x;
+                if (i >= 3 * P) break;
                 const int k = i / P, j = i - k * P;
                 T s = 0;
                 for (int e = 0; e < ne; ++e) s += wk[e * 3 + k] * gh[(size_t)e * P + j];
-                atomicAdd(Wb + i, s);
+                acc[q] += s;
             }
+        }
+#pragma unroll
+        for (int q = 0; q < P2M_MAX_OUT; ++q) {
+            const int i = threadIdx.x + q * blockDim.x;
+            if (i >= 3 * P) break;
+            atomicAdd(Wb + i, acc[q]);
         }
         __syncthreads();
     }
 }
 
+// P2M, part 2 (per leaf): M_hat = G W with G the P2M map of Eq. eve4 in row-compressed form
+// (its structural zeros dropped); one block per leaf, W staged in shared memory.
+template <typename T>
+__global__ void __launch_bounds__(P2M_THREADS) k_p2m_apply(int nleaf, const T* __restrict__ W, int P,
+                                                          CsrView<T> g, T* __restrict__ mult, int64_t ld) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* w = reinterpret_cast<T*>(smem_raw);  // [3P]
+    for (int b = blockIdx.x; b < nleaf; b += gridDim.x) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < 3 * P; i += blockDim.x) w[i] = W[(int64_t)b * 3 * P + i];
+        __syncthreads();
+        T* out = mult + (int64_t)b * ld;
+        for (int r = threadIdx.x; r < g.rows; r += blockDim.x) {
+            T acc = 0;
+            for (int k = g.rowptr[r]; k < g.rowptr[r + 1]; ++k) acc += g.val[k] * w[g.col[k]];
+            out[r] = acc;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
-// L2P (per leaf, after the grouped GEMM cf = E L_hat that forms the 12
-// coefficient vectors of v_k (Eq. evf3) and u_lk = D_{i_l} v_k (Eq. dt3)):
+// L2P (per tile of a leaf; the 12 coefficient vectors cf = E L_hat of v_k (Eq. evf3)
+// and u_lk = D_{i_l} v_k (Eq. dt3) come from the leaf's local expansion through the
+// row-compressed map E, in shared memory):
 //   v_k = (1/h) c_k . b(rho),   u_lk = (1/h^2) c_{3+3l+k} . b(rho),
 //   s_k = sum_l w_l u_lk (Eq. evf6),
 // b = real form of R_hat = nu R:  b[n^2] = R_hat_n^0,  2 Re R_hat_n^m,  -2 Im R_hat_n^m,
@@ -154,12 +188,13 @@ __global__ void __launch_bounds__(L2P_THREADS) k_l2p_eval(const int* __restrict_
                                                         const int* __restrict__ bend,
                                                         const SysCube* __restrict__ cubes,
                                                         const vec4_t<T>* __restrict__ xs,
-                                                        const vec4_t<T>* __restrict__ ws, const T* __restrict__ cfg,
-                                                        vec4_t<T>* __restrict__ vfar, vec4_t<T>* __restrict__ sfar,
-                                                        int p) {
+                                                        const vec4_t<T>* __restrict__ ws, const T* __restrict__ loc,
+                                                        int64_t ld, CsrView<T> e, vec4_t<T>* __restrict__ vfar,
+                                                        vec4_t<T>* __restrict__ sfar, int p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int P = p * p;
     T* cf = reinterpret_cast<T*>(smem_raw);  // [P][12]
+    T* lh = cf + 12 * P;                     // [2P] the leaf's local expansion
     const int ntiles = *ntiles_dev;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int2 tw = tiles[t];
@@ -167,10 +202,13 @@ __global__ void __launch_bounds__(L2P_THREADS) k_l2p_eval(const int* __restrict_
         double cx, cy, cz, h;
         box_geom(cubes, bkey[b], level, cx, cy, cz, h);
         __syncthreads();
-        const T* src = cfg + (int64_t)b * 12 * P;
-        for (int idx = threadIdx.x; idx < 12 * P; idx += blockDim.x) {
-            const int j = idx / P, i = idx - j * P;
-            cf[i * 12 + j] = src[idx];
+        for (int i = threadIdx.x; i < 2 * P; i += blockDim.x) lh[i] = loc[(int64_t)b * ld + i];
+        __syncthreads();
+        for (int r = threadIdx.x; r < 12 * P; r += blockDim.x) {  // output r = j P + i: vector j, entry i
+            T acc = 0;
+            for (int k = e.rowptr[r]; k < e.rowptr[r + 1]; ++k) acc += e.val[k] * lh[e.col[k]];
+            const int j = r / P, i = r - j * P;
+            cf[i * 12 + j] = acc;
         }
         __syncthreads();
         const T invh = (T)(1.0 / h);
@@ -228,8 +266,10 @@ template <typename T>
 void run_p2m(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs,
              const vec4_t<T>* ws, T* W, Grouped& gp, T* mult) {
     const int L = lv.L, nl = lv.nbox[L], o = lv.off[L], p = pl.p[L], P = p * p;
-    int chunk = (int)std::min<size_t>(128, (160 * 1024) / (sizeof(T) * (P + 3)));
-    chunk = std::max(32, chunk / 32 * 32);
+    // the harmonics of a chunk sit in shared memory: the largest chunk (128, 64 or 32 elements)
+    // that still leaves room for two blocks per SM
+    int chunk = 128;
+    while (chunk > 32 && sizeof(T) * (size_t)chunk * (P + 3) > 80 * 1024) chunk /= 2;
     const size_t smem = sizeof(T) * (size_t)chunk * (P + 3);
     cuda_check(cudaFuncSetAttribute(k_p2m_w<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "p2m attr");
     cuda_check(cudaMemsetAsync(W, 0, sizeof(T) * (size_t)nl * 3 * P, stream_of(c)), "p2m zero");
@@ -239,23 +279,14 @@ void run_p2m(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, co
         tb.cubes.as<SysCube>(), xs, ws, W, p, chunk);
     count_launch(c);
     check_launch("p2m w");
-    build_grouped(c, gp, 1, nl, nl, gemm_nc_for<T>(3 * P, 2 * P, nl), IdentItems{0, o});
-    GemmArgs<T> a{};
-    a.g0 = 0;
-    a.g1 = 1;
-    a.ops = pl.p2m;
-    a.ops_mod = 1;
-    a.R = 2 * P;
-    a.C = 3 * P;
-    a.psplit = 0;
-    a.in = W;
-    a.ldin = 3 * P;
-    a.out = mult;
-    a.ldout = pl.ld;
-    a.mode = GEMM_STORE;
-    a.scale = (T)1;  // the 1/h of each leaf is applied to W
-    a.pairs_hint = nl;
-    run_group_gemm<T>(c, gp, a);
+    const size_t smem2 = sizeof(T) * 3 * P;
+    cuda_check(cudaFuncSetAttribute(k_p2m_apply<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2),
+               "p2m apply attr");
+    k_p2m_apply<T><<<grid_for(nl, 1, 152 * 16), P2M_THREADS, smem2, stream_of(c)>>>(nl, W, P, pl.p2m_sp,
+                                                                                   mult + (int64_t)o * pl.ld, pl.ld);
+    count_launch(c);
+    check_launch("p2m apply");
+    (void)gp;
 }
 
 template <typename T>
@@ -340,47 +371,14 @@ void run_l2l(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, Gr
 
 template <typename T>
 void run_l2p(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs,
-             const vec4_t<T>* ws, const T* loc, T* cf, Grouped& gp, vec4_t<T>* vfar, vec4_t<T>* sfar) {
+             const vec4_t<T>* ws, const T* loc, vec4_t<T>* vfar, vec4_t<T>* sfar) {
     const int L = lv.L, nl = lv.nbox[L], o = lv.off[L], p = pl.p[L], P = p * p;
-    bool tc = false;
-    if constexpr (sizeof(T) == 4) tc = ctx_m2l_tc(c) && pl.l2p_tiles;
-    build_grouped(c, gp, 1, nl, nl, tc ? TC_PAIRS : gemm_nc_for<T>(2 * P, 12 * P, nl), IdentItems{o, 0});
-    GemmArgs<T> a{};
-    a.g0 = 0;
-    a.g1 = 1;
-    a.ops = pl.l2p;
-    a.ops_mod = 1;
-    a.R = 12 * P;
-    a.C = 2 * P;
-    a.psplit = 0;
-    a.in = loc;
-    a.ldin = pl.ld;
-    a.out = cf;
-    a.ldout = 12 * P;
-    a.mode = GEMM_STORE;
-    a.scale = (T)1;
-    a.pairs_hint = nl;
-    bool done = false;
-    if constexpr (sizeof(T) == 4) {
-        if (tc) {
-            // the leaf locals, split into TF32 hi/lo at their own offsets
-            Buf& hi = ctx_tmp(c, 12);
-            Buf& lo = ctx_tmp(c, 13);
-            const int64_t first = (int64_t)o * pl.ld, count = (int64_t)nl * pl.ld;
-            ensure(c, hi, (first + count) * 4);
-            ensure(c, lo, (first + count) * 4);
-            tc_split(c, count, loc + first, hi.as<float>() + first, lo.as<float>() + first);
-            run_tc_gemm(c, gp, a, pl.l2p_tiles, hi.as<float>(), lo.as<float>(), ctx_err_flag(c));
-            done = true;
-        }
-    }
-    if (!done) run_group_gemm<T>(c, gp, a);
-    const size_t smem = sizeof(T) * 12 * P;
+    const size_t smem = sizeof(T) * 14 * P;
     cuda_check(cudaFuncSetAttribute(k_l2p_eval<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "l2p attr");
     const int64_t max_tiles = nl + lv.n / P2P_TILE + 1;
     k_l2p_eval<T><<<grid_for(max_tiles, 1, 152 * 16), L2P_THREADS, smem, stream_of(c)>>>(
         tb.tile_count.as<int>(), tb.tiles.as<int2>(), L, tb.bkey.as<uint64_t>() + o, tb.bend.as<int>() + o,
-        tb.cubes.as<SysCube>(), xs, ws, cf, vfar, sfar, p);
+        tb.cubes.as<SysCube>(), xs, ws, loc + (int64_t)o * pl.ld, pl.ld, pl.l2p_sp, vfar, sfar, p);
     count_launch(c);
     check_launch("l2p");
 }
@@ -391,7 +389,7 @@ void run_l2p(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, co
     template void run_m2m<T>(Ctx*, const Plan<T>&, const TreeBufs&, const Levels&, Grouped&, T*);              \
     template void run_l2l<T>(Ctx*, const Plan<T>&, const TreeBufs&, const Levels&, Grouped&, T*);              \
     template void run_l2p<T>(Ctx*, const Plan<T>&, const TreeBufs&, const Levels&, const vec4_t<T>*,            \
-                             const vec4_t<T>*, const T*, T*, Grouped&, vec4_t<T>*, vec4_t<T>*);
+                             const vec4_t<T>*, const T*, vec4_t<T>*, vec4_t<T>*);
 LHV_INST(float)
 LHV_INST(double)
 #undef LHV_INST

@@ -122,6 +122,21 @@ void gather_sorted(Ctx* c, int64_t n, const int* perm, const vec4_t<T>* x4, cons
                    vec4_t<T>* xs, vec4_t<T>* ws);
 
 // ---- operators (operators.cu) -----------------------------------------------
+// Row-compressed form of a sparse map (rows = outputs): out[r] = sum val[k] in[col[k]],
+// k in [rowptr[r], rowptr[r+1]).
+struct Csr {
+    Buf rowptr, col, val;
+    int rows = 0;
+    int64_t nnz = 0;
+};
+template <typename T>
+struct CsrView {
+    const int* rowptr = nullptr;
+    const int* col = nullptr;
+    const T* val = nullptr;
+    int rows = 0;
+};
+
 struct OpTables {
     int p = 0;
     int P = 0;                 // p*p
@@ -132,7 +147,7 @@ struct OpTables {
     Buf l2p;                   // [2P][12P]     v_k (Eq. evf3) and u_lk (Eq. dt3) coefficients
     Buf p2m;                   // [3P][2P]      Eq. eve4 for w = i_x, i_y, i_z
     Buf m2l_tiles;             // TF32 hi/lo tiles of m2l for the tensor-core products (LHV_TF32X3)
-    Buf l2p_tiles;             // the same for the L2P map
+    Csr p2m_sp, l2p_sp;        // P2M and L2P in row-compressed form (their structural zeros dropped)
     Buf offsets;               // int[316][3] M2L offsets (dx, dy, dz)
     Buf slot_of;               // int[343] offset (dx+3)*49+(dy+3)*7+(dz+3) -> slot or -1
 };
@@ -146,6 +161,10 @@ void build_operators(Ctx* c, int p, OpTables& ops);
 enum OpKind : int { OP_M2L = 0, OP_M2M = 1, OP_L2L = 2, OP_L2P = 3, OP_P2M = 4 };
 template <typename T>
 void build_op(Ctx* c, int kind, int pout, int pin, Buf& dst);
+// P2M (2P x 3P) or L2P (12P x 2P) of truncation number p, rows = outputs, in T.
+template <typename T>
+void build_sparse(Ctx* c, int kind, int p, Csr& dst);
+void free_csr(Csr& m);
 void free_operators(OpTables& ops);
 int m2l_slot_host(int dx, int dy, int dz);   // same mapping as slot_of, on the host
 
@@ -166,7 +185,7 @@ struct Plan {
     const T* l2l[MAX_LEVELS + 1] = {};     // [l]: level l-1 -> l, 8 x [2P(l-1)][2P(l)]
     const T* m2l[MAX_LEVELS + 1] = {};     // [l]: 316 x [2P(l)][2P(l)]
     const float* m2l_tiles[MAX_LEVELS + 1] = {};  // tensor-core tiles of m2l[l] (LHV_TF32X3), or null
-    const float* l2p_tiles = nullptr;      // tensor-core tiles of l2p (LHV_TF32X3), or null
+    CsrView<T> p2m_sp, l2p_sp;             // P2M(p[L]), L2P(p[L]) in row-compressed form
     bool uniform = true;                   // p[l] equal over l = 2..L
 };
 
@@ -181,10 +200,10 @@ void run_m2m(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, Gr
 // L2L for all levels 2 -> 3 .. L-1 -> L (adds into loc).
 template <typename T>
 void run_l2l(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, Grouped& gp, T* loc);
-// L2P at the leaves; work buffer cf: nleaf * 12P reals.
+// L2P at the leaves.
 template <typename T>
 void run_l2p(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs,
-             const vec4_t<T>* ws, const T* loc, T* cf, Grouped& gp, vec4_t<T>* vfar, vec4_t<T>* sfar);
+             const vec4_t<T>* ws, const T* loc, vec4_t<T>* vfar, vec4_t<T>* sfar);
 
 // ---- M2L (m2l.cu) ------------------------------------------------------------
 // table: (off[L+1] - off[2]) * 316 ints; nc: pairs per GEMM chunk (gemm_nc).

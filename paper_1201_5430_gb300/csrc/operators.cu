@@ -404,14 +404,66 @@ int m2l_slot_host(int dx, int dy, int dz) {
 }
 
 void free_operators(OpTables& ops) {
-    Buf* all[] = {&ops.m2l,     &ops.m2m,     &ops.l2l,       &ops.l2p,      &ops.p2m,
-                  &ops.offsets, &ops.slot_of, &ops.m2l_tiles, &ops.l2p_tiles};
+    Buf* all[] = {&ops.m2l, &ops.m2m, &ops.l2l, &ops.l2p, &ops.p2m, &ops.offsets, &ops.slot_of, &ops.m2l_tiles};
     for (Buf* b : all) {
         if (b->ptr) cudaFree(b->ptr);
         b->ptr = nullptr;
         b->cap = 0;
     }
+    free_csr(ops.p2m_sp);
+    free_csr(ops.l2p_sp);
     ops.p = 0;
+}
+
+void free_csr(Csr& m) {
+    for (Buf* b : {&m.rowptr, &m.col, &m.val}) {
+        if (b->ptr) cudaFree(b->ptr);
+        b->ptr = nullptr;
+        b->cap = 0;
+    }
+    m.rows = 0;
+    m.nnz = 0;
+}
+
+template <typename T>
+void build_sparse(Ctx* c, int kind, int p, Csr& dst) {
+    // the dense FP64 map (k-major [C][R]), read back once and compressed by rows
+    const int P = p * p;
+    const int R = kind == OP_P2M ? 2 * P : 12 * P;
+    const int C = kind == OP_P2M ? 3 * P : 2 * P;
+    Buf dense;
+    std::vector<double> h((size_t)R * C);
+    try {
+        build_op<double>(c, kind, p, p, dense);
+        cuda_check(cudaMemcpy(h.data(), dense.ptr, h.size() * sizeof(double), cudaMemcpyDeviceToHost), "sparse read");
+    } catch (...) {
+        cudaFree(dense.ptr);
+        throw;
+    }
+    cudaFree(dense.ptr);
+    std::vector<int> rowptr(R + 1, 0), col;
+    std::vector<T> val;
+    for (int r = 0; r < R; ++r) {
+        for (int k = 0; k < C; ++k) {
+            const double v = h[(size_t)k * R + r];
+            if (v != 0.0) {
+                col.push_back(k);
+                val.push_back((T)v);
+            }
+        }
+        rowptr[r + 1] = (int)col.size();
+    }
+    free_csr(dst);
+    ensure(c, dst.rowptr, (int64_t)(R + 1) * 4);
+    ensure(c, dst.col, (int64_t)std::max<size_t>(col.size(), 1) * 4);
+    ensure(c, dst.val, (int64_t)std::max<size_t>(val.size(), 1) * sizeof(T));
+    cuda_check(cudaMemcpy(dst.rowptr.ptr, rowptr.data(), (R + 1) * 4, cudaMemcpyHostToDevice), "sparse rows");
+    if (!col.empty()) {
+        cuda_check(cudaMemcpy(dst.col.ptr, col.data(), col.size() * 4, cudaMemcpyHostToDevice), "sparse cols");
+        cuda_check(cudaMemcpy(dst.val.ptr, val.data(), val.size() * sizeof(T), cudaMemcpyHostToDevice), "sparse vals");
+    }
+    dst.rows = R;
+    dst.nnz = (int64_t)col.size();
 }
 
 void m2l_offsets(std::vector<int>& offs, std::vector<int>& slot_of) {
@@ -527,6 +579,8 @@ void build_operators(Ctx* c, int p, OpTables& ops) {
     cuda_check(cudaStreamSynchronize(s), "operators");
 }
 
+template void build_sparse<float>(Ctx*, int, int, Csr&);
+template void build_sparse<double>(Ctx*, int, int, Csr&);
 template void build_op<float>(Ctx*, int, int, int, Buf&);
 template void build_op<double>(Ctx*, int, int, int, Buf&);
 template void build_operators<float>(Ctx*, int, OpTables&);
