@@ -253,6 +253,57 @@ def run_blobs64(args, torch, LHV, local, world, rank, dist):
                           "speedup_vs_sequential_plain_fp32": val_b / val_s}), flush=True)
 
 
+def run_offset_rings(args, torch, LHV, local, world, rank, dist):
+    """Mixed-precision form on the two colliding offset rings (2 x 2^20 elements, p = 16):
+    evaluations of v and s per second, TF32x3 against plain FP32, each with its error
+    against FP64 direct sums at 10,000 random targets (GPU direct-sum kernel)."""
+    x, w, spec = workloads.make("offset_rings_2097152")
+    n = x.shape[0]
+    x0 = torch.from_numpy(workloads.to_f4(x)).cuda()
+    w0 = torch.from_numpy(workloads.to_f4(w)).cuda()
+    stream = torch.cuda.current_stream()
+    idx = torch.from_numpy(np.random.default_rng(3).choice(n, 10000, replace=False).astype(np.int32)).cuda()
+    ref = LHV(p=4, leaf_max=spec["leaf_max"], core_a=spec["a"])
+    v0, s0 = ref.direct_sampled(x0, w0, idx)
+    ref.close()
+    out = {}
+    for prec in ("fp32", "tf32x3"):
+        c = LHV(p=spec["p"], leaf_max=spec["leaf_max"], core_a=spec["a"], eps=spec["eps"], precision=prec)
+        c.autotune(x0, w0)
+        v, s = c.evaluate_velocity_stretching(x0, w0)
+        il = idx.long()
+        ev = float(torch.linalg.norm(v[il].double()[:, :3] - v0[:, :3]) / torch.linalg.norm(v0[:, :3]))
+        es = float(torch.linalg.norm(s[il].double()[:, :3] - s0[:, :3]) / torch.linalg.norm(s0[:, :3]))
+        for _ in range(3):
+            c.evaluate_velocity_stretching(x0, w0)
+        torch.cuda.synchronize()
+        c.set_timing(True)
+        c.reset_stats()
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ea.record(stream)
+        for _ in range(args.steps):
+            c.evaluate_velocity_stretching(x0, w0)
+        eb.record(stream)
+        eb.synchronize()
+        ms = max_over_ranks(ea.elapsed_time(eb), dist) / args.steps
+        st = c.stats()
+        out[prec] = {"ms_per_evaluation": ms, "evals_per_s": n * world / (ms / 1e3), "err_v": ev, "err_s": es,
+                     "stage_ms_per_evaluation": {k: v / args.steps for k, v in st["stage_ms"].items() if v > 0},
+                     "p2p_pairs": st["p2p_pairs"], "m2l_pairs": st["m2l_pairs"], "leaf_level": st["leaf_level"]}
+        c.close()
+    if rank == 0:
+        print(json.dumps({"metric": METRIC + " (mixed-precision form)", "value": out["tf32x3"]["evals_per_s"],
+                          "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": 3,
+                          "ms_per_step": out["tf32x3"]["ms_per_evaluation"], "higher_is_better": True,
+                          "scaling": "weak", "dtype": "f32+tf32x3", "data": "synthetic",
+                          "config": {"workload": "offset_rings_2097152", "n": n, "p": spec["p"], "a": spec["a"],
+                                     "step": "one evaluation of v and s",
+                                     "error_sample": "10,000 random targets, FP64 direct sums"},
+                          "arms": out,
+                          "speedup_vs_plain_fp32": out["fp32"]["ms_per_evaluation"] / out["tf32x3"]["ms_per_evaluation"]}),
+              flush=True)
+
+
 def run_leapfrog(args, torch, LHV, local, world, rank, dist, eps=1e-6):
     """Learned form on the leapfrogging ring pair (2 x 2^21 elements, dt = 5e-4): RK4 steps
     with the network choosing p per level once per step (TF32x3, target eps_2(v) <= 1e-6, the
@@ -397,7 +448,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "blobs64", "leapfrog"],
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "blobs64", "leapfrog", "offset_rings"],
                     help="blobs64: the batched form, 64 independent blob systems (not the headline line)")
     ap.add_argument("--precision", default="tf32x3", choices=["tf32x3", "fp32"],
                     help="tf32x3: translations on the tensor cores (TF32 split products); fp32: plain CUDA-core FMM")
@@ -427,6 +478,9 @@ def main():
         return
     if args.workload == "leapfrog":
         run_leapfrog(args, torch, LHV, local, world, rank, dist)
+        return
+    if args.workload == "offset_rings":
+        run_offset_rings(args, torch, LHV, local, world, rank, dist)
         return
     x, w, spec = workloads.make(WORKLOAD)
     n = x.shape[0]
