@@ -40,8 +40,8 @@ struct Ctx {
     OpTables ops;
     int ops_type = 0;  // sizeof(T) of the built tables
     Buf tmp[14];
-    Buf xs, ws, mult, loc, table, vfar, sfar, counters, W, cf;
-    Grouped gp_leaf, gp_m2m, gp_m2l, gp_l2l;
+    Buf xs, ws, mult, loc, table, vfar, sfar, counters, W;
+    Grouped gp_m2m, gp_m2l, gp_l2l;
     Buf rk[6];         // kv, ks, ax, aw, sx, sw
     Buf hx, hw;        // device copies for lhv_step_host
     bool have_far = false;
@@ -331,7 +331,7 @@ static int evaluate(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const ve
         T* loc = c->loc.as<T>();
         {
             StageScope sc(c, LHV_STAGE_P2M);
-            run_p2m<T>(c, pl, c->tb, lv, xs, ws, c->W.as<T>(), c->gp_leaf, mult);
+            run_p2m<T>(c, pl, c->tb, lv, xs, ws, c->W.as<T>(), mult);
         }
         {
             StageScope sc(c, LHV_STAGE_M2M);
@@ -718,9 +718,9 @@ void lhv_destroy(lhv_ctx* ctx) {
     for (auto* b : tree) lhv::release(*b);
     for (auto& b : c.tmp) lhv::release(b);
     lhv::Buf* rest[] = {&c.xs, &c.ws, &c.mult, &c.loc, &c.table, &c.vfar, &c.sfar, &c.counters, &c.hx, &c.hw,
-                        &c.W, &c.cf};
+                        &c.W};
     for (auto* b : rest) lhv::release(*b);
-    for (lhv::Grouped* g : {&c.gp_leaf, &c.gp_m2m, &c.gp_m2l, &c.gp_l2l}) {
+    for (lhv::Grouped* g : {&c.gp_m2m, &c.gp_m2l, &c.gp_l2l}) {
         lhv::Buf* gb[] = {&g->gcount, &g->goff, &g->gcursor, &g->choff, &g->chunks, &g->pairs, &g->tmp,
                           &g->scan_tmp, &g->work};
         for (auto* b : gb) lhv::release(*b);

@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(L2P_THREADS) k_l2p_eval(const int* __restrict_
 
 template <typename T>
 void run_p2m(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs,
-             const vec4_t<T>* ws, T* W, Grouped& gp, T* mult) {
+             const vec4_t<T>* ws, T* W, T* mult) {
     const int L = lv.L, nl = lv.nbox[L], o = lv.off[L], p = pl.p[L], P = p * p;
     // the harmonics of a chunk sit in shared memory: the largest chunk (128, 64 or 32 elements)
     // that still leaves room for two blocks per SM
@@ -286,7 +286,6 @@ void run_p2m(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, co
                                                                                    mult + (int64_t)o * pl.ld, pl.ld);
     count_launch(c);
     check_launch("p2m apply");
-    (void)gp;
 }
 
 template <typename T>
@@ -385,7 +384,7 @@ void run_l2p(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, co
 
 #define LHV_INST(T)                                                                                              \
     template void run_p2m<T>(Ctx*, const Plan<T>&, const TreeBufs&, const Levels&, const vec4_t<T>*,            \
-                             const vec4_t<T>*, T*, Grouped&, T*);                                               \
+                             const vec4_t<T>*, T*, T*);                                                         \
     template void run_m2m<T>(Ctx*, const Plan<T>&, const TreeBufs&, const Levels&, Grouped&, T*);              \
     template void run_l2l<T>(Ctx*, const Plan<T>&, const TreeBufs&, const Levels&, Grouped&, T*);              \
     template void run_l2p<T>(Ctx*, const Plan<T>&, const TreeBufs&, const Levels&, const vec4_t<T>*,            \

@@ -229,16 +229,6 @@ int gemm_nc(int C) {
     return 16;
 }
 
-template <typename T>
-int gemm_nc_for(int C, int R, int64_t pairs) {
-    // the widest chunk that still gives every SM a few (chunk, 32-row tile) items
-    const int64_t row_tiles = (R + 31) / 32;
-    const int fit = gemm_nc<T>(C);
-    for (int nc : {64, 32})
-        if (nc <= fit && (pairs / nc) * row_tiles >= 4 * 152) return nc;
-    return 16;
-}
-
 template <int NC, typename T>
 static void launch_tm(Ctx* c, const GemmArgs<T>& a, int tm) {
     if (tm == 8) launch_gemm<T, NC, 8>(c, a);
@@ -268,8 +258,6 @@ void run_group_gemm(Ctx* c, Grouped& gp, GemmArgs<T> a) {
 
 template int gemm_nc<float>(int);
 template int gemm_nc<double>(int);
-template int gemm_nc_for<float>(int, int, int64_t);
-template int gemm_nc_for<double>(int, int, int64_t);
 template void run_group_gemm<float>(Ctx*, Grouped&, GemmArgs<float>);
 template void run_group_gemm<double>(Ctx*, Grouped&, GemmArgs<double>);
 

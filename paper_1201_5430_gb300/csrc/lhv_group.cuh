@@ -81,9 +81,6 @@ void build_grouped(Ctx* c, Grouped& gp, int ngroups, int64_t nitems, int64_t max
 
 template <typename T>
 int gemm_nc(int C);
-// chunk width for about `pairs` pairs of an R x C map: narrower chunks when there are few
-template <typename T>
-int gemm_nc_for(int C, int R, int64_t pairs);
 
 template <typename T>
 void run_group_gemm(Ctx* c, Grouped& gp, GemmArgs<T> a);
@@ -99,17 +96,6 @@ void run_tc_gemm(Ctx* c, Grouped& gp, GemmArgs<float> a, const float* tiles, con
 void tc_split(Ctx* c, int64_t n, const float* x, float* hi, float* lo);
 
 // Item sources ---------------------------------------------------------------
-
-// Every box b of the global range [b0, b0 + n) to itself shifted: (src_off + i, dst_off + i), group 0.
-struct IdentItems {
-    int src_off, dst_off;
-    __device__ bool operator()(int64_t i, int& g, int& s, int& d) const {
-        g = 0;
-        s = src_off + (int)i;
-        d = dst_off + (int)i;
-        return true;
-    }
-};
 
 // Children of the levels [lo, hi] (global box indices off[lo] .. off[hi+1]-1)
 // with their parents; group = (level - lo) * 8 + octant (key & 7).

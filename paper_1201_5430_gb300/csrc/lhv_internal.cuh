@@ -193,7 +193,7 @@ struct Plan {
 // P2M into mult (leaf level), work buffer W: nleaf * 3P reals.
 template <typename T>
 void run_p2m(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs,
-             const vec4_t<T>* ws, T* W, Grouped& gp, T* mult);
+             const vec4_t<T>* ws, T* W, T* mult);
 // M2M for all levels L-1 .. 2 (mult of the levels < L is overwritten).
 template <typename T>
 void run_m2m(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, Grouped& gp, T* mult);
