@@ -311,6 +311,282 @@ __global__ void __launch_bounds__(P2P_TILE / TPT) k_p2p(const int* __restrict__ 
     if (threadIdx.x == 0 && my_pairs) atomicAdd(pairs, my_pairs);
 }
 
+// ---- packed FP32x2 form of the same pair loop (float only) ----
+// Each add/mul/fma of the pair loop works on a float2 holding two sources of
+// the stage (2m, 2m+1); the target's values are duplicated into both lanes.
+// rsqrt and ex2 stay per lane.  The lanes keep separate partial sums, added
+// before the compensated total of each stage.
+
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// kernel_fg for two pairs at once: the singular part packed; where either lane
+// lies inside x_cut a, the interpolant of each region that a lane needs is
+// evaluated for both lanes and taken by the lanes in that region.
+template <bool SMOOTH>
+__device__ __forceinline__ void kernel_fg2(float2 r2, const CoreConsts<float>& cc, float2& f, float2& g) {
+    float2 ri;
+    ri.x = rsqrt_ftz(r2.x);
+    ri.y = rsqrt_ftz(r2.y);
+    const float2 ri2 = mul2(ri, ri);
+    f = mul2(ri, ri2);
+    g = mul2(f, mul2(ri2, dup2(-3.0f)));
+    if (SMOOTH) {
+        const float2 u = mul2(r2, dup2(cc.inv_a2));
+        if (fminf(u.x, u.y) < cc.x2_cut) {
+            const bool ser_x = u.x < cc.u_series, ser_y = u.y < cc.u_series;
+            const bool fit_x = !ser_x && u.x < cc.x2_cut, fit_y = !ser_y && u.y < cc.x2_cut;
+            if (fit_x || fit_y) {
+                const float2 t = fma2(mul2(dup2(cc.a), ri), dup2(LHV_CORE_Y_SCALE), dup2(LHV_CORE_Y_SHIFT));
+                float2 E = kCoreFit2[LHV_CORE_FIT_DEG];
+#pragma unroll
+                for (int k = LHV_CORE_FIT_DEG - 1; k >= 0; --k) E = fma2(E, t, kCoreFit2[k]);
+                const float2 x = mul2(mul2(r2, ri), dup2(cc.inv_a));
+                const float2 R = fma2(dup2(0.79788456080286535588f), x, E);
+                const float2 ue = mul2(u, dup2(-0.72134752044448170368f));  // exp(-u/2) = 2^(-u/(2 ln 2))
+                float2 e;
+                e.x = ex2_ftz(ue.x);
+                e.y = ex2_ftz(ue.y);
+                const float2 K = fma2(mul2(e, R), dup2(-1.0f), dup2(1.0f));
+                const float2 fk = mul2(f, K);
+                const float2 gk = mul2(fma2(fk, dup2(-3.0f), mul2(dup2(cc.c3), e)), ri2);
+                if (fit_x) {
+                    f.x = fk.x;
+                    g.x = gk.x;
+                }
+                if (fit_y) {
+                    f.y = fk.y;
+                    g.y = gk.y;
+                }
+            }
+            if (ser_x || ser_y) {
+                const float2 s = fma2(u, dup2(2.0f / LHV_CORE_U_SER), dup2(-1.0f));
+                float2 F = kSerF2[LHV_CORE_SER_DEG], Fp = kSerFp2[LHV_CORE_SER_DEG];
+#pragma unroll
+                for (int k = LHV_CORE_SER_DEG - 1; k >= 0; --k) {
+                    F = fma2(F, s, kSerF2[k]);
+                    Fp = fma2(Fp, s, kSerFp2[k]);
+                }
+                const float2 fs = mul2(dup2(cc.c3), F);
+                const float2 gs = mul2(dup2(2.0f * cc.c5), Fp);
+                if (ser_x) {
+                    f.x = fs.x;
+                    g.x = gs.x;
+                }
+                if (ser_y) {
+                    f.y = fs.y;
+                    g.y = gs.y;
+                }
+            }
+        }
+    }
+}
+
+// Position of the padding source that evens out a stage with an odd number of
+// sources: zero strength, and so far away that f and g underflow to zero.
+constexpr float kPadPosition = 1.0e18f;
+
+// k_p2p for float with the pair loop in FP32x2 over source pairs.  The stage
+// holds each source pair as -x, -y, -z (so that d = x_i + (-x_j) is one add),
+// w and -w (so that each cross-product component is one mul and one fma).
+template <bool SMOOTH, int TPT, int CH>
+__global__ void __launch_bounds__(P2P_TILE / TPT) k_p2p_x2(const int* __restrict__ ntiles_dev,
+                                                          const int2* __restrict__ tiles, int* __restrict__ work,
+                                                          const int* __restrict__ bbeg, const int* __restrict__ bend,
+                                                          const int* __restrict__ bcol, const float4* __restrict__ xs,
+                                                          const float4* __restrict__ ws, const int* __restrict__ perm,
+                                                          const float4* __restrict__ vfar,
+                                                          const float4* __restrict__ sfar, float4* __restrict__ vout,
+                                                          float4* __restrict__ sout, CoreConsts<float> cc, int near,
+                                                          unsigned long long* __restrict__ pairs) {
+    constexpr int NT = P2P_TILE / TPT;
+    constexpr int NA = 9;
+    constexpr int CP = CH / 2;  // source pairs per stage
+    __shared__ float4 sA[CP];   // -x_2m, -x_2m+1, -y_2m, -y_2m+1
+    __shared__ float4 sB[CP];   // -z pair, w.x pair
+    __shared__ float4 sC[CP];   // w.y pair, w.z pair
+    __shared__ float4 sD[CP];   // -w.x pair, -w.y pair
+    __shared__ float2 sE[CP];   // -w.z pair
+    __shared__ int2 sid[CP];
+    __shared__ float tot[2][NA][TPT][NT];
+    __shared__ int cbeg[27], cpre[28];
+    __shared__ int cur;
+    const int ntiles = *ntiles_dev;
+    unsigned long long my_pairs = 0;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) cur = atomicAdd(work, 1);
+        __syncthreads();
+        const int tile = cur;
+        if (tile >= ntiles) break;
+        const int2 tw = tiles[tile];
+        const int leaf = tw.x;
+        const int tend = bend[leaf];
+        if (threadIdx.x == 0) {
+            int acc = 0;
+            for (int q = 0; q < 27; ++q) {
+                const int cb = bcol[(int64_t)leaf * 27 + q];
+                int cnt = 0;
+                if (cb >= 0) {
+                    cbeg[q] = bbeg[cb];
+                    cnt = bend[cb] - bbeg[cb];
+                } else {
+                    cbeg[q] = 0;
+                }
+                cpre[q] = acc;
+                acc += cnt;
+            }
+            cpre[27] = acc;
+        }
+        int ti[TPT];
+        bool act[TPT];
+        float4 wi[TPT];
+        float2 XI[TPT][3], WI[TPT][3];
+#pragma unroll
+        for (int q = 0; q < TPT; ++q) {
+            ti[q] = tw.y + threadIdx.x + q * NT;
+            act[q] = ti[q] < tend;
+            const float4 x = act[q] ? xs[ti[q]] : float4{};
+            wi[q] = act[q] ? ws[ti[q]] : float4{};
+            XI[q][0] = dup2(x.x);
+            XI[q][1] = dup2(x.y);
+            XI[q][2] = dup2(x.z);
+            WI[q][0] = dup2(wi[q].x);
+            WI[q][1] = dup2(wi[q].y);
+            WI[q][2] = dup2(wi[q].z);
+#pragma unroll
+            for (int a = 0; a < NA; ++a) {
+                tot[0][a][q][threadIdx.x] = 0;
+                tot[1][a][q][threadIdx.x] = 0;
+            }
+        }
+        __syncthreads();
+        const int nsrc = near ? cpre[27] : 0;
+        const int self_lo = cpre[13] + (tw.y - cbeg[13]);
+        const int self_hi = self_lo + P2P_TILE;
+        if (threadIdx.x == 0 && near) {
+            const int nt = min(P2P_TILE, tend - tw.y);
+            my_pairs += (unsigned long long)nt * (unsigned long long)(nsrc - 1);
+        }
+        for (int s0 = 0; s0 < nsrc; s0 += CH) {
+            const int ns = min(CH, nsrc - s0);
+            const int np = (ns + 1) >> 1;
+            for (int k = threadIdx.x; k < 2 * np; k += NT) {
+                const int v = s0 + k;
+                float4 x = make_float4(kPadPosition, kPadPosition, kPadPosition, 0.0f), w{};
+                int j = -1;
+                if (v < nsrc) {
+                    int q = 0;
+                    while (cpre[q + 1] <= v) ++q;
+                    j = cbeg[q] + (v - cpre[q]);
+                    x = xs[j];
+                    w = ws[j];
+                }
+                const int m = k >> 1, l = k & 1;
+                float* a = reinterpret_cast<float*>(&sA[m]);
+                float* b = reinterpret_cast<float*>(&sB[m]);
+                float* c = reinterpret_cast<float*>(&sC[m]);
+                float* d = reinterpret_cast<float*>(&sD[m]);
+                float* e = reinterpret_cast<float*>(&sE[m]);
+                a[l] = -x.x;
+                a[2 + l] = -x.y;
+                b[l] = -x.z;
+                b[2 + l] = w.x;
+                c[l] = w.y;
+                c[2 + l] = w.z;
+                d[l] = -w.x;
+                d[2 + l] = -w.y;
+                e[l] = -w.z;
+                reinterpret_cast<int*>(&sid[m])[l] = j;
+            }
+            __syncthreads();
+            float2 acc[NA][TPT];
+#pragma unroll
+            for (int a = 0; a < NA; ++a)
+#pragma unroll
+                for (int q = 0; q < TPT; ++q) acc[a][q] = make_float2(0.0f, 0.0f);
+            auto chunk = [&](auto check) {
+                for (int m = 0; m < np; ++m) {
+                    const float4 A = sA[m], B = sB[m], C = sC[m], D = sD[m];
+                    const float2 nxj = make_float2(A.x, A.y), nyj = make_float2(A.z, A.w);
+                    const float2 nzj = make_float2(B.x, B.y);
+                    const float2 wx = make_float2(B.z, B.w), wy = make_float2(C.x, C.y);
+                    const float2 wz = make_float2(C.z, C.w);
+                    const float2 nwx = make_float2(D.x, D.y), nwy = make_float2(D.z, D.w), nwz = sE[m];
+                    int2 j = make_int2(-1, -1);
+                    if (decltype(check)::value) j = sid[m];
+#pragma unroll
+                    for (int q = 0; q < TPT; ++q) {
+                        const float2 dx = add2(XI[q][0], nxj), dy = add2(XI[q][1], nyj), dz = add2(XI[q][2], nzj);
+                        const float2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+                        float2 f, g;
+                        kernel_fg2<SMOOTH>(r2, cc, f, g);
+                        if (decltype(check)::value) {
+                            if (j.x == ti[q]) {
+                                f.x = 0.0f;
+                                g.x = 0.0f;
+                            }
+                            if (j.y == ti[q]) {
+                                f.y = 0.0f;
+                                g.y = 0.0f;
+                            }
+                        }
+                        const float2 cx = fma2(nwz, dy, mul2(wy, dz));  // w_y d_z - w_z d_y
+                        const float2 cy = fma2(nwx, dz, mul2(wz, dx));  // w_z d_x - w_x d_z
+                        const float2 cz = fma2(nwy, dx, mul2(wx, dy));  // w_x d_y - w_y d_x
+                        acc[0][q] = fma2(f, cx, acc[0][q]);
+                        acc[1][q] = fma2(f, cy, acc[1][q]);
+                        acc[2][q] = fma2(f, cz, acc[2][q]);
+                        acc[3][q] = fma2(f, wx, acc[3][q]);
+                        acc[4][q] = fma2(f, wy, acc[4][q]);
+                        acc[5][q] = fma2(f, wz, acc[5][q]);
+                        const float2 h = mul2(g, fma2(WI[q][2], dz, fma2(WI[q][1], dy, mul2(WI[q][0], dx))));
+                        acc[6][q] = fma2(h, cx, acc[6][q]);
+                        acc[7][q] = fma2(h, cy, acc[7][q]);
+                        acc[8][q] = fma2(h, cz, acc[8][q]);
+                    }
+                }
+            };
+            if (s0 < self_hi && s0 + ns > self_lo) chunk(std::true_type{});
+            else chunk(std::false_type{});
+#pragma unroll
+            for (int a = 0; a < NA; ++a)
+#pragma unroll
+                for (int q = 0; q < TPT; ++q)
+                    two_sum_acc(tot[0][a][q][threadIdx.x], tot[1][a][q][threadIdx.x], acc[a][q].x + acc[a][q].y);
+            __syncthreads();
+        }
+#pragma unroll
+        for (int q = 0; q < TPT; ++q) {
+            if (!act[q]) continue;
+            float r[NA];
+#pragma unroll
+            for (int a = 0; a < NA; ++a) r[a] = tot[0][a][q][threadIdx.x] + tot[1][a][q][threadIdx.x];
+            const int i = ti[q];
+            float4 vf{}, sf{};
+            if (vfar) {
+                vf = vfar[i];
+                sf = sfar[i];
+            }
+            float4 vo, so;
+            vo.x = vf.x + r[0];
+            vo.y = vf.y + r[1];
+            vo.z = vf.z + r[2];
+            vo.w = 0;
+            so.x = sf.x + (r[4] * wi[q].z - r[5] * wi[q].y) + r[6];
+            so.y = sf.y + (r[5] * wi[q].x - r[3] * wi[q].z) + r[7];
+            so.z = sf.z + (r[3] * wi[q].y - r[4] * wi[q].x) + r[8];
+            so.w = 0;
+            const int o = perm[i];
+            vout[o] = vo;
+            sout[o] = so;
+        }
+    }
+    if (threadIdx.x == 0 && my_pairs) atomicAdd(pairs, my_pairs);
+}
+
 // acc = (first ? 0 : acc) + c_acc k;  stage = y0 + c_stage k  (x and w at once)
 template <typename T>
 __global__ void k_rk4_stage(int64_t n, const vec4_t<T>* __restrict__ x0, const vec4_t<T>* __restrict__ w0,
@@ -403,7 +679,12 @@ void run_p2p(Ctx* c, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs, 
     auto launch = [&](auto tpt, auto ch) {
         constexpr int TPT = decltype(tpt)::value;
         constexpr int CH = decltype(ch)::value;
-        auto kern = cc.smooth ? k_p2p<T, true, TPT, CH> : k_p2p<T, false, TPT, CH>;
+        auto kern = [&] {
+            if constexpr (std::is_same<T, float>::value)
+                return cc.smooth ? k_p2p_x2<true, TPT, CH> : k_p2p_x2<false, TPT, CH>;
+            else
+                return cc.smooth ? k_p2p<T, true, TPT, CH> : k_p2p<T, false, TPT, CH>;
+        }();
         int per_sm = 1, sms = 152, dev = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, P2P_TILE / TPT, 0);
         cudaGetDevice(&dev);
