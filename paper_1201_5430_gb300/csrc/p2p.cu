@@ -37,6 +37,9 @@ template <typename T> struct CoreConsts {
     T a, inv_a, inv_a2, c3, c5;  // a, 1/a, 1/a^2, sqrt(2/pi)/a^3, sqrt(2/pi)/a^5
     T x2_cut;                 // (r/a)^2 beyond which K = 1 in this precision
     T u_series;               // (r/a)^2 below which the Taylor series is used
+    // packed FP32x2 kernel: r^2 cut, a LHV_CORE_Y_SCALE, -sqrt(2/pi)/a,
+    // -sqrt(2/pi)/(3 a^3), -(2/3) sqrt(2/pi)/a^5
+    T r2_cut, t_scale, nr_scale, c3_3n, c5_g;
     int smooth;
 };
 
@@ -322,43 +325,44 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
-// kernel_fg for two pairs at once: the singular part packed; where either lane
-// lies inside x_cut a, the interpolant of each region that a lane needs is
-// evaluated for both lanes and taken by the lanes in that region.
+// kernel_fg for two pairs at once, returning f and gm = -g/3 (the factor -3
+// is applied to the finished sums).  The singular part is packed; where either
+// lane lies inside x_cut a, the interpolant of each region that a lane needs is
+// evaluated for both lanes and taken by the lanes in that region.  Inside the
+// fit region f = f_s (1 - e R) with f_s = 1/r^3 and e = exp(-u/2), and
+// gm = (f - sqrt(2/pi) e / (3 a^3)) / r^2.
 template <bool SMOOTH>
-__device__ __forceinline__ void kernel_fg2(float2 r2, const CoreConsts<float>& cc, float2& f, float2& g) {
+__device__ __forceinline__ void kernel_fg2(float2 r2, const CoreConsts<float>& cc, float2& f, float2& gm) {
     float2 ri;
     ri.x = rsqrt_ftz(r2.x);
     ri.y = rsqrt_ftz(r2.y);
     const float2 ri2 = mul2(ri, ri);
     f = mul2(ri, ri2);
-    g = mul2(f, mul2(ri2, dup2(-3.0f)));
+    gm = mul2(f, ri2);
     if (SMOOTH) {
-        const float2 u = mul2(r2, dup2(cc.inv_a2));
-        if (fminf(u.x, u.y) < cc.x2_cut) {
+        if (fminf(r2.x, r2.y) < cc.r2_cut) {
+            const float2 u = mul2(r2, dup2(cc.inv_a2));
             const bool ser_x = u.x < cc.u_series, ser_y = u.y < cc.u_series;
             const bool fit_x = !ser_x && u.x < cc.x2_cut, fit_y = !ser_y && u.y < cc.x2_cut;
             if (fit_x || fit_y) {
-                const float2 t = fma2(mul2(dup2(cc.a), ri), dup2(LHV_CORE_Y_SCALE), dup2(LHV_CORE_Y_SHIFT));
-                float2 E = kCoreFit2[LHV_CORE_FIT_DEG];
+                const float2 t = fma2(ri, dup2(cc.t_scale), dup2(LHV_CORE_Y_SHIFT));  // from y = 1/x = a/r
+                float2 nE = kCoreFitN2[LHV_CORE_FIT_DEG];
 #pragma unroll
-                for (int k = LHV_CORE_FIT_DEG - 1; k >= 0; --k) E = fma2(E, t, kCoreFit2[k]);
-                const float2 x = mul2(mul2(r2, ri), dup2(cc.inv_a));
-                const float2 R = fma2(dup2(0.79788456080286535588f), x, E);
-                const float2 ue = mul2(u, dup2(-0.72134752044448170368f));  // exp(-u/2) = 2^(-u/(2 ln 2))
+                for (int k = LHV_CORE_FIT_DEG - 1; k >= 0; --k) nE = fma2(nE, t, kCoreFitN2[k]);
+                const float2 nR = fma2(mul2(r2, ri), dup2(cc.nr_scale), nE);  // -R(x)
+                const float2 ue = mul2(u, dup2(-0.72134752044448170368f));    // exp(-u/2) = 2^(-u/(2 ln 2))
                 float2 e;
                 e.x = ex2_ftz(ue.x);
                 e.y = ex2_ftz(ue.y);
-                const float2 K = fma2(mul2(e, R), dup2(-1.0f), dup2(1.0f));
-                const float2 fk = mul2(f, K);
-                const float2 gk = mul2(fma2(fk, dup2(-3.0f), mul2(dup2(cc.c3), e)), ri2);
+                const float2 fk = fma2(mul2(f, e), nR, f);
+                const float2 gk = mul2(fma2(e, dup2(cc.c3_3n), fk), ri2);
                 if (fit_x) {
                     f.x = fk.x;
-                    g.x = gk.x;
+                    gm.x = gk.x;
                 }
                 if (fit_y) {
                     f.y = fk.y;
-                    g.y = gk.y;
+                    gm.y = gk.y;
                 }
             }
             if (ser_x || ser_y) {
@@ -370,14 +374,14 @@ __device__ __forceinline__ void kernel_fg2(float2 r2, const CoreConsts<float>& c
                     Fp = fma2(Fp, s, kSerFp2[k]);
                 }
                 const float2 fs = mul2(dup2(cc.c3), F);
-                const float2 gs = mul2(dup2(2.0f * cc.c5), Fp);
+                const float2 gs = mul2(dup2(cc.c5_g), Fp);
                 if (ser_x) {
                     f.x = fs.x;
-                    g.x = gs.x;
+                    gm.x = gs.x;
                 }
                 if (ser_y) {
                     f.y = fs.y;
-                    g.y = gs.y;
+                    gm.y = gs.y;
                 }
             }
         }
@@ -521,16 +525,16 @@ __global__ void __launch_bounds__(P2P_TILE / TPT) k_p2p_x2(const int* __restrict
                     for (int q = 0; q < TPT; ++q) {
                         const float2 dx = add2(XI[q][0], nxj), dy = add2(XI[q][1], nyj), dz = add2(XI[q][2], nzj);
                         const float2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
-                        float2 f, g;
-                        kernel_fg2<SMOOTH>(r2, cc, f, g);
+                        float2 f, gm;
+                        kernel_fg2<SMOOTH>(r2, cc, f, gm);
                         if (decltype(check)::value) {
                             if (j.x == ti[q]) {
                                 f.x = 0.0f;
-                                g.x = 0.0f;
+                                gm.x = 0.0f;
                             }
                             if (j.y == ti[q]) {
                                 f.y = 0.0f;
-                                g.y = 0.0f;
+                                gm.y = 0.0f;
                             }
                         }
                         const float2 cx = fma2(nwz, dy, mul2(wy, dz));  // w_y d_z - w_z d_y
@@ -542,7 +546,7 @@ __global__ void __launch_bounds__(P2P_TILE / TPT) k_p2p_x2(const int* __restrict
                         acc[3][q] = fma2(f, wx, acc[3][q]);
                         acc[4][q] = fma2(f, wy, acc[4][q]);
                         acc[5][q] = fma2(f, wz, acc[5][q]);
-                        const float2 h = mul2(g, fma2(WI[q][2], dz, fma2(WI[q][1], dy, mul2(WI[q][0], dx))));
+                        const float2 h = mul2(gm, fma2(WI[q][2], dz, fma2(WI[q][1], dy, mul2(WI[q][0], dx))));
                         acc[6][q] = fma2(h, cx, acc[6][q]);
                         acc[7][q] = fma2(h, cy, acc[7][q]);
                         acc[8][q] = fma2(h, cz, acc[8][q]);
@@ -575,9 +579,10 @@ __global__ void __launch_bounds__(P2P_TILE / TPT) k_p2p_x2(const int* __restrict
             vo.y = vf.y + r[1];
             vo.z = vf.z + r[2];
             vo.w = 0;
-            so.x = sf.x + (r[4] * wi[q].z - r[5] * wi[q].y) + r[6];
-            so.y = sf.y + (r[5] * wi[q].x - r[3] * wi[q].z) + r[7];
-            so.z = sf.z + (r[3] * wi[q].y - r[4] * wi[q].x) + r[8];
+            // the g-terms were summed with gm = -g/3
+            so.x = sf.x + (r[4] * wi[q].z - r[5] * wi[q].y) - 3.0f * r[6];
+            so.y = sf.y + (r[5] * wi[q].x - r[3] * wi[q].z) - 3.0f * r[7];
+            so.z = sf.z + (r[3] * wi[q].y - r[4] * wi[q].x) - 3.0f * r[8];
             so.w = 0;
             const int o = perm[i];
             vout[o] = vo;
@@ -668,6 +673,11 @@ void run_p2p(Ctx* c, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs, 
         const double xc = sizeof(T) == 4 ? 6.5 : 9.0;
         cc.x2_cut = (T)(xc * xc);
         cc.u_series = (T)(sizeof(T) == 4 ? LHV_CORE_U_SER : 1.0);
+        cc.r2_cut = (T)(xc * xc * a * a);
+        cc.t_scale = (T)(a * (double)LHV_CORE_Y_SCALE);
+        cc.nr_scale = (T)(-s2pi / a);
+        cc.c3_3n = (T)(-s2pi / (3.0 * a * a * a));
+        cc.c5_g = (T)(-2.0 / 3.0 * s2pi / (a * a * a * a * a));
     }
     int* work = reinterpret_cast<int*>(ctx_tmp(c, 6).ptr);
     ensure(c, ctx_tmp(c, 6), 64);
