@@ -227,10 +227,11 @@ __global__ void __launch_bounds__(P2P_TILE / TPT) k_p2p(const int* __restrict__ 
             const int nt = min(P2P_TILE, tend - tw.y);
             my_pairs += (unsigned long long)nt * (unsigned long long)(nsrc - 1);
         }
+        int qrun = 0;  // colleague of this thread's last staged source (its sources only move forward)
         for (int s0 = 0; s0 < nsrc; s0 += CH) {
             for (int v = s0 + threadIdx.x; v < min(nsrc, s0 + CH); v += NT) {
-                int q = 0;
-                while (cpre[q + 1] <= v) ++q;
+                while (cpre[qrun + 1] <= v) ++qrun;
+                const int q = qrun;
                 const int j = cbeg[q] + (v - cpre[q]);
                 sx[v - s0] = xs[j];
                 sw[v - s0] = ws[j];
@@ -326,64 +327,70 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
 // kernel_fg for two pairs at once, returning f and gm = -g/3 (the factor -3
-// is applied to the finished sums).  The singular part is packed; where either
-// lane lies inside x_cut a, the interpolant of each region that a lane needs is
-// evaluated for both lanes and taken by the lanes in that region.  Inside the
-// fit region f = f_s (1 - e R) with f_s = 1/r^3 and e = exp(-u/2), and
-// gm = (f - sqrt(2/pi) e / (3 a^3)) / r^2.
-template <bool SMOOTH>
-__device__ __forceinline__ void kernel_fg2(float2 r2, const CoreConsts<float>& cc, float2& f, float2& gm) {
-    float2 ri;
+// is applied to the finished sums).  fg2_singular gives the packed singular
+// part; fg2_core then replaces it where either lane lies inside x_cut a: the
+// interpolant of each region that a lane needs is evaluated for both lanes and
+// taken by the lanes in that region.  Inside the fit region f = f_s (1 - e R)
+// with f_s = 1/r^3 and e = exp(-u/2), and gm = (f - sqrt(2/pi) e / (3 a^3)) / r^2.
+__device__ __forceinline__ void fg2_singular(float2 r2, float2& ri, float2& ri2, float2& f, float2& gm) {
     ri.x = rsqrt_ftz(r2.x);
     ri.y = rsqrt_ftz(r2.y);
-    const float2 ri2 = mul2(ri, ri);
+    ri2 = mul2(ri, ri);
     f = mul2(ri, ri2);
     gm = mul2(f, ri2);
-    if (SMOOTH) {
-        if (fminf(r2.x, r2.y) < cc.r2_cut) {
-            const float2 u = mul2(r2, dup2(cc.inv_a2));
-            const bool ser_x = u.x < cc.u_series, ser_y = u.y < cc.u_series;
-            const bool fit_x = !ser_x && u.x < cc.x2_cut, fit_y = !ser_y && u.y < cc.x2_cut;
-            if (fit_x || fit_y) {
-                const float2 t = fma2(ri, dup2(cc.t_scale), dup2(LHV_CORE_Y_SHIFT));  // from y = 1/x = a/r
-                float2 nE = kCoreFitN2[LHV_CORE_FIT_DEG];
+}
+
+// Core correction for SU source pairs at once (their chains interleave).  The
+// branches are warp-uniform votes: every lane of the warp runs the pair loop.
+// The fit-region form is exact to FP32 rounding for every x >= 1.5 (beyond
+// x_cut, e R and e/(3 a^3) r^3 are below the unit roundoff, so f and gm come out
+// unchanged), so it is applied to every lane without a per-lane choice; the
+// series then overrides the lanes with x < 1.5.
+template <int SU>
+__device__ __forceinline__ void fg2_core(const float2 (&r2)[SU], const float2 (&ri)[SU], const float2 (&ri2)[SU],
+                                         const CoreConsts<float>& cc, float2 (&f)[SU], float2 (&gm)[SU]) {
+    float rmin = fminf(r2[0].x, r2[0].y);
 #pragma unroll
-                for (int k = LHV_CORE_FIT_DEG - 1; k >= 0; --k) nE = fma2(nE, t, kCoreFitN2[k]);
-                const float2 nR = fma2(mul2(r2, ri), dup2(cc.nr_scale), nE);  // -R(x)
-                const float2 ue = mul2(u, dup2(-0.72134752044448170368f));    // exp(-u/2) = 2^(-u/(2 ln 2))
-                float2 e;
-                e.x = ex2_ftz(ue.x);
-                e.y = ex2_ftz(ue.y);
-                const float2 fk = fma2(mul2(f, e), nR, f);
-                const float2 gk = mul2(fma2(e, dup2(cc.c3_3n), fk), ri2);
-                if (fit_x) {
-                    f.x = fk.x;
-                    gm.x = gk.x;
-                }
-                if (fit_y) {
-                    f.y = fk.y;
-                    gm.y = gk.y;
-                }
-            }
-            if (ser_x || ser_y) {
-                const float2 s = fma2(u, dup2(2.0f / LHV_CORE_U_SER), dup2(-1.0f));
-                float2 F = kSerF2[LHV_CORE_SER_DEG], Fp = kSerFp2[LHV_CORE_SER_DEG];
+    for (int v = 1; v < SU; ++v) rmin = fminf(rmin, fminf(r2[v].x, r2[v].y));
+    if (!__any_sync(0xffffffffu, rmin < cc.r2_cut)) return;
+    float2 u[SU];
 #pragma unroll
-                for (int k = LHV_CORE_SER_DEG - 1; k >= 0; --k) {
-                    F = fma2(F, s, kSerF2[k]);
-                    Fp = fma2(Fp, s, kSerFp2[k]);
-                }
-                const float2 fs = mul2(dup2(cc.c3), F);
-                const float2 gs = mul2(dup2(cc.c5_g), Fp);
-                if (ser_x) {
-                    f.x = fs.x;
-                    gm.x = gs.x;
-                }
-                if (ser_y) {
-                    f.y = fs.y;
-                    gm.y = gs.y;
-                }
-            }
+    for (int v = 0; v < SU; ++v) {
+        u[v] = mul2(r2[v], dup2(cc.inv_a2));
+        const float2 t = fma2(ri[v], dup2(cc.t_scale), dup2(LHV_CORE_Y_SHIFT));  // from y = 1/x = a/r
+        float2 nE = kCoreFitN2[LHV_CORE_FIT_DEG];
+#pragma unroll
+        for (int k = LHV_CORE_FIT_DEG - 1; k >= 0; --k) nE = fma2(nE, t, kCoreFitN2[k]);
+        const float2 nR = fma2(mul2(r2[v], ri[v]), dup2(cc.nr_scale), nE);  // -R(x)
+        const float2 ue = mul2(u[v], dup2(-0.72134752044448170368f));      // exp(-u/2) = 2^(-u/(2 ln 2))
+        float2 e;
+        e.x = ex2_ftz(ue.x);
+        e.y = ex2_ftz(ue.y);
+        f[v] = fma2(mul2(f[v], e), nR, f[v]);
+        gm[v] = mul2(fma2(e, dup2(cc.c3_3n), f[v]), ri2[v]);
+    }
+    float umin = fminf(u[0].x, u[0].y);
+#pragma unroll
+    for (int v = 1; v < SU; ++v) umin = fminf(umin, fminf(u[v].x, u[v].y));
+    if (!__any_sync(0xffffffffu, umin < cc.u_series)) return;
+#pragma unroll
+    for (int v = 0; v < SU; ++v) {
+        const float2 s = fma2(u[v], dup2(2.0f / LHV_CORE_U_SER), dup2(-1.0f));
+        float2 F = kSerF2[LHV_CORE_SER_DEG], Fp = kSerFp2[LHV_CORE_SER_DEG];
+#pragma unroll
+        for (int k = LHV_CORE_SER_DEG - 1; k >= 0; --k) {
+            F = fma2(F, s, kSerF2[k]);
+            Fp = fma2(Fp, s, kSerFp2[k]);
+        }
+        const float2 fs = mul2(dup2(cc.c3), F);
+        const float2 gs = mul2(dup2(cc.c5_g), Fp);
+        if (u[v].x < cc.u_series) {
+            f[v].x = fs.x;
+            gm[v].x = gs.x;
+        }
+        if (u[v].y < cc.u_series) {
+            f[v].y = fs.y;
+            gm[v].y = gs.y;
         }
     }
 }
@@ -408,6 +415,8 @@ __global__ void __launch_bounds__(P2P_TILE / TPT) k_p2p_x2(const int* __restrict
     constexpr int NT = P2P_TILE / TPT;
     constexpr int NA = 9;
     constexpr int CP = CH / 2;  // source pairs per stage
+    constexpr int SU = 2;       // source pairs per step of the pair loop
+    static_assert(CP % SU == 0, "a stage holds whole steps");
     __shared__ float4 sA[CP];   // -x_2m, -x_2m+1, -y_2m, -y_2m+1
     __shared__ float4 sB[CP];   // -z pair, w.x pair
     __shared__ float4 sC[CP];   // w.y pair, w.z pair
@@ -474,17 +483,17 @@ __global__ void __launch_bounds__(P2P_TILE / TPT) k_p2p_x2(const int* __restrict
             const int nt = min(P2P_TILE, tend - tw.y);
             my_pairs += (unsigned long long)nt * (unsigned long long)(nsrc - 1);
         }
+        int qrun = 0;  // colleague of this thread's last staged source (its sources only move forward)
         for (int s0 = 0; s0 < nsrc; s0 += CH) {
             const int ns = min(CH, nsrc - s0);
-            const int np = (ns + 1) >> 1;
+            const int np = (((ns + 1) >> 1) + SU - 1) / SU * SU;  // source pairs, padded to whole steps
             for (int k = threadIdx.x; k < 2 * np; k += NT) {
                 const int v = s0 + k;
                 float4 x = make_float4(kPadPosition, kPadPosition, kPadPosition, 0.0f), w{};
                 int j = -1;
                 if (v < nsrc) {
-                    int q = 0;
-                    while (cpre[q + 1] <= v) ++q;
-                    j = cbeg[q] + (v - cpre[q]);
+                    while (cpre[qrun + 1] <= v) ++qrun;
+                    j = cbeg[qrun] + (v - cpre[qrun]);
                     x = xs[j];
                     w = ws[j];
                 }
@@ -512,44 +521,63 @@ __global__ void __launch_bounds__(P2P_TILE / TPT) k_p2p_x2(const int* __restrict
 #pragma unroll
                 for (int q = 0; q < TPT; ++q) acc[a][q] = make_float2(0.0f, 0.0f);
             auto chunk = [&](auto check) {
-                for (int m = 0; m < np; ++m) {
-                    const float4 A = sA[m], B = sB[m], C = sC[m], D = sD[m];
-                    const float2 nxj = make_float2(A.x, A.y), nyj = make_float2(A.z, A.w);
-                    const float2 nzj = make_float2(B.x, B.y);
-                    const float2 wx = make_float2(B.z, B.w), wy = make_float2(C.x, C.y);
-                    const float2 wz = make_float2(C.z, C.w);
-                    const float2 nwx = make_float2(D.x, D.y), nwy = make_float2(D.z, D.w), nwz = sE[m];
-                    int2 j = make_int2(-1, -1);
-                    if (decltype(check)::value) j = sid[m];
+                for (int m = 0; m < np; m += SU) {
+                    float2 nxj[SU], nyj[SU], nzj[SU], wx[SU], wy[SU], wz[SU], nwx[SU], nwy[SU], nwz[SU];
+                    int2 j[SU];
+#pragma unroll
+                    for (int u = 0; u < SU; ++u) {
+                        const float4 A = sA[m + u], B = sB[m + u], C = sC[m + u], D = sD[m + u];
+                        nxj[u] = make_float2(A.x, A.y);
+                        nyj[u] = make_float2(A.z, A.w);
+                        nzj[u] = make_float2(B.x, B.y);
+                        wx[u] = make_float2(B.z, B.w);
+                        wy[u] = make_float2(C.x, C.y);
+                        wz[u] = make_float2(C.z, C.w);
+                        nwx[u] = make_float2(D.x, D.y);
+                        nwy[u] = make_float2(D.z, D.w);
+                        nwz[u] = sE[m + u];
+                        j[u] = make_int2(-1, -1);
+                        if (decltype(check)::value) j[u] = sid[m + u];
+                    }
 #pragma unroll
                     for (int q = 0; q < TPT; ++q) {
-                        const float2 dx = add2(XI[q][0], nxj), dy = add2(XI[q][1], nyj), dz = add2(XI[q][2], nzj);
-                        const float2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
-                        float2 f, gm;
-                        kernel_fg2<SMOOTH>(r2, cc, f, gm);
-                        if (decltype(check)::value) {
-                            if (j.x == ti[q]) {
-                                f.x = 0.0f;
-                                gm.x = 0.0f;
-                            }
-                            if (j.y == ti[q]) {
-                                f.y = 0.0f;
-                                gm.y = 0.0f;
-                            }
+                        float2 dx[SU], dy[SU], dz[SU], r2[SU], ri[SU], ri2[SU], f[SU], gm[SU];
+#pragma unroll
+                        for (int u = 0; u < SU; ++u) {
+                            dx[u] = add2(XI[q][0], nxj[u]);
+                            dy[u] = add2(XI[q][1], nyj[u]);
+                            dz[u] = add2(XI[q][2], nzj[u]);
+                            r2[u] = fma2(dz[u], dz[u], fma2(dy[u], dy[u], mul2(dx[u], dx[u])));
+                            fg2_singular(r2[u], ri[u], ri2[u], f[u], gm[u]);
                         }
-                        const float2 cx = fma2(nwz, dy, mul2(wy, dz));  // w_y d_z - w_z d_y
-                        const float2 cy = fma2(nwx, dz, mul2(wz, dx));  // w_z d_x - w_x d_z
-                        const float2 cz = fma2(nwy, dx, mul2(wx, dy));  // w_x d_y - w_y d_x
-                        acc[0][q] = fma2(f, cx, acc[0][q]);
-                        acc[1][q] = fma2(f, cy, acc[1][q]);
-                        acc[2][q] = fma2(f, cz, acc[2][q]);
-                        acc[3][q] = fma2(f, wx, acc[3][q]);
-                        acc[4][q] = fma2(f, wy, acc[4][q]);
-                        acc[5][q] = fma2(f, wz, acc[5][q]);
-                        const float2 h = mul2(gm, fma2(WI[q][2], dz, fma2(WI[q][1], dy, mul2(WI[q][0], dx))));
-                        acc[6][q] = fma2(h, cx, acc[6][q]);
-                        acc[7][q] = fma2(h, cy, acc[7][q]);
-                        acc[8][q] = fma2(h, cz, acc[8][q]);
+                        if (SMOOTH) fg2_core<SU>(r2, ri, ri2, cc, f, gm);
+#pragma unroll
+                        for (int u = 0; u < SU; ++u) {
+                            if (decltype(check)::value) {
+                                if (j[u].x == ti[q]) {
+                                    f[u].x = 0.0f;
+                                    gm[u].x = 0.0f;
+                                }
+                                if (j[u].y == ti[q]) {
+                                    f[u].y = 0.0f;
+                                    gm[u].y = 0.0f;
+                                }
+                            }
+                            const float2 cx = fma2(nwz[u], dy[u], mul2(wy[u], dz[u]));  // w_y d_z - w_z d_y
+                            const float2 cy = fma2(nwx[u], dz[u], mul2(wz[u], dx[u]));  // w_z d_x - w_x d_z
+                            const float2 cz = fma2(nwy[u], dx[u], mul2(wx[u], dy[u]));  // w_x d_y - w_y d_x
+                            acc[0][q] = fma2(f[u], cx, acc[0][q]);
+                            acc[1][q] = fma2(f[u], cy, acc[1][q]);
+                            acc[2][q] = fma2(f[u], cz, acc[2][q]);
+                            acc[3][q] = fma2(f[u], wx[u], acc[3][q]);
+                            acc[4][q] = fma2(f[u], wy[u], acc[4][q]);
+                            acc[5][q] = fma2(f[u], wz[u], acc[5][q]);
+                            const float2 h =
+                                mul2(gm[u], fma2(WI[q][2], dz[u], fma2(WI[q][1], dy[u], mul2(WI[q][0], dx[u]))));
+                            acc[6][q] = fma2(h, cx, acc[6][q]);
+                            acc[7][q] = fma2(h, cy, acc[7][q]);
+                            acc[8][q] = fma2(h, cz, acc[8][q]);
+                        }
                     }
                 }
             };
