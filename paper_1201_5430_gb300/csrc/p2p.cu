@@ -399,67 +399,88 @@ __device__ __forceinline__ void fg2_core(const float2 (&r2)[SU], const float2 (&
 // sources: zero strength, and so far away that f and g underflow to zero.
 constexpr float kPadPosition = 1.0e18f;
 
-// k_p2p for float with the pair loop in FP32x2 over source pairs.  The stage
-// holds each source pair as -x, -y, -z (so that d = x_i + (-x_j) is one add),
-// w and -w (so that each cross-product component is one mul and one fma).
+// k_p2p for float with the pair loop in FP32x2 over source pairs, one warp per
+// work item.  A warp tile is P2P_WT = 32 TPT consecutive targets of a near-field
+// tile (so a leaf wastes at most one partly filled warp, not one partly filled
+// 128-target tile); empty warp tiles are skipped.  Each warp stages its own
+// sources, holding each source pair as -x, -y, -z (so that d = x_i + (-x_j) is
+// one add), w and -w (so that each cross-product component is one mul and one
+// fma), and synchronises with __syncwarp only.
+constexpr int P2P_WARPS = 4;  // warps per block of the packed kernel
+
+template <int TPT, int CH>
+struct P2pWarpSmem {
+    static constexpr int CP = CH / 2;  // source pairs per stage
+    float4 A[CP];                      // -x pair, -y pair
+    float4 B[CP];                      // -z pair, w.x pair
+    float4 C[CP];                      // w.y pair, w.z pair
+    float4 D[CP];                      // -w.x pair, -w.y pair
+    float2 E[CP];                      // -w.z pair
+    int2 id[CP];                       // sorted indices of the pair (-1: padding)
+    float tot[2][9][TPT][32];          // compensated totals (hi, lo) per lane
+    int cbeg[27], cpre[28];
+};
+
 template <bool SMOOTH, int TPT, int CH>
-__global__ void __launch_bounds__(P2P_TILE / TPT) k_p2p_x2(const int* __restrict__ ntiles_dev,
-                                                          const int2* __restrict__ tiles, int* __restrict__ work,
-                                                          const int* __restrict__ bbeg, const int* __restrict__ bend,
-                                                          const int* __restrict__ bcol, const float4* __restrict__ xs,
-                                                          const float4* __restrict__ ws, const int* __restrict__ perm,
-                                                          const float4* __restrict__ vfar,
-                                                          const float4* __restrict__ sfar, float4* __restrict__ vout,
-                                                          float4* __restrict__ sout, CoreConsts<float> cc, int near,
-                                                          unsigned long long* __restrict__ pairs) {
-    constexpr int NT = P2P_TILE / TPT;
+__global__ void __launch_bounds__(32 * P2P_WARPS) k_p2p_x2(const int* __restrict__ ntiles_dev,
+                                                           const int2* __restrict__ tiles, int* __restrict__ work,
+                                                           const int* __restrict__ bbeg, const int* __restrict__ bend,
+                                                           const int* __restrict__ bcol, const float4* __restrict__ xs,
+                                                           const float4* __restrict__ ws, const int* __restrict__ perm,
+                                                           const float4* __restrict__ vfar,
+                                                           const float4* __restrict__ sfar, float4* __restrict__ vout,
+                                                           float4* __restrict__ sout, CoreConsts<float> cc, int near,
+                                                           unsigned long long* __restrict__ pairs) {
+    constexpr int WT = 32 * TPT;            // targets per warp tile
+    constexpr int SUBS = P2P_TILE / WT;     // warp tiles per near-field tile
     constexpr int NA = 9;
-    constexpr int CP = CH / 2;  // source pairs per stage
-    constexpr int SU = 2;       // source pairs per step of the pair loop
+    constexpr int CP = CH / 2;
+    constexpr int SU = 2;                   // source pairs per step of the pair loop
+    constexpr unsigned FULL = 0xffffffffu;
     static_assert(CP % SU == 0, "a stage holds whole steps");
-    __shared__ float4 sA[CP];   // -x_2m, -x_2m+1, -y_2m, -y_2m+1
-    __shared__ float4 sB[CP];   // -z pair, w.x pair
-    __shared__ float4 sC[CP];   // w.y pair, w.z pair
-    __shared__ float4 sD[CP];   // -w.x pair, -w.y pair
-    __shared__ float2 sE[CP];   // -w.z pair
-    __shared__ int2 sid[CP];
-    __shared__ float tot[2][NA][TPT][NT];
-    __shared__ int cbeg[27], cpre[28];
-    __shared__ int cur;
-    const int ntiles = *ntiles_dev;
+    static_assert(P2P_TILE % WT == 0, "warp tiles split a near-field tile");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    P2pWarpSmem<TPT, CH>& sm = reinterpret_cast<P2pWarpSmem<TPT, CH>*>(smem_raw)[threadIdx.x >> 5];
+    const int nitems = *ntiles_dev * SUBS;
     unsigned long long my_pairs = 0;
     for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) cur = atomicAdd(work, 1);
-        __syncthreads();
-        const int tile = cur;
-        if (tile >= ntiles) break;
-        const int2 tw = tiles[tile];
+        int item = 0;
+        if (lane == 0) item = atomicAdd(work, 1);
+        item = __shfl_sync(FULL, item, 0);
+        if (item >= nitems) break;
+        const int2 tw = tiles[item / SUBS];
         const int leaf = tw.x;
+        const int t0 = tw.y + (item % SUBS) * WT;  // first target of the warp tile
         const int tend = bend[leaf];
-        if (threadIdx.x == 0) {
-            int acc = 0;
-            for (int q = 0; q < 27; ++q) {
-                const int cb = bcol[(int64_t)leaf * 27 + q];
-                int cnt = 0;
-                if (cb >= 0) {
-                    cbeg[q] = bbeg[cb];
-                    cnt = bend[cb] - bbeg[cb];
-                } else {
-                    cbeg[q] = 0;
-                }
-                cpre[q] = acc;
-                acc += cnt;
+        if (t0 >= tend) continue;  // warp-uniform: the tile's leaf ends before this warp tile
+        // colleague table: lane q < 27 reads colleague q; a warp scan gives the prefix counts
+        int cnt = 0, beg = 0;
+        if (lane < 27) {
+            const int cb = bcol[(int64_t)leaf * 27 + lane];
+            if (cb >= 0) {
+                beg = bbeg[cb];
+                cnt = bend[cb] - beg;
             }
-            cpre[27] = acc;
         }
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane < 27) {
+            sm.cbeg[lane] = beg;
+            sm.cpre[lane] = incl - cnt;
+        }
+        if (lane == 26) sm.cpre[27] = incl;
         int ti[TPT];
         bool act[TPT];
         float4 wi[TPT];
         float2 XI[TPT][3], WI[TPT][3];
 #pragma unroll
         for (int q = 0; q < TPT; ++q) {
-            ti[q] = tw.y + threadIdx.x + q * NT;
+            ti[q] = t0 + lane + 32 * q;
             act[q] = ti[q] < tend;
             const float4 x = act[q] ? xs[ti[q]] : float4{};
             wi[q] = act[q] ? ws[ti[q]] : float4{};
@@ -471,38 +492,36 @@ __global__ void __launch_bounds__(P2P_TILE / TPT) k_p2p_x2(const int* __restrict
             WI[q][2] = dup2(wi[q].z);
 #pragma unroll
             for (int a = 0; a < NA; ++a) {
-                tot[0][a][q][threadIdx.x] = 0;
-                tot[1][a][q][threadIdx.x] = 0;
+                sm.tot[0][a][q][lane] = 0;
+                sm.tot[1][a][q][lane] = 0;
             }
         }
-        __syncthreads();
-        const int nsrc = near ? cpre[27] : 0;
-        const int self_lo = cpre[13] + (tw.y - cbeg[13]);
-        const int self_hi = self_lo + P2P_TILE;
-        if (threadIdx.x == 0 && near) {
-            const int nt = min(P2P_TILE, tend - tw.y);
-            my_pairs += (unsigned long long)nt * (unsigned long long)(nsrc - 1);
-        }
-        int qrun = 0;  // colleague of this thread's last staged source (its sources only move forward)
+        __syncwarp();
+        const int nsrc = near ? sm.cpre[27] : 0;
+        // virtual source positions of the warp tile's own targets (colleague 13 is the leaf itself)
+        const int self_lo = sm.cpre[13] + (t0 - sm.cbeg[13]);
+        const int self_hi = self_lo + WT;
+        if (lane == 0 && near) my_pairs += (unsigned long long)min(WT, tend - t0) * (unsigned long long)(nsrc - 1);
+        int qrun = 0;  // colleague of this lane's last staged source (its sources only move forward)
         for (int s0 = 0; s0 < nsrc; s0 += CH) {
             const int ns = min(CH, nsrc - s0);
             const int np = (((ns + 1) >> 1) + SU - 1) / SU * SU;  // source pairs, padded to whole steps
-            for (int k = threadIdx.x; k < 2 * np; k += NT) {
+            for (int k = lane; k < 2 * np; k += 32) {
                 const int v = s0 + k;
                 float4 x = make_float4(kPadPosition, kPadPosition, kPadPosition, 0.0f), w{};
                 int j = -1;
                 if (v < nsrc) {
-                    while (cpre[qrun + 1] <= v) ++qrun;
-                    j = cbeg[qrun] + (v - cpre[qrun]);
+                    while (sm.cpre[qrun + 1] <= v) ++qrun;
+                    j = sm.cbeg[qrun] + (v - sm.cpre[qrun]);
                     x = xs[j];
                     w = ws[j];
                 }
                 const int m = k >> 1, l = k & 1;
-                float* a = reinterpret_cast<float*>(&sA[m]);
-                float* b = reinterpret_cast<float*>(&sB[m]);
-                float* c = reinterpret_cast<float*>(&sC[m]);
-                float* d = reinterpret_cast<float*>(&sD[m]);
-                float* e = reinterpret_cast<float*>(&sE[m]);
+                float* a = reinterpret_cast<float*>(&sm.A[m]);
+                float* b = reinterpret_cast<float*>(&sm.B[m]);
+                float* c = reinterpret_cast<float*>(&sm.C[m]);
+                float* d = reinterpret_cast<float*>(&sm.D[m]);
+                float* e = reinterpret_cast<float*>(&sm.E[m]);
                 a[l] = -x.x;
                 a[2 + l] = -x.y;
                 b[l] = -x.z;
@@ -512,9 +531,9 @@ __global__ void __launch_bounds__(P2P_TILE / TPT) k_p2p_x2(const int* __restrict
                 d[l] = -w.x;
                 d[2 + l] = -w.y;
                 e[l] = -w.z;
-                reinterpret_cast<int*>(&sid[m])[l] = j;
+                reinterpret_cast<int*>(&sm.id[m])[l] = j;
             }
-            __syncthreads();
+            __syncwarp();
             float2 acc[NA][TPT];
 #pragma unroll
             for (int a = 0; a < NA; ++a)
@@ -526,7 +545,7 @@ __global__ void __launch_bounds__(P2P_TILE / TPT) k_p2p_x2(const int* __restrict
                     int2 j[SU];
 #pragma unroll
                     for (int u = 0; u < SU; ++u) {
-                        const float4 A = sA[m + u], B = sB[m + u], C = sC[m + u], D = sD[m + u];
+                        const float4 A = sm.A[m + u], B = sm.B[m + u], C = sm.C[m + u], D = sm.D[m + u];
                         nxj[u] = make_float2(A.x, A.y);
                         nyj[u] = make_float2(A.z, A.w);
                         nzj[u] = make_float2(B.x, B.y);
@@ -535,9 +554,9 @@ __global__ void __launch_bounds__(P2P_TILE / TPT) k_p2p_x2(const int* __restrict
                         wz[u] = make_float2(C.z, C.w);
                         nwx[u] = make_float2(D.x, D.y);
                         nwy[u] = make_float2(D.z, D.w);
-                        nwz[u] = sE[m + u];
+                        nwz[u] = sm.E[m + u];
                         j[u] = make_int2(-1, -1);
-                        if (decltype(check)::value) j[u] = sid[m + u];
+                        if (decltype(check)::value) j[u] = sm.id[m + u];
                     }
 #pragma unroll
                     for (int q = 0; q < TPT; ++q) {
@@ -587,15 +606,15 @@ __global__ void __launch_bounds__(P2P_TILE / TPT) k_p2p_x2(const int* __restrict
             for (int a = 0; a < NA; ++a)
 #pragma unroll
                 for (int q = 0; q < TPT; ++q)
-                    two_sum_acc(tot[0][a][q][threadIdx.x], tot[1][a][q][threadIdx.x], acc[a][q].x + acc[a][q].y);
-            __syncthreads();
+                    two_sum_acc(sm.tot[0][a][q][lane], sm.tot[1][a][q][lane], acc[a][q].x + acc[a][q].y);
+            __syncwarp();
         }
 #pragma unroll
         for (int q = 0; q < TPT; ++q) {
             if (!act[q]) continue;
             float r[NA];
 #pragma unroll
-            for (int a = 0; a < NA; ++a) r[a] = tot[0][a][q][threadIdx.x] + tot[1][a][q][threadIdx.x];
+            for (int a = 0; a < NA; ++a) r[a] = sm.tot[0][a][q][lane] + sm.tot[1][a][q][lane];
             const int i = ti[q];
             float4 vf{}, sf{};
             if (vfar) {
@@ -616,8 +635,9 @@ __global__ void __launch_bounds__(P2P_TILE / TPT) k_p2p_x2(const int* __restrict
             vout[o] = vo;
             sout[o] = so;
         }
+        __syncwarp();  // the next item rewrites this warp's colleague table
     }
-    if (threadIdx.x == 0 && my_pairs) atomicAdd(pairs, my_pairs);
+    if (lane == 0 && my_pairs) atomicAdd(pairs, my_pairs);
 }
 
 // acc = (first ? 0 : acc) + c_acc k;  stage = y0 + c_stage k  (x and w at once)
@@ -712,26 +732,36 @@ void run_p2p(Ctx* c, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs, 
     work = reinterpret_cast<int*>(ctx_tmp(c, 6).ptr);
     cuda_check(cudaMemsetAsync(work, 0, 4, s), "p2p counter");
     const int64_t max_tiles = lv.nbox[L] + n / P2P_TILE + 1;
-    // targets per thread: 1, 2 or 4 (128, 64 or 32 threads per tile of P2P_TILE targets);
-    // sources per shared-memory stage: 128 or 256
+    // targets per thread: 1, 2 or 4 (FP64: 128, 64 or 32 threads per tile of P2P_TILE targets;
+    // FP32: warp tiles of 32, 64 or 128 targets); sources per shared-memory stage: 128 or 256
     auto launch = [&](auto tpt, auto ch) {
         constexpr int TPT = decltype(tpt)::value;
         constexpr int CH = decltype(ch)::value;
-        auto kern = [&] {
-            if constexpr (std::is_same<T, float>::value)
-                return cc.smooth ? k_p2p_x2<true, TPT, CH> : k_p2p_x2<false, TPT, CH>;
-            else
-                return cc.smooth ? k_p2p<T, true, TPT, CH> : k_p2p<T, false, TPT, CH>;
-        }();
         int per_sm = 1, sms = 152, dev = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, P2P_TILE / TPT, 0);
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const int grid = (int)std::min<int64_t>(max_tiles, (int64_t)sms * std::max(per_sm, 1));
-        kern<<<grid, P2P_TILE / TPT, 0, s>>>(tb.tile_count.as<int>(), tb.tiles.as<int2>(), work,
-                                             tb.bbeg.as<int>() + o, tb.bend.as<int>() + o,
-                                             tb.bcol.as<int>() + (int64_t)o * 27, xs, ws, perm, vfar, sfar, v_out,
-                                             s_out, cc, near ? 1 : 0, pair_counter);
+        if constexpr (std::is_same<T, float>::value) {
+            // one warp per warp tile of 32 TPT targets, P2P_WARPS warps per block
+            auto kern = cc.smooth ? k_p2p_x2<true, TPT, CH> : k_p2p_x2<false, TPT, CH>;
+            const int smem = (int)(P2P_WARPS * sizeof(P2pWarpSmem<TPT, CH>));
+            cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem), "p2p attr");
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * P2P_WARPS, smem);
+            const int64_t items = max_tiles * (P2P_TILE / (32 * TPT));
+            const int grid = (int)std::min<int64_t>((items + P2P_WARPS - 1) / P2P_WARPS,
+                                                    (int64_t)sms * std::max(per_sm, 1));
+            kern<<<grid, 32 * P2P_WARPS, smem, s>>>(tb.tile_count.as<int>(), tb.tiles.as<int2>(), work,
+                                                    tb.bbeg.as<int>() + o, tb.bend.as<int>() + o,
+                                                    tb.bcol.as<int>() + (int64_t)o * 27, xs, ws, perm, vfar, sfar,
+                                                    v_out, s_out, cc, near ? 1 : 0, pair_counter);
+        } else {
+            auto kern = cc.smooth ? k_p2p<T, true, TPT, CH> : k_p2p<T, false, TPT, CH>;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, P2P_TILE / TPT, 0);
+            const int grid = (int)std::min<int64_t>(max_tiles, (int64_t)sms * std::max(per_sm, 1));
+            kern<<<grid, P2P_TILE / TPT, 0, s>>>(tb.tile_count.as<int>(), tb.tiles.as<int2>(), work,
+                                                 tb.bbeg.as<int>() + o, tb.bend.as<int>() + o,
+                                                 tb.bcol.as<int>() + (int64_t)o * 27, xs, ws, perm, vfar, sfar,
+                                                 v_out, s_out, cc, near ? 1 : 0, pair_counter);
+        }
     };
     using I1 = std::integral_constant<int, 1>;
     using I2 = std::integral_constant<int, 2>;
