@@ -179,41 +179,59 @@ __global__ void k_radix_hist(int64_t n, const uint64_t* __restrict__ keys, int s
     hist[threadIdx.x * nblocks + blockIdx.x] = cnt[threadIdx.x];
 }
 
-__global__ void k_radix_scatter(int64_t n, const uint64_t* __restrict__ kin, const int* __restrict__ vin,
-                                uint64_t* __restrict__ kout, int* __restrict__ vout, int shift, int nblocks,
-                                const int* __restrict__ offs) {
-    __shared__ int base[256];
-    __shared__ int wcnt[SORT_THREADS / 32][257];
+// Stable scatter of one digit.  Warp w of a block owns the SORT_TILE / 8
+// consecutive items [tile + w 512, tile + (w + 1) 512): it counts its digits
+// privately in order (rounds of 32 consecutive items), the warps' counts are
+// scanned per digit, and every item is written at
+//   block offset of its digit + items of that digit in earlier warps + its rank in the warp.
+constexpr int SORT_WARPS = SORT_THREADS / 32;
+constexpr int SORT_PER_WARP = SORT_TILE / SORT_WARPS;  // = 32 SORT_ITEMS
+__global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(int64_t n, const uint64_t* __restrict__ kin,
+                                                               const int* __restrict__ vin,
+                                                               uint64_t* __restrict__ kout, int* __restrict__ vout,
+                                                               int shift, int nblocks, const int* __restrict__ offs) {
+    __shared__ int wcnt[SORT_WARPS][256];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    base[t] = offs[t * nblocks + blockIdx.x];
-    for (int w = 0; w < SORT_THREADS / 32; ++w) wcnt[w][t] = 0;
+    for (int w = 0; w < SORT_WARPS; ++w) wcnt[w][t] = 0;
     __syncthreads();
-    const int64_t tile = (int64_t)blockIdx.x * SORT_TILE;
+    const int64_t first = (int64_t)blockIdx.x * SORT_TILE + (int64_t)warp * SORT_PER_WARP;
     const unsigned lt = (1u << lane) - 1u;
-    for (int j = 0; j < SORT_ITEMS; ++j) {
-        int64_t i = tile + j * SORT_THREADS + t;
-        bool valid = i < n;
-        uint64_t key = valid ? kin[i] : 0ull;
-        int val = valid ? vin[i] : 0;
-        int d = valid ? (int)((key >> shift) & 255u) : 256;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        int rank = __popc(peers & lt);
-        if (valid && rank == 0) wcnt[warp][d] = __popc(peers);
-        __syncthreads();
-        if (valid) {
-            int pos = base[d] + rank;
-            for (int w = 0; w < warp; ++w) pos += wcnt[w][d];
-            kout[pos] = key;
-            vout[pos] = val;
+    uint64_t key[SORT_ITEMS];
+    int val[SORT_ITEMS], rank[SORT_ITEMS];
+#pragma unroll
+    for (int r = 0; r < SORT_ITEMS; ++r) {
+        const int64_t i = first + r * 32 + lane;
+        key[r] = i < n ? kin[i] : 0ull;
+        val[r] = i < n ? vin[i] : 0;
+    }
+#pragma unroll
+    for (int r = 0; r < SORT_ITEMS; ++r) {
+        const int64_t i = first + r * 32 + lane;
+        const int d = i < n ? (int)((key[r] >> shift) & 255u) : 256;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        rank[r] = (d < 256 ? wcnt[warp][d] : 0) + __popc(peers & lt);
+        __syncwarp();
+        if (d < 256 && lane == __ffs(peers) - 1) wcnt[warp][d] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    {  // exclusive scan over the warps for digit t, plus the block's global offset
+        int run = offs[t * nblocks + blockIdx.x];
+        for (int w = 0; w < SORT_WARPS; ++w) {
+            const int c = wcnt[w][t];
+            wcnt[w][t] = run;
+            run += c;
         }
-        __syncthreads();
-        int add = 0;
-        for (int w = 0; w < SORT_THREADS / 32; ++w) {
-            add += wcnt[w][t];
-            wcnt[w][t] = 0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < SORT_ITEMS; ++r) {
+        const int64_t i = first + r * 32 + lane;
+        if (i < n) {
+            const int pos = wcnt[warp][(int)((key[r] >> shift) & 255u)] + rank[r];
+            kout[pos] = key[r];
+            vout[pos] = val[r];
         }
-        base[t] += add;
-        __syncthreads();
     }
 }
 

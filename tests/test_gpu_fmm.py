@@ -107,6 +107,20 @@ def test_singular_kernel_parity():
     assert rel(v, ref.v) < 1e-10 and rel(s, ref.s) < 1e-10
 
 
+@pytest.mark.parametrize("tpt", [1, 2, 4])
+def test_fp32_singular_kernel_parity(tpt):
+    """a = 0: the FP32 pair loop without the core correction, in each warp-tile
+    width (32, 64 and 128 targets), against the oracle."""
+    from paper_1201_5430_gb300 import LHV
+    x, w = workloads.cube(3001, 8)
+    ref = ofmm.fmm(x, w, 10, leaf_max=16, a=0.0)
+    ctx = LHV(p=10, leaf_max=16, core_a=0.0, precision="fp32")
+    ctx.set_launch_shape(tpt, 0, 1, p2p_sources_per_stage=128)
+    v4, s4 = ctx.evaluate_velocity_stretching(dev(x, "fp32"), dev(w, "fp32"))
+    ev, es = rel(host3(v4), ref.v), rel(host3(s4), ref.s)
+    assert ev < 1e-6 and es < 1e-6, (ev, es)
+
+
 def test_full_size_ring_sampled():
     """The bench workload (262,144-element ring, p = 12, FP32) in the bench's
     launch configuration: the near field of sampled targets against the oracle's
