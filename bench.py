@@ -597,7 +597,7 @@ def main():
                    "precision": args.precision,
                    "l2": "flushed between steps (256 MB write)", "parallelism": "replicas" if world > 1 else "1 GPU",
                    "leaf_level": st["leaf_level"], "boxes": st["nbox"]},
-        "roofline": {"kernel": "k_p2p (near field)", "bound": "alu", "achieved": achieved, "peak": peak,
+        "roofline": {"kernel": "k_p2p_x2 (near field, packed FP32x2)", "bound": "alu", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": f"FP32 FMA pipe: {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x "
                                   f"{peaks.get('sm_max_mhz', 2070.0)} MHz ({peak_kind} max clock)",
