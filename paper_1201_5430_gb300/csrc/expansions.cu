@@ -31,15 +31,51 @@ __device__ inline void box_geom(const SysCube* __restrict__ cubes, uint64_t key,
     cz = cb.x0[2] + ((double)c[2] + 0.5) * h;
 }
 
+// Coefficients of the recurrences of Q_n^m for n, m < p (they depend on (n, m)
+// only), built once per block in shared memory from double-precision values:
+//   Q_m^m     = cm[m] (x + i y) Q_{m-1}^{m-1},        cm[m] = -sqrt((2m - 1) / (2m)),
+//   Q_{m+1}^m = c1[m] z Q_m^m,                        c1[m] = sqrt(2m + 1),
+//   Q_n^m     = A[m][n] z Q_{n-1}^m - B[m][n] r^2 Q_{n-2}^m,
+//     A = (2n - 1) / sqrt((n + m)(n - m)),  B = sqrt((n + m - 1)(n - m - 1) / ((n + m)(n - m))).
+// The table takes qtab_reals(p) reals of the block's dynamic shared memory.
+template <typename T>
+struct QTab {
+    T *A, *B, *cm, *c1;
+    int p;
+};
+
+__host__ __device__ inline int qtab_reals(int p) { return 2 * p * p + 2 * p; }
+
+template <typename T>
+__device__ inline QTab<T> build_qtab(T* base, int p) {
+    QTab<T> q{base, base + p * p, base + 2 * p * p, base + 2 * p * p + p, p};
+    for (int i = threadIdx.x; i < p * p; i += blockDim.x) {
+        const int m = i / p, n = i - m * p;
+        double a = 0.0, b = 0.0;
+        if (n >= m + 2) {
+            const double d = (double)((n + m) * (n - m));
+            a = (double)(2 * n - 1) / sqrt(d);
+            b = sqrt((double)((n + m - 1) * (n - m - 1)) / d);
+        }
+        q.A[i] = (T)a;
+        q.B[i] = (T)b;
+    }
+    for (int m = threadIdx.x; m < p; m += blockDim.x) {
+        q.cm[m] = m > 0 ? (T)(-sqrt((double)(2 * m - 1) / (double)(2 * m))) : (T)0;
+        q.c1[m] = (T)sqrt((double)(2 * m + 1));
+    }
+    return q;
+}
+
 // Walks every (n, m), 0 <= m <= n < p, of the recurrence of Q_n^m at (x, y, z)
 // and calls f(n, m, Re Q, Im Q).  State is O(1).
 template <typename T, typename F>
-__device__ inline void for_each_Q(int p, T x, T y, T z, F&& f) {
+__device__ inline void for_each_Q(int p, T x, T y, T z, const QTab<T>& q, F&& f) {
     const T r2 = x * x + y * y + z * z;
     T dre = 1, dim = 0;  // Q_m^m
     for (int m = 0; m < p; ++m) {
         if (m > 0) {
-            T c = -sqrt((T)(2 * m - 1) / (T)(2 * m));
+            const T c = q.cm[m];
             T nre = c * (x * dre - y * dim);
             T nim = c * (x * dim + y * dre);
             dre = nre;
@@ -47,14 +83,13 @@ __device__ inline void for_each_Q(int p, T x, T y, T z, F&& f) {
         }
         f(m, m, dre, dim);
         if (m + 1 >= p) continue;
-        T c1 = sqrt((T)(2 * m + 1)) * z;
+        const T c1 = q.c1[m] * z;
         T pre = dre, pim = dim;             // Q_{n-2}
         T qre = c1 * dre, qim = c1 * dim;   // Q_{n-1} = Q_{m+1}^m
         f(m + 1, m, qre, qim);
         for (int n = m + 2; n < p; ++n) {
-            T inv = (T)1 / sqrt((T)((n + m) * (n - m)));
-            T a = (T)(2 * n - 1) * inv * z;
-            T b = sqrt((T)((n + m - 1) * (n - m - 1))) * inv * r2;
+            const T a = q.A[m * q.p + n] * z;
+            const T b = q.B[m * q.p + n] * r2;
             T nre = a * qre - b * pre;
             T nim = a * qim - b * pim;
             pre = qre;
@@ -89,8 +124,9 @@ __global__ void __launch_bounds__(P2M_THREADS) k_p2m_w(const int* __restrict__ n
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int P = p * p;
     T* gh = reinterpret_cast<T*>(smem_raw);  // [chunk][P]
-    T* wk = gh + (size_t)chunk * P;          // [chunk][3]
+    T* wk = gh + (size_t)chunk * P;          // [chunk][3]: w / h
     const int ntiles = *ntiles_dev;
+    const QTab<T> qt = build_qtab(wk + (size_t)chunk * 3, p);  // visible after the tile loop's first barrier
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int2 tw = tiles[t];
         const int b = tw.x;
@@ -113,7 +149,7 @@ __global__ void __launch_bounds__(P2M_THREADS) k_p2m_w(const int* __restrict__ n
                 T* g = gh + (size_t)e * P;
                 const T rx = (T)(((double)xv.x - cx) / h), ry = (T)(((double)xv.y - cy) / h),
                         rz = (T)(((double)xv.z - cz) / h);
-                for_each_Q<T>(p, rx, ry, rz, [&](int n, int m, T qr, T qi) {
+                for_each_Q<T>(p, rx, ry, rz, qt, [&](int n, int m, T qr, T qi) {
                     T re, im;  // i^m conj(Q)
                     switch (m & 3) {
                         case 0: re = qr; im = -qi; break;
@@ -196,6 +232,7 @@ __global__ void __launch_bounds__(L2P_THREADS) k_l2p_eval(const int* __restrict_
     T* cf = reinterpret_cast<T*>(smem_raw);  // [P][12]
     T* lh = cf + 12 * P;                     // [2P] the leaf's local expansion
     const int ntiles = *ntiles_dev;
+    const QTab<T> qt = build_qtab(lh + 2 * P, p);  // visible after the tile loop's first barrier
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int2 tw = tiles[t];
         const int b = tw.x;
@@ -220,7 +257,7 @@ __global__ void __launch_bounds__(L2P_THREADS) k_l2p_eval(const int* __restrict_
             T acc[12];
 #pragma unroll
             for (int j = 0; j < 12; ++j) acc[j] = 0;
-            for_each_Q<T>(p, rx, ry, rz, [&](int n, int m, T qr, T qi) {
+            for_each_Q<T>(p, rx, ry, rz, qt, [&](int n, int m, T qr, T qi) {
                 T re, im;  // (-1)^n i^m Q
                 switch (m & 3) {
                     case 0: re = qr; im = qi; break;
@@ -269,8 +306,8 @@ void run_p2m(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, co
     // the harmonics of a chunk sit in shared memory: the largest chunk (128, 64 or 32 elements)
     // that still leaves room for two blocks per SM
     int chunk = 128;
-    while (chunk > 32 && sizeof(T) * (size_t)chunk * (P + 3) > 80 * 1024) chunk /= 2;
-    const size_t smem = sizeof(T) * (size_t)chunk * (P + 3);
+    while (chunk > 32 && sizeof(T) * ((size_t)chunk * (P + 3) + qtab_reals(p)) > 80 * 1024) chunk /= 2;
+    const size_t smem = sizeof(T) * ((size_t)chunk * (P + 3) + qtab_reals(p));
     cuda_check(cudaFuncSetAttribute(k_p2m_w<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "p2m attr");
     cuda_check(cudaMemsetAsync(W, 0, sizeof(T) * (size_t)nl * 3 * P, stream_of(c)), "p2m zero");
     const int64_t max_tiles = nl + lv.n / P2P_TILE + 1;
@@ -372,7 +409,7 @@ template <typename T>
 void run_l2p(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs,
              const vec4_t<T>* ws, const T* loc, vec4_t<T>* vfar, vec4_t<T>* sfar) {
     const int L = lv.L, nl = lv.nbox[L], o = lv.off[L], p = pl.p[L], P = p * p;
-    const size_t smem = sizeof(T) * 14 * P;
+    const size_t smem = sizeof(T) * (14 * P + qtab_reals(p));
     cuda_check(cudaFuncSetAttribute(k_l2p_eval<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "l2p attr");
     const int64_t max_tiles = nl + lv.n / P2P_TILE + 1;
     k_l2p_eval<T><<<grid_for(max_tiles, 1, 152 * 16), L2P_THREADS, smem, stream_of(c)>>>(

@@ -49,6 +49,7 @@ __global__ void k_set_total(int ng, const int* __restrict__ cnt, int* __restrict
 
 constexpr int GG_THREADS = 256;
 constexpr int KC = 16;  // operator rows (input coefficients) staged per step
+constexpr int GG_DEPTH = 4;  // steps of operator rows in flight
 
 // RT = 16 * TM output rows per work item; NC columns, TN = NC / 16 per thread.
 template <typename T, int NC, int TM>
@@ -107,41 +108,48 @@ __global__ void __launch_bounds__(GG_THREADS) k_group_gemm(GemmArgs<T> a) {
 #pragma unroll
             for (int c = 0; c < TN; ++c) acc[j][c] = 0;
         const T* Ag = a.ops + (int64_t)(g % a.ops_mod) * a.C * a.R;
-        // operator rows [kc, kc + KC) of this row tile: each thread owns EPT entries; the next
-        // step's entries are loaded into registers while the current step computes
+        // operator rows [kc, kc + KC) of this row tile: each thread owns EPT entries of a step;
+        // the entries of the next GG_DEPTH steps are in flight in registers (a ring indexed at
+        // compile time) while the current step computes from shared memory
         constexpr int EPT = KC * RT / GG_THREADS;
-        T nxt[EPT];
-        auto load = [&](int kc) {
+        T nxt[GG_DEPTH][EPT];
+        auto load = [&](int kc, T(&dst)[EPT]) {
 #pragma unroll
             for (int q = 0; q < EPT; ++q) {
                 const int e = t + q * GG_THREADS;
                 const int kk = e / RT, r = e - kk * RT;
                 const int k = kc + kk, row = r0 + r;
-                nxt[q] = (k < a.C && row < a.R) ? Ag[(int64_t)k * a.R + row] : (T)0;
+                dst[q] = (k < a.C && row < a.R) ? Ag[(int64_t)k * a.R + row] : (T)0;
             }
         };
-        load(tile_kstart);
+#pragma unroll
+        for (int d = 0; d < GG_DEPTH; ++d) load(tile_kstart + d * KC, nxt[d]);
         int buf = 0;
-        for (int kc = tile_kstart; kc < a.C; kc += KC) {
-            T* Ab = A + buf * KC * RT;
+        for (int kc0 = tile_kstart; kc0 < a.C; kc0 += GG_DEPTH * KC) {
 #pragma unroll
-            for (int q = 0; q < EPT; ++q) Ab[t + q * GG_THREADS] = nxt[q];
-            __syncthreads();
-            if (kc + KC < a.C) load(kc + KC);
-            const int kn = min(KC, a.C - kc);
-            for (int kk = 0; kk < kn; ++kk) {
-                if (kc + kk < kstart) continue;
-                T av[TM], xv[TN];
+            for (int d = 0; d < GG_DEPTH; ++d) {
+                const int kc = kc0 + d * KC;
+                if (kc >= a.C) break;
+                T* Ab = A + buf * KC * RT;
 #pragma unroll
-                for (int j = 0; j < TM; ++j) av[j] = Ab[kk * RT + rg * TM + j];
+                for (int q = 0; q < EPT; ++q) Ab[t + q * GG_THREADS] = nxt[d][q];
+                __syncthreads();
+                if (kc + GG_DEPTH * KC < a.C) load(kc + GG_DEPTH * KC, nxt[d]);
+                const int kn = min(KC, a.C - kc);
+                for (int kk = 0; kk < kn; ++kk) {
+                    if (kc + kk < kstart) continue;
+                    T av[TM], xv[TN];
 #pragma unroll
-                for (int c = 0; c < TN; ++c) xv[c] = X[(kc + kk) * XS + cg * TN + c];
+                    for (int j = 0; j < TM; ++j) av[j] = Ab[kk * RT + rg * TM + j];
 #pragma unroll
-                for (int j = 0; j < TM; ++j)
+                    for (int c = 0; c < TN; ++c) xv[c] = X[(kc + kk) * XS + cg * TN + c];
 #pragma unroll
-                    for (int c = 0; c < TN; ++c) acc[j][c] += av[j] * xv[c];
+                    for (int j = 0; j < TM; ++j)
+#pragma unroll
+                        for (int c = 0; c < TN; ++c) acc[j][c] += av[j] * xv[c];
+                }
+                buf ^= 1;
             }
-            buf ^= 1;
         }
 #pragma unroll
         for (int c = 0; c < TN; ++c) {
