@@ -121,6 +121,24 @@ def test_fp32_singular_kernel_parity(tpt):
     assert ev < 1e-6 and es < 1e-6, (ev, es)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_coincident_elements(prec):
+    """Distinct elements at one point (r = 0, j != i) take the limits of the
+    smoothed kernel in the near field, in both precisions."""
+    x, w = workloads.cube(3001, 4)
+    x = x.copy()
+    x[1] = x[0]
+    x[7] = x[5]
+    x[100:104] = x[99]
+    a = 0.01
+    ref = ofmm.fmm(x, w, 10, leaf_max=32, a=a)
+    ctx, v, s = _run(x, w, 10, 32, a, prec)
+    assert np.isfinite(v).all() and np.isfinite(s).all()
+    tol = 1e-6 if prec == "fp32" else 1e-10
+    ev, es = rel(v, ref.v), rel(s, ref.s)
+    assert ev < tol and es < tol, (ev, es)
+
+
 def test_full_size_ring_sampled():
     """The bench workload (262,144-element ring, p = 12, FP32) in the bench's
     launch configuration: the near field of sampled targets against the oracle's
