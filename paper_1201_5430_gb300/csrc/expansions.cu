@@ -373,6 +373,7 @@ void run_m2m(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, Gr
         a.mode = GEMM_ATOMIC;
         a.scale = (T)1;
         a.pairs_hint = lv.nbox[l + 1];
+        a.may_split_k = 1;
         run_group_gemm<T>(c, gp, a);
     }
 }
@@ -398,9 +399,10 @@ void run_l2l(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, Gr
         a.ldin = pl.ld;
         a.out = loc;
         a.ldout = pl.ld;
-        a.mode = GEMM_ADD;
+        a.mode = GEMM_ATOMIC;  // one parent per child: the plain sum, issued without waiting for the old value
         a.scale = (T)1;
         a.pairs_hint = lv.nbox[l + 1];
+        a.may_split_k = 1;
         run_group_gemm<T>(c, gp, a);
     }
 }

@@ -52,7 +52,7 @@ constexpr int KC = 16;  // operator rows (input coefficients) staged per step
 constexpr int GG_DEPTH = 4;  // steps of operator rows in flight
 
 // RT = 16 * TM output rows per work item; NC columns, TN = NC / 16 per thread.
-template <typename T, int NC, int TM>
+template <typename T, int NC, int TM, bool SPLIT>
 __global__ void __launch_bounds__(GG_THREADS) k_group_gemm(GemmArgs<T> a) {
     constexpr int TN = NC / 16;
     constexpr int RT = 16 * TM;
@@ -66,19 +66,27 @@ __global__ void __launch_bounds__(GG_THREADS) k_group_gemm(GemmArgs<T> a) {
     const int cg = t % 16, rg = t / 16;
     const int nrt = (a.R + RT - 1) / RT;
     const int c_beg = a.choff[a.g0], c_end = a.choff[a.g1];
-    const int nwork = (c_end - c_beg) * nrt;
-    int last_chunk = -1;
+    // split K: segment ks covers inputs [ks kper, (ks + 1) kper) (kper a multiple of KC); the
+    // segments' partial products meet in the atomic adds of the epilogue
+    const int nks = SPLIT && a.ksplit > 1 ? a.ksplit : 1;
+    const int kper = SPLIT ? (a.C + nks * KC - 1) / (nks * KC) * KC : a.C;
+    const int nwork = (c_end - c_beg) * nrt * nks;
+    int last_key = -1;
     for (;;) {
         __syncthreads();
         if (t == 0) s_work = atomicAdd(a.work, 1);
         __syncthreads();
         const int w = s_work;
         if (w >= nwork) break;
-        const int chunk = c_beg + w / nrt, rt = w % nrt;
+        const int ks = SPLIT ? w % nks : 0, wc = SPLIT ? w / nks : w;
+        const int chunk = c_beg + wc / nrt, rt = wc % nrt;
+        const int kseg0 = ks * kper, kseg1 = SPLIT ? min(a.C, kseg0 + kper) : a.C;
+        if (kseg0 >= kseg1) continue;  // block-uniform: an empty last segment
         const int4 ch = a.chunks[chunk];
         const int g = ch.x, p0 = ch.y, np = ch.z;
         const int r0 = rt * RT;
-        if (chunk != last_chunk) {
+        const int key = chunk * nks + ks;
+        if (key != last_key) {
             if (t < NC) {
                 if (t < np) {
                     const int2 pr = a.pairs[p0 + t];
@@ -90,18 +98,20 @@ __global__ void __launch_bounds__(GG_THREADS) k_group_gemm(GemmArgs<T> a) {
                 }
             }
             __syncthreads();
-            for (int e = t; e < a.C * NC; e += GG_THREADS) {
-                const int col = e / a.C, k = e - col * a.C;
+            const int klen = kseg1 - kseg0;
+            for (int e = t; e < klen * NC; e += GG_THREADS) {
+                const int col = e / klen, k = kseg0 + (e - col * klen);
                 const int s = s_src[col];
                 X[k * XS + col] = (s >= 0) ? a.in[(int64_t)s * a.ldin + k] : (T)0;
             }
-            last_chunk = chunk;
+            last_key = key;
         }
         // rows of this thread: r0 + rg*TM + j; skip the zero block (rows >= psplit read inputs >= psplit only)
         const int myrow0 = r0 + rg * TM;
         const int pcol = a.psplit_c > 0 ? a.psplit_c : a.psplit;
         const int kstart = (a.psplit > 0 && myrow0 >= a.psplit) ? pcol : 0;
-        const int tile_kstart = (a.psplit > 0 && r0 >= a.psplit) ? pcol : 0;
+        const int kb = max((a.psplit > 0 && r0 >= a.psplit) ? pcol : 0, kseg0);  // this item's K range [kb, ke)
+        const int ke = kseg1;
         T acc[TM][TN];
 #pragma unroll
         for (int j = 0; j < TM; ++j)
@@ -119,23 +129,23 @@ __global__ void __launch_bounds__(GG_THREADS) k_group_gemm(GemmArgs<T> a) {
                 const int e = t + q * GG_THREADS;
                 const int kk = e / RT, r = e - kk * RT;
                 const int k = kc + kk, row = r0 + r;
-                dst[q] = (k < a.C && row < a.R) ? Ag[(int64_t)k * a.R + row] : (T)0;
+                dst[q] = (k < ke && row < a.R) ? Ag[(int64_t)k * a.R + row] : (T)0;
             }
         };
 #pragma unroll
-        for (int d = 0; d < GG_DEPTH; ++d) load(tile_kstart + d * KC, nxt[d]);
+        for (int d = 0; d < GG_DEPTH; ++d) load(kb + d * KC, nxt[d]);
         int buf = 0;
-        for (int kc0 = tile_kstart; kc0 < a.C; kc0 += GG_DEPTH * KC) {
+        for (int kc0 = kb; kc0 < ke; kc0 += GG_DEPTH * KC) {
 #pragma unroll
             for (int d = 0; d < GG_DEPTH; ++d) {
                 const int kc = kc0 + d * KC;
-                if (kc >= a.C) break;
+                if (kc >= ke) break;
                 T* Ab = A + buf * KC * RT;
 #pragma unroll
                 for (int q = 0; q < EPT; ++q) Ab[t + q * GG_THREADS] = nxt[d][q];
                 __syncthreads();
-                if (kc + GG_DEPTH * KC < a.C) load(kc + GG_DEPTH * KC, nxt[d]);
-                const int kn = min(KC, a.C - kc);
+                if (kc + GG_DEPTH * KC < ke) load(kc + GG_DEPTH * KC, nxt[d]);
+                const int kn = min(KC, ke - kc);
                 for (int kk = 0; kk < kn; ++kk) {
                     if (kc + kk < kstart) continue;
                     T av[TM], xv[TN];
@@ -170,18 +180,18 @@ __global__ void __launch_bounds__(GG_THREADS) k_group_gemm(GemmArgs<T> a) {
     }
 }
 
-template <typename T, int NC, int TM>
+template <typename T, int NC, int TM, bool SPLIT>
 void launch_gemm(Ctx* c, const GemmArgs<T>& a) {
     const size_t smem = sizeof(T) * ((size_t)a.C * (NC + 4) + 2 * (size_t)KC * 16 * TM);
-    cuda_check(cudaFuncSetAttribute(k_group_gemm<T, NC, TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+    cuda_check(cudaFuncSetAttribute(k_group_gemm<T, NC, TM, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                "gemm attr");
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_group_gemm<T, NC, TM>, GG_THREADS, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_group_gemm<T, NC, TM, SPLIT>, GG_THREADS, smem);
     if (per_sm < 1) per_sm = 1;
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    k_group_gemm<T, NC, TM><<<sms * per_sm, GG_THREADS, smem, stream_of(c)>>>(a);
+    k_group_gemm<T, NC, TM, SPLIT><<<sms * per_sm, GG_THREADS, smem, stream_of(c)>>>(a);
     count_launch(c);
     check_launch("group gemm");
 }
@@ -237,11 +247,11 @@ int gemm_nc(int C) {
     return 16;
 }
 
-template <int NC, typename T>
+template <int NC, bool SPLIT = false, typename T>
 static void launch_tm(Ctx* c, const GemmArgs<T>& a, int tm) {
-    if (tm == 8) launch_gemm<T, NC, 8>(c, a);
-    else if (tm == 4) launch_gemm<T, NC, 4>(c, a);
-    else launch_gemm<T, NC, 2>(c, a);
+    if (tm == 8) launch_gemm<T, NC, 8, SPLIT>(c, a);
+    else if (tm == 4) launch_gemm<T, NC, 4, SPLIT>(c, a);
+    else launch_gemm<T, NC, 2, SPLIT>(c, a);
 }
 
 template <typename T>
@@ -259,7 +269,15 @@ void run_group_gemm(Ctx* c, Grouped& gp, GemmArgs<T> a) {
         const int64_t chunks = a.pairs_hint / nc + (a.g1 - a.g0);
         while (tm > 2 && chunks * ((a.R + 16 * tm - 1) / (16 * tm)) < 4 * 152) tm /= 2;
     }
-    if (nc == 64) launch_tm<64>(c, a, tm);
+    // split K when the items would leave most resident blocks idle (a short level's few chunks
+    // each run one long serial K loop); only where the outputs are added atomically anyway
+    a.ksplit = 1;
+    if (a.may_split_k && nc == 16 && a.mode == GEMM_ATOMIC && a.pairs_hint > 0) {
+        const int64_t items = (a.pairs_hint / nc + (a.g1 - a.g0)) * ((a.R + 16 * tm - 1) / (16 * tm));
+        while (a.ksplit < 8 && items * a.ksplit < 2 * 152 * 4 && a.C >= 4 * KC * a.ksplit) a.ksplit *= 2;
+    }
+    if (a.ksplit > 1 && nc == 16) launch_tm<16, true>(c, a, tm);
+    else if (nc == 64) launch_tm<64>(c, a, tm);
     else if (nc == 32) launch_tm<32>(c, a, tm);
     else launch_tm<16>(c, a, tm);
 }

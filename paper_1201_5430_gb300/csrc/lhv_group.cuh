@@ -37,6 +37,8 @@ struct GemmArgs {
     int mode;             // GemmMode
     T scale;
     int64_t pairs_hint;   // about how many pairs this launch covers (0: unknown); picks the tile height
+    int may_split_k;      // 1: run_group_gemm may split K (GEMM_ATOMIC only; the translations between levels)
+    int ksplit;           // > 1: K in this many segments, one work item each (set by run_group_gemm)
 };
 
 // Items -> bucketed pairs.  An item functor `it(i, g, src, dst)` returns false
