@@ -236,7 +236,13 @@ int lhv_reset_stats(lhv_ctx* ctx);
  * the array (also when dst is NULL, to query it).  `level` selects the octree
  * level where the array is per level.  Returns LHV_EINVAL if the array does
  * not exist or does not fit.  Arrays:                                         */
-#define LHV_EXPORT_KEYS        1  /* uint64[n] Morton keys, sorted */
+#define LHV_EXPORT_KEYS        1  /* uint64[n] Morton keys in the tree's order: sorted (stable)
+                                     for a context's first tree and whenever the context has no
+                                     core radius and no level cap; otherwise sorted by their
+                                     prefix down to one level below the deepest level that the
+                                     core rule and the level cap allowed in the previous tree,
+                                     equal prefixes in input order (the boxes of every level the
+                                     tree uses are the same) */
 #define LHV_EXPORT_PERM        2  /* int32[n] sorted position -> caller index */
 #define LHV_EXPORT_BOX_KEYS    3  /* uint64[nbox(level)] key prefixes of the level's boxes */
 #define LHV_EXPORT_BOX_RANGE   4  /* int32[nbox(level)][2] sorted element range [begin, end) */
@@ -273,8 +279,9 @@ int lhv_export(lhv_ctx* ctx, int what, int level, void* dst, int64_t capacity_by
  * NaN/Inf).  Outputs (caller-owned device memory, also used as one side of the
  * sort's ping-pong): keys (uint64 [n]) the sorted Morton keys and perm (int32
  * [n]) sorted position -> caller index, identical to LHV_EXPORT_KEYS and
- * LHV_EXPORT_PERM after lhv_build_tree of the same positions (21 bits per axis,
- * stable order of equal keys).  Work is enqueued on cuda_stream (a cudaStream_t,
+ * LHV_EXPORT_PERM after lhv_build_tree of the same positions in a new context or
+ * one without core radius and level cap (21 bits per axis, stable order of
+ * equal keys).  Work is enqueued on cuda_stream (a cudaStream_t,
  * NULL = legacy default stream); the call returns after that stream has
  * finished it (one device-to-host read of the non-finite flag).  The only
  * scratch state that must start at zero (the non-finite flag) is cleared by the

@@ -54,6 +54,7 @@ struct Ctx {
     int eval_ld = 0;                    // their stride (reals per box)
     int leaf_override = 0;              // leaf cap chosen by the selector (0: cfg.leaf_max)
     bool tree_reuse = false;            // the next evaluation may use the tree just built for its inputs
+    int sort_levels = 0;                // Morton levels the next tree's sort orders (0: all; set by each tree)
     // launch shapes chosen by lhv_autotune
     int tune_tpt = 1;                   // P2P targets per thread
     int tune_ch = 128;                  // P2P sources per shared-memory stage
@@ -77,6 +78,7 @@ cudaStream_t stream_of(Ctx* c) { return c->stream; }
 int ctx_leaf_max(Ctx* c) { return c->leaf_override > 0 ? c->leaf_override : c->cfg.leaf_max; }
 int ctx_max_level(Ctx* c) { return c->cfg.max_level; }
 double ctx_rK(Ctx* c) { return c->rK; }
+int& ctx_sort_levels(Ctx* c) { return c->sort_levels; }
 Buf& ctx_tmp(Ctx* c, int i) { return c->tmp[i]; }
 bool ctx_use_tc(Ctx* c) { return c->cfg.precision == LHV_TF32X3; }
 int* ctx_err_flag(Ctx* c) { return reinterpret_cast<int*>(c->counters.as<unsigned long long>() + 2); }

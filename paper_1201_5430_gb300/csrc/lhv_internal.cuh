@@ -42,7 +42,8 @@ struct TreeParams {
     int deepest_shared; // deepest level at which leaf_max+1 consecutive keys share a box
     int bits;           // Morton bits per axis
     int nsys;
-    int pad[3];
+    int L_cap;          // deepest level any tree of these cubes may have: min(L_K, the level cap, bits)
+    int pad[2];
 };
 
 // Growable device allocation.
@@ -77,6 +78,7 @@ void ensure(Ctx* c, Buf& b, int64_t bytes);          // grow b to >= bytes (thro
 int ctx_leaf_max(Ctx* c);
 int ctx_max_level(Ctx* c);
 double ctx_rK(Ctx* c);
+int& ctx_sort_levels(Ctx* c);                        // Morton levels the next tree's sort orders (0: all)
 Buf& ctx_tmp(Ctx* c, int i);                         // scratch buffers 0..13 owned by the context
 bool ctx_use_tc(Ctx* c);                             // LHV_TF32X3: dense maps on the tensor cores
 int* ctx_err_flag(Ctx* c);                           // device word set by a timed-out device wait

@@ -389,9 +389,10 @@ __global__ void k_leaf_level(TreeParams* __restrict__ tp, const SysCube* __restr
         for (int l = 0; l <= bits; ++l)
             if (ldexp(min_side, -l) >= rK) L_K = l;
     }
-    int L = min(L_leaf, L_K);
-    if (max_level > 0) L = min(L, max_level);
-    tp->L = L;
+    int L_cap = L_K;
+    if (max_level > 0) L_cap = min(L_cap, max_level);
+    tp->L_cap = L_cap;
+    tp->L = min(L_leaf, L_cap);
 }
 
 // ---------------------------------------------------------------------------
@@ -648,34 +649,54 @@ int build_tree(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const vec4_t<
     count_launch(c);
     check_launch("keys");
 
-    // stable radix sort, 8 passes of 8 bits
+    // Stable LSD radix sort of 8-bit digits, then the leaf level.  A tree never goes below
+    // L_cap = min(L_K, the level cap); ordering the keys by their prefix down to a level
+    // S >= L_cap gives the same boxes at every level <= S and the same leaf level (keys that
+    // differ within the prefix give the same shared level either way, and keys that share
+    // their level-S box give a shared level >= S, beyond L_cap, either way).  S is the
+    // previous tree's L_cap + 1 (all levels for a context's first tree); if the new L_cap
+    // exceeds it, the sort is completed (a stable sort of the prefix-sorted keys is the
+    // stable sort) and the leaf level recomputed.
     uint64_t* kin = tb.keys_a.as<uint64_t>();
     uint64_t* kout = tb.keys_b.as<uint64_t>();
     int* vin = tb.idx_a.as<int>();
     int* vout = tb.idx_b.as<int>();
     int* hist = tb.hist.as<int>();
-    for (int pass = 0; pass < 8; ++pass) {
-        int shift = pass * 8;
-        k_radix_hist<<<nsort, SORT_THREADS, 0, s>>>(nn, kin, shift, nsort, hist);
+    auto sort_passes = [&](int first_pass) {
+        for (int pass = first_pass; pass < 8; ++pass) {
+            int shift = pass * 8;
+            k_radix_hist<<<nsort, SORT_THREADS, 0, s>>>(nn, kin, shift, nsort, hist);
+            count_launch(c);
+            exclusive_scan(c, (int64_t)nsort * 256, hist, hist, tb.scan_tmp.as<int>(), nullptr);
+            k_radix_scatter<<<nsort, SORT_THREADS, 0, s>>>(nn, kin, vin, kout, vout, shift, nsort, hist);
+            count_launch(c);
+            std::swap(kin, kout);
+            std::swap(vin, vout);
+        }
+        check_launch("sort");
+    };
+    auto leaf_level = [&]() {
+        k_shared_level<<<grid_for(nn, 256), 256, 0, s>>>(nn, leaf_max, bits, kin, tp);
         count_launch(c);
-        exclusive_scan(c, (int64_t)nsort * 256, hist, hist, tb.scan_tmp.as<int>(), nullptr);
-        k_radix_scatter<<<nsort, SORT_THREADS, 0, s>>>(nn, kin, vin, kout, vout, shift, nsort, hist);
+        k_leaf_level<<<1, 32, 0, s>>>(tp, cubes, nsys, bits, ctx_rK(c), ctx_max_level(c));
         count_launch(c);
-        std::swap(kin, kout);
-        std::swap(vin, vout);
+        check_launch("leaf level");
+        cuda_check(cudaMemcpyAsync(&hp, tp, sizeof(TreeParams), cudaMemcpyDeviceToHost, s), "read params");
+        cuda_check(cudaStreamSynchronize(s), "sync params");
+    };
+    int S = ctx_sort_levels(c);
+    if (S <= 0 || S > bits) S = bits;
+    const int first_pass = 3 * (bits - S) / 8;  // lower digits order nothing the tree uses
+    sort_passes(first_pass);
+    leaf_level();
+    if (first_pass > 0 && hp.L_cap > S && !hp.nonfinite) {
+        sort_passes(0);
+        cuda_check(cudaMemsetAsync(&tp->deepest_shared, 0, sizeof(int), s), "reset shared level");
+        leaf_level();
     }
-    check_launch("sort");
-    // after an even number of passes the result is back in keys_a / idx_a
+    ctx_sort_levels(c) = std::min(bits, hp.L_cap + 1);
     uint64_t* keys = kin;
     int* perm = vin;
-
-    k_shared_level<<<grid_for(nn, 256), 256, 0, s>>>(nn, leaf_max, bits, keys, tp);
-    count_launch(c);
-    k_leaf_level<<<1, 32, 0, s>>>(tp, cubes, nsys, bits, ctx_rK(c), ctx_max_level(c));
-    count_launch(c);
-    check_launch("leaf level");
-    cuda_check(cudaMemcpyAsync(&hp, tp, sizeof(TreeParams), cudaMemcpyDeviceToHost, s), "read params");
-    cuda_check(cudaStreamSynchronize(s), "sync params");
     if (hp.nonfinite) {
         err = {LHV_ENONFINITE, "non-finite position or strength"};
         return LHV_ENONFINITE;

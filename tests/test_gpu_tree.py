@@ -26,6 +26,11 @@ def _check(x, leaf_max, a=0.0, eps=1e-6, max_level=0):
     assert cube[3] == tr.side
     if max_level:
         tr = T.build_tree(x, leaf_max=leaf_max, a=a, eps=eps, L_override=L)
+    _boxes_match(ctx, tr, st, L)
+    ctx.close()
+
+
+def _boxes_match(ctx, tr, st, L):
     for lev in range(L + 1):
         d = tr.levels[lev]
         assert st["nbox"][lev] == d["keys"].shape[0]
@@ -37,6 +42,34 @@ def _check(x, leaf_max, a=0.0, eps=1e-6, max_level=0):
         col = ctx.export("colleagues", lev).cpu().numpy().reshape(-1, 27)
         for i in range(col.shape[0]):
             assert sorted(c for c in col[i] if c >= 0) == d["colleagues"][i]
+
+
+def test_repeated_trees_in_one_context():
+    """After a context's first tree the sort orders the keys only down to one level
+    below the previous depth cap (core rule): leaf level, boxes and colleagues stay
+    the oracle's, the keys are the oracle's keys of the permuted elements in prefix
+    order; a cube that grows (the cap moves two levels deeper) falls back to the full sort."""
+    from paper_1201_5430_gb300 import LHV
+    x, _ = workloads.ring(20000, 1)
+    a = workloads.RING_CORE_A
+    ctx = LHV(p=4, leaf_max=64, core_a=a, eps=1e-6)
+    for k, xs in enumerate((x, x + np.float32(1e-4), x * np.float32(4.0))):
+        ctx.build_tree(dev(xs, "fp32"))
+        tr = T.build_tree(xs, leaf_max=64, a=a, eps=1e-6)
+        st = ctx.stats()
+        L = st["leaf_level"]
+        assert L == tr.L
+        keys = ctx.export("keys").cpu().numpy().view(np.uint64)
+        perm = ctx.export("perm").cpu().numpy()
+        np.testing.assert_array_equal(np.sort(perm), np.arange(xs.shape[0]))
+        okeys, _, _ = T.morton_keys(xs)
+        np.testing.assert_array_equal(keys, okeys[perm])
+        if k != 1:  # a first tree, and the fallback, are fully sorted
+            np.testing.assert_array_equal(perm, tr.perm)
+        else:       # prefix order down to the previous cap + 1 >= L
+            pre = keys >> np.uint64(3 * (21 - (L + 1)))
+            assert (pre[1:] >= pre[:-1]).all()
+        _boxes_match(ctx, tr, st, L)
     ctx.close()
 
 
