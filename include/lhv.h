@@ -192,8 +192,9 @@ int lhv_direct_sampled_f64(lhv_ctx* ctx, int64_t n, const double* x4, const doub
 
 /* Autotuner (launch shapes, not in the paper): runs the evaluation of the given
  * elements once per candidate and keeps, for this context, the fastest P2P tile
- * shape (1, 2 or 4 targets per thread over tiles of 128 targets, i.e. 128, 64 or
- * 32 threads, times 128 or 256 sources staged in shared memory per step) and the
+ * shape (1, 2 or 4 targets per thread: FP32 warp tiles of 32, 64 or 128 targets,
+ * FP64 blocks of 128, 64 or 32 threads over tiles of 128 targets; times 128 or 256
+ * sources staged in shared memory per step) and the
  * fastest M2L grouping (box pairs of one offset per GEMM chunk: 64, 32 or 16 on
  * the CUDA cores; under TF32X3 also the tensor-core kernel with 128 or 64 pairs
  * per chunk), judged by CUDA-event stage times (best of 3 after a warm-up).  v4
