@@ -520,41 +520,39 @@ __global__ void k_lvl_children(int nbt, LevelTable lt, int* __restrict__ bcbeg, 
 }
 
 // 27 colleagues of every box of every level (binary search among its level's keys);
-// the system id above the level's 3*level Morton bits is kept.
+// the system id above the level's 3*level Morton bits is kept.  One thread per
+// (box, slot), slot = ((dx + 1) 3 + (dy + 1)) 3 + (dz + 1).
 __global__ void k_colleagues_all(int nbt, LevelTable lt, const uint64_t* __restrict__ bkey_all,
                                  int* __restrict__ col_all) {
-    for (int gb = blockIdx.x * blockDim.x + threadIdx.x; gb < nbt; gb += gridDim.x * blockDim.x) {
+    for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < (int64_t)nbt * 27;
+         it += (int64_t)gridDim.x * blockDim.x) {
+        const int gb = (int)(it / 27), slot = (int)(it - (int64_t)gb * 27);
+        const int dx = slot / 9 - 1, dy = (slot / 3) % 3 - 1, dz = slot % 3 - 1;
         const int level = level_of(lt, gb);
         const int o = lt.off[level], nb = lt.off[level + 1] - o, b = gb - o;
         const uint64_t* bkey = bkey_all + o;
-        int* col = col_all + (int64_t)o * 27;
         const int64_t dim = 1ll << level;
         const uint64_t mask = (level > 0) ? ((~0ull) >> (64 - 3 * level)) : 0ull;
         const uint64_t full = bkey[b];
         const uint64_t sysk = (level > 0) ? ((full >> (3 * level)) << (3 * level)) : full;
         const uint64_t key = full & mask;
-        int64_t cx = (int64_t)compact3(key), cy = (int64_t)compact3(key >> 1), cz = (int64_t)compact3(key >> 2);
-        int slot = 0;
-        for (int dx = -1; dx <= 1; ++dx)
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dz = -1; dz <= 1; ++dz, ++slot) {
-                    int64_t x = cx + dx, y = cy + dy, z = cz + dz;
-                    int found = -1;
-                    if (x >= 0 && y >= 0 && z >= 0 && x < dim && y < dim && z < dim) {
-                        uint64_t k2 = sysk | morton3((uint64_t)x, (uint64_t)y, (uint64_t)z);
-                        int lo = 0, hi = nb - 1;
-                        while (lo <= hi) {
-                            int mid = (lo + hi) >> 1;
-                            uint64_t km = bkey[mid];
-                            if (km == k2) {
-                                found = mid;
-                                break;
-                            }
-                            if (km < k2) lo = mid + 1; else hi = mid - 1;
-                        }
-                    }
-                    col[(int64_t)b * 27 + slot] = found;
+        const int64_t x = (int64_t)compact3(key) + dx, y = (int64_t)compact3(key >> 1) + dy,
+                      z = (int64_t)compact3(key >> 2) + dz;
+        int found = -1;
+        if (x >= 0 && y >= 0 && z >= 0 && x < dim && y < dim && z < dim) {
+            const uint64_t k2 = sysk | morton3((uint64_t)x, (uint64_t)y, (uint64_t)z);
+            int lo = 0, hi = nb - 1;
+            while (lo <= hi) {
+                const int mid = (lo + hi) >> 1;
+                const uint64_t km = bkey[mid];
+                if (km == k2) {
+                    found = mid;
+                    break;
                 }
+                if (km < k2) lo = mid + 1; else hi = mid - 1;
+            }
+        }
+        col_all[(int64_t)o * 27 + (int64_t)b * 27 + slot] = found;
     }
 }
 
@@ -752,7 +750,8 @@ int build_tree(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const vec4_t<
     k_lvl_children<<<grid_for(nbt, 256), 256, 0, s>>>((int)nbt, lt, tb.bcbeg.as<int>(), tb.bcend.as<int>());
     count_launch(c);
     ensure(c, tb.bcol, nbt * 27 * 4);
-    k_colleagues_all<<<grid_for(nbt, 128), 128, 0, s>>>((int)nbt, lt, tb.bkey.as<uint64_t>(), tb.bcol.as<int>());
+    k_colleagues_all<<<grid_for(nbt * 27, 128), 128, 0, s>>>((int)nbt, lt, tb.bkey.as<uint64_t>(),
+                                                              tb.bcol.as<int>());
     count_launch(c);
     check_launch("children, colleagues");
 
