@@ -55,18 +55,20 @@ template <typename T>
 __global__ void k_bbox_partial(int parts, const int64_t* __restrict__ sysoff, const vec4_t<T>* __restrict__ x4,
                                const vec4_t<T>* __restrict__ w4, double* __restrict__ part,
                                int* __restrict__ nonfinite) {
-    __shared__ double s[6][256];
+    // min/max in the input type (exact; its conversion to double is exact and monotonic)
+    __shared__ T s[6][256];
     const int sys = blockIdx.x / parts, q = blockIdx.x % parts;
     const int64_t o0 = sysoff[sys], len = sysoff[sys + 1] - o0;
     const int64_t beg = o0 + len * q / parts, end = o0 + len * (q + 1) / parts;
-    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    const T inf = (T)INFINITY;
+    T lo[3] = {inf, inf, inf}, hi[3] = {-inf, -inf, -inf};
     int bad = 0;
     for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
         vec4_t<T> p = x4[i];
         vec4_t<T> qv = w4 ? w4[i] : p;
-        double c[3] = {(double)p.x, (double)p.y, (double)p.z};
+        const T c[3] = {p.x, p.y, p.z};
         bad |= !(isfinite(c[0]) && isfinite(c[1]) && isfinite(c[2]));
-        bad |= !(isfinite((double)qv.x) && isfinite((double)qv.y) && isfinite((double)qv.z));
+        bad |= !(isfinite(qv.x) && isfinite(qv.y) && isfinite(qv.z));
         for (int k = 0; k < 3; ++k) {
             lo[k] = fmin(lo[k], c[k]);
             hi[k] = fmax(hi[k], c[k]);
@@ -87,7 +89,7 @@ __global__ void k_bbox_partial(int parts, const int64_t* __restrict__ sysoff, co
         }
         __syncthreads();
     }
-    if (threadIdx.x < 6) part[blockIdx.x * 6 + threadIdx.x] = s[threadIdx.x][0];
+    if (threadIdx.x < 6) part[blockIdx.x * 6 + threadIdx.x] = (double)s[threadIdx.x][0];
 }
 
 // one block per system: its cube (an empty system gets the unit cube at the origin)
@@ -633,7 +635,7 @@ int build_tree(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const vec4_t<
     cuda_check(cudaMemsetAsync(counts, 0, 64 * 4, s), "memset counts");
 
     // cubes and keys (the radix histogram buffer holds the bounding-box partials first)
-    const int parts = std::max(1, std::min(1024 / nsys, (int)((nn / nsys + 4095) / 4096)));
+    const int parts = std::max(1, std::min(1024 / nsys, (int)((nn / nsys + 1023) / 1024)));
     ensure(c, tb.hist, std::max<int64_t>((int64_t)nsort * 256 * 4 + 64, (int64_t)nsys * parts * 6 * 8));
     double* part = reinterpret_cast<double*>(tb.hist.ptr);
     const int64_t* dsysoff = tb.sysoff.as<int64_t>();
@@ -689,7 +691,7 @@ int build_tree(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const vec4_t<
     leaf_level();
     if (first_pass > 0 && hp.L_cap > S && !hp.nonfinite) {
         sort_passes(0);
-        cuda_check(cudaMemsetAsync(&tp->deepest_shared, 0, sizeof(int), s), "reset shared level");
+        cuda_check(cudaMemsetAsync(&tp->deepest_shared, 0xff, sizeof(int), s), "reset shared level");  // -1, as k_bbox_final sets it
         leaf_level();
     }
     ctx_sort_levels(c) = std::min(bits, hp.L_cap + 1);

@@ -71,6 +71,17 @@ def test_repeated_trees_in_one_context():
             assert (pre[1:] >= pre[:-1]).all()
         _boxes_match(ctx, tr, st, L)
     ctx.close()
+    # fewer elements than leaf_max + 1, first in a tiny region (cap 0), then spread over the
+    # unit cube (cap 4): the fallback recomputes the leaf level from scratch, which stays 0
+    xt, _ = workloads.cube(10, 5)
+    ctx = LHV(p=4, leaf_max=64, core_a=a, eps=1e-6)
+    for xs in (xt * np.float32(0.01), xt):
+        ctx.build_tree(dev(xs, "fp32"))
+        tr = T.build_tree(xs, leaf_max=64, a=a, eps=1e-6)
+        st = ctx.stats()
+        assert st["leaf_level"] == tr.L == 0
+        _boxes_match(ctx, tr, st, 0)
+    ctx.close()
 
 
 @pytest.mark.parametrize("n,leaf", [(1, 64), (2, 1), (64, 64), (65, 64), (4096, 64), (5000, 7)])
