@@ -24,29 +24,40 @@ __device__ inline void key_coords(uint64_t key, int level, int& x, int& y, int& 
     }
 }
 
+// Offsets of the levels in the global box order, for the one launch over levels 2 .. L.
+struct TableLevels {
+    int L;
+    int off[MAX_LEVELS + 2];
+};
+
 // table[t][slot] = GLOBAL index of the source box at offset `slot`, or -1 (the
-// table is cleared to -1 before).  One thread per (target box, colleague q of its
-// parent): the children of that colleague that are not colleagues of the target.
-__global__ void k_m2l_table(int nb, int level, int off_l, const uint64_t* __restrict__ bkey,
-                            const int* __restrict__ bparent, const int* __restrict__ pcol,
-                            const int* __restrict__ pcbeg, const int* __restrict__ pcend,
+// table is cleared to -1 before).  One thread per (target box of any level 2 .. L,
+// colleague q of its parent): the children of that colleague that are not
+// colleagues of the target.
+__global__ void k_m2l_table(int t0, int nt, TableLevels lv, const uint64_t* __restrict__ bkey,
+                            const int* __restrict__ bparent, const int* __restrict__ bcol,
+                            const int* __restrict__ bcbeg, const int* __restrict__ bcend,
                             const int* __restrict__ slot_of, int* __restrict__ table,
                             unsigned long long* __restrict__ pairs) {
     unsigned long long cnt = 0;
-    for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < (int64_t)nb * 27;
+    for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < (int64_t)nt * 27;
          it += (int64_t)gridDim.x * blockDim.x) {
-        const int b = (int)(it / 27), q = (int)(it - (int64_t)b * 27);
-        const int pc = pcol[(int64_t)bparent[b] * 27 + q];
+        const int gb = t0 + (int)(it / 27), q = (int)(it % 27);
+        int level = 2;
+        while (level < lv.L && gb >= lv.off[level + 1]) ++level;
+        const int o = lv.off[level], po = lv.off[level - 1];
+        // parent indices are relative to level - 1, child ranges relative to level
+        const int pc = bcol[((int64_t)po + bparent[gb]) * 27 + q];
         if (pc < 0) continue;
         int tx, ty, tz;
-        key_coords(bkey[b], level, tx, ty, tz);
-        int* row = table + (int64_t)b * NUM_OFFSETS;
-        for (int s = pcbeg[pc]; s < pcend[pc]; ++s) {
+        key_coords(bkey[gb], level, tx, ty, tz);
+        int* row = table + (int64_t)(gb - t0) * NUM_OFFSETS;
+        for (int s = bcbeg[po + pc]; s < bcend[po + pc]; ++s) {
             int sx, sy, sz;
-            key_coords(bkey[s], level, sx, sy, sz);
+            key_coords(bkey[o + s], level, sx, sy, sz);
             const int dx = sx - tx, dy = sy - ty, dz = sz - tz;
             if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1) continue;
-            row[slot_of[(dx + 3) * 49 + (dy + 3) * 7 + (dz + 3)]] = off_l + s;
+            row[slot_of[(dx + 3) * 49 + (dy + 3) * 7 + (dz + 3)]] = o + s;
             ++cnt;
         }
     }
@@ -64,14 +75,14 @@ void m2l_prepare(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& 
     const int t0 = lv.off[2];
     cuda_check(cudaMemsetAsync(table, 0xff, sizeof(int) * (size_t)(lv.off[L + 1] - t0) * NUM_OFFSETS, s),
                "m2l table clear");
-    for (int l = 2; l <= L; ++l) {
-        const int nb = lv.nbox[l], o = lv.off[l], po = lv.off[l - 1];
-        k_m2l_table<<<grid_for((int64_t)nb * 27, 128), 128, 0, s>>>(
-            nb, l, o, tb.bkey.as<uint64_t>() + o, tb.bparent.as<int>() + o, tb.bcol.as<int>() + (int64_t)po * 27,
-            tb.bcbeg.as<int>() + po, tb.bcend.as<int>() + po, ops.slot_of.as<int>(),
-            table + (int64_t)(o - t0) * NUM_OFFSETS, pair_counter);
-        count_launch(c);
-    }
+    TableLevels tl{};
+    tl.L = L;
+    for (int l = 0; l <= L + 1 && l <= MAX_LEVELS + 1; ++l) tl.off[l] = lv.off[l];
+    const int nt = lv.off[L + 1] - t0;  // target boxes of levels 2 .. L
+    k_m2l_table<<<grid_for((int64_t)nt * 27, 128), 128, 0, s>>>(
+        t0, nt, tl, tb.bkey.as<uint64_t>(), tb.bparent.as<int>(), tb.bcol.as<int>(), tb.bcbeg.as<int>(),
+        tb.bcend.as<int>(), ops.slot_of.as<int>(), table, pair_counter);
+    count_launch(c);
     check_launch("m2l table");
     const int64_t ntarget = lv.off[L + 1] - t0;
     M2LItems it{};
