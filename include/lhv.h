@@ -288,7 +288,11 @@ int lhv_export(lhv_ctx* ctx, int what, int level, void* dst, int64_t capacity_by
  * scratch state that must start at zero (the non-finite flag) is cleared by the
  * call's first kernel.  Returns LHV_ETOOBIG for n > LHV_NOALLOC_MAX_N,
  * LHV_EINVAL for n < 0, null or misaligned pointers, LHV_ENONFINITE for NaN/Inf,
- * LHV_ECUDA if a CUDA call failed, LHV_OK for n = 0 (nothing done).
+ * LHV_ECUDA if a CUDA call failed, LHV_OK for n = 0 (nothing done).  A CUDA
+ * error already pending on the calling thread when the call starts (from the
+ * caller's earlier work) makes it return LHV_ECUDA before launching anything,
+ * with that error left in place for the caller to read; any CUDA error after
+ * that point is this call's own.
  * Calls that overlap in time on one device (from several host threads, or on
  * several streams without ordering between them) share the one scratch array
  * and race: the caller serialises them. */
@@ -370,6 +374,30 @@ int lhv_selector_features(lhv_ctx* ctx, int64_t n, const float* x4, const float*
  * for other sizes, LHV_ETIMEOUT if the tensor-core work never signalled
  * completion (the kernel then stops by itself). */
 int lhv_tc_selftest(const float* X, const float* B, float* D, int N, int K);
+
+/* ---- throughput probes (the roofline denominators; not in the paper) ------
+ * Measures, at the GPU's current clocks (nothing is set or locked), the rate of
+ * one pipe with a register- or shared-memory-resident loop and no global traffic:
+ *   LHV_PEAK_FFMA      FP32 fused multiply-add, scalar fmaf (flop/s, 2 per lane-op)
+ *   LHV_PEAK_FFMA2     FP32 fused multiply-add, packed FP32x2 (flop/s, 4 per lane-op;
+ *                      the form of the near-field pair loop)
+ *   LHV_PEAK_MUFU      SFU reciprocal square root rsqrt.approx (operations/s)
+ *   LHV_PEAK_TF32_MMA  tcgen05.mma kind::tf32, 128 x 256 x 8 (flop/s, dense)
+ *   LHV_PEAK_BF16_MMA  tcgen05.mma kind::f16 with BF16 operands, 128 x 256 x 16 (flop/s)
+ * The FP32 and SFU probes run every SM at full occupancy, `iters` loop trips of 128
+ * operations per thread; the tensor probes 2 CTAs per SM, `iters` MMAs each.  One
+ * warm-up launch, then `reps` timed launches (CUDA events on cuda_stream, a
+ * cudaStream_t, NULL = legacy default stream); *rate_out receives the rate of the
+ * median launch and *ms_out (may be NULL) its duration.  Synchronous; allocates
+ * and frees a few bytes of device memory.  LHV_EINVAL for an unknown probe or
+ * iters, reps < 1; LHV_ECUDA if a CUDA error is pending on entry or a launch
+ * fails; LHV_ETIMEOUT if the tensor-core completion wait gave up (bounded). */
+#define LHV_PEAK_FFMA     1
+#define LHV_PEAK_FFMA2    2
+#define LHV_PEAK_MUFU     3
+#define LHV_PEAK_TF32_MMA 4
+#define LHV_PEAK_BF16_MMA 5
+int lhv_peak_probe(int what, int iters, int reps, void* cuda_stream, double* rate_out, double* ms_out);
 
 #ifdef __cplusplus
 }

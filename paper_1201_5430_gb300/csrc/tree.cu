@@ -845,6 +845,10 @@ extern "C" int lhv_morton_sort_noalloc(int64_t n, const float* x4, const float* 
     if ((reinterpret_cast<uintptr_t>(x4) | reinterpret_cast<uintptr_t>(w4)) % 16 != 0 ||
         reinterpret_cast<uintptr_t>(keys) % 8 != 0 || reinterpret_cast<uintptr_t>(perm) % 4 != 0)
         return LHV_EINVAL;
+    // An error left pending by the caller's earlier work would be read back (and cleared)
+    // by the launch check below and reported as this call's; refuse instead, leaving it
+    // in place for the caller.
+    if (cudaPeekAtLastError() != cudaSuccess) return LHV_ECUDA;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return LHV_ECUDA;
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return LHV_EUNSUPPORTED;
