@@ -67,9 +67,11 @@ SIGNATURES = {
     "lhv_evaluate_batched": (_int, [_vp, _int, ctypes.POINTER(_i64), _vp, _vp, _vp, _vp]),
     "lhv_step_batched": (_int, [_vp, _int, ctypes.POINTER(_i64), _vp, _vp, _dbl]),
     "lhv_morton_sort_noalloc": (_int, [_i64, _vp, _vp, _vp, _vp, _vp]),
+    "lhv_peak_probe": (_int, [_int, _int, _int, _vp, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl)]),
 }
 
 NOALLOC_MAX_N = 1 << 20  # LHV_NOALLOC_MAX_N
+PEAK = {"ffma": 1, "ffma2": 2, "mufu": 3, "tf32_mma": 4, "bf16_mma": 5}  # LHV_PEAK_*
 MLP_IN, MLP_OUT, MLP_NP, MLP_NW, MLP_NB = 12, 21, 17, 10304, 213  # LHV_MLP_*
 
 _lib = None

@@ -506,6 +506,110 @@ void run_tc_gemm(Ctx* c, Grouped& gp, GemmArgs<float> a, const float* tiles, con
     check_launch("tc gemm");
 }
 
+// ---- tensor-pipe throughput probe (lhv_peak_probe) --------------------------------
+// One CTA per (SM, half of TMEM): thread 0 issues `iters` MMAs of 128 x 256 x K8 (TF32)
+// or 128 x 256 x K16 (BF16) back to back from fixed shared-memory operands into its
+// 256 TMEM columns, committing every 32 MMAs and keeping at most two batches in
+// flight (bounded waits; a timeout sets *err).  No global traffic: the tensor pipe
+// alone bounds it.
+namespace {
+
+constexpr int PEAK_BATCH = 32;
+__global__ void __launch_bounds__(128, 2) k_tc_peak(int iters, int bf16, int* err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* As = smem;                     // 128 rows x 32 B (two k-steps' core matrices)
+    unsigned char* Bs = smem + TC_M * TC_KC * 4;  // 256 rows x 32 B
+    __shared__ uint64_t bar[2];
+    __shared__ uint32_t tmem_base;
+    const int t = threadIdx.x, warp = t >> 5;
+    // pseudo-random finite operands (exact in TF32 and BF16)
+    for (int e = t; e < (TC_M + TC_NMAX) * TC_KC; e += blockDim.x) {
+        const uint32_t h = (uint32_t)e * 2654435761u;
+        const float v = (float)((int)(h >> 24) - 128) * (1.0f / 128.0f);
+        if (bf16) {
+            const uint32_t b = __float_as_uint(v) >> 16;
+            reinterpret_cast<uint16_t*>(smem)[2 * e] = (uint16_t)b;
+            reinterpret_cast<uint16_t*>(smem)[2 * e + 1] = (uint16_t)b;
+        } else {
+            reinterpret_cast<float*>(smem)[e] = v;
+        }
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (t == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    if (t == 0) {
+        // kind::f16 with BF16 A/B: formats 1; kind::tf32: formats 2 (make_idesc)
+        const uint32_t idesc = bf16 ? ((1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_NMAX >> 3) << 17) |
+                                       ((uint32_t)(TC_M >> 4) << 24))
+                                    : make_idesc(TC_M, TC_NMAX);
+        const uint32_t lbo = 128, sbo = (TC_KC / 4) * 128;
+        const uint64_t a0 = make_desc(smem_u32(As), lbo, sbo), b0 = make_desc(smem_u32(Bs), lbo, sbo);
+        uint32_t par[2] = {0u, 0u};
+        int pend[2] = {0, 0};
+        bool ok = true;
+        const int nb = (iters + PEAK_BATCH - 1) / PEAK_BATCH;
+        for (int bi = 0; bi < nb && ok; ++bi) {
+            const int b = bi & 1;
+            if (pend[b]) {  // the batch two back used this barrier: wait for it
+                ok = mbar_wait(&bar[b], par[b]);
+                par[b] ^= 1u;
+                pend[b] = 0;
+            }
+            tc_fence_after();
+            const int cnt = min(PEAK_BATCH, iters - bi * PEAK_BATCH);
+            for (int k = 0; k < cnt; ++k) {
+                if (bf16)
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+                        "l"(a0), "l"(b0), "r"(idesc), "r"(1));
+                else
+                    mma_tf32(tmem, a0, b0, idesc, 1);
+            }
+            mma_commit(&bar[b]);
+            pend[b] = 1;
+        }
+        for (int b = 0; b < 2; ++b)
+            if (pend[b] && ok) {
+                ok = mbar_wait(&bar[b], par[b]);
+                pend[b] = 0;
+            }
+        if (!ok) atomicExch(err, 1);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+}  // namespace
+
+// FLOPs of one k_tc_peak launch and the launch itself (grid = 2 CTAs per SM).
+double tc_peak_launch(int iters, int bf16, int* err, cudaStream_t s) {
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem = (size_t)(TC_M + TC_NMAX) * TC_KC * 4 + 1024;
+    cudaFuncSetAttribute(k_tc_peak, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_tc_peak<<<sms * 2, 128, smem, s>>>(iters, bf16, err);
+    const double k = bf16 ? 16.0 : 8.0;
+    return 2.0 * TC_M * TC_NMAX * k * (double)iters * sms * 2;
+}
+
 }  // namespace lhv
 
 // Test entry (declared in include/lhv.h): D (128 x N) = X (128 x K) B^T with

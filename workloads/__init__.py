@@ -23,7 +23,7 @@ import math
 import numpy as np
 
 __all__ = [
-    "cube", "ring", "ring_pair", "blob_systems", "WORKLOADS", "make", "to_f4",
+    "cube", "ring", "ring_pair", "blob_systems", "WORKLOADS", "make", "make_spec", "to_f4",
     "RING_CORE_A",
 ]
 
@@ -102,13 +102,14 @@ def blob_systems(nsys=64, seed=4, n_lo=1e4, n_hi=5e5, blobs=8, sigma=0.05):
 
 # Named workloads: generator + the run parameters that go with it.
 #   p: truncation number (n = 0 .. p-1), leaf_max: elements per leaf bound,
-#   a: Gaussian core of Eq. vem1, eps: target accuracy, dt: RK4 step.
+#   a: Gaussian core of Eq. vem1, eps: target accuracy, dt: RK4 step, n: elements.
 WORKLOADS = {
-    "cube_4096": dict(gen=lambda: cube(4096, 0), p=8, leaf_max=64, a=0.01, eps=1e-6, dt=1e-3),
-    "ring_262144": dict(gen=lambda: ring(262144, 1), p=12, leaf_max=64, a=RING_CORE_A, eps=1e-6, dt=1e-3),
-    "offset_rings_2097152": dict(gen=lambda: ring_pair(1 << 20, 2, "offset"), p=16, leaf_max=64,
+    "cube_4096": dict(gen=lambda: cube(4096, 0), n=4096, p=8, leaf_max=64, a=0.01, eps=1e-6, dt=1e-3),
+    "ring_262144": dict(gen=lambda: ring(262144, 1), n=262144, p=12, leaf_max=64, a=RING_CORE_A, eps=1e-6,
+                        dt=1e-3),
+    "offset_rings_2097152": dict(gen=lambda: ring_pair(1 << 20, 2, "offset"), n=1 << 21, p=16, leaf_max=64,
                                  a=RING_CORE_A, eps=1e-6, dt=1e-3),
-    "leapfrog_rings_4194304": dict(gen=lambda: ring_pair(1 << 21, 5, "leapfrog"), p=12, leaf_max=64,
+    "leapfrog_rings_4194304": dict(gen=lambda: ring_pair(1 << 21, 5, "leapfrog"), n=1 << 22, p=12, leaf_max=64,
                                    a=RING_CORE_A, eps=1e-6, dt=5e-4),
 }
 
@@ -117,6 +118,13 @@ def make(name):
     spec = dict(WORKLOADS[name])
     x, w = spec.pop("gen")()
     return x, w, spec
+
+
+def make_spec(name):
+    """The run parameters of a named workload without drawing its elements: (None, None, spec)."""
+    spec = dict(WORKLOADS[name])
+    spec.pop("gen")
+    return None, None, spec
 
 
 def to_f4(a3, dtype=np.float32):
