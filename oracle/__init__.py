@@ -20,6 +20,9 @@ Everything is written for a reader who checks it against the paper by eye:
 * ``fmm``         -- the plain FP64 Lamb-Helmholtz FMM ("O2"), dense complex
                      translations, one conversion after every translation (Sec. 4).
 * ``rk4``         -- classical RK4 time step of Eq. s1.1.
+* ``scalar``      -- the paper's reference case (Sec. 5.2): phi and grad phi of
+                     monopoles, direct ("O1s") and by the scalar harmonic FMM
+                     over the same octree ("O2s").
 
 Coefficient arrays are complex, full-m, unscaled (the paper's basis): an array
 ``c`` of shape (p, 2p-1) holds c_n^m at ``c[n, m + p - 1]`` for n < p, |m| <= n,
