@@ -1,21 +1,35 @@
-"""Throughput of the GB300 Lamb-Helmholtz vortex FMM on the single-ring workload.
+"""Throughput of the GB300 Lamb-Helmholtz vortex FMM at equal accuracy eps = 1e-6.
 
-One step = one classical RK4 step (four evaluations of v and s = (w . grad) v,
-each with its own octree) of a 262,144-element vortex ring (R = 1, radial and
-axial jitter sigma = 0.03, Gaussian core a = 2 pi / 1000, p = 12, <= 64 per
-leaf, dt = 1e-3).  Metric: element evaluations (v and s at one element) per
-second = 4 N / step time.  Prints one JSON line (rank 0).
+Headline workload: the leapfrogging coaxial ring pair, N = 4,194,304 (two rings of
+2^21 at z = 0 and 0.1, R = 1, radial and axial jitter sigma = 0.03, Gaussian core
+a = 2 pi / 1000, <= 64 per leaf, dt = 5e-4), the largest single-system workload.
+One step = one classical RK4 step (four evaluations of v and s = (w . grad) v, each
+with its own octree); consecutive steps of the trajectory from the initial state.
+Metric: element evaluations (v and s at one element) per second = 4 N / step time.
+
+Forms compared at equal accuracy, eps_2(v) <= 1e-6 against FP64 direct sums at
+1000 sampled elements (relative L2):
+  plain_fp32   -- every kernel on the CUDA cores in FP32, the smallest uniform p
+                  that reaches eps;
+  tf32x3       -- M2L products on the tcgen05 tensor cores in split TF32, the smallest
+                  uniform p with tensor-core shapes (a multiple of 4) that reaches eps;
+  learned      -- TF32x3 with p per level chosen by the selector network every step
+                  (its sampled direct-sum check every 10th step).
+`value` is the fastest form that reached eps.  Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload leapfrog|ring_262144|offset_rings|blobs64]
 
-Multi-GPU (torchrun): every rank advances its own replica of the ring (the
-path has no data exchange to shard); value = all ranks' evaluations / the
-slowest rank's time ("replicas", weak scaling).
+Multi-GPU (torchrun): every rank advances its own replica (a single system has no
+data exchange to shard); value = all ranks' evaluations / the slowest rank's time
+("replicas", weak scaling).  blobs64 shards its independent systems over ranks.
 """
 import argparse
 import hashlib
 import json
+import multiprocessing as mp
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -30,16 +44,21 @@ if ROOT not in sys.path:
 
 import workloads  # noqa: E402
 
-WORKLOAD = "ring_262144"
 METRIC = "vortex-element v+stretching evals/sec at ε=1e-6 vs plain FP32 GPU FMM; % roofline"
 UNIT = "evals/s"
+EPS = 1e-6
+SINGLE = {"leapfrog": "leapfrog_rings_4194304", "ring_262144": "ring_262144"}
 # algorithmic FP32 work of one near-field pair (singular kernel): d (3), r^2 (5), 1/r^3 (3),
 # g = f'/r (2), w_j x d (9), v += f (w_j x d) (6), sum f w_j (6), (w_i . d) and g (w_i . d) (6),
 # s += g (w_i . d)(w_j x d) (6) = 46 flops
 P2P_FLOPS_PER_PAIR = 46
-FP32_LANES_PER_SM = 128
+# the oracle sample of the CPU legs: the headline geometry at 2 x 2048 elements
+CPU_SAMPLE_PER_RING = 2048
 
 
+# ---------------------------------------------------------------------------------------
+# host-side helpers (tested on the CPU)
+# ---------------------------------------------------------------------------------------
 def _measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -48,10 +67,10 @@ def _measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def _traffic_record(kernel_file):
-    """dram bytes per launch from the committed ncu summary, if it was taken on
-    the current source of the kernel (null otherwise)."""
-    path = os.path.join(ROOT, "profiles", "p2p_ring262144_traffic.txt")
+def _traffic_record(name, kernel_file):
+    """dram bytes per launch from a committed ncu summary, if it was taken on the current
+    source of the kernel (null otherwise)."""
+    path = os.path.join(ROOT, "profiles", name)
     src = os.path.join(ROOT, "paper_1201_5430_gb300", "csrc", kernel_file)
     if not (os.path.exists(path) and os.path.exists(src)):
         return None
@@ -67,6 +86,24 @@ def _traffic_record(kernel_file):
         return float(rec["dram_bytes_per_launch"])
     except (KeyError, ValueError):
         return None
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            k = line.split(":")[0].strip().lower()
+            if k in ("model name", "cpu model", "hardware"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.processor() or platform.machine()
 
 
 class Clocks:
@@ -101,21 +138,23 @@ class Clocks:
                 self.proc.kill()
 
     def summary(self):
-        rows = []
-        if self.path and os.path.exists(self.path):
-            for line in open(self.path):
-                parts = [p.strip() for p in line.split(",")]
-                if len(parts) >= 9:
-                    rows.append(parts)
-            os.unlink(self.path)
-        if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+        return clock_summary(open(self.path).read().splitlines() if self.path and os.path.exists(self.path) else [])
+
+
+def clock_summary(lines):
+    rows = []
+    for line in lines:
+        parts = [p.strip() for p in line.split(",")]
+        if len(parts) >= 9:
+            rows.append(parts)
+    if not rows:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+    sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+    mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+            "reasons": reasons, "samples": len(rows)}
 
 
 def max_over_ranks(ms, dist, device="cuda"):
@@ -142,52 +181,367 @@ def throughput(evals_per_rank, world, max_ms):
     return evals_per_rank * world / (max_ms / 1e3)
 
 
-def cpu_baseline(x, w, spec, budget_s=12.0):
-    """The oracle's direct sum (O1) as it stands, at a bounded random sample of
-    target elements (all N sources each): evals/s = targets / CPU seconds."""
-    from oracle import direct
-    rng = np.random.default_rng(0)
-    order = rng.permutation(x.shape[0])
-    done, t0 = 0, time.perf_counter()
-    while time.perf_counter() - t0 < budget_s:
-        direct.direct_at(x, w, spec["a"], order[done:done + 16])
-        done += 16
-    dt = time.perf_counter() - t0
-    return {"value": done / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"O1 direct sum (FP64 numpy) at {done} random targets of the {x.shape[0]}-element ring, "
-                      f"all sources each, {dt:.1f} s"}
+def pick_at_eps(trials, eps):
+    """The smallest p whose error meets eps, from (p, err) trials; None if none does."""
+    ok = [p for p, e in trials if e is not None and e <= eps]
+    return min(ok) if ok else None
+
+
+def fastest_form(arms, eps):
+    """Name of the fastest arm (lowest ms_per_step) among those whose err_v <= eps."""
+    cands = [(a["ms_per_step"], k) for k, a in arms.items() if a and a.get("err_v") is not None
+             and a["err_v"] <= eps and a.get("ms_per_step")]
+    return min(cands)[1] if cands else None
+
+
+# ---------------------------------------------------------------------------------------
+# the oracle on the host cores (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------------------
+def _o2_job(args):
+    """One O2 evaluation (plain FP64 CPU FMM) of the sample with seed `seed`; returns
+    (elements, seconds)."""
+    seed, n_per_ring, p, leaf, a, kind = args
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    from oracle import fmm as ofmm
+    x, w = workloads.ring_pair(n_per_ring, seed, kind)
+    t0 = time.perf_counter()
+    ofmm.fmm(x, w, p, leaf_max=leaf, a=a, eps=EPS)
+    return x.shape[0], time.perf_counter() - t0
+
+
+class OraclePool:
+    """Process pool (spawn) running O2 on every host core: one independent sample per
+    process per round (replicas of the headline geometry at a bounded size)."""
+
+    def __init__(self, cores=None):
+        self.cores = cores or os.cpu_count() or 1
+        saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in saved:
+            os.environ[k] = "1"  # one BLAS thread per process: the pool is the parallelism
+        self.pool = mp.get_context("spawn").Pool(self.cores)
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+    def round(self, n_per_ring, p, leaf, a, kind, seed0):
+        t0 = time.perf_counter()
+        res = self.pool.map(_o2_job, [(seed0 + k, n_per_ring, p, leaf, a, kind) for k in range(self.cores)])
+        return sum(r[0] for r in res), time.perf_counter() - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_baseline(p, spec, rounds=2, pool=None):
+    """The oracle's FMM (O2) as it stands on all host cores: `rounds` rounds of one
+    sample per core; evals/s = elements evaluated / wall seconds."""
+    own = pool is None
+    pool = pool or OraclePool()
+    try:
+        pool.round(256, p, spec["leaf_max"], spec["a"], "leapfrog", 900)  # imports and warm-up
+        tot_n, tot_s = 0, 0.0
+        for r in range(rounds):
+            n, s = pool.round(CPU_SAMPLE_PER_RING, p, spec["leaf_max"], spec["a"], "leapfrog", 1000 + 100 * r)
+            tot_n += n
+            tot_s += s
+    finally:
+        if own:
+            pool.close()
+    return {"value": tot_n / tot_s, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+            "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+            "sample": f"O2 (plain FP64 numpy Lamb-Helmholtz FMM, p = {p}) on {rounds} rounds of {pool.cores} "
+                      f"independent leapfrogging ring pairs of 2 x {CPU_SAMPLE_PER_RING} elements (same geometry, "
+                      f"core a and leaf rule as the headline workload, seeds 1000+), one process per core, "
+                      f"{tot_s:.1f} s wall; per-element cost at this N is below that of the full 4,194,304 "
+                      f"(fewer near-field sources per target)"}
 
 
 def run_reference(args, rank, world):
+    """The oracle (O2) timed on the host cores: each step is one round of one sample per
+    core (measured wall time, nothing extrapolated)."""
     if rank != 0:
         return
-    x, w, spec = workloads.make(WORKLOAD)
-    steps = []
-    if args.warmup > 0:
-        cpu_baseline(x, w, spec, budget_s=0.5)
-    per_step_budget = 4.0
-    for _ in range(args.steps):
-        cb = cpu_baseline(x, w, spec, budget_s=per_step_budget)
-        steps.append(cb["value"])
-    val = float(statistics.mean(steps)) if steps else 0.0
-    cb["value"] = val
-    n = x.shape[0]
+    name = SINGLE.get(args.workload, SINGLE["leapfrog"])
+    _, _, spec = workloads.make_spec(name)
+    p = 16
+    pool = OraclePool()
+    try:
+        for k in range(args.warmup):
+            pool.round(CPU_SAMPLE_PER_RING, p, spec["leaf_max"], spec["a"], "leapfrog", 2000 + k)
+        tot_n, walls = 0, []
+        for k in range(args.steps):
+            n, s = pool.round(CPU_SAMPLE_PER_RING, p, spec["leaf_max"], spec["a"], "leapfrog", 3000 + 100 * k)
+            tot_n += n
+            walls.append(s)
+    finally:
+        pool.close()
+    val = tot_n / sum(walls) if walls else 0.0
+    cb = {"value": val, "unit": UNIT, "cores": pool.cores, "kind": "oracle", "cpu_model": cpu_model(),
+          "nproc": os.cpu_count(),
+          "sample": f"each step: {pool.cores} O2 evaluations (plain FP64 numpy FMM, p = {p}) of independent "
+                    f"leapfrogging ring pairs of 2 x {CPU_SAMPLE_PER_RING} elements, one per core"}
     out = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": 4 * n / val * 1e3 if val else None,
+           "warmup": args.warmup, "ms_per_step": statistics.mean(walls) * 1e3 if walls else None,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "impl": "reference",
-           "config": {"workload": WORKLOAD, "n": n, "p": spec["p"], "leaf_max": spec["leaf_max"],
-                      "core_a": spec["a"], "dt": spec["dt"]},
+           "config": {"workload": name, "n": spec["n"], "p": p, "leaf_max": spec["leaf_max"], "core_a": spec["a"],
+                      "dt": spec["dt"], "eps": EPS, "sample_elements_per_step": tot_n // max(args.steps, 1)},
            "cpu_baseline": cb,
            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
 
+# ---------------------------------------------------------------------------------------
+# GPU arms
+# ---------------------------------------------------------------------------------------
+def measure_peaks(torch, lib, stream):
+    """Rates of the pipes the kernels are bound by, measured now (lhv_peak_probe)."""
+    import ctypes
+    from paper_1201_5430_gb300 import _lib
+    out = {}
+    plan = {"ffma": (20000, 20), "ffma2": (20000, 20), "mufu": (2500, 10), "tf32_mma": (60000, 10),
+            "bf16_mma": (60000, 10)}
+    for name, (iters, reps) in plan.items():
+        rate, ms = ctypes.c_double(0), ctypes.c_double(0)
+        st = lib.lhv_peak_probe(_lib.PEAK[name], iters, reps, ctypes.c_void_p(stream.cuda_stream),
+                                ctypes.byref(rate), ctypes.byref(ms))
+        out[name] = {"rate": rate.value / 1e12 if st == 0 else None, "ms": ms.value, "status": st}
+    out["unit"] = "TFLOP/s (mufu: Tops/s)"
+    return out
+
+
+def run_single(args, torch, LHV, local, world, rank, dist):
+    from paper_1201_5430_gb300 import _lib, selector
+    name = SINGLE[args.workload]
+    x, w, spec = workloads.make(name)
+    n = x.shape[0]
+    x0 = torch.from_numpy(workloads.to_f4(x)).cuda()
+    w0 = torch.from_numpy(workloads.to_f4(w)).cuda()
+    x4, w4 = x0.clone(), w0.clone()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    def ctx(p, prec):
+        return LHV(p=p, leaf_max=spec["leaf_max"], core_a=spec["a"], eps=spec["eps"], precision=prec)
+
+    if args.profile:  # ncu target: one warm-up evaluation and one evaluation, nothing else
+        c = ctx(16, "tf32x3")
+        for _ in range(2):
+            c.evaluate_velocity_stretching(x4, w4)
+        torch.cuda.synchronize()
+        return
+
+    # reference values at 1000 sampled elements: FP64 direct sums on the GPU
+    idx = torch.from_numpy(np.random.default_rng(0).choice(n, 1000, replace=False).astype(np.int32)).cuda()
+    il = idx.long()
+    ref = LHV(p=4, leaf_max=spec["leaf_max"], core_a=spec["a"])
+    v0, s0 = ref.direct_sampled(x0, w0, idx)
+    ref.close()
+
+    def errs(v, s):
+        ev = float(torch.linalg.norm(v[il].double()[:, :3] - v0[:, :3]) / torch.linalg.norm(v0[:, :3]))
+        es = float(torch.linalg.norm(s[il].double()[:, :3] - s0[:, :3]) / torch.linalg.norm(s0[:, :3]))
+        return ev, es
+
+    peaks, peak_kind = _measured_peaks()
+    with Clocks(local) as pclk:
+        probes = measure_peaks(torch, _lib.load(), stream)
+    probes["clocks"] = pclk.summary()
+
+    # launch shape of the near field (the same for every form): tuned once, outside the timed regions
+    tuner = ctx(16, "tf32x3")
+    shape = tuner.autotune(x0, w0)
+    tuner.close()
+
+    def configured(p, prec):
+        c = ctx(p, prec)
+        c.set_launch_shape(shape["p2p_targets_per_thread"], 0, 1 if prec == "tf32x3" else 0,
+                           p2p_sources_per_stage=shape["p2p_sources_per_stage"])
+        return c
+
+    # the smallest p that reaches eps, per precision (tensor-core shapes: multiples of 4)
+    search = {}
+    for prec, cand in (("fp32", range(13, 21)), ("tf32x3", (12, 16, 20))):
+        trials = []
+        for p in cand:
+            c = configured(p, prec)
+            v, s = c.evaluate_velocity_stretching(x0, w0)
+            trials.append((p, *errs(v, s)))
+            c.close()
+            if trials[-1][1] <= EPS:
+                break
+        search[prec] = {"trials": [{"p": p, "err_v": ev, "err_s": es} for p, ev, es in trials],
+                        "p": pick_at_eps([(p, ev) for p, ev, _ in trials], EPS)}
+
+    def timed(c, steps, warmup, clocks=None):
+        """consecutive RK4 steps from the initial state, L2 flushed before each, CUDA events
+        on the context stream around each step"""
+        x4.copy_(x0)
+        w4.copy_(w0)
+        for _ in range(max(warmup, 3)):
+            c.step(x4, w4, spec["dt"])
+        x4.copy_(x0)
+        w4.copy_(w0)
+        torch.cuda.synchronize()
+        c.set_timing(True)
+        c.reset_stats()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(steps):
+            flush.zero_()
+            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ea.record(stream)
+            c.step(x4, w4, spec["dt"])
+            eb.record(stream)
+            eb.synchronize()
+            times.append(ea.elapsed_time(eb))
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        st = c.stats()
+        c.set_timing(False)
+        return times, st
+
+    def arm_record(times, st, p, ev, es):
+        return {"p": p, "err_v": ev, "err_s": es, "ms_per_step": float(np.mean(times)),
+                "stage_ms_per_step": {k: v / len(times) for k, v in st["stage_ms"].items() if v > 0}}
+
+    # screening: every form over a few steps; then the fastest one at eps over all the steps
+    screen_steps = min(args.steps, 5)
+    arms, makers = {}, {}
+    for prec, key in (("fp32", "plain_fp32"), ("tf32x3", "tf32x3")):
+        p = search[prec]["p"]
+        if p is None:
+            arms[key] = None
+            continue
+        ev, es = next((t["err_v"], t["err_s"]) for t in search[prec]["trials"] if t["p"] == p)
+        makers[key] = (lambda p=p, prec=prec: configured(p, prec), p, ev, es)
+    W, b, _ = selector.load()
+
+    def learned():
+        c = configured(spec["p"], "tf32x3")
+        c.set_selector(W, b, eps=EPS, check_every=10, check_samples=1000)
+        return c
+
+    c = learned()
+    v, s = c.evaluate_velocity_stretching(x0, w0)
+    lev, les = errs(v, s)
+    lst = c.stats()
+    c.close()
+    makers["learned_tf32x3"] = (learned, None, lev, les)
+    for key, (mk, p, ev, es) in makers.items():
+        c = mk()
+        t, st = timed(c, screen_steps, 3)
+        arms[key] = arm_record(t, st, p if p else st["level_p"], ev, es)
+        if key == "learned_tf32x3":
+            arms[key]["initial_selection"] = {"level_p": lst["level_p"], "check_err_v": lst["selector"]["err_v"],
+                                              "check_err_s": lst["selector"]["err_s"],
+                                              "fallbacks": lst["selector"]["fallbacks"]}
+            arms[key]["checks_in_timed_steps"] = st["selector"]["checks"]
+            arms[key]["fallbacks_in_timed_steps"] = st["selector"]["fallbacks"]
+        c.close()
+    head = fastest_form(arms, EPS) or "tf32x3"
+    c = makers[head][0]()
+    with Clocks(local) as clk:
+        times, st = timed(c, args.steps, args.warmup)
+    total_ms = max_over_ranks(sum(times), dist)
+    value = throughput(4 * n * args.steps, world, total_ms)
+    arms[head]["ms_per_step_full_run"] = total_ms / args.steps
+
+    # roofline of the dominant kernel (near field): algorithmic FP32 flops per launch / its mean duration
+    p2p_ms = st["stage_ms"]["p2p"] / max(st["stage_launches"]["p2p"], 1)
+    pairs = st["p2p_pairs"]
+    achieved = P2P_FLOPS_PER_PAIR * pairs / (p2p_ms / 1e3) / 1e12
+    fma_peak = max(probes["ffma"]["rate"] or 0.0, probes["ffma2"]["rate"] or 0.0)
+    m2l_ms = st["stage_ms"].get("m2l_products", 0.0) / max(st["stage_launches"].get("m2l_products", 0), 1)
+    m2l_p = st["level_p"][-1] if st["level_p"] else spec["p"]
+    m2l_flops = 6.0 * m2l_p ** 4 * st["m2l_pairs"]
+    tf32_peak = probes["tf32_mma"]["rate"]
+    tc = head != "plain_fp32"
+
+    # end to end through the C ABI with host buffers (H2D, step, D2H inside the timed region),
+    # L2 flushed before each step as in the device-timed arm
+    hx = x0.cpu().pin_memory()
+    hw = w0.cpu().pin_memory()
+    hx0, hw0 = hx.clone(), hw.clone()
+    e2e_times = []
+    e2e_steps = min(args.steps, 5)
+    for i in range(e2e_steps + 1):
+        hx.copy_(hx0)
+        hw.copy_(hw0)
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c.step_host(hx, hw, spec["dt"])
+        if i > 0:  # the first is a warm-up of the host copies' buffers
+            e2e_times.append(time.perf_counter() - t0)
+    e2e_val = 4 * n * world / statistics.mean(e2e_times)
+    c.close()
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cb = None if args.no_cpu_baseline else cpu_baseline(arms[head]["p"] if isinstance(arms[head]["p"], int) else 16,
+                                                        spec)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if head == "plain_fp32" else "f32+tf32x3",
+        "data": "synthetic",
+        "config": {"workload": name, "n": n, "form": head, "p": arms[head]["p"], "leaf_max": spec["leaf_max"],
+                   "core_a": spec["a"], "eps": EPS, "dt": spec["dt"], "rk4_evals_per_step": 4,
+                   "steps": "consecutive RK4 steps of the trajectory from the initial state",
+                   "accuracy": "eps_2(v) vs FP64 direct sums at 1000 sampled elements (err_s reported)",
+                   "l2": "flushed before every step (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "1 GPU",
+                   "leaf_level": st["leaf_level"], "boxes": st["nbox"]},
+        "err_v": arms[head]["err_v"], "err_s": arms[head]["err_s"],
+        "forms_at_eps_1e-6": {"arms": arms, "p_search": search, "screen_steps": screen_steps,
+                              "speedup_vs_plain_fp32": {k: arms["plain_fp32"]["ms_per_step"] / a["ms_per_step"]
+                                                        for k, a in arms.items() if a and arms.get("plain_fp32")}},
+        "roofline": {"kernel": "k_p2p_x2 (near field, packed FP32x2)", "bound": "alu", "achieved": achieved,
+                     "peak": fma_peak, "unit": "TFLOP/s", "frac": achieved / fma_peak if fma_peak else None,
+                     "traffic": _traffic_record("p2p_leapfrog_traffic.txt", "p2p.cu"),
+                     "peak_kind": "measured in this run: FP32 FMA probe (lhv_peak_probe, max of scalar and "
+                                  "packed FP32x2), median of 20 launches at the running clocks",
+                     "pairs_per_launch": pairs, "flops_per_pair": P2P_FLOPS_PER_PAIR, "mean_launch_ms": p2p_ms},
+        "roofline_m2l": {"kernel": "M2L products, " + ("tcgen05 TF32 x3 (k_tc_gemm)" if tc else "CUDA cores"),
+                         "bound": "tensor" if tc else "alu",
+                         "achieved": m2l_flops / (m2l_ms / 1e3) / 1e12 if m2l_ms else None,
+                         "peak": tf32_peak if tc else fma_peak, "unit": "TFLOP/s",
+                         "frac": (m2l_flops / (m2l_ms / 1e3) / 1e12) / (tf32_peak if tc else fma_peak)
+                         if m2l_ms and (tf32_peak if tc else fma_peak) else None,
+                         "peak_kind": "measured in this run: tcgen05.mma kind::tf32 probe" if tc
+                         else "measured FP32 FMA probe", "box_pairs": st["m2l_pairs"],
+                         "flops_per_pair": 6 * m2l_p ** 4, "useful_only": "split products issue 3x these flops",
+                         "mean_launch_ms": m2l_ms},
+        "peaks_measured": probes,
+        "peaks_driver": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained")},
+        "peaks_driver_kind": peak_kind,
+        "stage_ms_per_step": {k: v / args.steps for k, v in st["stage_ms"].items() if v > 0},
+        "launch_shape": shape,
+        "cpu_baseline": cb,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(2 * n * 16),
+                "d2h_bytes_per_step": int(2 * n * 16), "steps": e2e_steps},
+        "gpu_launches": st["kernel_launches"],
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 def run_blobs64(args, torch, LHV, local, world, rank, dist):
     """Batched form: 64 independent Gaussian-blob systems (sizes log-uniform in
-    [1e4, 5e5], about 8e6 elements) advanced by one RK4 step per timed step,
+    [1e4, 5e5], about 1e7 elements) advanced by one RK4 step per timed step,
     (a) batched: one lhv_step_batched call for all systems, (b) sequential: the
-    plain FP32 single-system path called once per system."""
+    single-system path in the same precision called once per system."""
     systems = workloads.blob_systems(64, 4)
     mine = shard(64, rank, world)  # independent systems: a block of them per rank, no collective
     systems = [systems[k] for k in mine]
@@ -222,19 +576,19 @@ def run_blobs64(args, torch, LHV, local, world, rank, dist):
     cb = LHV(p=spec["p"], leaf_max=spec["leaf_max"], core_a=spec["a"], eps=spec["eps"], precision=args.precision)
     tuned = cb.autotune(x0, w0, offsets=off)  # launch shapes for the batch, outside the timed region
     t_b = timed(lambda: cb.step_batched(off, x4, w4, spec["dt"]), args.steps, args.warmup)
-    cs = LHV(p=spec["p"], leaf_max=spec["leaf_max"], core_a=spec["a"], eps=spec["eps"], precision="fp32")
+    cs = LHV(p=spec["p"], leaf_max=spec["leaf_max"], core_a=spec["a"], eps=spec["eps"], precision=args.precision)
+    cs.set_launch_shape(tuned["p2p_targets_per_thread"], tuned["m2l_pairs_per_chunk"], tuned["m2l_tensor_cores"],
+                        p2p_sources_per_stage=tuned["p2p_sources_per_stage"])
 
     def seq():
         for k in range(len(systems)):
             cs.step(x4[off[k]:off[k + 1]], w4[off[k]:off[k + 1]], spec["dt"])
 
     t_s = timed(seq, args.steps, args.warmup)
-    # whole job: every rank's elements over the slowest rank's time
     tb_max, ts_max = max_over_ranks(t_b, dist), max_over_ranks(t_s, dist)
     tot_n = n
     if dist:
-        import torch as _t
-        tn = _t.tensor([float(n)], dtype=_t.float64, device="cuda")
+        tn = torch.tensor([float(n)], dtype=torch.float64, device="cuda")
         dist.all_reduce(tn)
         tot_n = int(tn.item())
     val_b = 4 * tot_n * args.steps / (tb_max / 1e3)
@@ -243,14 +597,13 @@ def run_blobs64(args, torch, LHV, local, world, rank, dist):
         print(json.dumps({"metric": METRIC + " (batched form)", "value": val_b, "unit": UNIT, "n_gpus": world,
                           "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": tb_max / args.steps,
                           "higher_is_better": True, "scaling": "strong" if world > 1 else "weak",
-                          "dtype": "f32" if args.precision == "fp32"
-                          else "f32+tf32x3", "data": "synthetic",
+                          "dtype": "f32" if args.precision == "fp32" else "f32+tf32x3", "data": "synthetic",
                           "scaling_note": "64 systems split across the ranks (strong scaling)" if world > 1 else None,
                           "config": {"workload": "blobs64", "systems": 64, "n": tot_n, **spec,
                                      "precision": args.precision, "leaf_level": cb.stats()["leaf_level"]},
                           "launch_shape": tuned,
-                          "sequential_plain_fp32": {"value": val_s, "ms_per_step": ts_max / args.steps},
-                          "speedup_vs_sequential_plain_fp32": val_b / val_s}), flush=True)
+                          "sequential_same_precision": {"value": val_s, "ms_per_step": ts_max / args.steps},
+                          "speedup_vs_sequential": val_b / val_s}), flush=True)
 
 
 def run_offset_rings(args, torch, LHV, local, world, rank, dist):
@@ -304,143 +657,6 @@ def run_offset_rings(args, torch, LHV, local, world, rank, dist):
               flush=True)
 
 
-def run_leapfrog(args, torch, LHV, local, world, rank, dist, eps=1e-6):
-    """Learned form on the leapfrogging ring pair (2 x 2^21 elements, dt = 5e-4): RK4 steps
-    with the network choosing p per level once per step (TF32x3, target eps_2(v) <= 1e-6, the
-    first step checked against FP64 direct sums), against the fixed p = 12 of the workload
-    (its fallback) and a fixed p = 16, each timed over the same steps from the same state."""
-    from paper_1201_5430_gb300 import selector
-    x, w, spec = workloads.make("leapfrog_rings_4194304")
-    n = x.shape[0]
-    x0 = torch.from_numpy(workloads.to_f4(x)).cuda()
-    w0 = torch.from_numpy(workloads.to_f4(w)).cuda()
-    x4, w4 = x0.clone(), w0.clone()
-    stream = torch.cuda.current_stream()
-    idx = torch.from_numpy(np.random.default_rng(0).choice(n, 1000, replace=False).astype(np.int32)).cuda()
-    ref = LHV(p=4, leaf_max=spec["leaf_max"], core_a=spec["a"])
-    v0, _ = ref.direct_sampled(x0, w0, idx)
-    ref.close()
-
-    def err(c):
-        v, _ = c.evaluate_velocity_stretching(x0, w0)
-        return float(torch.linalg.norm(v[idx.long()].double()[:, :3] - v0[:, :3]) / torch.linalg.norm(v0[:, :3]))
-
-    def timed(c):
-        for _ in range(3):
-            x4.copy_(x0)
-            w4.copy_(w0)
-            c.step(x4, w4, spec["dt"])
-        torch.cuda.synchronize()
-        x4.copy_(x0)
-        w4.copy_(w0)
-        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ea.record(stream)
-        for _ in range(args.steps):
-            c.step(x4, w4, spec["dt"])  # consecutive steps of the trajectory
-        eb.record(stream)
-        eb.synchronize()
-        return max_over_ranks(ea.elapsed_time(eb), dist)
-
-    out = {}
-    for name, p, prec in (("fixed_p12", 12, "tf32x3"), ("fixed_p16", 16, "tf32x3")):
-        c = LHV(p=p, leaf_max=spec["leaf_max"], core_a=spec["a"], eps=spec["eps"], precision=prec)
-        c.autotune(x0, w0)
-        e = err(c)
-        ms = timed(c)
-        out[name] = {"p": p, "err_v": e, "ms_per_step": ms / args.steps}
-        c.close()
-    W, b, _ = selector.load()
-    c = LHV(p=12, leaf_max=spec["leaf_max"], core_a=spec["a"], eps=spec["eps"], precision="tf32x3")
-    c.set_selector(W, b, eps=eps, check_every=1, check_samples=1000)
-    v, _ = c.evaluate_velocity_stretching(x0, w0)
-    e = float(torch.linalg.norm(v[idx.long()].double()[:, :3] - v0[:, :3]) / torch.linalg.norm(v0[:, :3]))
-    st = c.stats()
-    c.autotune(x0, w0)
-    c.set_selector(W, b, eps=eps, check_every=0)  # checked once above, on the initial state
-    ms = timed(c)
-    st2 = c.stats()
-    out["learned"] = {"level_p": st["level_p"], "err_v": e, "ms_per_step": ms / args.steps,
-                      "initial_check": {"err_v": st["selector"]["err_v"], "fallbacks": st["selector"]["fallbacks"]},
-                      "level_p_last_step": st2["level_p"]}
-    c.close()
-    value = 4 * n * args.steps * world / (ms / 1e3)
-    if rank == 0:
-        print(json.dumps({"metric": METRIC + " (learned form)", "value": value, "unit": UNIT, "n_gpus": world,
-                          "steps": args.steps, "warmup": 3, "ms_per_step": ms / args.steps,
-                          "higher_is_better": True, "scaling": "weak", "dtype": "f32+tf32x3", "data": "synthetic",
-                          "config": {"workload": "leapfrog_rings_4194304", "n": n, "dt": spec["dt"],
-                                     "a": spec["a"], "eps_target": eps, "steps": "consecutive RK4 steps"},
-                          "arms": out,
-                          "speedup_vs_fixed_p12": out["fixed_p12"]["ms_per_step"] / out["learned"]["ms_per_step"],
-                          "speedup_vs_fixed_p16": out["fixed_p16"]["ms_per_step"] / out["learned"]["ms_per_step"]}),
-              flush=True)
-
-
-def forms_at_eps(torch, LHV, spec, x0, w0, x4, w4, timed_steps, args, eps=1e-6):
-    """Plain FP32 and TF32x3 at their smallest uniform p with eps_2(v) <= eps, and the
-    learned form (TF32x3, network choice per step), each timed over RK4 steps."""
-    from paper_1201_5430_gb300 import selector
-    n = x0.shape[0]
-    idx = torch.from_numpy(np.random.default_rng(0).choice(n, 1000, replace=False).astype(np.int32)).cuda()
-    ref = LHV(p=4, leaf_max=spec["leaf_max"], core_a=spec["a"])
-    v0, _ = ref.direct_sampled(x0, w0, idx)
-    ref.close()
-    il = idx.long()
-
-    def err(c):
-        v, _ = c.evaluate_velocity_stretching(x0, w0)
-        return float(torch.linalg.norm(v[il].double()[:, :3] - v0[:, :3]) / torch.linalg.norm(v0[:, :3]))
-
-    out = {"eps": eps, "criterion": "relative L2 of v vs FP64 direct sums, 1000 sampled elements"}
-    for prec in ("fp32", "tf32x3"):
-        # the smallest p that reaches eps; under TF32x3 also the next multiple of 4 (tensor cores)
-        cands = []
-        for p in range(spec["p"], 21):
-            c = LHV(p=p, leaf_max=spec["leaf_max"], core_a=spec["a"], eps=spec["eps"], precision=prec)
-            e = err(c)
-            c.close()
-            if e <= eps:
-                cands.append((p, e))
-                q = (p + 3) // 4 * 4
-                if prec == "tf32x3" and q != p and q <= 20:
-                    c = LHV(p=q, leaf_max=spec["leaf_max"], core_a=spec["a"], eps=spec["eps"], precision=prec)
-                    cands.append((q, err(c)))
-                    c.close()
-                break
-        best = None
-        for p, e in cands:
-            c = LHV(p=p, leaf_max=spec["leaf_max"], core_a=spec["a"], eps=spec["eps"], precision=prec)
-            c.autotune(x0, w0)
-            t, stf = timed_steps(c, args.steps, 1)
-            c.close()
-            r = {"p": p, "err_v": e, "ms_per_step": float(np.mean(t)),
-                 "stage_ms_per_step": {k: v / args.steps for k, v in stf["stage_ms"].items() if v > 0}}
-            if best is None or r["ms_per_step"] < best["ms_per_step"]:
-                best = r
-        if best:
-            out[prec] = best
-    W, b, _ = selector.load()
-    c = LHV(p=spec["p"], leaf_max=spec["leaf_max"], core_a=spec["a"], eps=spec["eps"], precision="tf32x3")
-    c.set_selector(W, b, eps=eps, check_every=1, check_samples=1000)
-    x4.copy_(x0)
-    w4.copy_(w0)
-    c.step(x4, w4, spec["dt"])
-    st = c.stats()
-    c.autotune(x0, w0)
-    c.set_selector(W, b, eps=eps, check_every=0)
-    t, st2 = timed_steps(c, args.steps, 1)
-    out["learned_tf32x3"] = {"level_p": st["level_p"], "err_v_checked": st["selector"]["err_v"],
-                             "fallbacks": st["selector"]["fallbacks"], "ms_per_step": float(np.mean(t)),
-                             "stage_ms_per_step": {k: v / args.steps for k, v in st2["stage_ms"].items() if v > 0}}
-    c.close()
-    if "fp32" in out:
-        base = out["fp32"]["ms_per_step"]
-        for k in ("tf32x3", "learned_tf32x3"):
-            if k in out:
-                out[k]["speedup_vs_plain_fp32"] = base / out[k]["ms_per_step"]
-    return out
-
-
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -448,11 +664,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "blobs64", "leapfrog", "offset_rings"],
-                    help="blobs64: the batched form, 64 independent blob systems (not the headline line)")
+    ap.add_argument("--workload", default="leapfrog", choices=list(SINGLE) + ["blobs64", "offset_rings"],
+                    help="leapfrog (headline), ring_262144 (single ring), offset_rings (mixed precision on "
+                         "configs' colliding rings), blobs64 (the batched form)")
     ap.add_argument("--precision", default="tf32x3", choices=["tf32x3", "fp32"],
-                    help="tf32x3: translations on the tensor cores (TF32 split products); fp32: plain CUDA-core FMM")
-    ap.add_argument("--no-forms", action="store_true", help="skip the equal-accuracy comparison of the forms")
+                    help="blobs64 only: tf32x3 (M2L on the tensor cores) or fp32")
     ap.add_argument("--profile", action="store_true",
                     help="ncu target: one warm-up evaluation and one evaluation of the workload, nothing else")
     args = ap.parse_args()
@@ -475,157 +691,10 @@ def main():
     from paper_1201_5430_gb300 import LHV
     if args.workload == "blobs64":
         run_blobs64(args, torch, LHV, local, world, rank, dist)
-        return
-    if args.workload == "leapfrog":
-        run_leapfrog(args, torch, LHV, local, world, rank, dist)
-        return
-    if args.workload == "offset_rings":
+    elif args.workload == "offset_rings":
         run_offset_rings(args, torch, LHV, local, world, rank, dist)
-        return
-    x, w, spec = workloads.make(WORKLOAD)
-    n = x.shape[0]
-    x0 = torch.from_numpy(workloads.to_f4(x)).cuda()
-    w0 = torch.from_numpy(workloads.to_f4(w)).cuda()
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > L2
-    stream = torch.cuda.current_stream()
-
-    def make_ctx(precision):
-        return LHV(p=spec["p"], leaf_max=spec["leaf_max"], core_a=spec["a"], eps=spec["eps"], precision=precision)
-
-    ctx = make_ctx(args.precision)
-    x4, w4 = x0.clone(), w0.clone()
-    if not args.profile:
-        ctx.autotune(x0, w0)  # launch shapes for this workload (outside every timed region)
-    if args.profile:
-        for _ in range(2):
-            ctx.evaluate_velocity_stretching(x4, w4)
-        torch.cuda.synchronize()
-        return
-
-    def timed_steps(c, steps, warmup, clocks=None):
-        for _ in range(max(warmup, 3)):
-            x4.copy_(x0)
-            w4.copy_(w0)
-            c.step(x4, w4, spec["dt"])
-        torch.cuda.synchronize()
-        c.set_timing(True)
-        c.reset_stats()
-        times = []
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        for _ in range(steps):
-            x4.copy_(x0)
-            w4.copy_(w0)
-            flush.zero_()
-            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            ea.record(stream)
-            c.step(x4, w4, spec["dt"])
-            eb.record(stream)
-            eb.synchronize()
-            times.append(ea.elapsed_time(eb))
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        st = c.stats()
-        c.set_timing(False)
-        return times, st
-
-    with Clocks(local) as clk:
-        times, st = timed_steps(ctx, args.steps, args.warmup)
-    total_ms = max_over_ranks(sum(times), dist)
-    evals = 4 * n * args.steps * world
-    value = throughput(4 * n * args.steps, world, total_ms)
-    plain = None
-    if args.precision != "fp32":
-        pctx = make_ctx("fp32")
-        pctx.autotune(x0, w0)
-        ptimes, pst = timed_steps(pctx, args.steps, args.warmup)
-        ptotal = max_over_ranks(sum(ptimes), dist)
-        plain = {"value": evals / (ptotal / 1e3), "ms_per_step": ptotal / args.steps,
-                 "stage_ms_per_step": {k: v / args.steps for k, v in pst["stage_ms"].items() if v > 0}}
-        pctx.close()
-
-    # the forms at equal accuracy: eps = 1e-6 on v (relative L2 against FP64 direct sums at
-    # 1000 sampled elements); fixed p = the smallest uniform p that reaches it
-    at_eps = None
-    if not args.no_forms:
-        at_eps = forms_at_eps(torch, LHV, spec, x0, w0, x4, w4, timed_steps, args)
-
-    # roofline of the dominant kernel (P2P): algorithmic FP32 flops per launch / its mean duration
-    peaks, peak_kind = _measured_peaks()
-    p2p_ms = st["stage_ms"]["p2p"] / max(st["stage_launches"]["p2p"], 1)
-    pairs = st["p2p_pairs"]
-    achieved = P2P_FLOPS_PER_PAIR * pairs / (p2p_ms / 1e3) / 1e12
-    sms = torch.cuda.get_device_properties(local).multi_processor_count
-    peak = sms * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    traffic = _traffic_record("p2p.cu")
-    # M2L products: useful flops 6 p^4 per box pair (the fused [[T, C12 T], [0, C22 T]] with its
-    # zero block skipped) over the mean duration of the products
-    m2l_ms = st["stage_ms"].get("m2l_products", 0.0) / max(st["stage_launches"].get("m2l_products", 0), 1)
-    m2l_flops = 6.0 * spec["p"] ** 4 * st["m2l_pairs"]
-    tf32_peak = peaks.get("bf16_tflops", 1862.0) * (1.1 / 2.25)
-
-    # end to end through the C ABI with host buffers (copies inside the timed region)
-    hx = x0.cpu().pin_memory()
-    hw = w0.cpu().pin_memory()
-    hx0, hw0 = hx.clone(), hw.clone()
-    e2e_times = []
-    for i in range(args.steps):
-        hx.copy_(hx0)
-        hw.copy_(hw0)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        ctx.step_host(hx, hw, spec["dt"])
-        e2e_times.append(time.perf_counter() - t0)
-    e2e_val = 4 * n * world / statistics.mean(e2e_times)
-
-    if rank != 0:
-        if dist:
-            dist.destroy_process_group()
-        return
-    cb = None
-    if not args.no_cpu_baseline:
-        cb = cpu_baseline(x, w, spec)
-    out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f32+tf32x3",
-        "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": n, "p": spec["p"], "leaf_max": spec["leaf_max"],
-                   "core_a": spec["a"], "eps": spec["eps"], "dt": spec["dt"], "rk4_evals_per_step": 4,
-                   "precision": args.precision,
-                   "l2": "flushed between steps (256 MB write)", "parallelism": "replicas" if world > 1 else "1 GPU",
-                   "leaf_level": st["leaf_level"], "boxes": st["nbox"]},
-        "roofline": {"kernel": "k_p2p_x2 (near field, packed FP32x2)", "bound": "alu", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-                     "peak_kind": f"FP32 FMA pipe: {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x "
-                                  f"{peaks.get('sm_max_mhz', 2070.0)} MHz ({peak_kind} max clock)",
-                     "pairs_per_launch": pairs, "flops_per_pair": P2P_FLOPS_PER_PAIR, "mean_launch_ms": p2p_ms},
-        "roofline_m2l": {"kernel": "grouped GEMM, M2L products" + (" (tcgen05 TF32 x3)" if args.precision == "tf32x3"
-                                                                      else " (FP32 CUDA cores)"),
-                         "bound": "tensor" if args.precision == "tf32x3" else "alu",
-                         "achieved": m2l_flops / (m2l_ms / 1e3) / 1e12 if m2l_ms else None,
-                         "peak": tf32_peak if args.precision == "tf32x3" else peak, "unit": "TFLOP/s",
-                         "frac": (m2l_flops / (m2l_ms / 1e3) / 1e12) / (tf32_peak if args.precision == "tf32x3" else peak)
-                         if m2l_ms else None,
-                         "peak_kind": "TF32 = measured BF16 burst x 1.1/2.25 (nominal ratio)" if args.precision == "tf32x3"
-                         else "FP32 FMA pipe", "box_pairs": st["m2l_pairs"], "flops_per_pair": 6 * spec["p"] ** 4,
-                         "useful_only": "split products issue 3x these flops", "mean_launch_ms": m2l_ms},
-        "stage_ms_per_step": {k: v / args.steps for k, v in st["stage_ms"].items() if v > 0},
-        "plain_fp32": plain,
-        "speedup_vs_plain_fp32": (value / plain["value"]) if plain else None,
-        "launch_shape": st["launch_shape"],
-        "forms_at_eps_1e-6": at_eps,
-        "cpu_baseline": cb,
-        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(2 * n * 16),
-                "d2h_bytes_per_step": int(2 * n * 16)},
-        "gpu_launches": st["kernel_launches"],
-        "clocks": clk.summary(),
-    }
-    print(json.dumps(out), flush=True)
-    if dist:
-        dist.destroy_process_group()
+    else:
+        run_single(args, torch, LHV, local, world, rank, dist)
 
 
 if __name__ == "__main__":

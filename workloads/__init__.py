@@ -8,7 +8,10 @@ parameters of each workload.
 Workloads (shapes follow the paper's test problems, Sec. 5):
 
 * ``cube``   -- N elements uniform in [0, 1]^3, w ~ N(0, 1) per component
-                (the error and timing tests of Sec. 5.1-5.2).
+                (the error and timing tests of Sec. 5.1-5.2, Table 1).
+* ``sphere`` -- N elements uniform on the unit sphere surface (normalised Gaussian
+                vectors), w ~ N(0, 1) per component (Table 2).
+* ``charges`` -- monopole strengths q ~ N(0, 1) for the scalar reference case.
 * ``ring``   -- a thin vortex ring of radius R: theta_i = 2 pi i / N, radial and
                 axial jitter ~ N(0, sigma^2); w_i = Gamma (2 pi R / N) / (4 pi) t_i
                 with t_i the unit tangent (the element field of Eq. 1 carries no
@@ -23,7 +26,7 @@ import math
 import numpy as np
 
 __all__ = [
-    "cube", "ring", "ring_pair", "blob_systems", "WORKLOADS", "make", "make_spec", "to_f4",
+    "cube", "sphere", "charges", "ring", "ring_pair", "blob_systems", "WORKLOADS", "make", "make_spec", "to_f4",
     "RING_CORE_A",
 ]
 
@@ -40,6 +43,18 @@ def cube(n, seed=0):
     x = rng.random((n, 3))
     w = rng.standard_normal((n, 3))
     return _f32(x), _f32(w)
+
+
+def sphere(n, seed=0):
+    rng = np.random.default_rng(seed)
+    g = rng.standard_normal((n, 3))
+    x = g / np.linalg.norm(g, axis=1)[:, None]
+    w = rng.standard_normal((n, 3))
+    return _f32(x), _f32(w)
+
+
+def charges(n, seed=0):
+    return np.ascontiguousarray(np.random.default_rng(seed).standard_normal(n).astype(np.float32))
 
 
 def _rot_x(deg):
