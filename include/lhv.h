@@ -175,6 +175,26 @@ int lhv_evaluate_velocity_stretching_f64(lhv_ctx* ctx, int64_t n, const double* 
                                          double* v4, double* s4);
 int lhv_step_f64(lhv_ctx* ctx, int64_t n, double* x4, double* w4, double dt);
 
+/* The paper's reference case (Sec. 5.2, Tables 1-2): the scalar harmonic FMM for the
+ * potential and its gradient of n monopoles of strength q_j,
+ *   phi(x_i) = sum_{j != i} q_j / |x_i - x_j|,  grad phi(x_i) = -sum_{j != i} q_j (x_i - x_j) / |x_i - x_j|^3
+ * (no 1/(4 pi), like Eq. 1; distinct elements at one point contribute nothing), on the same
+ * octree, lists and kernels as the vortex evaluation with one potential: P2M by the Green's
+ * expansion (Eq. rsbf5), M2M / M2L / L2L by the translation block of each fused operator
+ * (no conversion: there is no chi), L2P of phi and grad phi, and the direct sum over the
+ * colleague leaves.  It is what the ratio T(v, s) / T(phi, grad phi) of Sec. 5.2 is
+ * measured against.  x4: device [n][4] positions (lane 3 ignored); q: device [n] charges
+ * (float / double, not checked for NaN/Inf); pg4: device [n][4] output in the caller's
+ * order, lanes (d phi/dx, d phi/dy, d phi/dz, phi).  Uses lhv_config.p at every level
+ * (per-level p and the selector do not apply), leaf_max, max_level, terms and, for
+ * LHV_TF32X3, the tensor-core M2L products where p^2 is a multiple of 16.  The context
+ * must have core_a = 0 (the singular Laplace kernel of the reference case):
+ * LHV_EUNSUPPORTED otherwise.  LHV_EINVAL for null or misaligned pointers, n < 0, or a
+ * precision that does not match the entry point (FP32 / TF32X3 contexts for the float
+ * form, FP64 for _f64). */
+int lhv_evaluate_potential_gradient(lhv_ctx* ctx, int64_t n, const float* x4, const float* q, float* pg4);
+int lhv_evaluate_potential_gradient_f64(lhv_ctx* ctx, int64_t n, const double* x4, const double* q, double* pg4);
+
 /* The exact sum the FMM approximates, at m sampled targets: v and s of Eq.
  * s1.1 with the kernel of Eqs. 2/vem1 (the context's core_a) summed over every
  * element j != idx[k] (excluded by index), in FP64 arithmetic.  This is the
@@ -240,7 +260,7 @@ int lhv_reset_stats(lhv_ctx* ctx);
 #define LHV_EXPORT_KEYS        1  /* uint64[n] Morton keys in the tree's order: sorted (stable)
                                      for a context's first tree and whenever the context has no
                                      core radius and no level cap; otherwise sorted by their
-                                     prefix down to one level below the deepest level that the
+                                     prefix down to five levels below the deepest level that the
                                      core rule and the level cap allowed in the previous tree,
                                      equal prefixes in input order (the boxes of every level the
                                      tree uses are the same) */

@@ -67,6 +67,8 @@ SIGNATURES = {
     "lhv_evaluate_batched": (_int, [_vp, _int, ctypes.POINTER(_i64), _vp, _vp, _vp, _vp]),
     "lhv_step_batched": (_int, [_vp, _int, ctypes.POINTER(_i64), _vp, _vp, _dbl]),
     "lhv_morton_sort_noalloc": (_int, [_i64, _vp, _vp, _vp, _vp, _vp]),
+    "lhv_evaluate_potential_gradient": (_int, [_vp, _i64, _vp, _vp, _vp]),
+    "lhv_evaluate_potential_gradient_f64": (_int, [_vp, _i64, _vp, _vp, _vp]),
     "lhv_peak_probe": (_int, [_int, _int, _int, _vp, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl)]),
 }
 

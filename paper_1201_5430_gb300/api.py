@@ -74,6 +74,19 @@ class LHV:
         self._check(fn(self.h, n, _ptr(x4), _ptr(w4), _ptr(v4), _ptr(s4)), "evaluate_velocity_stretching")
         return v4, s4
 
+    def evaluate_potential_gradient(self, x4, q, pg4=None):
+        """The scalar reference case (lhv_evaluate_potential_gradient): monopoles q (CUDA [n],
+        the context's dtype) at x4; returns pg4 [n, 4] = (grad phi, phi)."""
+        self._elems(x4)
+        if q.device.type != "cuda" or q.dtype != self.dtype or q.dim() != 1 or q.shape[0] != x4.shape[0] \
+                or not q.is_contiguous():
+            raise ValueError(f"expected a contiguous CUDA {self.dtype} vector of {x4.shape[0]} charges")
+        pg4 = torch.empty_like(x4) if pg4 is None else self._elems(pg4)
+        fn = self.lib.lhv_evaluate_potential_gradient_f64 if self.precision == "fp64" else \
+            self.lib.lhv_evaluate_potential_gradient
+        self._check(fn(self.h, x4.shape[0], _ptr(x4), _ptr(q), _ptr(pg4)), "evaluate_potential_gradient")
+        return pg4
+
     def evaluate_batched(self, offsets, x4, w4, v4=None, s4=None):
         """Independent systems: system k owns rows offsets[k]:offsets[k+1]."""
         self._elems(x4)

@@ -70,6 +70,10 @@ struct Ctx {
     int sel_leaf = 0;
     int64_t sel_idx_n = -1;
     Buf sel_W, sel_b, sel_X, sel_Z, sel_choice, sel_idx, sel_dv, sel_ds, sel_err;
+    // scalar reference case (lhv_evaluate_potential_gradient)
+    Buf s_m2l, s_m2m, s_l2l, s_tiles;   // translation blocks of the fused tables, TF32 tiles of s_m2l
+    int s_p = 0, s_type = 0;
+    Buf qs, pgfar;
 };
 
 // ---- helpers used by every translation unit ------------------------------
@@ -374,6 +378,135 @@ static int evaluate(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const ve
     return LHV_OK;
 }
 
+// ---- scalar reference case (Sec. 5.2): phi and grad phi of monopoles ------------------
+// The same octree, lists and kernels with one potential: P2M by Eq. rsbf5, the translation
+// block T of each fused operator (no conversion), L2P of phi and grad phi, and the direct
+// sum over the colleague leaves with the singular kernel.
+template <typename T>
+__global__ void k_gather_charges(int64_t n, const int* __restrict__ perm, const vec4_t<T>* __restrict__ x4,
+                                 const T* __restrict__ q, vec4_t<T>* __restrict__ xs, T* __restrict__ qs) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int j = perm[i];
+        vec4_t<T> a = x4[j];
+        a.w = 0;
+        xs[i] = a;
+        qs[i] = q[j];
+    }
+}
+
+template <typename T>
+static void ensure_scalar_ops(Ctx* c) {
+    ensure_ops<T>(c);
+    if (c->s_p == c->cfg.p && c->s_type == (int)sizeof(T)) return;
+    StageScope sc(c, LHV_STAGE_OPS);
+    const int P = c->ops.P;
+    translation_block<T>(c, c->ops.m2l.as<T>(), NUM_OFFSETS, P, c->s_m2l);
+    translation_block<T>(c, c->ops.m2m.as<T>(), 8, P, c->s_m2m);
+    translation_block<T>(c, c->ops.l2l.as<T>(), 8, P, c->s_l2l);
+    if constexpr (sizeof(T) == 4) {
+        if (ctx_use_tc(c) && tc_supported(P, P, 0)) {
+            tc_tiles_build(c, c->s_m2l.as<float>(), NUM_OFFSETS, P, P, 0, c->s_tiles);
+        } else {
+            release(c->s_tiles);
+        }
+    }
+    cuda_check(cudaStreamSynchronize(c->stream), "scalar tables");
+    c->s_p = c->cfg.p;
+    c->s_type = (int)sizeof(T);
+}
+
+template <typename T>
+static int evaluate_scalar(Ctx* c, int64_t n, const vec4_t<T>* x4, const T* q, vec4_t<T>* out) {
+    if (n == 0) return LHV_OK;
+    ensure_scalar_ops<T>(c);
+    if (!c->counters.ptr) {
+        ensure(c, c->counters, 64);
+        cuda_check(cudaMemsetAsync(c->counters.ptr, 0, 64, c->stream), "counters init");
+    }
+    unsigned long long* cnt = c->counters.as<unsigned long long>();
+    cuda_check(cudaMemsetAsync(cnt, 0, 16, c->stream), "counters");
+    Error err{LHV_OK, ""};
+    const int64_t off[2] = {0, n};
+    {
+        StageScope sc(c, LHV_STAGE_TREE);
+        if (build_tree<T>(c, n, 1, off, x4, nullptr, c->tb, c->lv, c->hp, err) != LHV_OK) throw err;
+        c->tree_n = n;
+        ensure(c, c->xs, n * (int64_t)sizeof(vec4_t<T>));
+        ensure(c, c->qs, n * (int64_t)sizeof(T));
+        k_gather_charges<T><<<grid_for(n, 256), 256, 0, c->stream>>>(n, c->tb.perm.as<int>(), x4, q,
+                                                                      c->xs.as<vec4_t<T>>(), c->qs.as<T>());
+        count_launch(c);
+        check_launch("gather charges");
+    }
+    c->tree_reuse = false;
+    const Levels& lv = c->lv;
+    const int L = lv.L;
+    const int terms = c->cfg.terms ? c->cfg.terms : LHV_TERMS_ALL;
+    const bool far = (terms & LHV_TERMS_FAR) && L >= 2;
+    const bool near = (terms & LHV_TERMS_NEAR) != 0;
+    const vec4_t<T>* xs = c->xs.as<vec4_t<T>>();
+    const T* qs = c->qs.as<T>();
+    vec4_t<T>* pgfar = nullptr;
+    c->have_far = false;  // the vortex expansions are not the ones in mult / loc
+    if (far) {
+        Plan<T> pl;
+        pl.L = L;
+        pl.scalar = true;
+        const int p = c->cfg.p, P = p * p;
+        for (int l = 0; l <= L; ++l) pl.p[l] = p;
+        pl.ld = (P + 7) / 8 * 8;
+        for (int l = 0; l <= L; ++l) {
+            pl.m2m[l] = c->s_m2m.as<T>();
+            pl.l2l[l] = c->s_l2l.as<T>();
+            pl.m2l[l] = c->s_m2l.as<T>();
+            pl.m2l_tiles[l] = c->s_tiles.ptr ? c->s_tiles.as<float>() : nullptr;
+        }
+        pl.l2p_sp = view<T>(c->ops.l2p_sp);
+        const int64_t nbt = lv.off[L + 1];
+        ensure(c, c->mult, nbt * pl.ld * (int64_t)sizeof(T));
+        ensure(c, c->loc, nbt * pl.ld * (int64_t)sizeof(T));
+        ensure(c, c->table, (nbt - lv.off[2]) * (int64_t)NUM_OFFSETS * 4);
+        ensure(c, c->pgfar, n * (int64_t)sizeof(vec4_t<T>));
+        T* mult = c->mult.as<T>();
+        T* loc = c->loc.as<T>();
+        {
+            StageScope sc(c, LHV_STAGE_P2M);
+            run_p2m_scalar<T>(c, pl, c->tb, lv, xs, qs, mult);
+        }
+        {
+            StageScope sc(c, LHV_STAGE_M2M);
+            run_m2m<T>(c, pl, c->tb, lv, c->gp_m2m, mult);
+        }
+        {
+            StageScope sc(c, LHV_STAGE_M2L);
+            cuda_check(cudaMemsetAsync(loc + (int64_t)lv.off[2] * pl.ld, 0,
+                                       sizeof(T) * (size_t)(nbt - lv.off[2]) * pl.ld, c->stream),
+                       "zero locals");
+            const bool tc = sizeof(T) == 4 && ctx_m2l_tc(c) && pl.m2l_tiles[2];
+            const int nc = tc && c->tune_nc == 0 ? TC_PAIRS : ctx_m2l_nc(c, gemm_nc<T>(P));
+            m2l_prepare(c, c->ops, c->tb, lv, c->table.as<int>(), c->gp_m2l, nc, true, cnt + 1);
+            StageScope sg(c, LHV_STAGE_M2L_PRODUCTS);
+            m2l_apply<T>(c, pl, lv, c->gp_m2l, mult, loc);
+        }
+        {
+            StageScope sc(c, LHV_STAGE_L2L);
+            run_l2l<T>(c, pl, c->tb, lv, c->gp_l2l, loc);
+        }
+        pgfar = c->pgfar.as<vec4_t<T>>();
+        {
+            StageScope sc(c, LHV_STAGE_L2P);
+            run_l2p_scalar<T>(c, pl, c->tb, lv, xs, loc, pgfar);
+        }
+        for (int l = 0; l <= MAX_LEVELS; ++l) c->eval_p[l] = l <= L ? p : 0;
+        c->eval_ld = pl.ld;
+    }
+    {
+        StageScope sc(c, LHV_STAGE_P2P);
+        run_p2p_scalar<T>(c, c->tb, lv, xs, qs, c->tb.perm.as<int>(), pgfar, out, near, n, cnt);
+    }
+    return LHV_OK;
+}
+
 // ---- learned form: per-level p and leaf cap from the selector network ----------
 static const int kLeafCaps[4] = {16, 32, 64, 128};
 
@@ -662,6 +795,24 @@ int direct_entry(lhv_ctx* ctx, int64_t n, const T* x4, const T* w4, int m, const
     });
 }
 
+template <typename T>
+int scalar_entry(lhv_ctx* ctx, int64_t n, const T* x4, const T* q, T* pg4, int want_prec) {
+    int st = check_elems(ctx, n, {x4, pg4}, 4 * sizeof(T), want_prec);
+    if (st != LHV_OK) return st;
+    if (n > 0 && (!q || !aligned(q, sizeof(T)))) {
+        ctx->c.last_error = "null or misaligned charge buffer";
+        return LHV_EINVAL;
+    }
+    if (ctx->c.cfg.core_a != 0.0) {
+        ctx->c.last_error = "the scalar reference case uses the singular kernel: a context with core_a = 0";
+        return LHV_EUNSUPPORTED;
+    }
+    return guarded(ctx, [&] {
+        return lhv::evaluate_scalar<T>(&ctx->c, n, reinterpret_cast<const lhv::vec4_t<T>*>(x4), q,
+                                       reinterpret_cast<lhv::vec4_t<T>*>(pg4));
+    });
+}
+
 }  // namespace
 
 extern "C" {
@@ -711,7 +862,8 @@ void lhv_destroy(lhv_ctx* ctx) {
     c.opcache.clear();
     for (auto& kv : c.spcache) lhv::free_csr(kv.second);
     c.spcache.clear();
-    for (auto* b : {&c.sel_W, &c.sel_b, &c.sel_X, &c.sel_Z, &c.sel_choice, &c.sel_idx, &c.sel_dv, &c.sel_ds, &c.sel_err})
+    for (auto* b : {&c.sel_W, &c.sel_b, &c.sel_X, &c.sel_Z, &c.sel_choice, &c.sel_idx, &c.sel_dv, &c.sel_ds, &c.sel_err,
+                    &c.s_m2l, &c.s_m2m, &c.s_l2l, &c.s_tiles, &c.qs, &c.pgfar})
         lhv::release(*b);
     lhv::TreeBufs& t = c.tb;
     lhv::Buf* tree[] = {&t.keys_a, &t.keys_b, &t.idx_a, &t.idx_b, &t.hist, &t.boxof_a, &t.boxof_b, &t.flags,
@@ -793,6 +945,14 @@ int lhv_step_f64(lhv_ctx* ctx, int64_t n, double* x4, double* w4, double dt) {
         return lhv::step<double>(&ctx->c, n, 1, off, reinterpret_cast<lhv::dbl4*>(x4), reinterpret_cast<lhv::dbl4*>(w4),
                                  dt);
     });
+}
+
+int lhv_evaluate_potential_gradient(lhv_ctx* ctx, int64_t n, const float* x4, const float* q, float* pg4) {
+    return scalar_entry<float>(ctx, n, x4, q, pg4, LHV_FP32);
+}
+
+int lhv_evaluate_potential_gradient_f64(lhv_ctx* ctx, int64_t n, const double* x4, const double* q, double* pg4) {
+    return scalar_entry<double>(ctx, n, x4, q, pg4, LHV_FP64);
 }
 
 int lhv_mlp_forward(int rows, const float* X, const uint16_t* W, const float* b, float* Z, void* cuda_stream) {

@@ -113,18 +113,21 @@ constexpr int P2M_MAX_OUT = (3 * 24 * 24 + P2M_THREADS - 1) / P2M_THREADS;  // W
 // Work items are the tiles of at most P2P_TILE consecutive elements of one leaf
 // (the near-field tiles), so a crowded leaf is spread over several blocks; each
 // block adds its partial W into the leaf's (zeroed) W with atomics.
-template <typename T>
+// NC = 3: W of the vortex elements (rows of 3P per leaf); NC = 1: the scalar reference
+// case, monopoles q: the scaled S coefficients of Eq. rsbf5, (1/h) sum_e q_e g_hat(rho_e),
+// written straight into the leaf's multipole row (ldw reals per leaf).
+template <typename T, int NC>
 __global__ void __launch_bounds__(P2M_THREADS) k_p2m_w(const int* __restrict__ ntiles_dev,
                                                      const int2* __restrict__ tiles, int level,
                                                      const uint64_t* __restrict__ bkey, const int* __restrict__ bend,
                                                      const SysCube* __restrict__ cubes,
                                                      const vec4_t<T>* __restrict__ xs,
-                                                     const vec4_t<T>* __restrict__ ws, T* __restrict__ Wout, int p,
-                                                     int chunk) {
+                                                     const vec4_t<T>* __restrict__ ws, const T* __restrict__ qs,
+                                                     T* __restrict__ Wout, int64_t ldw, int p, int chunk) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int P = p * p;
     T* gh = reinterpret_cast<T*>(smem_raw);  // [chunk][P]
-    T* wk = gh + (size_t)chunk * P;          // [chunk][3]: w / h
+    T* wk = gh + (size_t)chunk * P;          // [chunk][NC]: strength / h
     const int ntiles = *ntiles_dev;
     const QTab<T> qt = build_qtab(wk + (size_t)chunk * 3, p);  // visible after the tile loop's first barrier
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -133,7 +136,7 @@ __global__ void __launch_bounds__(P2M_THREADS) k_p2m_w(const int* __restrict__ n
         double cx, cy, cz, h;
         box_geom(cubes, bkey[b], level, cx, cy, cz, h);
         const T invh = (T)(1.0 / h);
-        T* Wb = Wout + (int64_t)b * 3 * P;
+        T* Wb = Wout + (int64_t)b * ldw;
         const int e0 = tw.y, e1 = min(bend[b], tw.y + P2P_TILE);
         T acc[P2M_MAX_OUT];  // outputs i = threadIdx.x + q blockDim.x of this tile, summed over its chunks
 #pragma unroll
@@ -142,10 +145,15 @@ __global__ void __launch_bounds__(P2M_THREADS) k_p2m_w(const int* __restrict__ n
             const int ne = min(chunk, e1 - c0);
             __syncthreads();
             for (int e = threadIdx.x; e < ne; e += blockDim.x) {
-                vec4_t<T> xv = xs[c0 + e], wv = ws[c0 + e];
-                wk[e * 3 + 0] = wv.x * invh;  // M_hat carries 1/h (P2M scaling)
-                wk[e * 3 + 1] = wv.y * invh;
-                wk[e * 3 + 2] = wv.z * invh;
+                vec4_t<T> xv = xs[c0 + e];
+                if constexpr (NC == 3) {
+                    const vec4_t<T> wv = ws[c0 + e];
+                    wk[e * 3 + 0] = wv.x * invh;  // M_hat carries 1/h (P2M scaling)
+                    wk[e * 3 + 1] = wv.y * invh;
+                    wk[e * 3 + 2] = wv.z * invh;
+                } else {
+                    wk[e] = qs[c0 + e] * invh;
+                }
                 T* g = gh + (size_t)e * P;
                 const T rx = (T)(((double)xv.x - cx) / h), ry = (T)(((double)xv.y - cy) / h),
                         rz = (T)(((double)xv.z - cz) / h);
@@ -169,17 +177,17 @@ __global__ void __launch_bounds__(P2M_THREADS) k_p2m_w(const int* __restrict__ n
 #pragma unroll
             for (int q = 0; q < P2M_MAX_OUT; ++q) {
                 const int i = threadIdx.x + q * blockDim.x;
-                if (i >= 3 * P) break;
+                if (i >= NC * P) break;
                 const int k = i / P, j = i - k * P;
                 T s = 0;
-                for (int e = 0; e < ne; ++e) s += wk[e * 3 + k] * gh[(size_t)e * P + j];
+                for (int e = 0; e < ne; ++e) s += wk[e * NC + k] * gh[(size_t)e * P + j];
                 acc[q] += s;
             }
         }
 #pragma unroll
         for (int q = 0; q < P2M_MAX_OUT; ++q) {
             const int i = threadIdx.x + q * blockDim.x;
-            if (i >= 3 * P) break;
+            if (i >= NC * P) break;
             atomicAdd(Wb + i, acc[q]);
         }
         __syncthreads();
@@ -297,6 +305,87 @@ __global__ void __launch_bounds__(L2P_THREADS) k_l2p_eval(const int* __restrict_
     }
 }
 
+
+// Scalar reference case: phi = L_hat . b(rho) (no factor: R coefficients carry h^n / nu)
+// and grad phi_k = (1/h) c_k . b(rho), with c_k the velocity rows of the L2P map (Eq. evf3)
+// applied to (L_hat, 0): with chi = 0, v = grad phi (Eq. 4).  Lanes of the output: grad phi
+// in x, y, z, phi in w.
+template <typename T>
+__global__ void __launch_bounds__(L2P_THREADS) k_l2p_scalar(const int* __restrict__ ntiles_dev,
+                                                          const int2* __restrict__ tiles, int level,
+                                                          const uint64_t* __restrict__ bkey,
+                                                          const int* __restrict__ bend,
+                                                          const SysCube* __restrict__ cubes,
+                                                          const vec4_t<T>* __restrict__ xs, const T* __restrict__ loc,
+                                                          int64_t ld, CsrView<T> e, vec4_t<T>* __restrict__ pgfar,
+                                                          int p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int P = p * p;
+    T* cf = reinterpret_cast<T*>(smem_raw);  // [P][4]
+    T* lh = cf + 4 * P;                      // [2P] (L_hat, 0)
+    const int ntiles = *ntiles_dev;
+    const QTab<T> qt = build_qtab(lh + 2 * P, p);
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int2 tw = tiles[t];
+        const int b = tw.x;
+        double cx, cy, cz, h;
+        box_geom(cubes, bkey[b], level, cx, cy, cz, h);
+        __syncthreads();
+        for (int i = threadIdx.x; i < 2 * P; i += blockDim.x) lh[i] = i < P ? loc[(int64_t)b * ld + i] : (T)0;
+        __syncthreads();
+        for (int r = threadIdx.x; r < 4 * P; r += blockDim.x) {  // vector j = 0: phi itself, 1..3: rows of v_x, v_y, v_z
+            const int j = r / P, i = r - j * P;
+            T acc = 0;
+            if (j == 0) {
+                acc = lh[i];
+            } else {
+                const int row = r - P;
+                for (int k = e.rowptr[row]; k < e.rowptr[row + 1]; ++k) acc += e.val[k] * lh[e.col[k]];
+            }
+            cf[i * 4 + j] = acc;
+        }
+        __syncthreads();
+        const T invh = (T)(1.0 / h);
+        const int e1 = min(bend[b], tw.y + P2P_TILE);
+        for (int el = tw.y + threadIdx.x; el < e1; el += blockDim.x) {
+            const vec4_t<T> xv = xs[el];
+            const T rx = (T)(((double)xv.x - cx) / h), ry = (T)(((double)xv.y - cy) / h),
+                    rz = (T)(((double)xv.z - cz) / h);
+            T acc[4] = {0, 0, 0, 0};
+            for_each_Q<T>(p, rx, ry, rz, qt, [&](int n, int m, T qr, T qi) {
+                T re, im;  // (-1)^n i^m Q
+                switch (m & 3) {
+                    case 0: re = qr; im = qi; break;
+                    case 1: re = -qi; im = qr; break;
+                    case 2: re = -qr; im = -qi; break;
+                    default: re = qi; im = -qr; break;
+                }
+                if (n & 1) {
+                    re = -re;
+                    im = -im;
+                }
+                if (m == 0) {
+                    const T* c = cf + (n * n) * 4;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[j] += c[j] * re;
+                } else {
+                    const T* c1 = cf + (n * n + 2 * m - 1) * 4;
+                    const T* c2 = c1 + 4;
+                    const T b1 = 2 * re, b2 = -2 * im;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[j] += c1[j] * b1 + c2[j] * b2;
+                }
+            });
+            vec4_t<T> o;
+            o.x = acc[1] * invh;
+            o.y = acc[2] * invh;
+            o.z = acc[3] * invh;
+            o.w = acc[0];
+            pgfar[el] = o;
+        }
+    }
+}
+
 }  // namespace
 
 template <typename T>
@@ -308,12 +397,13 @@ void run_p2m(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, co
     int chunk = 128;
     while (chunk > 32 && sizeof(T) * ((size_t)chunk * (P + 3) + qtab_reals(p)) > 80 * 1024) chunk /= 2;
     const size_t smem = sizeof(T) * ((size_t)chunk * (P + 3) + qtab_reals(p));
-    cuda_check(cudaFuncSetAttribute(k_p2m_w<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "p2m attr");
+    cuda_check(cudaFuncSetAttribute(k_p2m_w<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+               "p2m attr");
     cuda_check(cudaMemsetAsync(W, 0, sizeof(T) * (size_t)nl * 3 * P, stream_of(c)), "p2m zero");
     const int64_t max_tiles = nl + lv.n / P2P_TILE + 1;
-    k_p2m_w<T><<<grid_for(max_tiles, 1, 152 * 16), P2M_THREADS, smem, stream_of(c)>>>(
+    k_p2m_w<T, 3><<<grid_for(max_tiles, 1, 152 * 16), P2M_THREADS, smem, stream_of(c)>>>(
         tb.tile_count.as<int>(), tb.tiles.as<int2>(), L, tb.bkey.as<uint64_t>() + o, tb.bend.as<int>() + o,
-        tb.cubes.as<SysCube>(), xs, ws, W, p, chunk);
+        tb.cubes.as<SysCube>(), xs, ws, nullptr, W, (int64_t)3 * P, p, chunk);
     count_launch(c);
     check_launch("p2m w");
     const size_t smem2 = sizeof(T) * 3 * P;
@@ -362,10 +452,10 @@ void run_m2m(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, Gr
         a.g1 = a.g0 + 8;
         a.ops = pl.m2m[l];
         a.ops_mod = 8;
-        a.R = 2 * Pout;
-        a.C = 2 * Pin;
-        a.psplit = Pout;
-        a.psplit_c = Pin;
+        a.R = pl.scalar ? Pout : 2 * Pout;  // scalar case: the translation block alone, no chi
+        a.C = pl.scalar ? Pin : 2 * Pin;
+        a.psplit = pl.scalar ? 0 : Pout;
+        a.psplit_c = pl.scalar ? 0 : Pin;
         a.in = mult;
         a.ldin = pl.ld;
         a.out = mult;
@@ -391,10 +481,10 @@ void run_l2l(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, Gr
         a.g1 = a.g0 + 8;
         a.ops = pl.l2l[l + 1];
         a.ops_mod = 8;
-        a.R = 2 * Pout;
-        a.C = 2 * Pin;
-        a.psplit = Pout;
-        a.psplit_c = Pin;
+        a.R = pl.scalar ? Pout : 2 * Pout;
+        a.C = pl.scalar ? Pin : 2 * Pin;
+        a.psplit = pl.scalar ? 0 : Pout;
+        a.psplit_c = pl.scalar ? 0 : Pin;
         a.in = loc;
         a.ldin = pl.ld;
         a.out = loc;
@@ -421,13 +511,53 @@ void run_l2p(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, co
     check_launch("l2p");
 }
 
+
+// Scalar reference case: P2M of the monopoles straight into the leaf multipoles.
+template <typename T>
+void run_p2m_scalar(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs,
+                    const T* qs, T* mult) {
+    const int L = lv.L, nl = lv.nbox[L], o = lv.off[L], p = pl.p[L], P = p * p;
+    int chunk = 128;
+    while (chunk > 32 && sizeof(T) * ((size_t)chunk * (P + 3) + qtab_reals(p)) > 80 * 1024) chunk /= 2;
+    const size_t smem = sizeof(T) * ((size_t)chunk * (P + 3) + qtab_reals(p));
+    cuda_check(cudaFuncSetAttribute(k_p2m_w<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+               "p2m attr");
+    T* leaf_rows = mult + (int64_t)o * pl.ld;
+    cuda_check(cudaMemsetAsync(leaf_rows, 0, sizeof(T) * (size_t)nl * pl.ld, stream_of(c)), "p2m zero");
+    const int64_t max_tiles = nl + lv.n / P2P_TILE + 1;
+    k_p2m_w<T, 1><<<grid_for(max_tiles, 1, 152 * 16), P2M_THREADS, smem, stream_of(c)>>>(
+        tb.tile_count.as<int>(), tb.tiles.as<int2>(), L, tb.bkey.as<uint64_t>() + o, tb.bend.as<int>() + o,
+        tb.cubes.as<SysCube>(), xs, nullptr, qs, leaf_rows, pl.ld, p, chunk);
+    count_launch(c);
+    check_launch("p2m scalar");
+}
+
+template <typename T>
+void run_l2p_scalar(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs,
+                    const T* loc, vec4_t<T>* pgfar) {
+    const int L = lv.L, nl = lv.nbox[L], o = lv.off[L], p = pl.p[L], P = p * p;
+    const size_t smem = sizeof(T) * (6 * P + qtab_reals(p));
+    cuda_check(cudaFuncSetAttribute(k_l2p_scalar<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+               "l2p attr");
+    const int64_t max_tiles = nl + lv.n / P2P_TILE + 1;
+    k_l2p_scalar<T><<<grid_for(max_tiles, 1, 152 * 16), L2P_THREADS, smem, stream_of(c)>>>(
+        tb.tile_count.as<int>(), tb.tiles.as<int2>(), L, tb.bkey.as<uint64_t>() + o, tb.bend.as<int>() + o,
+        tb.cubes.as<SysCube>(), xs, loc + (int64_t)o * pl.ld, pl.ld, pl.l2p_sp, pgfar, p);
+    count_launch(c);
+    check_launch("l2p scalar");
+}
+
 #define LHV_INST(T)                                                                                              \
     template void run_p2m<T>(Ctx*, const Plan<T>&, const TreeBufs&, const Levels&, const vec4_t<T>*,            \
                              const vec4_t<T>*, T*, T*);                                                         \
     template void run_m2m<T>(Ctx*, const Plan<T>&, const TreeBufs&, const Levels&, Grouped&, T*);              \
     template void run_l2l<T>(Ctx*, const Plan<T>&, const TreeBufs&, const Levels&, Grouped&, T*);              \
     template void run_l2p<T>(Ctx*, const Plan<T>&, const TreeBufs&, const Levels&, const vec4_t<T>*,            \
-                             const vec4_t<T>*, const T*, vec4_t<T>*, vec4_t<T>*);
+                             const vec4_t<T>*, const T*, vec4_t<T>*, vec4_t<T>*);                      \
+    template void run_p2m_scalar<T>(Ctx*, const Plan<T>&, const TreeBufs&, const Levels&, const vec4_t<T>*,     \
+                                    const T*, T*);                                                               \
+    template void run_l2p_scalar<T>(Ctx*, const Plan<T>&, const TreeBufs&, const Levels&, const vec4_t<T>*,     \
+                                    const T*, vec4_t<T>*);
 LHV_INST(float)
 LHV_INST(double)
 #undef LHV_INST

@@ -168,6 +168,9 @@ template <typename T>
 void build_sparse(Ctx* c, int kind, int p, Csr& dst);
 void free_csr(Csr& m);
 void free_operators(OpTables& ops);
+// dst = the translation block T ([P][P] per group, k-major) of ngroups fused [2P][2P] tables.
+template <typename T>
+void translation_block(Ctx* c, const T* fused, int ngroups, int P, Buf& dst);
 int m2l_slot_host(int dx, int dy, int dz);   // same mapping as slot_of, on the host
 
 struct Grouped;
@@ -189,6 +192,8 @@ struct Plan {
     const float* m2l_tiles[MAX_LEVELS + 1] = {};  // tensor-core tiles of m2l[l] (LHV_TF32X3), or null
     CsrView<T> p2m_sp, l2p_sp;             // P2M(p[L]), L2P(p[L]) in row-compressed form
     bool uniform = true;                   // p[l] equal over l = 2..L
+    bool scalar = false;                   // scalar reference case: one potential, P x P translation
+                                           // tables (the T block of the fused operators), no conversion
 };
 
 // ---- expansions (expansions.cu) ----------------------------------------------
@@ -207,6 +212,15 @@ template <typename T>
 void run_l2p(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs,
              const vec4_t<T>* ws, const T* loc, vec4_t<T>* vfar, vec4_t<T>* sfar);
 
+// Scalar reference case (Sec. 5.2): P2M of monopoles into the leaf multipoles, and L2P of
+// phi and grad phi (output lanes: grad phi in x, y, z, phi in w).
+template <typename T>
+void run_p2m_scalar(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs,
+                    const T* qs, T* mult);
+template <typename T>
+void run_l2p_scalar(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs,
+                    const T* loc, vec4_t<T>* pgfar);
+
 // ---- M2L (m2l.cu) ------------------------------------------------------------
 // table: (off[L+1] - off[2]) * 316 ints; nc: pairs per GEMM chunk (gemm_nc).
 // uniform: pairs of all levels bucketed by offset; else by (level, offset).
@@ -221,6 +235,12 @@ template <typename T>
 void run_p2p(Ctx* c, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs, const vec4_t<T>* ws,
              const int* perm, const vec4_t<T>* vfar, const vec4_t<T>* sfar, vec4_t<T>* v_out, vec4_t<T>* s_out,
              double a, bool near, int64_t n, unsigned long long* pair_counter);
+
+// scalar reference case: phi, grad phi over the colleague leaves (singular kernel), added
+// to `far` (may be null) and written to out in the caller's order
+template <typename T>
+void run_p2p_scalar(Ctx* c, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs, const T* qs, const int* perm,
+                    const vec4_t<T>* far, vec4_t<T>* out, bool near, int64_t n, unsigned long long* pair_counter);
 
 // ---- direct sums at sampled targets (direct.cu) ---------------------------------
 // v4, s4: device double [m][4]; synchronous; LHV_EINVAL if an index is out of range.

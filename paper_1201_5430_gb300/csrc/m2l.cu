@@ -127,9 +127,9 @@ void m2l_apply(Ctx* c, const Plan<T>& pl, const Levels& lv, Grouped& gp, const T
         a.g1 = pl.uniform ? NUM_OFFSETS : (l1 - 2) * NUM_OFFSETS;
         a.ops = pl.m2l[l0];
         a.ops_mod = NUM_OFFSETS;
-        a.R = 2 * P;
-        a.C = 2 * P;
-        a.psplit = P;
+        a.R = pl.scalar ? P : 2 * P;  // scalar case: the translation block alone, no chi
+        a.C = pl.scalar ? P : 2 * P;
+        a.psplit = pl.scalar ? 0 : P;
         a.in = mult;
         a.ldin = pl.ld;
         a.out = loc;

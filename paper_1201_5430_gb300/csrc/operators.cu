@@ -579,6 +579,33 @@ void build_operators(Ctx* c, int p, OpTables& ops) {
     cuda_check(cudaStreamSynchronize(s), "operators");
 }
 
+
+// The translation block T (inputs j < P, outputs i < P) of `ngroups` fused k-major
+// [2P][2P] tables [[T, C12 T], [0, C22 T]]: with chi = 0 the fused map reduces to T, the
+// plain (S|S), (S|R) or (R|R) translation of one potential (the scalar reference case).
+template <typename T>
+__global__ void k_translation_block(int ngroups, int P, const T* __restrict__ fused, T* __restrict__ dst) {
+    const int64_t per = (int64_t)P * P;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ngroups * per;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = e / per, r = e - g * per;
+        const int64_t j = r / P, i = r - j * P;
+        dst[e] = fused[g * 4 * per + j * 2 * P + i];
+    }
+}
+
+template <typename T>
+void translation_block(Ctx* c, const T* fused, int ngroups, int P, Buf& dst) {
+    ensure(c, dst, (int64_t)ngroups * P * P * (int64_t)sizeof(T));
+    k_translation_block<T><<<grid_for((int64_t)ngroups * P * P, 256), 256, 0, stream_of(c)>>>(ngroups, P, fused,
+                                                                                            dst.as<T>());
+    count_launch(c);
+    check_launch("translation block");
+}
+
+template void translation_block<float>(Ctx*, const float*, int, int, Buf&);
+template void translation_block<double>(Ctx*, const double*, int, int, Buf&);
+
 template void build_sparse<float>(Ctx*, int, int, Csr&);
 template void build_sparse<double>(Ctx*, int, int, Csr&);
 template void build_op<float>(Ctx*, int, int, int, Buf&);

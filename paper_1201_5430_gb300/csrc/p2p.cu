@@ -692,6 +692,259 @@ __global__ void k_rk4_final(int64_t n, vec4_t<T>* x, vec4_t<T>* w, const vec4_t<
     }
 }
 
+
+// ---- scalar reference case (Sec. 5.2: phi and grad phi of monopoles) ----------------
+// phi_i = sum_{j != i} q_j / r and grad phi_i = -sum_{j != i} q_j d / r^3, d = x_i - x_j,
+// j over the 27 colleague leaves, excluded by index; the singular kernel has no value at
+// r = 0, so distinct elements at one point contribute nothing to each other.  The result
+// is added to the far field (lanes: grad phi in x, y, z, phi in w) and written in the
+// caller's order.
+
+// Generic form (FP64 twin): one thread per target of a P2P_TILE tile, CH sources staged
+// per step, blocked accumulation with a compensated (TwoSum) total per target.
+template <typename T, int CH>
+__global__ void __launch_bounds__(P2P_TILE) k_p2p_scalar(const int* __restrict__ ntiles_dev,
+                                                        const int2* __restrict__ tiles, int* __restrict__ work,
+                                                        const int* __restrict__ bbeg, const int* __restrict__ bend,
+                                                        const int* __restrict__ bcol,
+                                                        const vec4_t<T>* __restrict__ xs, const T* __restrict__ qs,
+                                                        const int* __restrict__ perm,
+                                                        const vec4_t<T>* __restrict__ far,
+                                                        vec4_t<T>* __restrict__ out, int near,
+                                                        unsigned long long* __restrict__ pairs) {
+    __shared__ vec4_t<T> sx[CH];  // (x, y, z, q)
+    __shared__ int sid[CH];
+    __shared__ int cbeg[27], cpre[28];
+    __shared__ int cur;
+    const int ntiles = *ntiles_dev;
+    unsigned long long my_pairs = 0;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) cur = atomicAdd(work, 1);
+        __syncthreads();
+        const int tile = cur;
+        if (tile >= ntiles) break;
+        const int2 tw = tiles[tile];
+        const int leaf = tw.x;
+        const int tend = bend[leaf];
+        if (threadIdx.x == 0) {
+            int acc = 0;
+            for (int q = 0; q < 27; ++q) {
+                const int cb = bcol[(int64_t)leaf * 27 + q];
+                int cnt = 0;
+                if (cb >= 0) {
+                    cbeg[q] = bbeg[cb];
+                    cnt = bend[cb] - bbeg[cb];
+                } else {
+                    cbeg[q] = 0;
+                }
+                cpre[q] = acc;
+                acc += cnt;
+            }
+            cpre[27] = acc;
+        }
+        const int ti = tw.y + threadIdx.x;
+        const bool act = ti < tend;
+        const vec4_t<T> xi = act ? xs[ti] : vec4_t<T>{};
+        T hp = 0, lp = 0, hg[3] = {0, 0, 0}, lg[3] = {0, 0, 0};
+        __syncthreads();
+        const int nsrc = near ? cpre[27] : 0;
+        const int self_lo = cpre[13] + (tw.y - cbeg[13]);
+        const int self_hi = self_lo + P2P_TILE;
+        if (threadIdx.x == 0 && near) {
+            const int nt = min(P2P_TILE, tend - tw.y);
+            my_pairs += (unsigned long long)nt * (unsigned long long)(nsrc - 1);
+        }
+        int qrun = 0;
+        for (int s0 = 0; s0 < nsrc; s0 += CH) {
+            for (int v = s0 + threadIdx.x; v < min(nsrc, s0 + CH); v += P2P_TILE) {
+                while (cpre[qrun + 1] <= v) ++qrun;
+                const int j = cbeg[qrun] + (v - cpre[qrun]);
+                vec4_t<T> a = xs[j];
+                a.w = qs[j];
+                sx[v - s0] = a;
+                sid[v - s0] = j;
+            }
+            __syncthreads();
+            const int ns = min(CH, nsrc - s0);
+            const bool check = s0 < self_hi && s0 + ns > self_lo;
+            T ap = 0, ag0 = 0, ag1 = 0, ag2 = 0;
+            for (int k = 0; k < ns; ++k) {
+                const vec4_t<T> xj = sx[k];
+                const T dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+                const T r2 = dx * dx + dy * dy + dz * dz;
+                T ri = r2 > (T)0 ? rsqrt(r2) : (T)0;
+                if (check && sid[k] == ti) ri = 0;
+                const T qr = xj.w * ri;
+                const T g = qr * ri * ri;
+                ap += qr;
+                ag0 += g * dx;
+                ag1 += g * dy;
+                ag2 += g * dz;
+            }
+            two_sum_acc(hp, lp, ap);
+            two_sum_acc(hg[0], lg[0], ag0);
+            two_sum_acc(hg[1], lg[1], ag1);
+            two_sum_acc(hg[2], lg[2], ag2);
+            __syncthreads();
+        }
+        if (act) {
+            const vec4_t<T> f = far ? far[ti] : vec4_t<T>{};
+            vec4_t<T> o;
+            o.x = f.x - (hg[0] + lg[0]);
+            o.y = f.y - (hg[1] + lg[1]);
+            o.z = f.z - (hg[2] + lg[2]);
+            o.w = f.w + (hp + lp);
+            out[perm[ti]] = o;
+        }
+    }
+    if (threadIdx.x == 0 && my_pairs) atomicAdd(pairs, my_pairs);
+}
+
+// Packed FP32x2 form: one warp per warp tile of 32 targets (the vortex kernel's scheme),
+// each instruction over two sources of the stage held as -x, -y, -z and q pairs.
+template <int CH>
+struct P2psWarpSmem {
+    static constexpr int CP = CH / 2;
+    float4 A[CP];  // -x pair, -y pair
+    float4 B[CP];  // -z pair, q pair
+    int2 id[CP];   // sorted indices of the pair (-1: padding)
+    int cbeg[27], cpre[28];
+};
+
+template <int CH>
+__global__ void __launch_bounds__(32 * P2P_WARPS) k_p2p_scalar_x2(const int* __restrict__ ntiles_dev,
+                                                                  const int2* __restrict__ tiles,
+                                                                  int* __restrict__ work,
+                                                                  const int* __restrict__ bbeg,
+                                                                  const int* __restrict__ bend,
+                                                                  const int* __restrict__ bcol,
+                                                                  const float4* __restrict__ xs,
+                                                                  const float* __restrict__ qs,
+                                                                  const int* __restrict__ perm,
+                                                                  const float4* __restrict__ far,
+                                                                  float4* __restrict__ out, int near,
+                                                                  unsigned long long* __restrict__ pairs) {
+    constexpr int WT = 32;
+    constexpr int SUBS = P2P_TILE / WT;
+    constexpr int CP = CH / 2;
+    constexpr int SU = 2;
+    constexpr unsigned FULL = 0xffffffffu;
+    static_assert(CP % SU == 0, "a stage holds whole steps");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    P2psWarpSmem<CH>& sm = reinterpret_cast<P2psWarpSmem<CH>*>(smem_raw)[threadIdx.x >> 5];
+    const int nitems = *ntiles_dev * SUBS;
+    unsigned long long my_pairs = 0;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(work, 1);
+        item = __shfl_sync(FULL, item, 0);
+        if (item >= nitems) break;
+        const int2 tw = tiles[item / SUBS];
+        const int leaf = tw.x;
+        const int t0 = tw.y + (item % SUBS) * WT;
+        const int tend = bend[leaf];
+        if (t0 >= tend) continue;  // warp-uniform
+        int cnt = 0, beg = 0;
+        if (lane < 27) {
+            const int cb = bcol[(int64_t)leaf * 27 + lane];
+            if (cb >= 0) {
+                beg = bbeg[cb];
+                cnt = bend[cb] - beg;
+            }
+        }
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane < 27) {
+            sm.cbeg[lane] = beg;
+            sm.cpre[lane] = incl - cnt;
+        }
+        if (lane == 26) sm.cpre[27] = incl;
+        const int ti = t0 + lane;
+        const bool act = ti < tend;
+        const float4 x = act ? xs[ti] : float4{};
+        const float2 X0 = dup2(x.x), X1 = dup2(x.y), X2 = dup2(x.z);
+        float hp = 0.f, lp = 0.f, hg[3] = {0.f, 0.f, 0.f}, lg[3] = {0.f, 0.f, 0.f};
+        __syncwarp();
+        const int nsrc = near ? sm.cpre[27] : 0;
+        const int self_lo = sm.cpre[13] + (t0 - sm.cbeg[13]);
+        const int self_hi = self_lo + WT;
+        if (lane == 0 && near) my_pairs += (unsigned long long)min(WT, tend - t0) * (unsigned long long)(nsrc - 1);
+        int qrun = 0;
+        for (int s0 = 0; s0 < nsrc; s0 += CH) {
+            const int ns = min(CH, nsrc - s0);
+            const int np = (((ns + 1) >> 1) + SU - 1) / SU * SU;
+            for (int k = lane; k < 2 * np; k += 32) {
+                const int v = s0 + k;
+                float4 xv = make_float4(kPadPosition, kPadPosition, kPadPosition, 0.0f);
+                float qv = 0.0f;
+                int j = -1;
+                if (v < nsrc) {
+                    while (sm.cpre[qrun + 1] <= v) ++qrun;
+                    j = sm.cbeg[qrun] + (v - sm.cpre[qrun]);
+                    xv = xs[j];
+                    qv = qs[j];
+                }
+                const int m = k >> 1, l = k & 1;
+                float* a = reinterpret_cast<float*>(&sm.A[m]);
+                float* b = reinterpret_cast<float*>(&sm.B[m]);
+                a[l] = -xv.x;
+                a[2 + l] = -xv.y;
+                b[l] = -xv.z;
+                b[2 + l] = qv;
+                reinterpret_cast<int*>(&sm.id[m])[l] = j;
+            }
+            __syncwarp();
+            float2 ap = make_float2(0.f, 0.f), ag0 = ap, ag1 = ap, ag2 = ap;
+            auto chunk = [&](auto check) {
+                for (int m = 0; m < np; m += SU) {
+#pragma unroll
+                    for (int u = 0; u < SU; ++u) {
+                        const float4 A = sm.A[m + u], B = sm.B[m + u];
+                        const float2 dx = add2(X0, make_float2(A.x, A.y));
+                        const float2 dy = add2(X1, make_float2(A.z, A.w));
+                        const float2 dz = add2(X2, make_float2(B.x, B.y));
+                        const float2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+                        float2 ri;
+                        ri.x = r2.x > 0.0f ? rsqrt_ftz(r2.x) : 0.0f;
+                        ri.y = r2.y > 0.0f ? rsqrt_ftz(r2.y) : 0.0f;
+                        if (decltype(check)::value) {
+                            const int2 j = sm.id[m + u];
+                            if (j.x == ti) ri.x = 0.0f;
+                            if (j.y == ti) ri.y = 0.0f;
+                        }
+                        const float2 qr = mul2(make_float2(B.z, B.w), ri);
+                        const float2 g = mul2(qr, mul2(ri, ri));
+                        ap = add2(ap, qr);
+                        ag0 = fma2(g, dx, ag0);
+                        ag1 = fma2(g, dy, ag1);
+                        ag2 = fma2(g, dz, ag2);
+                    }
+                }
+            };
+            if (s0 < self_hi && s0 + ns > self_lo) chunk(std::true_type{});
+            else chunk(std::false_type{});
+            two_sum_acc(hp, lp, ap.x + ap.y);
+            two_sum_acc(hg[0], lg[0], ag0.x + ag0.y);
+            two_sum_acc(hg[1], lg[1], ag1.x + ag1.y);
+            two_sum_acc(hg[2], lg[2], ag2.x + ag2.y);
+            __syncwarp();
+        }
+        if (act) {
+            const float4 f = far ? far[ti] : float4{};
+            out[perm[ti]] = make_float4(f.x - (hg[0] + lg[0]), f.y - (hg[1] + lg[1]), f.z - (hg[2] + lg[2]),
+                                        f.w + (hp + lp));
+        }
+        __syncwarp();  // the next item rewrites this warp's colleague table
+    }
+    if (lane == 0 && my_pairs) atomicAdd(pairs, my_pairs);
+}
+
 }  // namespace
 
 template <typename T>
@@ -778,6 +1031,43 @@ void run_p2p(Ctx* c, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs, 
     check_launch("p2p");
 }
 
+
+template <typename T>
+void run_p2p_scalar(Ctx* c, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs, const T* qs, const int* perm,
+                    const vec4_t<T>* far, vec4_t<T>* out, bool near, int64_t n, unsigned long long* pair_counter) {
+    cudaStream_t s = stream_of(c);
+    const int L = lv.L, o = lv.off[L];
+    ensure(c, ctx_tmp(c, 6), 64);
+    int* work = reinterpret_cast<int*>(ctx_tmp(c, 6).ptr);
+    cuda_check(cudaMemsetAsync(work, 0, 4, s), "p2p counter");
+    const int64_t max_tiles = lv.nbox[L] + n / P2P_TILE + 1;
+    int per_sm = 1, sms = 152, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    constexpr int CH = 256;
+    if constexpr (std::is_same<T, float>::value) {
+        auto kern = k_p2p_scalar_x2<CH>;
+        const int smem = (int)(P2P_WARPS * sizeof(P2psWarpSmem<CH>));
+        cuda_check(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem), "p2p attr");
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * P2P_WARPS, smem);
+        const int64_t items = max_tiles * (P2P_TILE / 32);
+        const int grid = (int)std::min<int64_t>((items + P2P_WARPS - 1) / P2P_WARPS, (int64_t)sms * std::max(per_sm, 1));
+        kern<<<grid, 32 * P2P_WARPS, smem, s>>>(tb.tile_count.as<int>(), tb.tiles.as<int2>(), work,
+                                                tb.bbeg.as<int>() + o, tb.bend.as<int>() + o,
+                                                tb.bcol.as<int>() + (int64_t)o * 27, xs, qs, perm, far, out,
+                                                near ? 1 : 0, pair_counter);
+    } else {
+        auto kern = k_p2p_scalar<T, 128>;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, P2P_TILE, 0);
+        const int grid = (int)std::min<int64_t>(max_tiles, (int64_t)sms * std::max(per_sm, 1));
+        kern<<<grid, P2P_TILE, 0, s>>>(tb.tile_count.as<int>(), tb.tiles.as<int2>(), work, tb.bbeg.as<int>() + o,
+                                       tb.bend.as<int>() + o, tb.bcol.as<int>() + (int64_t)o * 27, xs, qs, perm, far,
+                                       out, near ? 1 : 0, pair_counter);
+    }
+    count_launch(c);
+    check_launch("p2p scalar");
+}
+
 template <typename T>
 void run_rk4_stage(Ctx* c, int64_t n, const vec4_t<T>* x0, const vec4_t<T>* w0, const vec4_t<T>* kv,
                    const vec4_t<T>* ks, vec4_t<T>* ax, vec4_t<T>* aw, vec4_t<T>* sx, vec4_t<T>* sw, double c_acc,
@@ -795,7 +1085,9 @@ void run_rk4_stage(Ctx* c, int64_t n, const vec4_t<T>* x0, const vec4_t<T>* w0, 
     template void run_rk4_stage<T>(Ctx*, int64_t, const vec4_t<T>*, const vec4_t<T>*, const vec4_t<T>*,             \
                                    const vec4_t<T>*, vec4_t<T>*, vec4_t<T>*, vec4_t<T>*, vec4_t<T>*, double, double, \
                                    int);                                                                           \
-    template void run_rk4_final<T>(Ctx*, int64_t, vec4_t<T>*, vec4_t<T>*, const vec4_t<T>*, const vec4_t<T>*, double);
+    template void run_rk4_final<T>(Ctx*, int64_t, vec4_t<T>*, vec4_t<T>*, const vec4_t<T>*, const vec4_t<T>*, double); \
+    template void run_p2p_scalar<T>(Ctx*, const TreeBufs&, const Levels&, const vec4_t<T>*, const T*, const int*,     \
+                                    const vec4_t<T>*, vec4_t<T>*, bool, int64_t, unsigned long long*);
 LHV_INST(float)
 LHV_INST(double)
 #undef LHV_INST
