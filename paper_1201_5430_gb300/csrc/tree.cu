@@ -604,6 +604,8 @@ int key_bits_for(int nsys) {
     return std::min(KEY_BITS, (63 - sysbits) / 3);
 }
 
+constexpr int SORT_BELOW_CAP = 5;
+
 template <typename T>
 int build_tree(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const vec4_t<T>* x4, const vec4_t<T>* w4,
                TreeBufs& tb, Levels& lv, TreeParams& hp, Error& err) {
@@ -654,9 +656,10 @@ int build_tree(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const vec4_t<
     // S >= L_cap gives the same boxes at every level <= S and the same leaf level (keys that
     // differ within the prefix give the same shared level either way, and keys that share
     // their level-S box give a shared level >= S, beyond L_cap, either way).  S is the
-    // previous tree's L_cap + 1 (all levels for a context's first tree); if the new L_cap
+    // previous tree's L_cap + SORT_BELOW_CAP (all levels for a context's first tree); if the new L_cap
     // exceeds it, the sort is completed (a stable sort of the prefix-sorted keys is the
-    // stable sort) and the leaf level recomputed.
+    // stable sort) and the leaf level recomputed.  S is set a few levels below the previous
+    // cap (SORT_BELOW_CAP), which also orders each leaf's elements spatially.
     uint64_t* kin = tb.keys_a.as<uint64_t>();
     uint64_t* kout = tb.keys_b.as<uint64_t>();
     int* vin = tb.idx_a.as<int>();
@@ -694,7 +697,10 @@ int build_tree(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const vec4_t<
         cuda_check(cudaMemsetAsync(&tp->deepest_shared, 0xff, sizeof(int), s), "reset shared level");  // -1, as k_bbox_final sets it
         leaf_level();
     }
-    ctx_sort_levels(c) = std::min(bits, hp.L_cap + 1);
+    // the next tree orders its keys down to SORT_BELOW_CAP levels below the cap: the leaves
+    // only need one, the rest keeps consecutive elements of a leaf (the near-field warp tiles)
+    // spatially compact
+    ctx_sort_levels(c) = std::min(bits, hp.L_cap + SORT_BELOW_CAP);
     uint64_t* keys = kin;
     int* perm = vin;
     if (hp.nonfinite) {

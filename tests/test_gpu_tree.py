@@ -45,15 +45,15 @@ def _boxes_match(ctx, tr, st, L):
 
 
 def test_repeated_trees_in_one_context():
-    """After a context's first tree the sort orders the keys only down to one level
+    """After a context's first tree the sort orders the keys only down to five levels
     below the previous depth cap (core rule): leaf level, boxes and colleagues stay
     the oracle's, the keys are the oracle's keys of the permuted elements in prefix
-    order; a cube that grows (the cap moves two levels deeper) falls back to the full sort."""
+    order; a cube that grows (the cap moves six levels deeper) falls back to the full sort."""
     from paper_1201_5430_gb300 import LHV
     x, _ = workloads.ring(20000, 1)
     a = workloads.RING_CORE_A
     ctx = LHV(p=4, leaf_max=64, core_a=a, eps=1e-6)
-    for k, xs in enumerate((x, x + np.float32(1e-4), x * np.float32(4.0))):
+    for k, xs in enumerate((x, x + np.float32(1e-4), x * np.float32(64.0))):
         ctx.build_tree(dev(xs, "fp32"))
         tr = T.build_tree(xs, leaf_max=64, a=a, eps=1e-6)
         st = ctx.stats()
@@ -66,7 +66,7 @@ def test_repeated_trees_in_one_context():
         np.testing.assert_array_equal(keys, okeys[perm])
         if k != 1:  # a first tree, and the fallback, are fully sorted
             np.testing.assert_array_equal(perm, tr.perm)
-        else:       # prefix order down to the previous cap + 1 >= L
+        else:       # prefix order down to the previous cap + 5 > L
             pre = keys >> np.uint64(3 * (21 - (L + 1)))
             assert (pre[1:] >= pre[:-1]).all()
         _boxes_match(ctx, tr, st, L)
