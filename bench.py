@@ -313,6 +313,49 @@ def measure_peaks(torch, lib, stream):
     return out
 
 
+
+def scalar_ratio(torch, LHV, n=1 << 20, p=12, leaves=(32, 64, 128, 256)):
+    """The paper's central cost ratio (Sec. 5.2, Tables 1-2, Fig. 3): run time of v and s
+    (vortex elements, singular kernel) over that of phi and grad phi (the scalar reference
+    case, monopoles) on the same distribution, p = 12, each at its fastest leaf size (the
+    paper optimises l_max per case); uniform cube and sphere surface.  One evaluation
+    each, CUDA events, mean of 3 after a warm-up."""
+    out = {"p": p, "n": n, "precision": "tf32x3", "paper_mean_ratio": 1.405}
+
+    def t(c, f):
+        f()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            f()
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1) / 3
+
+    for dist, gen in (("cube", workloads.cube), ("sphere", workloads.sphere)):
+        x, w = gen(n, 7)
+        q = workloads.charges(n, 8)
+        x0 = torch.from_numpy(workloads.to_f4(x)).cuda()
+        w0 = torch.from_numpy(workloads.to_f4(w)).cuda()
+        q0 = torch.from_numpy(q).cuda()
+        rec = {}
+        for form in ("v_s", "phi_grad"):
+            best = None
+            for leaf in leaves:
+                c = LHV(p=p, leaf_max=leaf, core_a=0.0, precision="tf32x3")
+                f = (lambda: c.evaluate_velocity_stretching(x0, w0)) if form == "v_s" else \
+                    (lambda: c.evaluate_potential_gradient(x0, q0))
+                ms = t(c, f)
+                if best is None or ms < best["ms"]:
+                    best = {"ms": ms, "leaf_max": leaf, "leaf_level": c.stats()["leaf_level"]}
+                c.close()
+            rec[form] = best
+        rec["ratio"] = rec["v_s"]["ms"] / rec["phi_grad"]["ms"]
+        out[dist] = rec
+    return out
+
+
 def run_single(args, torch, LHV, local, world, rank, dist):
     from paper_1201_5430_gb300 import _lib, selector
     name = SINGLE[args.workload]
@@ -482,6 +525,7 @@ def run_single(args, torch, LHV, local, world, rank, dist):
             e2e_times.append(time.perf_counter() - t0)
     e2e_val = 4 * n * world / statistics.mean(e2e_times)
     c.close()
+    ratio = None if args.no_scalar_ratio else scalar_ratio(torch, LHV)
 
     if rank != 0:
         if dist:
@@ -526,6 +570,7 @@ def run_single(args, torch, LHV, local, world, rank, dist):
         "peaks_driver_kind": peak_kind,
         "stage_ms_per_step": {k: v / args.steps for k, v in st["stage_ms"].items() if v > 0},
         "launch_shape": shape,
+        "t_vs_over_t_phigrad": ratio,
         "cpu_baseline": cb,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(2 * n * 16),
                 "d2h_bytes_per_step": int(2 * n * 16), "steps": e2e_steps},
@@ -664,6 +709,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-scalar-ratio", action="store_true",
+                    help="skip T(v, s) / T(phi, grad phi) against the scalar reference case")
     ap.add_argument("--workload", default="leapfrog", choices=list(SINGLE) + ["blobs64", "offset_rings"],
                     help="leapfrog (headline), ring_262144 (single ring), offset_rings (mixed precision on "
                          "configs' colliding rings), blobs64 (the batched form)")
