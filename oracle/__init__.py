@@ -20,6 +20,9 @@ Everything is written for a reader who checks it against the paper by eye:
 * ``fmm``         -- the plain FP64 Lamb-Helmholtz FMM ("O2"), dense complex
                      translations, one conversion after every translation (Sec. 4).
 * ``rk4``         -- classical RK4 time step of Eq. s1.1.
+* ``complex_psi`` -- one complex FMM for Psi = phi + i chi (Sec. 4.2, Eq. chf1):
+                     one complex translation per box pair, conversions on the
+                     real potentials split from Psi.
 * ``scalar``      -- the paper's reference case (Sec. 5.2): phi and grad phi of
                      monopoles, direct ("O1s") and by the scalar harmonic FMM
                      over the same octree ("O2s").
