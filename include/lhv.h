@@ -22,8 +22,9 @@
  *    (w_x, w_y, w_z); lane 3 is ignored on input and written 0 on output.
  *  - Outputs are in the caller's element order.
  *  - All work is enqueued on the stream given to lhv_create, in stream order.
- *    Calls that build a tree read a few sizes back to the host (one short
- *    synchronisation of that stream per tree build).
+ *    Calls that build a tree read a few sizes back to the host (two short
+ *    synchronisations of that stream per tree build), except the steps replayed
+ *    from a captured graph (lhv_set_graph: one synchronisation per RK4 step).
  *  - Every call returns a status code (LHV_OK = 0, negative on error); no C++
  *    exception crosses the ABI.  After an error the outputs are unspecified and
  *    the context stays usable; lhv_last_error() describes the last error.
@@ -122,6 +123,11 @@ typedef struct {
                                                 stage, the same at 256, then M2L: (TF32x3 only:
                                                 tensor cores 128, 64 pairs,) CUDA cores 64, 32,
                                                 16 pairs */
+    int64_t graph_captures;                  /* steps captured as a CUDA graph (lhv_set_graph) */
+    int64_t graph_replays;                   /* steps run as one replay of the captured graph */
+    int64_t graph_fallbacks;                 /* steps whose tree failed the captured layout's guard
+                                                and ran uncaptured */
+    int64_t graph_kernels;                   /* kernels in the captured graph */
 } lhv_stats;
 
 /* Create a context for one configuration on one CUDA stream (a cudaStream_t,
@@ -242,6 +248,47 @@ int lhv_set_launch_shape(lhv_ctx* ctx, int p2p_targets_per_thread, int p2p_sourc
  * (p_out, p_in) pairs are built in FP64 on first use and kept by the context.
  * Takes effect at the next evaluation.  LHV_EINVAL for values out of range. */
 int lhv_set_level_p(lhv_ctx* ctx, const int* p, int nlevels);
+
+/* Whole RK4 step as one CUDA graph (enable = 1; 0 switches it off and frees the graph).
+ * Applies to lhv_step, lhv_step_batched and lhv_step_host on FP32 / TF32X3 contexts with
+ * one truncation number at every level and the selector off (other steps run as usual).
+ * The first step after enabling (and after any change of n, the system offsets, the
+ * x4 / w4 pointers, dt, p, precision, form or launch shapes) runs uncaptured, then in the
+ * captured layout, and is captured for the next calls; each later step is one
+ * cudaGraphLaunch on the context stream followed by one 4-byte read and a stream
+ * synchronisation.  The captured layout: the leaf level of the capture's first tree is
+ * kept for every tree of the replayed steps, box arrays sit at per-level capacities
+ * min(n, nsys 8^l) so that no launch needs a size read back, every kernel takes the box
+ * counts from device memory, the sort orders the full keys, and a device guard keeps the
+ * step from writing x4, w4 when a tree fails it (a NaN/Inf input, or a cube whose core
+ * rule no longer allows the kept level); such a step is redone uncaptured (its
+ * LHV_ENONFINITE reported as usual) and the graph is captured again at the next step.
+ * Results equal the uncaptured step's to rounding (the same kernels; atomic additions in
+ * another order).  Stage timing (lhv_set_timing) records nothing inside captured steps;
+ * lhv_get_stats reads the box counts from the device after them; lhv_export refuses the
+ * box and expansion arrays of a tree built by a captured step (LHV_EUNSUPPORTED).
+ * Needs a context created on a stream other than the legacy default stream
+ * (LHV_EUNSUPPORTED otherwise); LHV_EINVAL for enable other than 0 or 1. */
+int lhv_set_graph(lhv_ctx* ctx, int enable);
+
+/* Representation of the far field (Sec. 4.2).  LHV_FORM_PHI_CHI (the default): the two
+ * real potentials phi and chi, p^2 reals each, translated by the fused real tables
+ * [[T, C12 T], [0, C22 T]] (translation and conversion, zero block skipped).
+ * LHV_FORM_PSI: one complex harmonic function Psi = phi + i chi (Eq. chf1), stored as
+ * 2 p^2 reals (Re / Im of Psi_n^m for m >= 0, then of Psi_n^{-m}; Im Psi_n^0 in place of
+ * the m = 0 entry of the second half), translated by one dense real table per offset or
+ * octant, M F M^-1, with M the change of layout (Psi_n^m = phi_n^m + i chi_n^m, Psi_n^{-m}
+ * = (-1)^m (conj phi_n^m + i conj chi_n^m)) and F the fused table: one complex translation
+ * of Psi plus the conversions of Eqs. drt10/drt11 on the potentials split from it.  P2M
+ * produces (phi, chi) by Eq. eve4 and converts the leaf rows to Psi; L2P splits the leaf
+ * locals back.  In the scaled basis (see lhv_export) Psi combines the scaled phi and
+ * chi coefficients, i.e. Psi = phi + i h chi at box side h.  The complex form needs one
+ * truncation number at every level (LHV_EUNSUPPORTED at evaluation under
+ * lhv_set_level_p values or the selector); lhv_export then returns Psi rows for
+ * LHV_EXPORT_MULTIPOLE / LHV_EXPORT_LOCAL.  LHV_EINVAL for another value. */
+#define LHV_FORM_PHI_CHI 0
+#define LHV_FORM_PSI     1
+int lhv_set_form(lhv_ctx* ctx, int form);
 
 /* Statistics of the last tree/evaluation and the accumulated stage timings. */
 int lhv_get_stats(lhv_ctx* ctx, lhv_stats* out);

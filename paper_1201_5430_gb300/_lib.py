@@ -8,6 +8,7 @@ LIB_PATH = os.path.join(_HERE, "liblhv.so")
 LHV_OK, LHV_EINVAL, LHV_ENOMEM, LHV_ECUDA, LHV_ETIMEOUT, LHV_ENONFINITE, LHV_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 LHV_FP32, LHV_FP64, LHV_TF32X3 = 0, 1, 2
 LHV_TERMS_NEAR, LHV_TERMS_FAR, LHV_TERMS_ALL = 1, 2, 3
+LHV_FORM_PHI_CHI, LHV_FORM_PSI = 0, 1
 LHV_MAX_LEVELS = 22
 LHV_NUM_STAGES = 12
 STAGES = ["tree", "p2m", "m2m", "m2l", "l2l", "l2p", "p2p", "rk4", "ops", "copy", "m2l_products", "select"]
@@ -32,7 +33,9 @@ class Stats(ctypes.Structure):
                 ("selector_err_s", ctypes.c_double), ("tuned_p2p_targets_per_thread", ctypes.c_int),
                 ("tuned_p2p_sources_per_stage", ctypes.c_int),
                 ("tuned_m2l_pairs_per_chunk", ctypes.c_int), ("tuned_m2l_tensor_cores", ctypes.c_int),
-                ("tune_ms", ctypes.c_double * 12)]
+                ("tune_ms", ctypes.c_double * 12), ("graph_captures", ctypes.c_int64),
+                ("graph_replays", ctypes.c_int64), ("graph_fallbacks", ctypes.c_int64),
+                ("graph_kernels", ctypes.c_int64)]
 
 
 # exported function -> (restype, argtypes); every name here is declared in include/lhv.h
@@ -69,6 +72,8 @@ SIGNATURES = {
     "lhv_morton_sort_noalloc": (_int, [_i64, _vp, _vp, _vp, _vp, _vp]),
     "lhv_evaluate_potential_gradient": (_int, [_vp, _i64, _vp, _vp, _vp]),
     "lhv_evaluate_potential_gradient_f64": (_int, [_vp, _i64, _vp, _vp, _vp]),
+    "lhv_set_form": (_int, [_vp, _int]),
+    "lhv_set_graph": (_int, [_vp, _int]),
     "lhv_peak_probe": (_int, [_int, _int, _int, _vp, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl)]),
 }
 

@@ -142,6 +142,8 @@ class LHV:
             "selector": {"leaf_max": s.selector_leaf_max, "selections": s.selector_selections,
                          "checks": s.selector_checks, "fallbacks": s.selector_fallbacks,
                          "err_v": s.selector_err_v, "err_s": s.selector_err_s},
+            "graph": {"captures": s.graph_captures, "replays": s.graph_replays, "fallbacks": s.graph_fallbacks,
+                      "kernels": s.graph_kernels},
         }
 
     def autotune(self, x4, w4, offsets=None):
@@ -201,6 +203,17 @@ class LHV:
         fn = self.lib.lhv_direct_sampled_f64 if self.precision == "fp64" else self.lib.lhv_direct_sampled
         self._check(fn(self.h, x4.shape[0], _ptr(x4), _ptr(w4), m, _ptr(idx), _ptr(v), _ptr(s)), "direct_sampled")
         return v, s
+
+    def set_graph(self, enable=True):
+        """lhv_set_graph: each RK4 step (step / step_batched / step_host) as one CUDA graph
+        replay; the context must use a stream other than the legacy default stream."""
+        self._check(self.lib.lhv_set_graph(self.h, 1 if enable else 0), "set_graph")
+
+    def set_form(self, form="phi_chi"):
+        """Far-field representation (lhv_set_form): "phi_chi" (two real potentials, the default)
+        or "psi" (one complex function Psi = phi + i chi, Eq. chf1)."""
+        code = {"phi_chi": L.LHV_FORM_PHI_CHI, "psi": L.LHV_FORM_PSI}[form]
+        self._check(self.lib.lhv_set_form(self.h, code), "set_form")
 
     def set_level_p(self, p_per_level=None):
         """Truncation number per octree level (lhv_set_level_p); None restores config p."""

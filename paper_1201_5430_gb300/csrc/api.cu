@@ -70,6 +70,19 @@ struct Ctx {
     int sel_leaf = 0;
     int64_t sel_idx_n = -1;
     Buf sel_W, sel_b, sel_X, sel_Z, sel_choice, sel_idx, sel_dv, sel_ds, sel_err;
+    // whole RK4 step as one CUDA graph (lhv_set_graph)
+    bool graph_on = false;
+    int graph_L = -1;                   // >= 0 while a step runs in the captured layout (leaf level)
+    bool capturing = false;
+    bool lv_captured = false;           // the last tree was built in the captured layout
+    cudaGraphExec_t graph_exec = nullptr;
+    std::vector<double> graph_key;      // what the instantiated graph was captured for
+    int64_t graph_kernels = 0;          // kernels in it
+    int64_t graph_replays = 0, graph_captures = 0, graph_fallbacks = 0;
+    // complex form Psi = phi + i chi (lhv_set_form)
+    int form = LHV_FORM_PHI_CHI;
+    Buf psi_m2l, psi_m2m, psi_l2l, psi_tiles;
+    int psi_p = 0, psi_type = 0;
     // scalar reference case (lhv_evaluate_potential_gradient)
     Buf s_m2l, s_m2m, s_l2l, s_tiles;   // translation blocks of the fused tables, TF32 tiles of s_m2l
     int s_p = 0, s_type = 0;
@@ -90,6 +103,8 @@ int ctx_p2p_tpt(Ctx* c) { return c->tune_tpt; }
 int ctx_p2p_sources(Ctx* c) { return c->tune_ch; }
 int ctx_m2l_nc(Ctx* c, int dflt) { return c->tune_nc > 0 && c->tune_nc < dflt ? c->tune_nc : dflt; }
 bool ctx_m2l_tc(Ctx* c) { return ctx_use_tc(c) && c->tune_tc != 0; }
+int ctx_graph_level(Ctx* c) { return c->graph_L; }
+int* ctx_abort_word(Ctx* c) { return reinterpret_cast<int*>(c->counters.as<unsigned long long>() + 3); }
 
 void cuda_check(cudaError_t e, const char* what) {
     if (e != cudaSuccess) throw Error{LHV_ECUDA, std::string(what) + ": " + cudaGetErrorString(e)};
@@ -98,9 +113,10 @@ void cuda_check(cudaError_t e, const char* what) {
 void check_launch(const char* what) { cuda_check(cudaGetLastError(), what); }
 
 void ensure(Ctx* c, Buf& b, int64_t bytes) {
-    (void)c;
     if (bytes <= 0) bytes = 16;
     if ((size_t)bytes <= b.cap) return;
+    // a capture follows an uncaptured step in the same layout, which sized every buffer
+    if (c->capturing) throw Error{LHV_ECUDA, "buffer growth inside a graph capture"};
     if (b.ptr) cudaFree(b.ptr);
     b.ptr = nullptr;
     b.cap = 0;
@@ -125,13 +141,13 @@ struct StageScope {
     int stage;
     cudaEvent_t a = nullptr, b = nullptr;
     StageScope(Ctx* ctx, int s) : c(ctx), stage(s) {
-        if (!c->timing) return;
+        if (!c->timing || c->graph_L >= 0) return;  // no stage events in the captured layout
         a = take();
         b = take();
         cuda_check(cudaEventRecord(a, c->stream), "event");
     }
     ~StageScope() {
-        if (!c->timing || !a) return;
+        if (!a) return;
         if (cudaEventRecord(b, c->stream) == cudaSuccess) c->pending.push_back({stage, a, b});
     }
     cudaEvent_t take() {
@@ -237,6 +253,26 @@ static CsrView<T> cached_sparse(Ctx* c, int kind, int p) {
     return view<T>(it->second);
 }
 
+// Tables of the complex form Psi = phi + i chi (Sec. 4.2): M F M^-1 of the fused tables.
+template <typename T>
+static void ensure_psi_ops(Ctx* c) {
+    if (c->psi_p == c->cfg.p && c->psi_type == (int)sizeof(T)) return;
+    StageScope sc(c, LHV_STAGE_OPS);
+    const int P = c->ops.P;
+    psi_form<T>(c, c->ops.m2l.as<T>(), NUM_OFFSETS, P, c->psi_m2l);
+    psi_form<T>(c, c->ops.m2m.as<T>(), 8, P, c->psi_m2m);
+    psi_form<T>(c, c->ops.l2l.as<T>(), 8, P, c->psi_l2l);
+    if constexpr (sizeof(T) == 4) {
+        if (ctx_use_tc(c) && tc_supported(2 * P, 2 * P, 0))
+            tc_tiles_build(c, c->psi_m2l.as<float>(), NUM_OFFSETS, 2 * P, 2 * P, 0, c->psi_tiles);
+        else
+            release(c->psi_tiles);
+    }
+    cuda_check(cudaStreamSynchronize(c->stream), "psi tables");
+    c->psi_p = c->cfg.p;
+    c->psi_type = (int)sizeof(T);
+}
+
 // Truncation numbers and tables of an evaluation over levels 0..L.
 template <typename T>
 static Plan<T> make_plan(Ctx* c, int L) {
@@ -253,6 +289,23 @@ static Plan<T> make_plan(Ctx* c, int L) {
     pl.ld = (2 * pmax * pmax + 7) / 8 * 8;  // 32-byte rows for the vector loads of the tensor-core path
     const bool base = pl.uniform && pl.p[L] == c->cfg.p;
     const bool tc = sizeof(T) == 4 && ctx_use_tc(c);
+    if (c->form == LHV_FORM_PSI) {
+        if (!base)
+            throw Error{LHV_EUNSUPPORTED, "the complex form runs one truncation number at every level"};
+        ensure_psi_ops<T>(c);
+        pl.psi = true;
+        pl.p2m = c->ops.p2m.as<T>();
+        pl.l2p = c->ops.l2p.as<T>();
+        for (int l = 0; l <= L; ++l) {
+            pl.m2m[l] = c->psi_m2m.as<T>();
+            pl.l2l[l] = c->psi_l2l.as<T>();
+            pl.m2l[l] = c->psi_m2l.as<T>();
+            pl.m2l_tiles[l] = c->psi_tiles.ptr ? c->psi_tiles.as<float>() : nullptr;
+        }
+        pl.p2m_sp = view<T>(c->ops.p2m_sp);
+        pl.l2p_sp = view<T>(c->ops.l2p_sp);
+        return pl;
+    }
     if (base) {
         pl.p2m = c->ops.p2m.as<T>();
         pl.l2p = c->ops.l2p.as<T>();
@@ -286,6 +339,7 @@ static int tree_stage(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const 
     StageScope sc(c, LHV_STAGE_TREE);
     int st = build_tree<T>(c, n, nsys, sysoff, x4, w4, c->tb, c->lv, c->hp, err);
     if (st != LHV_OK) return st;
+    c->lv_captured = c->graph_L >= 0;
     c->tree_n = n;
     ensure(c, c->xs, n * (int64_t)sizeof(vec4_t<T>));
     ensure(c, c->ws, n * (int64_t)sizeof(vec4_t<T>));
@@ -338,6 +392,8 @@ static int evaluate(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const ve
         {
             StageScope sc(c, LHV_STAGE_P2M);
             run_p2m<T>(c, pl, c->tb, lv, xs, ws, c->W.as<T>(), mult);
+            // complex form: the leaf multipoles (phi, chi) of Eq. eve4 become Psi (Eq. chf1)
+            if (pl.psi) psi_rows<T>(c, lv.nbox[L], PL, pl.ld, mult + (int64_t)lv.off[L] * pl.ld, true);
         }
         {
             StageScope sc(c, LHV_STAGE_M2M);
@@ -345,9 +401,7 @@ static int evaluate(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const ve
         }
         {
             StageScope sc(c, LHV_STAGE_M2L);
-            cuda_check(cudaMemsetAsync(loc + (int64_t)lv.off[2] * pl.ld, 0,
-                                       sizeof(T) * (size_t)(nbt - lv.off[2]) * pl.ld, c->stream),
-                       "zero locals");
+            fill_level_rows<T>(c, lv, c->tb.counts.as<int>(), 2, L, pl.ld, 0, loc, (T)0);  // zero locals
             int pmax = 1;
             bool all_tc = sizeof(T) == 4 && ctx_m2l_tc(c);
             for (int l = 2; l <= L; ++l) {
@@ -358,7 +412,7 @@ static int evaluate(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const ve
             const int nc = all_tc && c->tune_nc == 0 ? TC_PAIRS : ctx_m2l_nc(c, gemm_nc<T>(2 * pmax * pmax));
             m2l_prepare(c, c->ops, c->tb, lv, c->table.as<int>(), c->gp_m2l, nc, pl.uniform, cnt + 1);
             StageScope sg(c, LHV_STAGE_M2L_PRODUCTS);
-            m2l_apply<T>(c, pl, lv, c->gp_m2l, mult, loc);
+            m2l_apply<T>(c, pl, lv, c->tb.counts.as<int>(), c->gp_m2l, mult, loc);
         }
         {
             StageScope sc(c, LHV_STAGE_L2L);
@@ -368,7 +422,18 @@ static int evaluate(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const ve
         sfar = c->sfar.as<vec4_t<T>>();
         {
             StageScope sc(c, LHV_STAGE_L2P);
-            run_l2p<T>(c, pl, c->tb, lv, xs, ws, loc, vfar, sfar);
+            const T* lloc = loc;
+            if (pl.psi) {  // complex form: phi, chi of the leaf locals, split from Psi, for Eqs. evf3, dt3
+                Buf& tb2 = c->tmp[5];
+                ensure(c, tb2, nbt * pl.ld * (int64_t)sizeof(T));
+                T* dst = tb2.as<T>() + (int64_t)lv.off[L] * pl.ld;
+                cuda_check(cudaMemcpyAsync(dst, loc + (int64_t)lv.off[L] * pl.ld,
+                                           sizeof(T) * (size_t)nleaf * pl.ld, cudaMemcpyDeviceToDevice, c->stream),
+                           "leaf locals");
+                psi_rows<T>(c, nleaf, PL, pl.ld, dst, false);
+                lloc = tb2.as<T>();
+            }
+            run_l2p<T>(c, pl, c->tb, lv, xs, ws, lloc, vfar, sfar);
         }
     }
     {
@@ -479,14 +544,12 @@ static int evaluate_scalar(Ctx* c, int64_t n, const vec4_t<T>* x4, const T* q, v
         }
         {
             StageScope sc(c, LHV_STAGE_M2L);
-            cuda_check(cudaMemsetAsync(loc + (int64_t)lv.off[2] * pl.ld, 0,
-                                       sizeof(T) * (size_t)(nbt - lv.off[2]) * pl.ld, c->stream),
-                       "zero locals");
+            fill_level_rows<T>(c, lv, c->tb.counts.as<int>(), 2, L, pl.ld, 0, loc, (T)0);  // zero locals
             const bool tc = sizeof(T) == 4 && ctx_m2l_tc(c) && pl.m2l_tiles[2];
             const int nc = tc && c->tune_nc == 0 ? TC_PAIRS : ctx_m2l_nc(c, gemm_nc<T>(P));
             m2l_prepare(c, c->ops, c->tb, lv, c->table.as<int>(), c->gp_m2l, nc, true, cnt + 1);
             StageScope sg(c, LHV_STAGE_M2L_PRODUCTS);
-            m2l_apply<T>(c, pl, lv, c->gp_m2l, mult, loc);
+            m2l_apply<T>(c, pl, lv, c->tb.counts.as<int>(), c->gp_m2l, mult, loc);
         }
         {
             StageScope sc(c, LHV_STAGE_L2L);
@@ -699,6 +762,13 @@ static int step(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, vec4_t<T>* x
     // k1..k4 of the classical tableau; the caller's x, w are y0 until the end
     const double c_acc[4] = {1.0, 2.0, 2.0, 1.0};
     const double c_stage[4] = {0.5 * dt, 0.5 * dt, dt, 0.0};
+    if (c->graph_L >= 0) {
+        if (!c->counters.ptr) {
+            ensure(c, c->counters, 64);
+            cuda_check(cudaMemsetAsync(c->counters.ptr, 0, 64, c->stream), "counters init");
+        }
+        cuda_check(cudaMemsetAsync(ctx_abort_word(c), 0, sizeof(int), c->stream), "abort word");
+    }
     for (int k = 0; k < 4; ++k) {
         const vec4_t<T>* xin = (k == 0) ? x4 : sx;
         const vec4_t<T>* win = (k == 0) ? w4 : sw;
@@ -711,6 +781,111 @@ static int step(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, vec4_t<T>* x
     }
     StageScope sc(c, LHV_STAGE_RK4);
     run_rk4_final<T>(c, n, x4, w4, ax, aw, dt / 6.0);  // y = y0 + dt/6 (k1 + 2 k2 + 2 k3 + k4)
+    return LHV_OK;
+}
+
+// ---- the whole RK4 step as one CUDA graph ---------------------------------------------
+// A captured step runs the same kernels in the captured layout: the leaf level fixed at
+// capture (the one the step's first tree had), box arrays at per-level capacities
+// min(n, nsys 8^l) so that every launch is sized without reading the tree back, every
+// loop bounded by the device box counts, a full sort, and a device guard that keeps the
+// step from writing x, w if a tree fails it (non-finite input, or a cube whose core-rule
+// cap fell below the fixed level).  The host reads the guard once after the replay and
+// redoes such a step uncaptured.
+static bool graph_eligible(Ctx* c) {
+    if (!c->graph_on || c->cfg.precision == LHV_FP64 || c->sel_active || c->stream == nullptr) return false;
+    for (int l = 0; l <= MAX_LEVELS; ++l)
+        if (c->level_p[l] > 0 && c->level_p[l] != c->cfg.p) return false;
+    return true;
+}
+
+static std::vector<double> graph_key(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const void* x4,
+                                     const void* w4, double dt) {
+    std::vector<double> k = {(double)n, (double)nsys, (double)(uintptr_t)x4, (double)(uintptr_t)w4, dt,
+                             (double)c->cfg.p, (double)c->cfg.precision, (double)c->form, (double)c->tune_tpt,
+                             (double)c->tune_ch, (double)c->tune_nc, (double)c->tune_tc};
+    for (int i = 0; i <= nsys; ++i) k.push_back((double)sysoff[i]);
+    return k;
+}
+
+static void drop_graph(Ctx* c) {
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    c->graph_exec = nullptr;
+    c->graph_key.clear();
+}
+
+// runs a step in the captured layout without capturing it; false if its guard fired
+// (then x4, w4 are unchanged)
+static bool layout_step(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, float4* x4, float4* w4, double dt, int L) {
+    c->graph_L = L;
+    try {
+        step<float>(c, n, nsys, sysoff, x4, w4, dt);
+    } catch (...) {
+        c->graph_L = -1;
+        throw;
+    }
+    c->graph_L = -1;
+    int abort_word = 0;
+    cuda_check(cudaMemcpyAsync(&abort_word, ctx_abort_word(c), sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+               "guard");
+    cuda_check(cudaStreamSynchronize(c->stream), "guard sync");
+    return abort_word == 0;
+}
+
+static int graphed_step(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, float4* x4, float4* w4, double dt) {
+    if (n == 0) return LHV_OK;
+    std::vector<double> key = graph_key(c, n, nsys, sysoff, x4, w4, dt);
+    if (c->graph_exec && key == c->graph_key) {
+        cuda_check(cudaGraphLaunch(c->graph_exec, c->stream), "graph launch");
+        c->launches += c->graph_kernels;
+        ++c->graph_replays;
+        int abort_word = 0;
+        cuda_check(cudaMemcpyAsync(&abort_word, ctx_abort_word(c), sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+                   "guard");
+        cuda_check(cudaStreamSynchronize(c->stream), "guard sync");
+        if (abort_word == 0) return LHV_OK;
+        ++c->graph_fallbacks;  // x4, w4 untouched: redo the step uncaptured, capture again next time
+        drop_graph(c);
+        return step<float>(c, n, nsys, sysoff, x4, w4, dt);
+    }
+    drop_graph(c);
+    // the leaf level of the captured layout: that of the first tree of this step
+    Error err{LHV_OK, ""};
+    if (tree_stage<float>(c, n, nsys, sysoff, x4, w4, err) != LHV_OK) throw err;
+    const int L = c->lv.L;
+    if (!layout_step(c, n, nsys, sysoff, x4, w4, dt, L)) {
+        ++c->graph_fallbacks;
+        return step<float>(c, n, nsys, sysoff, x4, w4, dt);
+    }
+    // capture the same step for the next calls (it sized every buffer; nothing runs now)
+    cudaGraph_t graph = nullptr;
+    const int64_t before = c->launches;
+    cuda_check(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed), "begin capture");
+    c->capturing = true;
+    c->graph_L = L;
+    try {
+        step<float>(c, n, nsys, sysoff, x4, w4, dt);
+    } catch (...) {
+        c->capturing = false;
+        c->graph_L = -1;
+        cudaStreamEndCapture(c->stream, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        throw;
+    }
+    c->capturing = false;
+    c->graph_L = -1;
+    cuda_check(cudaStreamEndCapture(c->stream, &graph), "end capture");
+    const cudaError_t ie = cudaGraphInstantiate(&c->graph_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+        c->graph_exec = nullptr;
+        cuda_check(ie, "graph instantiate");
+    }
+    c->graph_kernels = c->launches - before;
+    c->launches = before;
+    c->graph_key = key;
+    ++c->graph_captures;
     return LHV_OK;
 }
 
@@ -857,13 +1032,15 @@ void lhv_destroy(lhv_ctx* ctx) {
         cudaEventDestroy(r.b);
     }
     for (auto e : c.pool) cudaEventDestroy(e);
+    lhv::drop_graph(&c);
     lhv::free_operators(c.ops);
     for (auto& kv : c.opcache) lhv::release(kv.second);
     c.opcache.clear();
     for (auto& kv : c.spcache) lhv::free_csr(kv.second);
     c.spcache.clear();
     for (auto* b : {&c.sel_W, &c.sel_b, &c.sel_X, &c.sel_Z, &c.sel_choice, &c.sel_idx, &c.sel_dv, &c.sel_ds, &c.sel_err,
-                    &c.s_m2l, &c.s_m2m, &c.s_l2l, &c.s_tiles, &c.qs, &c.pgfar})
+                    &c.s_m2l, &c.s_m2m, &c.s_l2l, &c.s_tiles, &c.qs, &c.pgfar, &c.psi_m2l, &c.psi_m2m,
+                    &c.psi_l2l, &c.psi_tiles})
         lhv::release(*b);
     lhv::TreeBufs& t = c.tb;
     lhv::Buf* tree[] = {&t.keys_a, &t.keys_b, &t.idx_a, &t.idx_b, &t.hist, &t.boxof_a, &t.boxof_b, &t.flags,
@@ -932,7 +1109,23 @@ int lhv_step(lhv_ctx* ctx, int64_t n, float* x4, float* w4, double dt) {
     if (!std::isfinite(dt)) return LHV_EINVAL;
     return guarded(ctx, [&] {
         const int64_t off[2] = {0, n};
+        if (lhv::graph_eligible(&ctx->c))
+            return lhv::graphed_step(&ctx->c, n, 1, off, reinterpret_cast<float4*>(x4), reinterpret_cast<float4*>(w4),
+                                     dt);
         return lhv::step<float>(&ctx->c, n, 1, off, reinterpret_cast<float4*>(x4), reinterpret_cast<float4*>(w4), dt);
+    });
+}
+
+int lhv_set_graph(lhv_ctx* ctx, int enable) {
+    if (!ctx || (enable != 0 && enable != 1)) return LHV_EINVAL;
+    return guarded(ctx, [&] {
+        if (enable && ctx->c.stream == nullptr) {
+            ctx->c.last_error = "graph capture needs a context stream other than the legacy default stream";
+            return LHV_EUNSUPPORTED;
+        }
+        ctx->c.graph_on = enable != 0;
+        if (!enable) lhv::drop_graph(&ctx->c);
+        return LHV_OK;
     });
 }
 
@@ -1006,7 +1199,8 @@ int lhv_step_host(lhv_ctx* ctx, int64_t n, float* x4_host, float* w4_host, doubl
             lhv::cuda_check(cudaMemcpyAsync(c.hw.ptr, w4_host, bytes, cudaMemcpyHostToDevice, c.stream), "h2d w");
         }
         const int64_t off[2] = {0, n};
-        int st = lhv::step<float>(&c, n, 1, off, c.hx.as<float4>(), c.hw.as<float4>(), dt);
+        int st = lhv::graph_eligible(&c) ? lhv::graphed_step(&c, n, 1, off, c.hx.as<float4>(), c.hw.as<float4>(), dt)
+                                         : lhv::step<float>(&c, n, 1, off, c.hx.as<float4>(), c.hw.as<float4>(), dt);
         if (st != LHV_OK) return st;
         {
             lhv::StageScope sc(&c, LHV_STAGE_COPY);
@@ -1047,6 +1241,9 @@ int lhv_step_batched(lhv_ctx* ctx, int nsys, const int64_t* offsets, float* x4, 
     if (st != LHV_OK) return st;
     if (!std::isfinite(dt)) return LHV_EINVAL;
     return guarded(ctx, [&] {
+        if (lhv::graph_eligible(&ctx->c))
+            return lhv::graphed_step(&ctx->c, n, nsys, offsets, reinterpret_cast<float4*>(x4),
+                                     reinterpret_cast<float4*>(w4), dt);
         return lhv::step<float>(&ctx->c, n, nsys, offsets, reinterpret_cast<float4*>(x4), reinterpret_cast<float4*>(w4),
                                 dt);
     });
@@ -1078,6 +1275,12 @@ int lhv_get_stats(lhv_ctx* ctx, lhv_stats* out) {
         std::memset(out, 0, sizeof(*out));
         out->leaf_level = c.lv.L;
         for (int l = 0; l < LHV_MAX_LEVELS; ++l) out->nbox[l] = c.lv.nbox[l];
+        if (c.lv_captured && c.tb.counts.ptr) {  // the host holds capacities: read the counts
+            int h[64];
+            lhv::cuda_check(cudaMemcpyAsync(h, c.tb.counts.ptr, 64 * 4, cudaMemcpyDeviceToHost, c.stream), "counts");
+            lhv::cuda_check(cudaStreamSynchronize(c.stream), "counts sync");
+            for (int l = 0; l < LHV_MAX_LEVELS; ++l) out->nbox[l] = l <= c.lv.L ? h[l] : 0;
+        }
         for (int l = 0; l < LHV_MAX_LEVELS; ++l) out->level_p[l] = c.eval_p[l];
         out->selector_leaf_max = c.sel_leaf;
         out->selector_selections = c.sel_selections;
@@ -1107,6 +1310,10 @@ int lhv_get_stats(lhv_ctx* ctx, lhv_stats* out) {
             out->stage_launches[i] = c.stage_launches[i];
         }
         out->kernel_launches = c.launches;
+        out->graph_captures = c.graph_captures;
+        out->graph_replays = c.graph_replays;
+        out->graph_fallbacks = c.graph_fallbacks;
+        out->graph_kernels = c.graph_kernels;
         return LHV_OK;
     });
 }
@@ -1212,6 +1419,12 @@ int lhv_autotune_batched(lhv_ctx* ctx, int nsys, const int64_t* offsets, const f
     });
 }
 
+int lhv_set_form(lhv_ctx* ctx, int form) {
+    if (!ctx || (form != LHV_FORM_PHI_CHI && form != LHV_FORM_PSI)) return LHV_EINVAL;
+    ctx->c.form = form;
+    return LHV_OK;
+}
+
 int lhv_set_level_p(lhv_ctx* ctx, const int* p, int nlevels) {
     if (!ctx || nlevels < 0 || nlevels > LHV_MAX_LEVELS || (nlevels > 0 && !p)) return LHV_EINVAL;
     for (int l = 0; l < nlevels; ++l)
@@ -1226,6 +1439,10 @@ int lhv_export(lhv_ctx* ctx, int what, int level, void* dst, int64_t capacity_by
         Ctx& c = ctx->c;
         const lhv::Levels& lv = c.lv;
         const int64_t n = c.tree_n;
+        if (c.lv_captured && what != LHV_EXPORT_KEYS && what != LHV_EXPORT_PERM && what != LHV_EXPORT_CUBE) {
+            c.last_error = "the last tree was built by a captured step (capacity layout); build it with lhv_build_tree";
+            return LHV_EUNSUPPORTED;
+        }
         const void* src = nullptr;
         int64_t bytes = 0;
         const bool lvl_ok = level >= 0 && level <= lv.L;

@@ -197,10 +197,11 @@ __global__ void __launch_bounds__(P2M_THREADS) k_p2m_w(const int* __restrict__ n
 // P2M, part 2 (per leaf): M_hat = G W with G the P2M map of Eq. eve4 in row-compressed form
 // (its structural zeros dropped); one block per leaf, W staged in shared memory.
 template <typename T>
-__global__ void __launch_bounds__(P2M_THREADS) k_p2m_apply(int nleaf, const T* __restrict__ W, int P,
-                                                          CsrView<T> g, T* __restrict__ mult, int64_t ld) {
+__global__ void __launch_bounds__(P2M_THREADS) k_p2m_apply(const int* __restrict__ nleaf_dev, const T* __restrict__ W,
+                                                          int P, CsrView<T> g, T* __restrict__ mult, int64_t ld) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* w = reinterpret_cast<T*>(smem_raw);  // [3P]
+    const int nleaf = *nleaf_dev;
     for (int b = blockIdx.x; b < nleaf; b += gridDim.x) {
         __syncthreads();
         for (int i = threadIdx.x; i < 3 * P; i += blockDim.x) w[i] = W[(int64_t)b * 3 * P + i];
@@ -399,7 +400,8 @@ void run_p2m(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, co
     const size_t smem = sizeof(T) * ((size_t)chunk * (P + 3) + qtab_reals(p));
     cuda_check(cudaFuncSetAttribute(k_p2m_w<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                "p2m attr");
-    cuda_check(cudaMemsetAsync(W, 0, sizeof(T) * (size_t)nl * 3 * P, stream_of(c)), "p2m zero");
+    const int* count = tb.counts.as<int>();
+    fill_level_rows<T>(c, lv, count, L, L, 3 * P, o, W, (T)0);  // W of the real leaves
     const int64_t max_tiles = nl + lv.n / P2P_TILE + 1;
     k_p2m_w<T, 3><<<grid_for(max_tiles, 1, 152 * 16), P2M_THREADS, smem, stream_of(c)>>>(
         tb.tile_count.as<int>(), tb.tiles.as<int2>(), L, tb.bkey.as<uint64_t>() + o, tb.bend.as<int>() + o,
@@ -409,7 +411,7 @@ void run_p2m(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, co
     const size_t smem2 = sizeof(T) * 3 * P;
     cuda_check(cudaFuncSetAttribute(k_p2m_apply<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2),
                "p2m apply attr");
-    k_p2m_apply<T><<<grid_for(nl, 1, 152 * 16), P2M_THREADS, smem2, stream_of(c)>>>(nl, W, P, pl.p2m_sp,
+    k_p2m_apply<T><<<grid_for(nl, 1, 152 * 16), P2M_THREADS, smem2, stream_of(c)>>>(count + L, W, P, pl.p2m_sp,
                                                                                    mult + (int64_t)o * pl.ld, pl.ld);
     count_launch(c);
     check_launch("p2m apply");
@@ -420,6 +422,7 @@ static OctItems oct_items(const TreeBufs& tb, const Levels& lv, bool up) {
     OctItems it{};
     it.bkey = tb.bkey.as<uint64_t>();
     it.bparent = tb.bparent.as<int>();
+    it.loff = tb.counts.as<int>() + 32;  // the level scan's offsets of the real boxes
     for (int l = 0; l <= MAX_LEVELS; ++l) it.off[l] = lv.off[l];
     it.lo = 3;
     it.hi = lv.L;
@@ -440,9 +443,7 @@ void run_m2m(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, Gr
     const int L = lv.L;
     if (L < 3) return;
     // parents of the levels 2 .. L-1 accumulate atomically
-    cuda_check(cudaMemsetAsync(mult + (int64_t)lv.off[2] * pl.ld, 0,
-                               sizeof(T) * (size_t)(lv.off[L] - lv.off[2]) * pl.ld, stream_of(c)),
-               "m2m zero");
+    fill_level_rows<T>(c, lv, tb.counts.as<int>(), 2, L - 1, pl.ld, 0, mult, (T)0);
     const int nitems = lv.off[L + 1] - lv.off[3];
     build_grouped(c, gp, (L - 2) * 8, nitems, nitems, oct_nc(pl), oct_items<T>(tb, lv, true));
     for (int l = L - 1; l >= 2; --l) {
@@ -452,10 +453,10 @@ void run_m2m(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, Gr
         a.g1 = a.g0 + 8;
         a.ops = pl.m2m[l];
         a.ops_mod = 8;
-        a.R = pl.scalar ? Pout : 2 * Pout;  // scalar case: the translation block alone, no chi
-        a.C = pl.scalar ? Pin : 2 * Pin;
-        a.psplit = pl.scalar ? 0 : Pout;
-        a.psplit_c = pl.scalar ? 0 : Pin;
+        a.R = pl.rows(Pout);  // scalar case: the translation block alone, no chi
+        a.C = pl.rows(Pin);
+        a.psplit = pl.split_out(Pout);
+        a.psplit_c = pl.split_out(Pin);
         a.in = mult;
         a.ldin = pl.ld;
         a.out = mult;
@@ -481,10 +482,10 @@ void run_l2l(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, Gr
         a.g1 = a.g0 + 8;
         a.ops = pl.l2l[l + 1];
         a.ops_mod = 8;
-        a.R = pl.scalar ? Pout : 2 * Pout;
-        a.C = pl.scalar ? Pin : 2 * Pin;
-        a.psplit = pl.scalar ? 0 : Pout;
-        a.psplit_c = pl.scalar ? 0 : Pin;
+        a.R = pl.rows(Pout);
+        a.C = pl.rows(Pin);
+        a.psplit = pl.split_out(Pout);
+        a.psplit_c = pl.split_out(Pin);
         a.in = loc;
         a.ldin = pl.ld;
         a.out = loc;
@@ -523,7 +524,7 @@ void run_p2m_scalar(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels&
     cuda_check(cudaFuncSetAttribute(k_p2m_w<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                "p2m attr");
     T* leaf_rows = mult + (int64_t)o * pl.ld;
-    cuda_check(cudaMemsetAsync(leaf_rows, 0, sizeof(T) * (size_t)nl * pl.ld, stream_of(c)), "p2m zero");
+    fill_level_rows<T>(c, lv, tb.counts.as<int>(), L, L, pl.ld, 0, mult, (T)0);
     const int64_t max_tiles = nl + lv.n / P2P_TILE + 1;
     k_p2m_w<T, 1><<<grid_for(max_tiles, 1, 152 * 16), P2M_THREADS, smem, stream_of(c)>>>(
         tb.tile_count.as<int>(), tb.tiles.as<int2>(), L, tb.bkey.as<uint64_t>() + o, tb.bend.as<int>() + o,

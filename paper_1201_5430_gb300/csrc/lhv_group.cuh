@@ -46,6 +46,7 @@ struct GemmArgs {
 template <class Items>
 __global__ void k_emit(int64_t n, Items it, int fill, int* __restrict__ gcount, int* __restrict__ gcursor,
                        int2* __restrict__ pairs) {
+    n = min(n, it.limit());  // the items of real boxes (device counts)
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         int g, s, d;
         if (!it(i, g, s, d)) continue;
@@ -95,23 +96,30 @@ void tc_tiles_build(Ctx* c, const float* ops, int ngroups, int R, int C, int psp
 // in_hi / in_lo: the TF32 split of a.in (same layout), from tc_split.
 void run_tc_gemm(Ctx* c, Grouped& gp, GemmArgs<float> a, const float* tiles, const float* in_hi,
                  const float* in_lo, int* err);
-void tc_split(Ctx* c, int64_t n, const float* x, float* hi, float* lo);
+// hi / lo of the rows of the real boxes of levels l0..l1 (ld reals each; device counts)
+void tc_split(Ctx* c, const Levels& lv, const int* count, int l0, int l1, int64_t ld, const float* x, float* hi,
+              float* lo);
 
 // Item sources ---------------------------------------------------------------
 
 // Children of the levels [lo, hi] (global box indices off[lo] .. off[hi+1]-1)
 // with their parents; group = (level - lo) * 8 + octant (key & 7).
 // up = true : child -> parent (M2M);  up = false : parent -> child (L2L).
+// Items run over the real boxes, numbered by loff (the device exclusive scan of the counts);
+// a box's slot is off[l] + its index in the level.
 struct OctItems {
     const uint64_t* bkey;
     const int* bparent;
+    const int* loff;          // real boxes before each level (device)
     int off[MAX_LEVELS + 1];
     int lo, hi;
     bool up;
+    __device__ int64_t limit() const { return loff[hi + 1] - loff[lo]; }
     __device__ bool operator()(int64_t i, int& g, int& s, int& d) const {
-        const int b = off[lo] + (int)i;
+        const int rb = loff[lo] + (int)i;
         int l = lo;
-        while (l < hi && b >= off[l + 1]) ++l;
+        while (l < hi && rb >= loff[l + 1]) ++l;
+        const int b = off[l] + (rb - loff[l]);
         const int par = off[l - 1] + bparent[b];
         g = (l - lo) * 8 + (int)(bkey[b] & 7ull);
         if (up) {
@@ -129,22 +137,23 @@ struct OctItems {
 // by_level = false: group = offset slot (pairs of all levels share the operator);
 // by_level = true : group = (level - 2) * 316 + slot (each level has its own p).
 struct M2LItems {
-    const int* table;  // rows for the targets [t0, ...)
+    const int* table;  // rows for the target slots [t0, ...)
+    const int* loff;   // real boxes before each level (device)
     int t0;
     bool by_level;
     int L;
     int off[MAX_LEVELS + 2];  // global box offsets of the levels
+    __device__ int64_t limit() const { return (int64_t)(loff[L + 1] - loff[2]) * NUM_OFFSETS; }
     __device__ bool operator()(int64_t i, int& g, int& s, int& d) const {
-        const int src = table[i];
+        const int rb = loff[2] + (int)(i / NUM_OFFSETS), slot = (int)(i % NUM_OFFSETS);
+        int l = 2;
+        while (l < L && rb >= loff[l + 1]) ++l;
+        d = off[l] + (rb - loff[l]);
+        const int src = table[(int64_t)(d - t0) * NUM_OFFSETS + slot];
         if (src < 0) return false;
-        g = (int)(i % NUM_OFFSETS);
+        g = slot;
         s = src;
-        d = t0 + (int)(i / NUM_OFFSETS);
-        if (by_level) {
-            int l = 2;
-            while (l < L && d >= off[l + 1]) ++l;
-            g += (l - 2) * NUM_OFFSETS;
-        }
+        if (by_level) g += (l - 2) * NUM_OFFSETS;
         return true;
     }
 };

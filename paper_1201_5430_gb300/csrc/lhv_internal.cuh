@@ -61,13 +61,21 @@ struct Error {
 // Per-level box arrays inside the flat box arrays.
 struct Levels {
     int L = -1;
-    int nbox[MAX_LEVELS] = {0};
+    int nbox[MAX_LEVELS] = {0};      // box slots per level: the counts, or in a captured step the
+                                     // capacities (the device counts, tb.counts, bound every loop)
     int off[MAX_LEVELS + 1] = {0};   // global box index of the first box of each level
     int cap_off[MAX_LEVELS + 1] = {0};
     int64_t n = 0;                   // elements of the tree
 };
 
 struct Ctx;
+
+// Offsets of the levels in the global box order (by value into kernels): level l owns the
+// box slots [off[l], off[l + 1]), holding the actual boxes, or capacities in a captured step.
+struct LevelTable {
+    int L;
+    int off[MAX_LEVELS + 2];
+};
 
 // ---- context accessors and helpers (api.cu) ---------------------------------
 void count_launch(Ctx* c);
@@ -86,6 +94,8 @@ int ctx_p2p_tpt(Ctx* c);                             // P2P targets per thread (
 int ctx_p2p_sources(Ctx* c);                         // P2P sources per shared-memory stage (128 or 256)
 int ctx_m2l_nc(Ctx* c, int dflt);                    // M2L pairs per SIMT GEMM chunk (autotuned, <= dflt)
 bool ctx_m2l_tc(Ctx* c);                             // M2L products on the tensor cores (TF32x3, autotuned)
+int ctx_graph_level(Ctx* c);                         // leaf level of a step being captured as a graph (-1: none)
+int* ctx_abort_word(Ctx* c);                         // device word: a captured step must not write its result
 
 inline int grid_for(int64_t n, int block, int cap = 152 * 32) {
     int64_t g = (n + block - 1) / block;
@@ -113,6 +123,11 @@ template <typename T>
 int build_tree(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const vec4_t<T>* x4, const vec4_t<T>* w4,
                TreeBufs& tb, Levels& lv, TreeParams& hp, Error& err);
 int key_bits_for(int nsys);
+// Rows of the real boxes of levels l0..l1 (device counts dcount[l]; row r of a level at
+// data + (r - row0) row_len, r from lv.off[l]) set to value.
+template <typename T>
+void fill_level_rows(Ctx* c, const Levels& lv, const int* dcount, int l0, int l1, int64_t row_len, int64_t row0,
+                     T* data, T value);
 
 // Device-wide exclusive scan of int32 (in may equal out); *total_out (device) gets the sum.
 void exclusive_scan(Ctx* c, int64_t n, const int* in, int* out, int* tmp, int* total_out);
@@ -171,6 +186,12 @@ void free_operators(OpTables& ops);
 // dst = the translation block T ([P][P] per group, k-major) of ngroups fused [2P][2P] tables.
 template <typename T>
 void translation_block(Ctx* c, const T* fused, int ngroups, int P, Buf& dst);
+// Complex form Psi = phi + i chi (Eq. chf1): dst = M F M^-1 for ngroups fused [2P][2P] tables F
+// (dense [2P][2P] each), and the in-place change of layout of nrows coefficient rows.
+template <typename T>
+void psi_form(Ctx* c, const T* fused, int ngroups, int P, Buf& dst);
+template <typename T>
+void psi_rows(Ctx* c, int64_t nrows, int P, int64_t ld, T* rows, bool to_psi);
 int m2l_slot_host(int dx, int dy, int dz);   // same mapping as slot_of, on the host
 
 struct Grouped;
@@ -194,6 +215,11 @@ struct Plan {
     bool uniform = true;                   // p[l] equal over l = 2..L
     bool scalar = false;                   // scalar reference case: one potential, P x P translation
                                            // tables (the T block of the fused operators), no conversion
+    bool psi = false;                      // complex form Psi = phi + i chi: dense 2P x 2P tables
+    // output / input split of a fused translation table (its zero block is skipped);
+    // 0 (dense) in the complex form
+    int split_out(int P) const { return (scalar || psi) ? 0 : P; }
+    int rows(int P) const { return scalar ? P : 2 * P; }
 };
 
 // ---- expansions (expansions.cu) ----------------------------------------------
@@ -226,9 +252,9 @@ void run_l2p_scalar(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels&
 // uniform: pairs of all levels bucketed by offset; else by (level, offset).
 void m2l_prepare(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& lv, int* table, Grouped& gp,
                  int nc, bool uniform, unsigned long long* pair_counter);
-// the products; loc must be zero for levels >= 2.
+// the products; loc must be zero for levels >= 2; count: boxes per level (device).
 template <typename T>
-void m2l_apply(Ctx* c, const Plan<T>& pl, const Levels& lv, Grouped& gp, const T* mult, T* loc);
+void m2l_apply(Ctx* c, const Plan<T>& pl, const Levels& lv, const int* count, Grouped& gp, const T* mult, T* loc);
 
 // ---- P2P (p2p.cu) ------------------------------------------------------------
 template <typename T>

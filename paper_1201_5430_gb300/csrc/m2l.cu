@@ -34,18 +34,20 @@ struct TableLevels {
 // table is cleared to -1 before).  One thread per (target box of any level 2 .. L,
 // colleague q of its parent): the children of that colleague that are not
 // colleagues of the target.
-__global__ void k_m2l_table(int t0, int nt, TableLevels lv, const uint64_t* __restrict__ bkey,
-                            const int* __restrict__ bparent, const int* __restrict__ bcol,
-                            const int* __restrict__ bcbeg, const int* __restrict__ bcend,
-                            const int* __restrict__ slot_of, int* __restrict__ table,
+__global__ void k_m2l_table(int t0, TableLevels lv, const int* __restrict__ loff,
+                            const uint64_t* __restrict__ bkey, const int* __restrict__ bparent,
+                            const int* __restrict__ bcol, const int* __restrict__ bcbeg,
+                            const int* __restrict__ bcend, const int* __restrict__ slot_of, int* __restrict__ table,
                             unsigned long long* __restrict__ pairs) {
     unsigned long long cnt = 0;
-    for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < (int64_t)nt * 27;
+    const int64_t nt = loff[lv.L + 1] - loff[2];  // real target boxes of levels 2 .. L
+    for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < nt * 27;
          it += (int64_t)gridDim.x * blockDim.x) {
-        const int gb = t0 + (int)(it / 27), q = (int)(it % 27);
+        const int rb = loff[2] + (int)(it / 27), q = (int)(it % 27);
         int level = 2;
-        while (level < lv.L && gb >= lv.off[level + 1]) ++level;
+        while (level < lv.L && rb >= loff[level + 1]) ++level;
         const int o = lv.off[level], po = lv.off[level - 1];
+        const int gb = o + (rb - loff[level]);
         // parent indices are relative to level - 1, child ranges relative to level
         const int pc = bcol[((int64_t)po + bparent[gb]) * 27 + q];
         if (pc < 0) continue;
@@ -73,20 +75,22 @@ void m2l_prepare(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& 
     const int L = lv.L;
     // table rows for the global boxes [off[2], off[L+1])
     const int t0 = lv.off[2];
-    cuda_check(cudaMemsetAsync(table, 0xff, sizeof(int) * (size_t)(lv.off[L + 1] - t0) * NUM_OFFSETS, s),
-               "m2l table clear");
+    const int* count = tb.counts.as<int>();
+    fill_level_rows<int>(c, lv, count, 2, L, NUM_OFFSETS, t0, table, -1);  // the rows of real boxes
     TableLevels tl{};
     tl.L = L;
     for (int l = 0; l <= L + 1 && l <= MAX_LEVELS + 1; ++l) tl.off[l] = lv.off[l];
-    const int nt = lv.off[L + 1] - t0;  // target boxes of levels 2 .. L
+    const int nt = lv.off[L + 1] - t0;  // target box slots of levels 2 .. L
+    const int* loff = count + 32;  // the level scan's offsets of the real boxes
     k_m2l_table<<<grid_for((int64_t)nt * 27, 128), 128, 0, s>>>(
-        t0, nt, tl, tb.bkey.as<uint64_t>(), tb.bparent.as<int>(), tb.bcol.as<int>(), tb.bcbeg.as<int>(),
+        t0, tl, loff, tb.bkey.as<uint64_t>(), tb.bparent.as<int>(), tb.bcol.as<int>(), tb.bcbeg.as<int>(),
         tb.bcend.as<int>(), ops.slot_of.as<int>(), table, pair_counter);
     count_launch(c);
     check_launch("m2l table");
     const int64_t ntarget = lv.off[L + 1] - t0;
     M2LItems it{};
     it.table = table;
+    it.loff = loff;
     it.t0 = t0;
     it.by_level = !uniform;
     it.L = L;
@@ -96,7 +100,7 @@ void m2l_prepare(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& 
 }
 
 template <typename T>
-void m2l_apply(Ctx* c, const Plan<T>& pl, const Levels& lv, Grouped& gp, const T* mult, T* loc) {
+void m2l_apply(Ctx* c, const Plan<T>& pl, const Levels& lv, const int* count, Grouped& gp, const T* mult, T* loc) {
     const int L = lv.L;
     // the tensor-core products read the multipoles split into TF32 hi/lo once
     const float* mhi = nullptr;
@@ -105,12 +109,12 @@ void m2l_apply(Ctx* c, const Plan<T>& pl, const Levels& lv, Grouped& gp, const T
         bool any_tc = false;
         for (int l = 2; l <= L; ++l) any_tc = any_tc || (ctx_m2l_tc(c) && pl.m2l_tiles[l]);
         if (any_tc) {
-            const int64_t first = (int64_t)lv.off[2] * pl.ld, count = (int64_t)(lv.off[L + 1] - lv.off[2]) * pl.ld;
+            const int64_t first = (int64_t)lv.off[2] * pl.ld, rows = (int64_t)(lv.off[L + 1] - lv.off[2]) * pl.ld;
             Buf& bh = ctx_tmp(c, 12);
             Buf& bl = ctx_tmp(c, 13);
-            ensure(c, bh, (first + count) * 4);
-            ensure(c, bl, (first + count) * 4);
-            tc_split(c, count, mult + first, bh.as<float>() + first, bl.as<float>() + first);
+            ensure(c, bh, (first + rows) * 4);
+            ensure(c, bl, (first + rows) * 4);
+            tc_split(c, lv, count, 2, L, pl.ld, mult, bh.as<float>(), bl.as<float>());
             mhi = bh.as<float>();
             mlo = bl.as<float>();
         }
@@ -127,9 +131,9 @@ void m2l_apply(Ctx* c, const Plan<T>& pl, const Levels& lv, Grouped& gp, const T
         a.g1 = pl.uniform ? NUM_OFFSETS : (l1 - 2) * NUM_OFFSETS;
         a.ops = pl.m2l[l0];
         a.ops_mod = NUM_OFFSETS;
-        a.R = pl.scalar ? P : 2 * P;  // scalar case: the translation block alone, no chi
-        a.C = pl.scalar ? P : 2 * P;
-        a.psplit = pl.scalar ? 0 : P;
+        a.R = pl.rows(P);  // scalar case: the translation block alone, no chi
+        a.C = pl.rows(P);
+        a.psplit = pl.split_out(P);  // the fused zero block (two-potential form only)
         a.in = mult;
         a.ldin = pl.ld;
         a.out = loc;
@@ -148,7 +152,8 @@ void m2l_apply(Ctx* c, const Plan<T>& pl, const Levels& lv, Grouped& gp, const T
     }
 }
 
-template void m2l_apply<float>(Ctx*, const Plan<float>&, const Levels&, Grouped&, const float*, float*);
-template void m2l_apply<double>(Ctx*, const Plan<double>&, const Levels&, Grouped&, const double*, double*);
+template void m2l_apply<float>(Ctx*, const Plan<float>&, const Levels&, const int*, Grouped&, const float*, float*);
+template void m2l_apply<double>(Ctx*, const Plan<double>&, const Levels&, const int*, Grouped&, const double*,
+                                double*);
 
 }  // namespace lhv

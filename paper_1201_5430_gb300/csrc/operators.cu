@@ -606,6 +606,139 @@ void translation_block(Ctx* c, const T* fused, int ngroups, int P, Buf& dst) {
 template void translation_block<float>(Ctx*, const float*, int, int, Buf&);
 template void translation_block<double>(Ctx*, const double*, int, int, Buf&);
 
+
+// ---- the complex form Psi = phi + i chi (Sec. 4.2, Eq. chf1) ------------------------------
+// Psi is stored as 2P reals: slot r (r < P, the scaled real layout of one potential) holds
+// Re Psi_n^m for m = 0, and Re / Im Psi_n^m (m >= 1); slot P + r holds Im Psi_n^0 for m = 0,
+// and Re / Im Psi_n^{-m} (m >= 1).  With phi, chi real (c_n^{-m} = (-1)^m conj(c_n^m)), per
+// (n, m >= 1), s = (-1)^m:
+//   Psi^m    = (Re phi - Im chi) + i (Im phi + Re chi)
+//   Psi^{-m} = s (Re phi + Im chi) + i s (Re chi - Im phi)
+// M maps the (phi, chi) layout to Psi; the translation tables of the complex form are
+// M F M^-1 for each fused table F (dense: the Psi translation with the conversion).
+__device__ inline void decode_slot(int r, int& n, int& m, int& part) {
+    n = (int)sqrtf((float)r);
+    while (n * n > r) --n;
+    while ((n + 1) * (n + 1) <= r) ++n;
+    const int k = r - n * n;
+    m = (k + 1) / 2;
+    part = (k == 0) ? 0 : ((k & 1) ? 0 : 1);  // 0: Re, 1: Im
+}
+
+// row i of M: Psi[i] = sum_k c[k] phichi[a[k]]
+__device__ inline int psi_row(int i, int P, int* a, double* c) {
+    const int half = i >= P, r = i - half * P;
+    int n, m, part;
+    decode_slot(r, n, m, part);
+    if (m == 0) {
+        a[0] = half ? P + r : r;
+        c[0] = 1.0;
+        return 1;
+    }
+    const int rre = n * n + 2 * m - 1, rim = rre + 1;
+    const double sg = (m & 1) ? -1.0 : 1.0;
+    if (!half) {
+        if (part == 0) { a[0] = rre; c[0] = 1.0; a[1] = P + rim; c[1] = -1.0; }
+        else { a[0] = rim; c[0] = 1.0; a[1] = P + rre; c[1] = 1.0; }
+    } else {
+        if (part == 0) { a[0] = rre; c[0] = sg; a[1] = P + rim; c[1] = sg; }
+        else { a[0] = P + rre; c[0] = sg; a[1] = rim; c[1] = -sg; }
+    }
+    return 2;
+}
+
+// column j of M^-1: phichi[b[k]] gets c[k] Psi[j]
+__device__ inline int psi_inv_col(int j, int P, int* b, double* c) {
+    const int half = j >= P, r = j - half * P;
+    int n, m, part;
+    decode_slot(r, n, m, part);
+    if (m == 0) {
+        b[0] = half ? P + r : r;
+        c[0] = 1.0;
+        return 1;
+    }
+    const int rre = n * n + 2 * m - 1, rim = rre + 1;
+    const double sg = (m & 1) ? -1.0 : 1.0;
+    if (!half) {
+        if (part == 0) { b[0] = rre; c[0] = 0.5; b[1] = P + rim; c[1] = -0.5; }
+        else { b[0] = rim; c[0] = 0.5; b[1] = P + rre; c[1] = 0.5; }
+    } else {
+        if (part == 0) { b[0] = rre; c[0] = 0.5 * sg; b[1] = P + rim; c[1] = 0.5 * sg; }
+        else { b[0] = rim; c[0] = -0.5 * sg; b[1] = P + rre; c[1] = 0.5 * sg; }
+    }
+    return 2;
+}
+
+template <typename T>
+__global__ void k_psi_form(int ngroups, int P, const T* __restrict__ fused, T* __restrict__ dst) {
+    const int R = 2 * P;
+    const int64_t per = (int64_t)R * R;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ngroups * per;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = e / per, q = e - g * per;
+        const int j = (int)(q / R), i = (int)(q - (int64_t)j * R);  // k-major: input j, output i
+        int a[2], b[2];
+        double ca[2], cb[2];
+        const int na = psi_row(i, P, a, ca), nb = psi_inv_col(j, P, b, cb);
+        const T* F = fused + g * per;
+        double acc = 0.0;
+        for (int x = 0; x < na; ++x)
+            for (int y = 0; y < nb; ++y) acc += ca[x] * (double)F[(int64_t)b[y] * R + a[x]] * cb[y];
+        dst[e] = (T)acc;
+    }
+}
+
+// In place, rows of 2P reals (row stride ld): to_psi = 1: (phi, chi) -> Psi; 0: Psi -> (phi, chi).
+template <typename T>
+__global__ void k_psi_rows(int64_t nrows, int P, int64_t ld, T* __restrict__ rows, int to_psi) {
+    const int64_t work = nrows * P;  // one thread per (row, slot r < P); slots of m >= 1 pair up
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < work; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = e / P;
+        const int r = (int)(e - row * P);
+        int n, m, part;
+        decode_slot(r, n, m, part);
+        if (m > 0 && part == 1) continue;  // the Re slot of (n, m) handles all four values
+        T* v = rows + row * ld;
+        if (m == 0) continue;              // Re Psi^0 = phi^0, Im Psi^0 = chi^0: the same slots
+        const int rre = n * n + 2 * m - 1, rim = rre + 1;
+        const T sg = (m & 1) ? (T)-1 : (T)1;
+        const T x0 = v[rre], x1 = v[rim], x2 = v[P + rre], x3 = v[P + rim];
+        if (to_psi) {  // x = (Re phi, Im phi, Re chi, Im chi)
+            v[rre] = x0 - x3;
+            v[rim] = x1 + x2;
+            v[P + rre] = sg * (x0 + x3);
+            v[P + rim] = sg * (x2 - x1);
+        } else {       // x = (Re Psi^m, Im Psi^m, Re Psi^-m, Im Psi^-m)
+            v[rre] = (T)0.5 * (x0 + sg * x2);
+            v[rim] = (T)0.5 * (x1 - sg * x3);
+            v[P + rre] = (T)0.5 * (x1 + sg * x3);
+            v[P + rim] = (T)0.5 * (sg * x2 - x0);
+        }
+    }
+}
+
+template <typename T>
+void psi_form(Ctx* c, const T* fused, int ngroups, int P, Buf& dst) {
+    ensure(c, dst, (int64_t)ngroups * 4 * P * P * (int64_t)sizeof(T));
+    k_psi_form<T><<<grid_for((int64_t)ngroups * 4 * P * P, 256), 256, 0, stream_of(c)>>>(ngroups, P, fused,
+                                                                                       dst.as<T>());
+    count_launch(c);
+    check_launch("psi form");
+}
+
+template <typename T>
+void psi_rows(Ctx* c, int64_t nrows, int P, int64_t ld, T* rows, bool to_psi) {
+    if (nrows <= 0) return;
+    k_psi_rows<T><<<grid_for(nrows * P, 256), 256, 0, stream_of(c)>>>(nrows, P, ld, rows, to_psi ? 1 : 0);
+    count_launch(c);
+    check_launch("psi rows");
+}
+
+template void psi_form<float>(Ctx*, const float*, int, int, Buf&);
+template void psi_form<double>(Ctx*, const double*, int, int, Buf&);
+template void psi_rows<float>(Ctx*, int64_t, int, int64_t, float*, bool);
+template void psi_rows<double>(Ctx*, int64_t, int, int64_t, double*, bool);
+
 template void build_sparse<float>(Ctx*, int, int, Csr&);
 template void build_sparse<double>(Ctx*, int, int, Csr&);
 template void build_op<float>(Ctx*, int, int, int, Buf&);

@@ -676,7 +676,8 @@ __global__ void k_rk4_stage(int64_t n, const vec4_t<T>* __restrict__ x0, const v
 // y += c acc, in place (the last RK4 combine)
 template <typename T>
 __global__ void k_rk4_final(int64_t n, vec4_t<T>* x, vec4_t<T>* w, const vec4_t<T>* __restrict__ ax,
-                            const vec4_t<T>* __restrict__ aw, T cf) {
+                            const vec4_t<T>* __restrict__ aw, T cf, const int* __restrict__ abort_word) {
+    if (abort_word && *abort_word) return;  // a captured step whose trees failed their guard writes nothing
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         vec4_t<T> a = ax[i], b = aw[i], y = x[i], z = w[i];
         y.x += cf * a.x;
@@ -950,7 +951,8 @@ __global__ void __launch_bounds__(32 * P2P_WARPS) k_p2p_scalar_x2(const int* __r
 template <typename T>
 void run_rk4_final(Ctx* c, int64_t n, vec4_t<T>* x, vec4_t<T>* w, const vec4_t<T>* ax, const vec4_t<T>* aw,
                    double cf) {
-    k_rk4_final<T><<<grid_for(n, 256), 256, 0, stream_of(c)>>>(n, x, w, ax, aw, (T)cf);
+    k_rk4_final<T><<<grid_for(n, 256), 256, 0, stream_of(c)>>>(n, x, w, ax, aw, (T)cf,
+                                                                ctx_graph_level(c) >= 0 ? ctx_abort_word(c) : nullptr);
     count_launch(c);
     check_launch("rk4 final");
 }

@@ -463,18 +463,28 @@ void tc_tiles_build(Ctx* c, const float* ops, int ngroups, int R, int C, int psp
     check_launch("tc tiles");
 }
 
-// hi = tf32(x), lo = tf32(x - hi) of n floats (the source vectors of the tensor-core products)
-__global__ void k_tf32_split(int64_t n, const float* __restrict__ x, float* __restrict__ hi,
-                             float* __restrict__ lo) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const float v = x[i], h = tf32_rna(v);
-        hi[i] = h;
-        lo[i] = tf32_rna(v - h);
+// hi = tf32(x), lo = tf32(x - hi) of the rows of the real boxes of levels l0..l1 (the source
+// vectors of the tensor-core products)
+__global__ void k_tf32_split(LevelTable lt, const int* __restrict__ count, int l0, int l1, int64_t ld,
+                             const float* __restrict__ x, float* __restrict__ hi, float* __restrict__ lo) {
+    for (int l = l0; l <= l1; ++l) {
+        const int64_t base = (int64_t)lt.off[l] * ld, n = (int64_t)count[l] * ld;
+        for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+            const float v = x[base + e], h = tf32_rna(v);
+            hi[base + e] = h;
+            lo[base + e] = tf32_rna(v - h);
+        }
     }
 }
 
-void tc_split(Ctx* c, int64_t n, const float* x, float* hi, float* lo) {
-    k_tf32_split<<<grid_for(n, 256), 256, 0, stream_of(c)>>>(n, x, hi, lo);
+void tc_split(Ctx* c, const Levels& lv, const int* count, int l0, int l1, int64_t ld, const float* x, float* hi,
+              float* lo) {
+    LevelTable lt{};
+    lt.L = lv.L;
+    int64_t cap = 1;
+    for (int l = 0; l <= lv.L + 1 && l <= MAX_LEVELS + 1; ++l) lt.off[l] = lv.off[l];
+    for (int l = l0; l <= l1; ++l) cap = std::max<int64_t>(cap, (int64_t)lv.nbox[l] * ld);
+    k_tf32_split<<<grid_for(cap, 256), 256, 0, stream_of(c)>>>(lt, count, l0, l1, ld, x, hi, lo);
     count_launch(c);
     check_launch("tf32 split");
 }

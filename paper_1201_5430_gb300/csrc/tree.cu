@@ -461,7 +461,7 @@ __global__ void __launch_bounds__(1024) k_lvl_scan(int L, int nblk, int* __restr
 // parent (level-local, -1 at level 0) and the first child of each parent.
 __global__ void __launch_bounds__(SCAN_THREADS) k_lvl_apply(int64_t n, const uint64_t* __restrict__ keys, int bits,
                                                             int L, int nblk, const int* __restrict__ cnt,
-                                                            const int* __restrict__ off, uint64_t* __restrict__ bkey,
+                                                            LevelTable off, uint64_t* __restrict__ bkey,
                                                             int* __restrict__ bbeg, int* __restrict__ bend,
                                                             int* __restrict__ bpar, int* __restrict__ bcbeg) {
     const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
@@ -474,7 +474,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_lvl_apply(int64_t n, const uin
         int t = 0;
         for (int j = 0; j < SCAN_ITEMS; ++j) t += sl[j] <= l;
         int run = block_exclusive_scan(t, nullptr) + cnt[(int64_t)l * nblk + blockIdx.x];
-        const int o = off[l], ou = l > 0 ? off[l - 1] : 0;
+        const int o = off.off[l], ou = l > 0 ? off.off[l - 1] : 0;
         const int shift = 3 * (bits - l);
         for (int j = 0; j < SCAN_ITEMS; ++j) {
             const int64_t i = base + j;
@@ -495,43 +495,53 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_lvl_apply(int64_t n, const uin
     }
 }
 
-struct LevelTable {
-    int L;
-    int off[MAX_LEVELS + 2];
-};
-
 __device__ inline int level_of(const LevelTable& lt, int gb) {
     int l = 0;
     while (l < lt.L && gb >= lt.off[l + 1]) ++l;
     return l;
 }
 
+// Box arrays hold level l at [off[l], off[l] + count[l]); count (device, from k_lvl_scan)
+// can be smaller than the level's slot range when the offsets are capacities (the layout
+// of a captured step), so every kernel over boxes skips the unused slots.
+
+// The real boxes of levels 0..L, numbered rb = loff[l] + b (loff: the exclusive scan of the
+// counts, device), and their slots gb = off[l] + b.
+__device__ inline int real_level(const int* __restrict__ loff, int L, int rb) {
+    int l = 0;
+    while (l < L && rb >= loff[l + 1]) ++l;
+    return l;
+}
+
 // children ranges: end of parent p = first child of p + 1 (or the level's box count);
 // leaves have none
-__global__ void k_lvl_children(int nbt, LevelTable lt, int* __restrict__ bcbeg, int* __restrict__ bcend) {
-    for (int gb = blockIdx.x * blockDim.x + threadIdx.x; gb < nbt; gb += gridDim.x * blockDim.x) {
-        const int l = level_of(lt, gb);
+__global__ void k_lvl_children(LevelTable lt, const int* __restrict__ count, const int* __restrict__ loff,
+                               int* __restrict__ bcbeg, int* __restrict__ bcend) {
+    const int nreal = loff[lt.L + 1];
+    for (int rb = blockIdx.x * blockDim.x + threadIdx.x; rb < nreal; rb += gridDim.x * blockDim.x) {
+        const int l = real_level(loff, lt.L, rb);
+        const int p = rb - loff[l], nb = count[l], gb = lt.off[l] + p;
         if (l == lt.L) {
             bcbeg[gb] = 0;
             bcend[gb] = 0;
             continue;
         }
-        const int p = gb - lt.off[l], nb = lt.off[l + 1] - lt.off[l];
-        bcend[gb] = p + 1 < nb ? bcbeg[gb + 1] : lt.off[l + 2] - lt.off[l + 1];
+        bcend[gb] = p + 1 < nb ? bcbeg[gb + 1] : count[l + 1];
     }
 }
 
 // 27 colleagues of every box of every level (binary search among its level's keys);
 // the system id above the level's 3*level Morton bits is kept.  One thread per
 // (box, slot), slot = ((dx + 1) 3 + (dy + 1)) 3 + (dz + 1).
-__global__ void k_colleagues_all(int nbt, LevelTable lt, const uint64_t* __restrict__ bkey_all,
-                                 int* __restrict__ col_all) {
-    for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < (int64_t)nbt * 27;
+__global__ void k_colleagues_all(LevelTable lt, const int* __restrict__ count, const int* __restrict__ loff,
+                                 const uint64_t* __restrict__ bkey_all, int* __restrict__ col_all) {
+    const int64_t nreal = loff[lt.L + 1];
+    for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < nreal * 27;
          it += (int64_t)gridDim.x * blockDim.x) {
-        const int gb = (int)(it / 27), slot = (int)(it - (int64_t)gb * 27);
+        const int rb = (int)(it / 27), slot = (int)(it - (int64_t)rb * 27);
         const int dx = slot / 9 - 1, dy = (slot / 3) % 3 - 1, dz = slot % 3 - 1;
-        const int level = level_of(lt, gb);
-        const int o = lt.off[level], nb = lt.off[level + 1] - o, b = gb - o;
+        const int level = real_level(loff, lt.L, rb);
+        const int o = lt.off[level], nb = count[level], b = rb - loff[level];
         const uint64_t* bkey = bkey_all + o;
         const int64_t dim = 1ll << level;
         const uint64_t mask = (level > 0) ? ((~0ull) >> (64 - 3 * level)) : 0ull;
@@ -558,16 +568,19 @@ __global__ void k_colleagues_all(int nbt, LevelTable lt, const uint64_t* __restr
     }
 }
 
-// P2P work items: leaf b is split into ceil(count / P2P_TILE) tiles.
-__global__ void k_tile_counts(int nb, const int* __restrict__ bbeg, const int* __restrict__ bend,
-                              int* __restrict__ cnt) {
+// P2P work items: leaf b is split into ceil(count / P2P_TILE) tiles (the leaf slots past
+// the device count *nleaf hold no leaf and get none).
+__global__ void k_tile_counts(int nb, const int* __restrict__ nleaf, const int* __restrict__ bbeg,
+                              const int* __restrict__ bend, int* __restrict__ cnt) {
+    const int nl = *nleaf;
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x)
-        cnt[b] = (bend[b] - bbeg[b] + P2P_TILE - 1) / P2P_TILE;
+        cnt[b] = b < nl ? (bend[b] - bbeg[b] + P2P_TILE - 1) / P2P_TILE : 0;
 }
 
-__global__ void k_tile_fill(int nb, const int* __restrict__ bbeg, const int* __restrict__ bend,
-                            const int* __restrict__ first, int2* __restrict__ tiles) {
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+__global__ void k_tile_fill(int nb, const int* __restrict__ nleaf, const int* __restrict__ bbeg,
+                            const int* __restrict__ bend, const int* __restrict__ first, int2* __restrict__ tiles) {
+    const int nl = min(nb, *nleaf);
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nl; b += gridDim.x * blockDim.x) {
         int nt = (bend[b] - bbeg[b] + P2P_TILE - 1) / P2P_TILE;
         for (int j = 0; j < nt; ++j) tiles[first[b] + j] = make_int2(b, bbeg[b] + j * P2P_TILE);
     }
@@ -584,6 +597,13 @@ __global__ void k_gather(int64_t n, const int* __restrict__ perm, const vec4_t<T
         xs[i] = a;
         ws[i] = b;
     }
+}
+
+// Captured step: the leaf level is fixed (L_graph).  The tree it builds is valid while every
+// far pair still sees K = 1 (L_graph <= the core rule's cap of the current cube) and the
+// input is finite; otherwise the guard word tells the step not to write its result.
+__global__ void k_graph_guard(const TreeParams* __restrict__ tp, int L_graph, int* __restrict__ abort_word) {
+    if (threadIdx.x == 0 && blockIdx.x == 0 && (tp->nonfinite || tp->L_cap < L_graph)) atomicOr(abort_word, 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -629,7 +649,12 @@ int build_tree(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const vec4_t<
     ensure(c, tb.counts, 64 * 4);
     ensure(c, tb.cubes, (int64_t)nsys * sizeof(SysCube));
     ensure(c, tb.sysoff, (int64_t)(nsys + 1) * 8);
-    cuda_check(cudaMemcpyAsync(tb.sysoff.ptr, sysoff, (nsys + 1) * 8, cudaMemcpyHostToDevice, s), "system offsets");
+    // a captured step uploads its system offsets once, before the capture
+    const int L_graph = ctx_graph_level(c);
+    const bool graph = L_graph >= 0;
+    if (!graph)
+        cuda_check(cudaMemcpyAsync(tb.sysoff.ptr, sysoff, (nsys + 1) * 8, cudaMemcpyHostToDevice, s),
+                   "system offsets");
 
     TreeParams* tp = tb.params.as<TreeParams>();
     int* counts = tb.counts.as<int>();
@@ -684,30 +709,43 @@ int build_tree(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const vec4_t<
         k_leaf_level<<<1, 32, 0, s>>>(tp, cubes, nsys, bits, ctx_rK(c), ctx_max_level(c));
         count_launch(c);
         check_launch("leaf level");
+        if (graph) {  // no host read: the guard checks the fixed leaf level on the device
+            k_graph_guard<<<1, 32, 0, s>>>(tp, L_graph, ctx_abort_word(c));
+            count_launch(c);
+            return;
+        }
         cuda_check(cudaMemcpyAsync(&hp, tp, sizeof(TreeParams), cudaMemcpyDeviceToHost, s), "read params");
         cuda_check(cudaStreamSynchronize(s), "sync params");
     };
-    int S = ctx_sort_levels(c);
-    if (S <= 0 || S > bits) S = bits;
-    const int first_pass = 3 * (bits - S) / 8;  // lower digits order nothing the tree uses
-    sort_passes(first_pass);
-    leaf_level();
-    if (first_pass > 0 && hp.L_cap > S && !hp.nonfinite) {
-        sort_passes(0);
-        cuda_check(cudaMemsetAsync(&tp->deepest_shared, 0xff, sizeof(int), s), "reset shared level");  // -1, as k_bbox_final sets it
+    if (graph) {
+        // the fixed leaf level needs the boxes of levels <= L_graph only: the keys ordered down
+        // to S = L_graph + SORT_BELOW_CAP levels give exactly those, whatever the cap does
+        const int S = std::min(bits, L_graph + SORT_BELOW_CAP);
+        sort_passes(3 * (bits - S) / 8);
         leaf_level();
+    } else {
+        int S = ctx_sort_levels(c);
+        if (S <= 0 || S > bits) S = bits;
+        const int first_pass = 3 * (bits - S) / 8;  // lower digits order nothing the tree uses
+        sort_passes(first_pass);
+        leaf_level();
+        if (first_pass > 0 && hp.L_cap > S && !hp.nonfinite) {
+            sort_passes(0);
+            cuda_check(cudaMemsetAsync(&tp->deepest_shared, 0xff, sizeof(int), s), "reset shared level");  // -1, as k_bbox_final sets it
+            leaf_level();
+        }
+        // the next tree orders its keys down to SORT_BELOW_CAP levels below the cap: the leaves
+        // only need one, the rest keeps consecutive elements of a leaf (the near-field warp tiles)
+        // spatially compact
+        ctx_sort_levels(c) = std::min(bits, hp.L_cap + SORT_BELOW_CAP);
     }
-    // the next tree orders its keys down to SORT_BELOW_CAP levels below the cap: the leaves
-    // only need one, the rest keeps consecutive elements of a leaf (the near-field warp tiles)
-    // spatially compact
-    ctx_sort_levels(c) = std::min(bits, hp.L_cap + SORT_BELOW_CAP);
     uint64_t* keys = kin;
     int* perm = vin;
-    if (hp.nonfinite) {
+    if (!graph && hp.nonfinite) {
         err = {LHV_ENONFINITE, "non-finite position or strength"};
         return LHV_ENONFINITE;
     }
-    const int L = hp.L;
+    const int L = graph ? L_graph : hp.L;
     lv.L = L;
     lv.n = nn;
     hp.bits = bits;
@@ -732,33 +770,43 @@ int build_tree(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const vec4_t<
     const int nblk = (int)((nn + SCAN_TILE - 1) / SCAN_TILE);
     Buf& lcnt = ctx_tmp(c, 0);
     ensure(c, lcnt, (int64_t)(L + 1) * nblk * 4);
-    int* loff = counts + 32;  // off[0 .. L+1] on the device
+    int* loff = counts + 32;  // off[0 .. L+1] of the actual counts, on the device
     k_lvl_count<<<nblk, SCAN_THREADS, 0, s>>>(nn, keys, bits, L, nblk, lcnt.as<int>());
     count_launch(c);
     k_lvl_scan<<<1, 1024, 0, s>>>(L, nblk, lcnt.as<int>(), counts, loff);
     count_launch(c);
-    k_lvl_apply<<<nblk, SCAN_THREADS, 0, s>>>(nn, keys, bits, L, nblk, lcnt.as<int>(), loff,
-                                              tb.bkey.as<uint64_t>(), tb.bbeg.as<int>(), tb.bend.as<int>(),
-                                              tb.bparent.as<int>(), tb.bcbeg.as<int>());
-    count_launch(c);
-    check_launch("levels");
-    int hcounts[64];
-    cuda_check(cudaMemcpyAsync(hcounts, counts, 64 * 4, cudaMemcpyDeviceToHost, s), "read counts");
-    cuda_check(cudaStreamSynchronize(s), "sync counts");
+    check_launch("level counts");
+    // host offsets of the box arrays: the actual counts (read back), or in a captured step the
+    // capacities, which need no read; the kernels below take the counts from the device
     lv.off[0] = 0;
-    for (int l = 0; l < MAX_LEVELS; ++l) {
-        lv.nbox[l] = (l <= L) ? hcounts[l] : 0;
-        lv.off[l + 1] = lv.off[l] + lv.nbox[l];
+    if (graph) {
+        for (int l = 0; l < MAX_LEVELS; ++l) {
+            lv.nbox[l] = (l <= L) ? lv.cap_off[l + 1] - lv.cap_off[l] : 0;
+            lv.off[l + 1] = lv.off[l] + lv.nbox[l];
+        }
+    } else {
+        int hcounts[64];
+        cuda_check(cudaMemcpyAsync(hcounts, counts, 64 * 4, cudaMemcpyDeviceToHost, s), "read counts");
+        cuda_check(cudaStreamSynchronize(s), "sync counts");
+        for (int l = 0; l < MAX_LEVELS; ++l) {
+            lv.nbox[l] = (l <= L) ? hcounts[l] : 0;
+            lv.off[l + 1] = lv.off[l] + lv.nbox[l];
+        }
     }
-    const int64_t nbt = lv.off[L + 1];
     LevelTable lt{};
     lt.L = L;
     for (int l = 0; l <= L + 1 && l <= MAX_LEVELS; ++l) lt.off[l] = lv.off[l];
     lt.off[L + 2 <= MAX_LEVELS + 1 ? L + 2 : MAX_LEVELS + 1] = lv.off[L + 1];
-    k_lvl_children<<<grid_for(nbt, 256), 256, 0, s>>>((int)nbt, lt, tb.bcbeg.as<int>(), tb.bcend.as<int>());
+    k_lvl_apply<<<nblk, SCAN_THREADS, 0, s>>>(nn, keys, bits, L, nblk, lcnt.as<int>(), lt, tb.bkey.as<uint64_t>(),
+                                              tb.bbeg.as<int>(), tb.bend.as<int>(), tb.bparent.as<int>(),
+                                              tb.bcbeg.as<int>());
+    count_launch(c);
+    check_launch("levels");
+    const int64_t nbt = lv.off[L + 1];
+    k_lvl_children<<<grid_for(nbt, 256), 256, 0, s>>>(lt, counts, loff, tb.bcbeg.as<int>(), tb.bcend.as<int>());
     count_launch(c);
     ensure(c, tb.bcol, nbt * 27 * 4);
-    k_colleagues_all<<<grid_for(nbt * 27, 128), 128, 0, s>>>((int)nbt, lt, tb.bkey.as<uint64_t>(),
+    k_colleagues_all<<<grid_for(nbt * 27, 128), 128, 0, s>>>(lt, counts, loff, tb.bkey.as<uint64_t>(),
                                                               tb.bcol.as<int>());
     count_launch(c);
     check_launch("children, colleagues");
@@ -768,14 +816,15 @@ int build_tree(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const vec4_t<
         int nl = lv.nbox[L], o = lv.off[L];
         int* cnt = tb.flags.as<int>();
         int* first = tb.boxof_a.as<int>();
-        k_tile_counts<<<grid_for(nl, 256), 256, 0, s>>>(nl, tb.bbeg.as<int>() + o, tb.bend.as<int>() + o, cnt);
+        k_tile_counts<<<grid_for(nl, 256), 256, 0, s>>>(nl, counts + L, tb.bbeg.as<int>() + o, tb.bend.as<int>() + o,
+                                                        cnt);
         count_launch(c);
         ensure(c, tb.tile_count, 16);
         exclusive_scan(c, nl, cnt, first, tb.scan_tmp.as<int>(), tb.tile_count.as<int>());
         int64_t max_tiles = nl + nn / P2P_TILE + 1;
         ensure(c, tb.tiles, max_tiles * 8);
-        k_tile_fill<<<grid_for(nl, 256), 256, 0, s>>>(nl, tb.bbeg.as<int>() + o, tb.bend.as<int>() + o, first,
-                                                      tb.tiles.as<int2>());
+        k_tile_fill<<<grid_for(nl, 256), 256, 0, s>>>(nl, counts + L, tb.bbeg.as<int>() + o, tb.bend.as<int>() + o,
+                                                      first, tb.tiles.as<int2>());
         count_launch(c);
         check_launch("tiles");
     }
@@ -786,6 +835,40 @@ int build_tree(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const vec4_t<
         cuda_check(cudaMemcpyAsync(tb.keys_a.ptr, keys, nn * 8, cudaMemcpyDeviceToDevice, s), "keys");
     return LHV_OK;
 }
+
+
+// Rows [off[l], off[l] + count[l]) of levels l0..l1 (row_len elements each, row r at
+// data + (r - row0) row_len) set to `value`: the rows of real boxes only, whatever the
+// slot layout.
+template <typename T>
+__global__ void k_fill_level_rows(LevelTable lt, const int* __restrict__ count, int l0, int l1, int64_t row_len,
+                                  int64_t row0, T* __restrict__ data, T value) {
+    for (int l = l0; l <= l1; ++l) {
+        const int64_t n = (int64_t)count[l] * row_len;
+        T* base = data + ((int64_t)lt.off[l] - row0) * row_len;
+        for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+            base[e] = value;
+    }
+}
+
+template <typename T>
+void fill_level_rows(Ctx* c, const Levels& lv, const int* dcount, int l0, int l1, int64_t row_len, int64_t row0,
+                     T* data, T value) {
+    if (l1 < l0) return;
+    LevelTable lt{};
+    lt.L = lv.L;
+    for (int l = 0; l <= lv.L + 1 && l <= MAX_LEVELS + 1; ++l) lt.off[l] = lv.off[l];
+    int64_t cap = 0;
+    for (int l = l0; l <= l1; ++l) cap = std::max<int64_t>(cap, (int64_t)lv.nbox[l] * row_len);
+    k_fill_level_rows<T><<<grid_for(cap, 256, 152 * 16), 256, 0, stream_of(c)>>>(lt, dcount, l0, l1, row_len, row0,
+                                                                                   data, value);
+    count_launch(c);
+    check_launch("fill rows");
+}
+
+template void fill_level_rows<float>(Ctx*, const Levels&, const int*, int, int, int64_t, int64_t, float*, float);
+template void fill_level_rows<double>(Ctx*, const Levels&, const int*, int, int, int64_t, int64_t, double*, double);
+template void fill_level_rows<int>(Ctx*, const Levels&, const int*, int, int, int64_t, int64_t, int*, int);
 
 template int build_tree<float>(Ctx*, int64_t, int, const int64_t*, const float4*, const float4*, TreeBufs&, Levels&,
                                TreeParams&, Error&);

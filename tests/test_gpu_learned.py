@@ -74,27 +74,35 @@ def test_network_meets_the_target_the_fixed_p_misses(net, name):
     assert e_fixed > 4 * EPS
 
 
-def test_network_against_the_best_uniform_p(net):
-    """The method without the network needs the smallest uniform p that reaches
-    eps, found by trial evaluations against direct sums.  The network picks its
-    schedule in one pass; on the cube, under TF32x3 (p a multiple of 4 runs on the
-    tensor cores), it is faster than that best uniform p in plain FP32."""
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
+def test_network_against_the_best_uniform_p_at_equal_precision(net, prec):
+    """The method without the network needs the fastest uniform p that reaches eps, found
+    by trial evaluations against direct sums, in the same arithmetic as the learned form
+    (so the tensor cores are credited to neither).  On the held-out cube the network's
+    one-pass schedule is faster than that best uniform p in plain FP32; under TF32x3,
+    where the uniform arm already runs its M2L on the tensor cores (p a multiple of 4),
+    it is not slower by more than 10 % (a measured outcome, printed)."""
     from paper_1201_5430_gb300 import LHV
     x, w, a = _case("cube")
     x4, w4 = dev(x, "fp32"), dev(w, "fp32")
     idx = torch.from_numpy(np.random.default_rng(0).choice(x.shape[0], 1000, replace=False).astype(np.int32)).cuda()
     v0, _ = LHV(p=4, leaf_max=64, core_a=a).direct_sampled(x4, w4, idx)
-    best = None
+    cands = []
     for p in range(14, 21):
-        ctx = LHV(p=p, leaf_max=64, core_a=a)
+        ctx = LHV(p=p, leaf_max=64, core_a=a, precision=prec)
         v, _ = ctx.evaluate_velocity_stretching(x4, w4)
         if _err(v, v0, idx.long()) <= EPS:
-            best = (p, _ms(ctx, x4, w4))
-            break
-    assert best is not None
-    ctx = LHV(p=12, leaf_max=64, core_a=a, precision="tf32x3")
+            cands.append((_ms(ctx, x4, w4), p))
+            if prec == "fp32" or p % 4 == 0:
+                break  # the next p costs more on the same pipes
+    assert cands
+    best = min(cands)
+    ctx = LHV(p=12, leaf_max=64, core_a=a, precision=prec)
     ctx.set_selector(*net, eps=EPS, check_every=0)
     t_learned = _ms(ctx, x4, w4)
-    print(f"cube: best uniform p {best[0]} (fp32) {best[1]:.1f} ms; learned tf32x3 {ctx.stats()['level_p']} "
-          f"{t_learned:.1f} ms")
-    assert t_learned < best[1]
+    print(f"cube {prec}: best uniform p {best[1]} {best[0]:.1f} ms; learned {ctx.stats()['level_p']} "
+          f"{t_learned:.1f} ms ({best[0] / t_learned:.2f}x)")
+    if prec == "fp32":
+        assert t_learned < best[0]
+    else:
+        assert t_learned < 1.10 * best[0]
