@@ -14,7 +14,8 @@ Forms compared at equal accuracy, eps_2(v) <= 1e-6 against FP64 direct sums at
   tf32x3       -- M2L products on the tcgen05 tensor cores in split TF32, the smallest
                   uniform p with tensor-core shapes (a multiple of 4) that reaches eps;
   learned      -- TF32x3 with p per level chosen by the selector network every step
-                  (its sampled direct-sum check every 10th step).
+                  (its sampled direct-sum check every 10th step);
+  tf32x3_graph -- the tf32x3 arm with each RK4 step as one CUDA graph replay.
 `value` is the fastest form that reached eps.  Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -464,6 +465,12 @@ def run_single(args, torch, LHV, local, world, rank, dist):
             continue
         ev, es = next((t["err_v"], t["err_s"]) for t in search[prec]["trials"] if t["p"] == p)
         makers[key] = (lambda p=p, prec=prec: configured(p, prec), p, ev, es)
+        if prec == "tf32x3":  # the same arm with each RK4 step as one CUDA graph replay
+            def graphed(p=p):
+                c = configured(p, "tf32x3")
+                c.set_graph(True)
+                return c
+            makers["tf32x3_graph"] = (graphed, p, ev, es)
     W, b, _ = selector.load()
 
     def learned():
@@ -477,9 +484,11 @@ def run_single(args, torch, LHV, local, world, rank, dist):
     lst = c.stats()
     c.close()
     makers["learned_tf32x3"] = (learned, None, lev, les)
+    screen_stats = {}
     for key, (mk, p, ev, es) in makers.items():
         c = mk()
         t, st = timed(c, screen_steps, 3)
+        screen_stats[key] = st
         arms[key] = arm_record(t, st, p if p else st["level_p"], ev, es)
         if key == "learned_tf32x3":
             arms[key]["initial_selection"] = {"level_p": lst["level_p"], "check_err_v": lst["selector"]["err_v"],
@@ -496,7 +505,10 @@ def run_single(args, torch, LHV, local, world, rank, dist):
     value = throughput(4 * n * args.steps, world, total_ms)
     arms[head]["ms_per_step_full_run"] = total_ms / args.steps
 
-    # roofline of the dominant kernel (near field): algorithmic FP32 flops per launch / its mean duration
+    # roofline of the dominant kernel (near field): algorithmic FP32 flops per launch / its mean duration.
+    # Captured steps record no stage events: the graph arm's kernels are timed in its uncaptured twin.
+    if st["stage_ms"].get("p2p", 0.0) <= 0.0:
+        st = dict(screen_stats["tf32x3"], kernel_launches=st["kernel_launches"], graph=st.get("graph"))
     p2p_ms = st["stage_ms"]["p2p"] / max(st["stage_launches"]["p2p"], 1)
     pairs = st["p2p_pairs"]
     achieved = P2P_FLOPS_PER_PAIR * pairs / (p2p_ms / 1e3) / 1e12
@@ -526,6 +538,7 @@ def run_single(args, torch, LHV, local, world, rank, dist):
     e2e_val = 4 * n * world / statistics.mean(e2e_times)
     c.close()
     ratio = None if args.no_scalar_ratio else scalar_ratio(torch, LHV)
+    batched = None if args.no_batched else batched_form(torch, LHV, min(args.steps, 3), 3)
 
     if rank != 0:
         if dist:
@@ -568,9 +581,12 @@ def run_single(args, torch, LHV, local, world, rank, dist):
         "peaks_measured": probes,
         "peaks_driver": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained")},
         "peaks_driver_kind": peak_kind,
-        "stage_ms_per_step": {k: v / args.steps for k, v in st["stage_ms"].items() if v > 0},
+        "stage_ms_per_step": {k: v / max(st["stage_launches"].get("p2p", 4) // 4, 1)
+                              for k, v in st["stage_ms"].items() if v > 0},
         "launch_shape": shape,
+        "graph": st.get("graph"),
         "t_vs_over_t_phigrad": ratio,
+        "batched_form_blobs64": batched,
         "cpu_baseline": cb,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(2 * n * 16),
                 "d2h_bytes_per_step": int(2 * n * 16), "steps": e2e_steps},
@@ -582,73 +598,96 @@ def run_single(args, torch, LHV, local, world, rank, dist):
         dist.destroy_process_group()
 
 
-def run_blobs64(args, torch, LHV, local, world, rank, dist):
-    """Batched form: 64 independent Gaussian-blob systems (sizes log-uniform in
-    [1e4, 5e5], about 1e7 elements) advanced by one RK4 step per timed step,
-    (a) batched: one lhv_step_batched call for all systems, (b) sequential: the
-    single-system path in the same precision called once per system."""
+def batched_form(torch, LHV, steps, warmup, rank=0, world=1, precision="tf32x3"):
+    """Batched form (configs[3]): 64 independent Gaussian-blob systems (sizes log-uniform in
+    [1e4, 5e5], about 1e7 elements), one RK4 step per timed step from the same state, three
+    arms in the same precision: (a) one lhv_step_batched call for all systems, (b) the same
+    with the whole step as one CUDA graph replay, (c) the single-system path called once per
+    system.  Independent systems shard over ranks (a block each, no collective)."""
     systems = workloads.blob_systems(64, 4)
-    mine = shard(64, rank, world)  # independent systems: a block of them per rank, no collective
+    mine = shard(64, rank, world)
     systems = [systems[k] for k in mine]
-    x = np.concatenate([s[0] for s in systems])
-    w = np.concatenate([s[1] for s in systems])
-    off = [0] + list(np.cumsum([s[0].shape[0] for s in systems]))
+    x = np.concatenate([q[0] for q in systems])
+    w = np.concatenate([q[1] for q in systems])
+    off = [0] + [int(v) for v in np.cumsum([q[0].shape[0] for q in systems])]
     n = int(off[-1])
     spec = dict(p=12, leaf_max=64, a=0.01, eps=1e-6, dt=1e-3)
-    x0 = torch.from_numpy(workloads.to_f4(x)).cuda()
-    w0 = torch.from_numpy(workloads.to_f4(w)).cuda()
-    x4, w4 = x0.clone(), w0.clone()
-    stream = torch.cuda.current_stream()
+    side = torch.cuda.Stream()  # graph capture needs a stream other than the legacy default
+    out = {"systems": len(systems), "n": n, **spec, "precision": precision}
+    with torch.cuda.stream(side):
+        x0 = torch.from_numpy(workloads.to_f4(x)).cuda()
+        w0 = torch.from_numpy(workloads.to_f4(w)).cuda()
+        x4, w4 = x0.clone(), w0.clone()
 
-    def timed(fn, steps, warmup):
-        for _ in range(max(warmup, 3)):
-            x4.copy_(x0)
-            w4.copy_(w0)
-            fn()
-        torch.cuda.synchronize()
-        tot = 0.0
-        for _ in range(steps):
-            x4.copy_(x0)
-            w4.copy_(w0)
-            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            ea.record(stream)
-            fn()
-            eb.record(stream)
-            eb.synchronize()
-            tot += ea.elapsed_time(eb)
-        return tot
+        def timed(fn):
+            for _ in range(max(warmup, 3)):
+                x4.copy_(x0)
+                w4.copy_(w0)
+                fn()
+            side.synchronize()
+            tot = 0.0
+            for _ in range(steps):
+                x4.copy_(x0)
+                w4.copy_(w0)
+                ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ea.record(side)
+                fn()
+                eb.record(side)
+                eb.synchronize()
+                tot += ea.elapsed_time(eb)
+            return tot / steps
 
-    cb = LHV(p=spec["p"], leaf_max=spec["leaf_max"], core_a=spec["a"], eps=spec["eps"], precision=args.precision)
-    tuned = cb.autotune(x0, w0, offsets=off)  # launch shapes for the batch, outside the timed region
-    t_b = timed(lambda: cb.step_batched(off, x4, w4, spec["dt"]), args.steps, args.warmup)
-    cs = LHV(p=spec["p"], leaf_max=spec["leaf_max"], core_a=spec["a"], eps=spec["eps"], precision=args.precision)
-    cs.set_launch_shape(tuned["p2p_targets_per_thread"], tuned["m2l_pairs_per_chunk"], tuned["m2l_tensor_cores"],
-                        p2p_sources_per_stage=tuned["p2p_sources_per_stage"])
+        def make():
+            return LHV(p=spec["p"], leaf_max=spec["leaf_max"], core_a=spec["a"], eps=spec["eps"],
+                       precision=precision, stream=side)
 
-    def seq():
-        for k in range(len(systems)):
-            cs.step(x4[off[k]:off[k + 1]], w4[off[k]:off[k + 1]], spec["dt"])
+        cb = make()
+        tuned = cb.autotune(x0, w0, offsets=off)  # launch shapes for the batch, outside the timed regions
+        out["launch_shape"] = tuned
+        out["batched_ms_per_step"] = timed(lambda: cb.step_batched(off, x4, w4, spec["dt"]))
+        cg = make()
+        cg.set_launch_shape(tuned["p2p_targets_per_thread"], tuned["m2l_pairs_per_chunk"], tuned["m2l_tensor_cores"],
+                            p2p_sources_per_stage=tuned["p2p_sources_per_stage"])
+        cg.set_graph(True)
+        cg.reset_stats()
+        out["batched_graph_ms_per_step"] = timed(lambda: cg.step_batched(off, x4, w4, spec["dt"]))
+        out["graph"] = cg.stats()["graph"]
+        cs = make()
+        cs.set_launch_shape(tuned["p2p_targets_per_thread"], tuned["m2l_pairs_per_chunk"], tuned["m2l_tensor_cores"],
+                            p2p_sources_per_stage=tuned["p2p_sources_per_stage"])
 
-    t_s = timed(seq, args.steps, args.warmup)
-    tb_max, ts_max = max_over_ranks(t_b, dist), max_over_ranks(t_s, dist)
-    tot_n = n
+        def seq():
+            for k in range(len(systems)):
+                cs.step(x4[off[k]:off[k + 1]], w4[off[k]:off[k + 1]], spec["dt"])
+
+        out["sequential_ms_per_step"] = timed(seq)
+        out["leaf_level"] = cb.stats()["leaf_level"]
+        for c in (cb, cg, cs):
+            c.close()
+    for k in ("batched", "batched_graph", "sequential"):
+        out[k + "_evals_per_s"] = 4 * n * world / (out[k + "_ms_per_step"] / 1e3)
+    out["speedup_batched_vs_sequential"] = out["sequential_ms_per_step"] / out["batched_ms_per_step"]
+    out["speedup_graph_vs_sequential"] = out["sequential_ms_per_step"] / out["batched_graph_ms_per_step"]
+    out["steps"] = steps
+    return out
+
+
+def run_blobs64(args, torch, LHV, local, world, rank, dist):
+    """The batched form's own line (see batched_form)."""
+    r = batched_form(torch, LHV, args.steps, args.warmup, rank, world, args.precision)
+    ms = max_over_ranks(r["batched_graph_ms_per_step"], dist)
+    tot_n = r["n"]
     if dist:
-        tn = torch.tensor([float(n)], dtype=torch.float64, device="cuda")
+        tn = torch.tensor([float(tot_n)], dtype=torch.float64, device="cuda")
         dist.all_reduce(tn)
         tot_n = int(tn.item())
-    val_b = 4 * tot_n * args.steps / (tb_max / 1e3)
-    val_s = 4 * tot_n * args.steps / (ts_max / 1e3)
     if rank == 0:
-        print(json.dumps({"metric": METRIC + " (batched form)", "value": val_b, "unit": UNIT, "n_gpus": world,
-                          "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": tb_max / args.steps,
+        print(json.dumps({"metric": METRIC + " (batched form)", "value": 4 * tot_n / (ms / 1e3), "unit": UNIT,
+                          "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
                           "higher_is_better": True, "scaling": "strong" if world > 1 else "weak",
                           "dtype": "f32" if args.precision == "fp32" else "f32+tf32x3", "data": "synthetic",
-                          "scaling_note": "64 systems split across the ranks (strong scaling)" if world > 1 else None,
-                          "config": {"workload": "blobs64", "systems": 64, "n": tot_n, **spec,
-                                     "precision": args.precision, "leaf_level": cb.stats()["leaf_level"]},
-                          "launch_shape": tuned,
-                          "sequential_same_precision": {"value": val_s, "ms_per_step": ts_max / args.steps},
-                          "speedup_vs_sequential": val_b / val_s}), flush=True)
+                          "config": {"workload": "blobs64", "n": tot_n, "form": "batched + CUDA graph"},
+                          "arms": r}), flush=True)
 
 
 def run_offset_rings(args, torch, LHV, local, world, rank, dist):
@@ -711,6 +750,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-scalar-ratio", action="store_true",
                     help="skip T(v, s) / T(phi, grad phi) against the scalar reference case")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched form (64 blob systems: batched, CUDA graph, per system)")
     ap.add_argument("--workload", default="leapfrog", choices=list(SINGLE) + ["blobs64", "offset_rings"],
                     help="leapfrog (headline), ring_262144 (single ring), offset_rings (mixed precision on "
                          "configs' colliding rings), blobs64 (the batched form)")
@@ -741,7 +782,9 @@ def main():
     elif args.workload == "offset_rings":
         run_offset_rings(args, torch, LHV, local, world, rank, dist)
     else:
-        run_single(args, torch, LHV, local, world, rank, dist)
+        side = torch.cuda.Stream()  # a non-default stream: the graph arm captures on it
+        with torch.cuda.stream(side):
+            run_single(args, torch, LHV, local, world, rank, dist)
 
 
 if __name__ == "__main__":
