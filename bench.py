@@ -357,6 +357,44 @@ def scalar_ratio(torch, LHV, n=1 << 20, p=12, leaves=(32, 64, 128, 256)):
     return out
 
 
+
+def vfm_ring(torch, LHV, n=1 << 20, p=16, reps=3):
+    """Vortex filaments (Sec. 5.3): one closed ring of n segments (R = 1, Gamma = 1), v at the
+    n nodes by the FMM (TF32x3, segments in closed form near, Gauss-Legendre S-expansions far).
+    Error against the FP64 FMM at p = 20 at every node; the mean axial speed against Eq. dis6,
+    Gamma / (4 pi R) ln(2 n / pi)."""
+    import math
+    th = 2.0 * math.pi * np.arange(n) / n
+    x = np.stack([np.cos(th), np.sin(th), np.zeros(n)], axis=1)
+    g = np.ones(n)
+    out = {"n": n, "p": p, "precision": "tf32x3"}
+    ref = LHV(p=20, leaf_max=64, core_a=0.0, precision="fp64")
+    x64 = torch.from_numpy(workloads.to_f4(x.astype(np.float32), np.float64)).cuda()
+    v64 = ref.evaluate_filaments([0, n], [True], x64, torch.from_numpy(g).cuda())
+    ref.close()
+    c = LHV(p=p, leaf_max=64, core_a=0.0, precision="tf32x3")
+    x32 = torch.from_numpy(workloads.to_f4(x.astype(np.float32))).cuda()
+    g32 = torch.ones(n, device="cuda")
+    v = c.evaluate_filaments([0, n], [True], x32, g32)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        c.evaluate_filaments([0, n], [True], x32, g32, v)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    d = (v[:, :3].double() - v64[:, :3])
+    out["ms_per_evaluation"] = ms
+    out["evals_per_s"] = n / (ms / 1e3)
+    out["err_v_vs_fp64_p20"] = float(torch.linalg.norm(d) / torch.linalg.norm(v64[:, :3]))
+    out["mean_axial_speed"] = float(v[:, 2].double().mean())
+    out["eq_dis6"] = math.log(2 * n / math.pi) / (4.0 * math.pi)
+    out["leaf_level"] = c.stats()["leaf_level"]
+    c.close()
+    return out
+
+
 def run_single(args, torch, LHV, local, world, rank, dist):
     from paper_1201_5430_gb300 import _lib, selector
     name = SINGLE[args.workload]
@@ -539,6 +577,7 @@ def run_single(args, torch, LHV, local, world, rank, dist):
     c.close()
     ratio = None if args.no_scalar_ratio else scalar_ratio(torch, LHV)
     batched = None if args.no_batched else batched_form(torch, LHV, min(args.steps, 3), 3)
+    filaments = None if args.no_filaments else vfm_ring(torch, LHV)
 
     if rank != 0:
         if dist:
@@ -587,6 +626,7 @@ def run_single(args, torch, LHV, local, world, rank, dist):
         "graph": st.get("graph"),
         "t_vs_over_t_phigrad": ratio,
         "batched_form_blobs64": batched,
+        "filaments_ring": filaments,
         "cpu_baseline": cb,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(2 * n * 16),
                 "d2h_bytes_per_step": int(2 * n * 16), "steps": e2e_steps},
@@ -750,9 +790,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-scalar-ratio", action="store_true",
                     help="skip T(v, s) / T(phi, grad phi) against the scalar reference case")
+    ap.add_argument("--no-filaments", action="store_true",
+                    help="skip the vortex filament ring (segments, Sec. 5.3)")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched form (64 blob systems: batched, CUDA graph, per system)")
-    ap.add_argument("--workload", default="leapfrog", choices=list(SINGLE) + ["blobs64", "offset_rings"],
+    ap.add_argument("--workload", default="leapfrog", choices=list(SINGLE) + ["blobs64", "offset_rings", "filaments"],
                     help="leapfrog (headline), ring_262144 (single ring), offset_rings (mixed precision on "
                          "configs' colliding rings), blobs64 (the batched form)")
     ap.add_argument("--precision", default="tf32x3", choices=["tf32x3", "fp32"],
@@ -777,7 +819,16 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     from paper_1201_5430_gb300 import LHV
-    if args.workload == "blobs64":
+    if args.workload == "filaments":
+        r = vfm_ring(torch, LHV)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC + " (vortex filaments)", "value": r["evals_per_s"] * world,
+                              "unit": UNIT, "n_gpus": world, "steps": 3, "warmup": 1,
+                              "ms_per_step": r["ms_per_evaluation"], "higher_is_better": True, "scaling": "weak",
+                              "dtype": "f32+tf32x3", "data": "synthetic",
+                              "config": {"workload": "vfm_ring", "n": r["n"], "p": r["p"]}, "details": r}),
+                  flush=True)
+    elif args.workload == "blobs64":
         run_blobs64(args, torch, LHV, local, world, rank, dist)
     elif args.workload == "offset_rings":
         run_offset_rings(args, torch, LHV, local, world, rank, dist)

@@ -201,6 +201,27 @@ int lhv_step_f64(lhv_ctx* ctx, int64_t n, double* x4, double* w4, double dt);
 int lhv_evaluate_potential_gradient(lhv_ctx* ctx, int64_t n, const float* x4, const float* q, float* pg4);
 int lhv_evaluate_potential_gradient_f64(lhv_ctx* ctx, int64_t n, const double* x4, const double* q, double* pg4);
 
+/* Vortex filaments (Sec. 5.3, App. B): v at the nodes of nfil polylines.  Filament f owns
+ * the nodes [offsets[f], offsets[f+1]) of x4 (offsets: HOST int64 [nfil+1], offsets[0] = 0,
+ * non-decreasing); segment k runs from node k to node k + 1, or from the last node back to
+ * the first when closed[f] != 0 (closed: HOST int32 [nfil]), with constant circulation
+ * gamma[k] (device [n], the segment that starts at node k; unused for the last node of an
+ * open filament).  Each node receives, from every segment that does not start or end at
+ * it, the closed form of Eq. dis2,
+ *   v = gamma / (4 pi) (r1 x r2) / (r1 r2 + r1 . r2) (1/r1 + 1/r2),  rj = node - end j,
+ * summed by the FMM: the octree of the nodes, each segment in the leaf of its first node;
+ * far field from its S-expansion by Gauss-Legendre quadrature with [(p - 1)/2] + 1 points
+ * (Eqs. vf5-vf7: Eq. eve4 with (gamma / 8 pi) l in place of w), the near field in closed
+ * form over the segments of the colleague leaves (a node on a segment's line gets 0 from
+ * it).  Segments should be short against the leaf side.  v4: device [n][4] output in the
+ * caller's order (lane 3 written 0).  Needs core_a = 0, the two-potential form and the
+ * selector off (LHV_EUNSUPPORTED otherwise); LHV_EINVAL for bad offsets or pointers, or a
+ * precision that does not match the entry point. */
+int lhv_evaluate_filaments(lhv_ctx* ctx, int nfil, const int64_t* offsets, const int32_t* closed, const float* x4,
+                           const float* gamma, float* v4);
+int lhv_evaluate_filaments_f64(lhv_ctx* ctx, int nfil, const int64_t* offsets, const int32_t* closed,
+                               const double* x4, const double* gamma, double* v4);
+
 /* The exact sum the FMM approximates, at m sampled targets: v and s of Eq.
  * s1.1 with the kernel of Eqs. 2/vem1 (the context's core_a) summed over every
  * element j != idx[k] (excluded by index), in FP64 arithmetic.  This is the

@@ -74,6 +74,9 @@ SIGNATURES = {
     "lhv_evaluate_potential_gradient_f64": (_int, [_vp, _i64, _vp, _vp, _vp]),
     "lhv_set_form": (_int, [_vp, _int]),
     "lhv_set_graph": (_int, [_vp, _int]),
+    "lhv_evaluate_filaments": (_int, [_vp, _int, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_int32), _vp, _vp, _vp]),
+    "lhv_evaluate_filaments_f64": (_int, [_vp, _int, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_int32), _vp, _vp,
+                                          _vp]),
     "lhv_peak_probe": (_int, [_int, _int, _int, _vp, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl)]),
 }
 

@@ -87,6 +87,22 @@ class LHV:
         self._check(fn(self.h, x4.shape[0], _ptr(x4), _ptr(q), _ptr(pg4)), "evaluate_potential_gradient")
         return pg4
 
+    def evaluate_filaments(self, offsets, closed, x4, gamma, v4=None):
+        """Vortex filaments (lhv_evaluate_filaments): filament f owns the nodes
+        offsets[f]:offsets[f+1] of x4, closed[f] joins its last node to its first; gamma
+        (CUDA [n], the context's dtype) is the circulation of the segment starting at each
+        node.  Returns v at the nodes, [n, 4]."""
+        self._elems(x4)
+        if gamma.device.type != "cuda" or gamma.dtype != self.dtype or gamma.dim() != 1 or \
+                gamma.shape[0] != x4.shape[0] or not gamma.is_contiguous():
+            raise ValueError(f"expected a contiguous CUDA {self.dtype} vector of {x4.shape[0]} circulations")
+        off = (ctypes.c_int64 * len(offsets))(*[int(o) for o in offsets])
+        cl = (ctypes.c_int32 * len(closed))(*[1 if c else 0 for c in closed])
+        v4 = torch.empty_like(x4) if v4 is None else self._elems(v4)
+        fn = self.lib.lhv_evaluate_filaments_f64 if self.precision == "fp64" else self.lib.lhv_evaluate_filaments
+        self._check(fn(self.h, len(offsets) - 1, off, cl, _ptr(x4), _ptr(gamma), _ptr(v4)), "evaluate_filaments")
+        return v4
+
     def evaluate_batched(self, offsets, x4, w4, v4=None, s4=None):
         """Independent systems: system k owns rows offsets[k]:offsets[k+1]."""
         self._elems(x4)

@@ -87,6 +87,8 @@ struct Ctx {
     Buf s_m2l, s_m2m, s_l2l, s_tiles;   // translation blocks of the fused tables, TF32 tiles of s_m2l
     int s_p = 0, s_type = 0;
     Buf qs, pgfar;
+    // filament segments (lhv_evaluate_filaments)
+    Buf f_off, f_closed, f_seg, f_next, f_segs, f_nexts;
 };
 
 // ---- helpers used by every translation unit ------------------------------
@@ -570,6 +572,171 @@ static int evaluate_scalar(Ctx* c, int64_t n, const vec4_t<T>* x4, const T* q, v
     return LHV_OK;
 }
 
+// ---- filament segments (Sec. 5.3, App. B) -------------------------------------------------
+// Gauss-Legendre nodes and weights on [-1, 1]: the roots of P_nq by Newton's method from the
+// estimate cos(pi (i - 1/4) / (nq + 1/2)), P_nq and P'_nq by the three-term recurrence, and
+// w = 2 / ((1 - x^2) P'_nq(x)^2).
+GaussRule gauss_legendre(int nq) {
+    GaussRule r;
+    r.nq = nq;
+    for (int i = 0; i < (nq + 1) / 2; ++i) {
+        double x = std::cos(3.14159265358979323846 * (i + 0.75) / (nq + 0.5)), dp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = x;
+            for (int k = 2; k <= nq; ++k) {
+                const double pk = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = pk;
+            }
+            if (nq == 1) p1 = x, p0 = 1.0;
+            dp = nq * (x * p1 - p0) / (x * x - 1.0);
+            const double dx = p1 / dp;
+            x -= dx;
+            if (std::fabs(dx) < 1e-16) break;
+        }
+        const double w = 2.0 / ((1.0 - x * x) * dp * dp);
+        r.xi[i] = -x;
+        r.w[i] = w;
+        r.xi[nq - 1 - i] = x;
+        r.w[nq - 1 - i] = w;
+    }
+    return r;
+}
+
+// per node: the segment it owns (l = next node - node, Gamma) and the caller index of its
+// end node (-1: none, the last node of an open filament)
+template <typename T>
+__global__ void k_segments(int64_t n, int nfil, const int64_t* __restrict__ off, const int* __restrict__ closed,
+                           const vec4_t<T>* __restrict__ x4, const T* __restrict__ gamma, vec4_t<T>* __restrict__ seg,
+                           int* __restrict__ next) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = nfil - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (off[mid] <= i) lo = mid; else hi = mid - 1;
+        }
+        const int64_t a = off[lo], b = off[lo + 1];
+        const int64_t nx = i + 1 < b ? i + 1 : (closed[lo] && b - a >= 2 ? a : -1);
+        vec4_t<T> sv{};
+        if (nx >= 0) {
+            const vec4_t<T> p = x4[i], q = x4[nx];
+            sv.x = q.x - p.x;
+            sv.y = q.y - p.y;
+            sv.z = q.z - p.z;
+            sv.w = gamma[i];
+        }
+        seg[i] = sv;
+        next[i] = (int)nx;
+    }
+}
+
+// sorted order of the per-node segment data (all four lanes: Gamma rides in the fourth) and
+// of the end-node indices
+template <typename T>
+__global__ void k_gather_segments(int64_t n, const int* __restrict__ perm, const vec4_t<T>* __restrict__ seg,
+                                  const int* __restrict__ next, vec4_t<T>* __restrict__ segs, int* __restrict__ nexts) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int j = perm[i];
+        segs[i] = seg[j];
+        nexts[i] = next[j];
+    }
+}
+
+template <typename T>
+static int evaluate_filaments(Ctx* c, int nfil, const int64_t* offsets, const int* closed, const vec4_t<T>* x4,
+                              const T* gamma, vec4_t<T>* v4) {
+    const int64_t n = offsets[nfil];
+    if (n == 0) return LHV_OK;
+    ensure_ops<T>(c);
+    if (!c->counters.ptr) {
+        ensure(c, c->counters, 64);
+        cuda_check(cudaMemsetAsync(c->counters.ptr, 0, 64, c->stream), "counters init");
+    }
+    unsigned long long* cnt = c->counters.as<unsigned long long>();
+    cuda_check(cudaMemsetAsync(cnt, 0, 16, c->stream), "counters");
+    ensure(c, c->f_off, (int64_t)(nfil + 1) * 8);
+    ensure(c, c->f_closed, (int64_t)nfil * 4);
+    std::vector<int> cl(closed, closed + nfil);
+    cuda_check(cudaMemcpyAsync(c->f_off.ptr, offsets, (size_t)(nfil + 1) * 8, cudaMemcpyHostToDevice, c->stream),
+               "filament offsets");
+    cuda_check(cudaMemcpyAsync(c->f_closed.ptr, cl.data(), (size_t)nfil * 4, cudaMemcpyHostToDevice, c->stream),
+               "filament flags");
+    cuda_check(cudaStreamSynchronize(c->stream), "filament upload");  // the host vector goes out of scope
+    ensure(c, c->f_seg, n * (int64_t)sizeof(vec4_t<T>));
+    ensure(c, c->f_next, n * 4);
+    k_segments<T><<<grid_for(n, 256), 256, 0, c->stream>>>(n, nfil, c->f_off.as<int64_t>(), c->f_closed.as<int>(), x4,
+                                                            gamma, c->f_seg.as<vec4_t<T>>(), c->f_next.as<int>());
+    count_launch(c);
+    check_launch("segments");
+    Error err{LHV_OK, ""};
+    const int64_t off1[2] = {0, n};
+    if (tree_stage<T>(c, n, 1, off1, x4, c->f_seg.as<vec4_t<T>>(), err) != LHV_OK) throw err;
+    c->tree_reuse = false;
+    const Levels& lv = c->lv;
+    const int L = lv.L;
+    ensure(c, c->f_nexts, n * 4);
+    ensure(c, c->f_segs, n * (int64_t)sizeof(vec4_t<T>));
+    k_gather_segments<T><<<grid_for(n, 256), 256, 0, c->stream>>>(n, c->tb.perm.as<int>(), c->f_seg.as<vec4_t<T>>(),
+                                                                   c->f_next.as<int>(), c->f_segs.as<vec4_t<T>>(),
+                                                                   c->f_nexts.as<int>());
+    count_launch(c);
+    check_launch("gather segments");
+    const int terms = c->cfg.terms ? c->cfg.terms : LHV_TERMS_ALL;
+    const bool far = (terms & LHV_TERMS_FAR) && L >= 2;
+    const bool near = (terms & LHV_TERMS_NEAR) != 0;
+    const vec4_t<T>* xs = c->xs.as<vec4_t<T>>();
+    const vec4_t<T>* segs = c->f_segs.as<vec4_t<T>>();
+    vec4_t<T>* vfar = nullptr;
+    c->have_far = far;
+    if (far) {
+        const Plan<T> pl = make_plan<T>(c, L);
+        for (int l = 0; l <= MAX_LEVELS; ++l) c->eval_p[l] = l <= L ? pl.p[l] : 0;
+        c->eval_ld = pl.ld;
+        const int PL = pl.p[L] * pl.p[L];
+        const int64_t nbt = lv.off[L + 1];
+        ensure(c, c->mult, nbt * pl.ld * (int64_t)sizeof(T));
+        ensure(c, c->loc, nbt * pl.ld * (int64_t)sizeof(T));
+        ensure(c, c->table, (nbt - lv.off[2]) * (int64_t)NUM_OFFSETS * 4);
+        ensure(c, c->W, (int64_t)lv.nbox[L] * 3 * PL * (int64_t)sizeof(T));
+        ensure(c, c->vfar, n * (int64_t)sizeof(vec4_t<T>));
+        ensure(c, c->sfar, n * (int64_t)sizeof(vec4_t<T>));
+        T* mult = c->mult.as<T>();
+        T* loc = c->loc.as<T>();
+        {
+            StageScope sc(c, LHV_STAGE_P2M);
+            run_p2m_segments<T>(c, pl, c->tb, lv, xs, segs, gauss_legendre((pl.p[L] - 1) / 2 + 1), c->W.as<T>(), mult);
+        }
+        {
+            StageScope sc(c, LHV_STAGE_M2M);
+            run_m2m<T>(c, pl, c->tb, lv, c->gp_m2m, mult);
+        }
+        {
+            StageScope sc(c, LHV_STAGE_M2L);
+            fill_level_rows<T>(c, lv, c->tb.counts.as<int>(), 2, L, pl.ld, 0, loc, (T)0);
+            const bool tc = sizeof(T) == 4 && ctx_m2l_tc(c) && pl.m2l_tiles[2];
+            const int nc = tc && c->tune_nc == 0 ? TC_PAIRS : ctx_m2l_nc(c, gemm_nc<T>(2 * PL));
+            m2l_prepare(c, c->ops, c->tb, lv, c->table.as<int>(), c->gp_m2l, nc, pl.uniform, cnt + 1);
+            StageScope sg(c, LHV_STAGE_M2L_PRODUCTS);
+            m2l_apply<T>(c, pl, lv, c->tb.counts.as<int>(), c->gp_m2l, mult, loc);
+        }
+        {
+            StageScope sc(c, LHV_STAGE_L2L);
+            run_l2l<T>(c, pl, c->tb, lv, c->gp_l2l, loc);
+        }
+        vfar = c->vfar.as<vec4_t<T>>();
+        {
+            StageScope sc(c, LHV_STAGE_L2P);  // v at the nodes (the s lanes are not used)
+            run_l2p<T>(c, pl, c->tb, lv, xs, segs, loc, vfar, c->sfar.as<vec4_t<T>>());
+        }
+    }
+    {
+        StageScope sc(c, LHV_STAGE_P2P);
+        run_p2p_segments<T>(c, c->tb, lv, xs, segs, c->tb.perm.as<int>(), c->f_nexts.as<int>(), vfar, v4, near, n,
+                            cnt);
+    }
+    return LHV_OK;
+}
+
 // ---- learned form: per-level p and leaf cap from the selector network ----------
 static const int kLeafCaps[4] = {16, 32, 64, 128};
 
@@ -988,6 +1155,27 @@ int scalar_entry(lhv_ctx* ctx, int64_t n, const T* x4, const T* q, T* pg4, int w
     });
 }
 
+template <typename T>
+int filament_entry(lhv_ctx* ctx, int nfil, const int64_t* offsets, const int32_t* closed, const T* x4, const T* gamma,
+                   T* v4, int want_prec) {
+    if (!ctx || nfil < 1 || !offsets || !closed || offsets[0] != 0) return LHV_EINVAL;
+    for (int f = 0; f < nfil; ++f)
+        if (offsets[f + 1] < offsets[f]) return LHV_EINVAL;
+    const int64_t n = offsets[nfil];
+    int st = check_elems(ctx, n, {x4, v4}, 4 * sizeof(T), want_prec);
+    if (st != LHV_OK) return st;
+    if (n > 0 && (!gamma || !aligned(gamma, sizeof(T)))) return LHV_EINVAL;
+    if (ctx->c.cfg.core_a != 0.0 || ctx->c.form != LHV_FORM_PHI_CHI || ctx->c.sel_active) {
+        ctx->c.last_error = "filament segments use the singular kernel of Eq. dis2 (core_a = 0), the two-potential "
+                            "form and no selector";
+        return LHV_EUNSUPPORTED;
+    }
+    return guarded(ctx, [&] {
+        return lhv::evaluate_filaments<T>(&ctx->c, nfil, offsets, closed, reinterpret_cast<const lhv::vec4_t<T>*>(x4),
+                                          gamma, reinterpret_cast<lhv::vec4_t<T>*>(v4));
+    });
+}
+
 }  // namespace
 
 extern "C" {
@@ -1040,7 +1228,7 @@ void lhv_destroy(lhv_ctx* ctx) {
     c.spcache.clear();
     for (auto* b : {&c.sel_W, &c.sel_b, &c.sel_X, &c.sel_Z, &c.sel_choice, &c.sel_idx, &c.sel_dv, &c.sel_ds, &c.sel_err,
                     &c.s_m2l, &c.s_m2m, &c.s_l2l, &c.s_tiles, &c.qs, &c.pgfar, &c.psi_m2l, &c.psi_m2m,
-                    &c.psi_l2l, &c.psi_tiles})
+                    &c.psi_l2l, &c.psi_tiles, &c.f_off, &c.f_closed, &c.f_seg, &c.f_next, &c.f_segs, &c.f_nexts})
         lhv::release(*b);
     lhv::TreeBufs& t = c.tb;
     lhv::Buf* tree[] = {&t.keys_a, &t.keys_b, &t.idx_a, &t.idx_b, &t.hist, &t.boxof_a, &t.boxof_b, &t.flags,
@@ -1138,6 +1326,16 @@ int lhv_step_f64(lhv_ctx* ctx, int64_t n, double* x4, double* w4, double dt) {
         return lhv::step<double>(&ctx->c, n, 1, off, reinterpret_cast<lhv::dbl4*>(x4), reinterpret_cast<lhv::dbl4*>(w4),
                                  dt);
     });
+}
+
+int lhv_evaluate_filaments(lhv_ctx* ctx, int nfil, const int64_t* offsets, const int32_t* closed, const float* x4,
+                           const float* gamma, float* v4) {
+    return filament_entry<float>(ctx, nfil, offsets, closed, x4, gamma, v4, LHV_FP32);
+}
+
+int lhv_evaluate_filaments_f64(lhv_ctx* ctx, int nfil, const int64_t* offsets, const int32_t* closed,
+                               const double* x4, const double* gamma, double* v4) {
+    return filament_entry<double>(ctx, nfil, offsets, closed, x4, gamma, v4, LHV_FP64);
 }
 
 int lhv_evaluate_potential_gradient(lhv_ctx* ctx, int64_t n, const float* x4, const float* q, float* pg4) {

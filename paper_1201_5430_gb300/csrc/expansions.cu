@@ -116,14 +116,18 @@ constexpr int P2M_MAX_OUT = (3 * 24 * 24 + P2M_THREADS - 1) / P2M_THREADS;  // W
 // NC = 3: W of the vortex elements (rows of 3P per leaf); NC = 1: the scalar reference
 // case, monopoles q: the scaled S coefficients of Eq. rsbf5, (1/h) sum_e q_e g_hat(rho_e),
 // written straight into the leaf's multipole row (ldw reals per leaf).
-template <typename T, int NC>
+// SEG (NC = 3): the element is a filament node owning the segment x -> x + l with
+// circulation Gamma, ws = (l, Gamma): W gets (Gamma l / (8 pi h)) sum_j w_j g_hat(rho_j) at
+// the Gauss-Legendre points x + l (1 + xi_j) / 2 (Eqs. vf5, vf6).
+template <typename T, int NC, bool SEG = false>
 __global__ void __launch_bounds__(P2M_THREADS) k_p2m_w(const int* __restrict__ ntiles_dev,
                                                      const int2* __restrict__ tiles, int level,
                                                      const uint64_t* __restrict__ bkey, const int* __restrict__ bend,
                                                      const SysCube* __restrict__ cubes,
                                                      const vec4_t<T>* __restrict__ xs,
                                                      const vec4_t<T>* __restrict__ ws, const T* __restrict__ qs,
-                                                     T* __restrict__ Wout, int64_t ldw, int p, int chunk) {
+                                                     T* __restrict__ Wout, int64_t ldw, int p, int chunk,
+                                                     GaussRule rule = GaussRule{}) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int P = p * p;
     T* gh = reinterpret_cast<T*>(smem_raw);  // [chunk][P]
@@ -148,30 +152,46 @@ __global__ void __launch_bounds__(P2M_THREADS) k_p2m_w(const int* __restrict__ n
                 vec4_t<T> xv = xs[c0 + e];
                 if constexpr (NC == 3) {
                     const vec4_t<T> wv = ws[c0 + e];
-                    wk[e * 3 + 0] = wv.x * invh;  // M_hat carries 1/h (P2M scaling)
-                    wk[e * 3 + 1] = wv.y * invh;
-                    wk[e * 3 + 2] = wv.z * invh;
+                    // M_hat carries 1/h (P2M scaling); a segment's strength is Gamma l / (8 pi)
+                    const T sc = SEG ? wv.w * (T)(0.039788735772973833942) * invh : invh;  // 1/(8 pi)
+                    wk[e * 3 + 0] = wv.x * sc;
+                    wk[e * 3 + 1] = wv.y * sc;
+                    wk[e * 3 + 2] = wv.z * sc;
                 } else {
                     wk[e] = qs[c0 + e] * invh;
                 }
                 T* g = gh + (size_t)e * P;
-                const T rx = (T)(((double)xv.x - cx) / h), ry = (T)(((double)xv.y - cy) / h),
-                        rz = (T)(((double)xv.z - cz) / h);
-                for_each_Q<T>(p, rx, ry, rz, qt, [&](int n, int m, T qr, T qi) {
-                    T re, im;  // i^m conj(Q)
-                    switch (m & 3) {
-                        case 0: re = qr; im = -qi; break;
-                        case 1: re = qi; im = qr; break;
-                        case 2: re = -qr; im = qi; break;
-                        default: re = -qi; im = -qr; break;
+                const int nq = SEG ? rule.nq : 1;
+                for (int j = 0; j < nq; ++j) {
+                    double px = (double)xv.x, py = (double)xv.y, pz = (double)xv.z;
+                    T wq = 1;
+                    if constexpr (SEG) {  // Gauss point j of the segment (Eq. vf6)
+                        const vec4_t<T> wv = ws[c0 + e];
+                        const double t = 0.5 * (1.0 + rule.xi[j]);
+                        px += t * (double)wv.x;
+                        py += t * (double)wv.y;
+                        pz += t * (double)wv.z;
+                        wq = (T)rule.w[j];
                     }
-                    if (m == 0) {
-                        g[n * n] = re;
-                    } else {
-                        g[n * n + 2 * m - 1] = re;
-                        g[n * n + 2 * m] = im;
-                    }
-                });
+                    const T rx = (T)((px - cx) / h), ry = (T)((py - cy) / h), rz = (T)((pz - cz) / h);
+                    for_each_Q<T>(p, rx, ry, rz, qt, [&](int n, int m, T qr, T qi) {
+                        T re, im;  // i^m conj(Q)
+                        switch (m & 3) {
+                            case 0: re = qr; im = -qi; break;
+                            case 1: re = qi; im = qr; break;
+                            case 2: re = -qr; im = qi; break;
+                            default: re = -qi; im = -qr; break;
+                        }
+                        const int k0 = m == 0 ? n * n : n * n + 2 * m - 1;
+                        if (j == 0) {
+                            g[k0] = wq * re;
+                            if (m > 0) g[k0 + 1] = wq * im;
+                        } else {
+                            g[k0] += wq * re;
+                            if (m > 0) g[k0 + 1] += wq * im;
+                        }
+                    });
+                }
             }
             __syncthreads();
 #pragma unroll
@@ -513,6 +533,34 @@ void run_l2p(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, co
 }
 
 
+// Filament segments (Sec. 5.3): W by Gauss-Legendre quadrature along each node's segment,
+// then the P2M map of Eq. eve4 as for vortex elements (Eqs. vf5-vf7).
+template <typename T>
+void run_p2m_segments(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs,
+                      const vec4_t<T>* seg, const GaussRule& rule, T* W, T* mult) {
+    const int L = lv.L, nl = lv.nbox[L], o = lv.off[L], p = pl.p[L], P = p * p;
+    int chunk = 128;
+    while (chunk > 32 && sizeof(T) * ((size_t)chunk * (P + 3) + qtab_reals(p)) > 80 * 1024) chunk /= 2;
+    const size_t smem = sizeof(T) * ((size_t)chunk * (P + 3) + qtab_reals(p));
+    cuda_check(cudaFuncSetAttribute(k_p2m_w<T, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+               "p2m attr");
+    const int* count = tb.counts.as<int>();
+    fill_level_rows<T>(c, lv, count, L, L, 3 * P, o, W, (T)0);
+    const int64_t max_tiles = nl + lv.n / P2P_TILE + 1;
+    k_p2m_w<T, 3, true><<<grid_for(max_tiles, 1, 152 * 16), P2M_THREADS, smem, stream_of(c)>>>(
+        tb.tile_count.as<int>(), tb.tiles.as<int2>(), L, tb.bkey.as<uint64_t>() + o, tb.bend.as<int>() + o,
+        tb.cubes.as<SysCube>(), xs, seg, nullptr, W, (int64_t)3 * P, p, chunk, rule);
+    count_launch(c);
+    check_launch("p2m segments");
+    const size_t smem2 = sizeof(T) * 3 * P;
+    cuda_check(cudaFuncSetAttribute(k_p2m_apply<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2),
+               "p2m apply attr");
+    k_p2m_apply<T><<<grid_for(nl, 1, 152 * 16), P2M_THREADS, smem2, stream_of(c)>>>(count + L, W, P, pl.p2m_sp,
+                                                                                   mult + (int64_t)o * pl.ld, pl.ld);
+    count_launch(c);
+    check_launch("p2m apply");
+}
+
 // Scalar reference case: P2M of the monopoles straight into the leaf multipoles.
 template <typename T>
 void run_p2m_scalar(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs,
@@ -557,6 +605,8 @@ void run_l2p_scalar(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels&
                              const vec4_t<T>*, const T*, vec4_t<T>*, vec4_t<T>*);                      \
     template void run_p2m_scalar<T>(Ctx*, const Plan<T>&, const TreeBufs&, const Levels&, const vec4_t<T>*,     \
                                     const T*, T*);                                                               \
+    template void run_p2m_segments<T>(Ctx*, const Plan<T>&, const TreeBufs&, const Levels&, const vec4_t<T>*,   \
+                                      const vec4_t<T>*, const GaussRule&, T*, T*);                               \
     template void run_l2p_scalar<T>(Ctx*, const Plan<T>&, const TreeBufs&, const Levels&, const vec4_t<T>*,     \
                                     const T*, vec4_t<T>*);
 LHV_INST(float)

@@ -238,6 +238,19 @@ template <typename T>
 void run_l2p(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs,
              const vec4_t<T>* ws, const T* loc, vec4_t<T>* vfar, vec4_t<T>* sfar);
 
+// Gauss-Legendre rule on [-1, 1] (nodes xi, weights w), up to 12 points (Eq. vf7 at p <= 24).
+struct GaussRule {
+    int nq = 0;
+    double xi[12] = {};
+    double w[12] = {};
+};
+GaussRule gauss_legendre(int nq);
+// Filament segments (Sec. 5.3): W by quadrature along each node's segment (seg = (l, Gamma)),
+// then the P2M map of Eq. eve4 into the leaf multipoles.
+template <typename T>
+void run_p2m_segments(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs,
+                      const vec4_t<T>* seg, const GaussRule& rule, T* W, T* mult);
+
 // Scalar reference case (Sec. 5.2): P2M of monopoles into the leaf multipoles, and L2P of
 // phi and grad phi (output lanes: grad phi in x, y, z, phi in w).
 template <typename T>
@@ -267,6 +280,14 @@ void run_p2p(Ctx* c, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs, 
 template <typename T>
 void run_p2p_scalar(Ctx* c, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs, const T* qs, const int* perm,
                     const vec4_t<T>* far, vec4_t<T>* out, bool near, int64_t n, unsigned long long* pair_counter);
+
+// filament segments: v at the nodes from Eq. dis2 over the segments owned by the nodes of
+// the colleague leaves (segs = (l, Gamma) per sorted node, nexts = caller index of the end
+// node or -1), added to `far` (may be null) and written to out in the caller's order
+template <typename T>
+void run_p2p_segments(Ctx* c, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs, const vec4_t<T>* segs,
+                      const int* perm, const int* nexts, const vec4_t<T>* far, vec4_t<T>* out, bool near, int64_t n,
+                      unsigned long long* pair_counter);
 
 // ---- direct sums at sampled targets (direct.cu) ---------------------------------
 // v4, s4: device double [m][4]; synchronous; LHV_EINVAL if an index is out of range.

@@ -946,6 +946,114 @@ __global__ void __launch_bounds__(32 * P2P_WARPS) k_p2p_scalar_x2(const int* __r
     if (lane == 0 && my_pairs) atomicAdd(pairs, my_pairs);
 }
 
+
+// ---- filament segments (Sec. 5.3, Eq. dis2) --------------------------------------------
+// v_i += Gamma_j / (4 pi) (r1 x r2) / (r1 r2 + r1 . r2) (1/r1 + 1/r2), r1 = x_i - x_j,
+// r2 = r1 - l_j, for the segment x_j -> x_j + l_j that node j of a colleague leaf owns, except
+// the segments that start or end at node i (v = 0 on the segment, applied by index).  When
+// r1 . r2 < 0 (the node lies beside the segment) the denominator is formed as
+// |r1 x r2|^2 / (r1 r2 - r1 . r2), which does not cancel; a node on the segment's line gets 0.
+template <typename T, int CH>
+__global__ void __launch_bounds__(P2P_TILE) k_p2p_seg(const int* __restrict__ ntiles_dev, const int2* __restrict__ tiles,
+                                                     int* __restrict__ work, const int* __restrict__ bbeg,
+                                                     const int* __restrict__ bend, const int* __restrict__ bcol,
+                                                     const vec4_t<T>* __restrict__ xs, const vec4_t<T>* __restrict__ segs,
+                                                     const int* __restrict__ perm, const int* __restrict__ nexts,
+                                                     const vec4_t<T>* __restrict__ far, vec4_t<T>* __restrict__ out,
+                                                     int near, unsigned long long* __restrict__ pairs) {
+    __shared__ vec4_t<T> sx[CH];
+    __shared__ vec4_t<T> sl[CH];
+    __shared__ int sown[CH], snext[CH];
+    __shared__ int cbeg[27], cpre[28];
+    __shared__ int cur;
+    const int ntiles = *ntiles_dev;
+    const T inv4pi = (T)0.079577471545947667884;
+    unsigned long long my_pairs = 0;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) cur = atomicAdd(work, 1);
+        __syncthreads();
+        const int tile = cur;
+        if (tile >= ntiles) break;
+        const int2 tw = tiles[tile];
+        const int leaf = tw.x;
+        const int tend = bend[leaf];
+        if (threadIdx.x == 0) {
+            int acc = 0;
+            for (int q = 0; q < 27; ++q) {
+                const int cb = bcol[(int64_t)leaf * 27 + q];
+                int cnt = 0;
+                if (cb >= 0) {
+                    cbeg[q] = bbeg[cb];
+                    cnt = bend[cb] - bbeg[cb];
+                } else {
+                    cbeg[q] = 0;
+                }
+                cpre[q] = acc;
+                acc += cnt;
+            }
+            cpre[27] = acc;
+        }
+        const int ti = tw.y + threadIdx.x;
+        const bool act = ti < tend;
+        const vec4_t<T> xi = act ? xs[ti] : vec4_t<T>{};
+        const int ci = act ? perm[ti] : -2;
+        T h[3] = {0, 0, 0}, lo[3] = {0, 0, 0};
+        __syncthreads();
+        const int nsrc = near ? cpre[27] : 0;
+        if (threadIdx.x == 0 && near) my_pairs += (unsigned long long)min(P2P_TILE, tend - tw.y) * (unsigned long long)nsrc;
+        int qrun = 0;
+        for (int s0 = 0; s0 < nsrc; s0 += CH) {
+            for (int v = s0 + threadIdx.x; v < min(nsrc, s0 + CH); v += P2P_TILE) {
+                while (cpre[qrun + 1] <= v) ++qrun;
+                const int j = cbeg[qrun] + (v - cpre[qrun]);
+                sx[v - s0] = xs[j];
+                sl[v - s0] = segs[j];
+                sown[v - s0] = perm[j];
+                snext[v - s0] = nexts[j];
+            }
+            __syncthreads();
+            const int ns = min(CH, nsrc - s0);
+            T a0 = 0, a1 = 0, a2 = 0;
+            for (int k = 0; k < ns; ++k) {
+                const vec4_t<T> l = sl[k];
+                if (l.w == (T)0) continue;                       // no segment (block-uniform)
+                if (ci == sown[k] || ci == snext[k]) continue;   // the node's own segments
+                const vec4_t<T> xj = sx[k];
+                const T r1x = xi.x - xj.x, r1y = xi.y - xj.y, r1z = xi.z - xj.z;
+                const T r2x = r1x - l.x, r2y = r1y - l.y, r2z = r1z - l.z;
+                const T ia = rsqrt(r1x * r1x + r1y * r1y + r1z * r1z);
+                const T ib = rsqrt(r2x * r2x + r2y * r2y + r2z * r2z);
+                const T cx = r1y * r2z - r1z * r2y, cy = r1z * r2x - r1x * r2z, cz = r1x * r2y - r1y * r2x;
+                const T cc = cx * cx + cy * cy + cz * cz;
+                const T dot = r1x * r2x + r1y * r2y + r1z * r2z;
+                const T ab = (T)1 / (ia * ib);
+                const T sum = ia + ib;
+                T f = dot >= (T)0 ? sum / (ab + dot) : sum * (ab - dot) / cc;
+                if (!(cc > (T)0)) f = 0;
+                f *= l.w * inv4pi;
+                a0 += f * cx;
+                a1 += f * cy;
+                a2 += f * cz;
+            }
+            two_sum_acc(h[0], lo[0], a0);
+            two_sum_acc(h[1], lo[1], a1);
+            two_sum_acc(h[2], lo[2], a2);
+            __syncthreads();
+        }
+        if (act) {
+            const vec4_t<T> f = far ? far[ti] : vec4_t<T>{};
+            vec4_t<T> o;
+            o.x = f.x + (h[0] + lo[0]);
+            o.y = f.y + (h[1] + lo[1]);
+            o.z = f.z + (h[2] + lo[2]);
+            o.w = 0;
+            out[ci] = o;
+        }
+    }
+    if (threadIdx.x == 0 && my_pairs) atomicAdd(pairs, my_pairs);
+}
+
 }  // namespace
 
 template <typename T>
@@ -1070,6 +1178,30 @@ void run_p2p_scalar(Ctx* c, const TreeBufs& tb, const Levels& lv, const vec4_t<T
     check_launch("p2p scalar");
 }
 
+
+template <typename T>
+void run_p2p_segments(Ctx* c, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs, const vec4_t<T>* segs,
+                      const int* perm, const int* nexts, const vec4_t<T>* far, vec4_t<T>* out, bool near, int64_t n,
+                      unsigned long long* pair_counter) {
+    cudaStream_t s = stream_of(c);
+    const int L = lv.L, o = lv.off[L];
+    ensure(c, ctx_tmp(c, 6), 64);
+    int* work = reinterpret_cast<int*>(ctx_tmp(c, 6).ptr);
+    cuda_check(cudaMemsetAsync(work, 0, 4, s), "p2p counter");
+    const int64_t max_tiles = lv.nbox[L] + n / P2P_TILE + 1;
+    int per_sm = 1, sms = 152, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    auto kern = k_p2p_seg<T, 128>;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, P2P_TILE, 0);
+    const int grid = (int)std::min<int64_t>(max_tiles, (int64_t)sms * std::max(per_sm, 1));
+    kern<<<grid, P2P_TILE, 0, s>>>(tb.tile_count.as<int>(), tb.tiles.as<int2>(), work, tb.bbeg.as<int>() + o,
+                                   tb.bend.as<int>() + o, tb.bcol.as<int>() + (int64_t)o * 27, xs, segs, perm, nexts,
+                                   far, out, near ? 1 : 0, pair_counter);
+    count_launch(c);
+    check_launch("p2p segments");
+}
+
 template <typename T>
 void run_rk4_stage(Ctx* c, int64_t n, const vec4_t<T>* x0, const vec4_t<T>* w0, const vec4_t<T>* kv,
                    const vec4_t<T>* ks, vec4_t<T>* ax, vec4_t<T>* aw, vec4_t<T>* sx, vec4_t<T>* sw, double c_acc,
@@ -1089,7 +1221,10 @@ void run_rk4_stage(Ctx* c, int64_t n, const vec4_t<T>* x0, const vec4_t<T>* w0, 
                                    int);                                                                           \
     template void run_rk4_final<T>(Ctx*, int64_t, vec4_t<T>*, vec4_t<T>*, const vec4_t<T>*, const vec4_t<T>*, double); \
     template void run_p2p_scalar<T>(Ctx*, const TreeBufs&, const Levels&, const vec4_t<T>*, const T*, const int*,     \
-                                    const vec4_t<T>*, vec4_t<T>*, bool, int64_t, unsigned long long*);
+                                    const vec4_t<T>*, vec4_t<T>*, bool, int64_t, unsigned long long*);             \
+    template void run_p2p_segments<T>(Ctx*, const TreeBufs&, const Levels&, const vec4_t<T>*, const vec4_t<T>*,     \
+                                      const int*, const int*, const vec4_t<T>*, vec4_t<T>*, bool, int64_t,          \
+                                      unsigned long long*);
 LHV_INST(float)
 LHV_INST(double)
 #undef LHV_INST
