@@ -23,6 +23,8 @@ Everything is written for a reader who checks it against the paper by eye:
 * ``complex_psi`` -- one complex FMM for Psi = phi + i chi (Sec. 4.2, Eq. chf1):
                      one complex translation per box pair, conversions on the
                      real potentials split from Psi.
+* ``rcr``         -- rotation - coaxial translation - back rotation with the coaxial
+                     conversions of Eq. rcr1 (Sec. 4.4).
 * ``vfm``         -- vortex filament elements (Sec. 5.3, App. B): the closed-form
                      segment field (Eq. dis2), its Gauss-Legendre S-expansion
                      (Eqs. vf5-vf7) and the FMM with the nodes as receivers.
