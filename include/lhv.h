@@ -306,9 +306,20 @@ int lhv_set_graph(lhv_ctx* ctx, int enable);
  * chi coefficients, i.e. Psi = phi + i h chi at box side h.  The complex form needs one
  * truncation number at every level (LHV_EUNSUPPORTED at evaluation under
  * lhv_set_level_p values or the selector); lhv_export then returns Psi rows for
- * LHV_EXPORT_MULTIPOLE / LHV_EXPORT_LOCAL.  LHV_EINVAL for another value. */
+ * LHV_EXPORT_MULTIPOLE / LHV_EXPORT_LOCAL.
+ * LHV_FORM_RCR: the two potentials as in LHV_FORM_PHI_CHI, with every M2L translation
+ * done by rotation - coaxial translation - back rotation (Sec. 4.4, Fig. 1b): the
+ * coefficients of each potential are rotated degree by degree into the frame whose z
+ * axis is t, translated along z by |t|, converted by the coaxial form of Eq. drt10
+ * (Eq. rcr1) and rotated back; O(p^3) per translation on the CUDA cores instead of the
+ * O(p^4) fused table.  M2M and L2L keep the fused tables (one per box).  Tables are
+ * built in FP64 at the first evaluation (synchronous).  FP32 only, one truncation
+ * number p <= 20 at every level: LHV_EUNSUPPORTED at evaluation otherwise (FP64
+ * precision, lhv_set_level_p values, the selector, p > 20).  The results equal those of
+ * the other forms up to rounding.  LHV_EINVAL for another value. */
 #define LHV_FORM_PHI_CHI 0
 #define LHV_FORM_PSI     1
+#define LHV_FORM_RCR     2
 int lhv_set_form(lhv_ctx* ctx, int form);
 
 /* Statistics of the last tree/evaluation and the accumulated stage timings. */

@@ -8,7 +8,7 @@ LIB_PATH = os.path.join(_HERE, "liblhv.so")
 LHV_OK, LHV_EINVAL, LHV_ENOMEM, LHV_ECUDA, LHV_ETIMEOUT, LHV_ENONFINITE, LHV_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 LHV_FP32, LHV_FP64, LHV_TF32X3 = 0, 1, 2
 LHV_TERMS_NEAR, LHV_TERMS_FAR, LHV_TERMS_ALL = 1, 2, 3
-LHV_FORM_PHI_CHI, LHV_FORM_PSI = 0, 1
+LHV_FORM_PHI_CHI, LHV_FORM_PSI, LHV_FORM_RCR = 0, 1, 2
 LHV_MAX_LEVELS = 22
 LHV_NUM_STAGES = 12
 STAGES = ["tree", "p2m", "m2m", "m2l", "l2l", "l2p", "p2p", "rk4", "ops", "copy", "m2l_products", "select"]

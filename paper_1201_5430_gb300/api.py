@@ -226,9 +226,10 @@ class LHV:
         self._check(self.lib.lhv_set_graph(self.h, 1 if enable else 0), "set_graph")
 
     def set_form(self, form="phi_chi"):
-        """Far-field representation (lhv_set_form): "phi_chi" (two real potentials, the default)
-        or "psi" (one complex function Psi = phi + i chi, Eq. chf1)."""
-        code = {"phi_chi": L.LHV_FORM_PHI_CHI, "psi": L.LHV_FORM_PSI}[form]
+        """Far-field representation (lhv_set_form): "phi_chi" (two real potentials, the default),
+        "psi" (one complex function Psi = phi + i chi, Eq. chf1) or "rcr" (the two potentials
+        with M2L by rotation - coaxial translation - back rotation, Sec. 4.4, Eq. rcr1)."""
+        code = {"phi_chi": L.LHV_FORM_PHI_CHI, "psi": L.LHV_FORM_PSI, "rcr": L.LHV_FORM_RCR}[form]
         self._check(self.lib.lhv_set_form(self.h, code), "set_form")
 
     def set_level_p(self, p_per_level=None):

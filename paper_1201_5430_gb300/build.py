@@ -11,7 +11,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblhv.so")
-SOURCES = ["api.cu", "tree.cu", "operators.cu", "expansions.cu", "m2l.cu", "p2p.cu", "group_gemm.cu", "tc_gemm.cu",
+SOURCES = ["api.cu", "tree.cu", "operators.cu", "expansions.cu", "m2l.cu", "rcr.cu", "p2p.cu", "group_gemm.cu", "tc_gemm.cu",
            "direct.cu", "mlp.cu", "selector.cu", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

@@ -83,6 +83,8 @@ struct Ctx {
     int form = LHV_FORM_PHI_CHI;
     Buf psi_m2l, psi_m2m, psi_l2l, psi_tiles;
     int psi_p = 0, psi_type = 0;
+    // M2L by rotation - coaxial - rotation (LHV_FORM_RCR)
+    RcrTables rcr;
     // scalar reference case (lhv_evaluate_potential_gradient)
     Buf s_m2l, s_m2m, s_l2l, s_tiles;   // translation blocks of the fused tables, TF32 tiles of s_m2l
     int s_p = 0, s_type = 0;
@@ -291,6 +293,12 @@ static Plan<T> make_plan(Ctx* c, int L) {
     pl.ld = (2 * pmax * pmax + 7) / 8 * 8;  // 32-byte rows for the vector loads of the tensor-core path
     const bool base = pl.uniform && pl.p[L] == c->cfg.p;
     const bool tc = sizeof(T) == 4 && ctx_use_tc(c);
+    if (c->form == LHV_FORM_RCR) {
+        if (!base || sizeof(T) != 4 || c->cfg.p > RCR_PMAX)
+            throw Error{LHV_EUNSUPPORTED, "RCR translations run FP32 with one truncation number p <= 20 at every level"};
+        if (c->rcr.p != c->cfg.p) rcr_build(c, c->cfg.p, c->rcr);
+        pl.rcr = &c->rcr;
+    }
     if (c->form == LHV_FORM_PSI) {
         if (!base)
             throw Error{LHV_EUNSUPPORTED, "the complex form runs one truncation number at every level"};
@@ -411,7 +419,8 @@ static int evaluate(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const ve
                 all_tc = all_tc && pl.m2l_tiles[l];
             }
             // the tensor-core kernel takes 128 pairs per MMA; the CUDA-core kernel at most 64
-            const int nc = all_tc && c->tune_nc == 0 ? TC_PAIRS : ctx_m2l_nc(c, gemm_nc<T>(2 * pmax * pmax));
+            const int nc = pl.rcr ? pl.rcr->nc
+                                  : all_tc && c->tune_nc == 0 ? TC_PAIRS : ctx_m2l_nc(c, gemm_nc<T>(2 * pmax * pmax));
             m2l_prepare(c, c->ops, c->tb, lv, c->table.as<int>(), c->gp_m2l, nc, pl.uniform, cnt + 1);
             StageScope sg(c, LHV_STAGE_M2L_PRODUCTS);
             m2l_apply<T>(c, pl, lv, c->tb.counts.as<int>(), c->gp_m2l, mult, loc);
@@ -579,27 +588,7 @@ static int evaluate_scalar(Ctx* c, int64_t n, const vec4_t<T>* x4, const T* q, v
 GaussRule gauss_legendre(int nq) {
     GaussRule r;
     r.nq = nq;
-    for (int i = 0; i < (nq + 1) / 2; ++i) {
-        double x = std::cos(3.14159265358979323846 * (i + 0.75) / (nq + 0.5)), dp = 0.0;
-        for (int it = 0; it < 100; ++it) {
-            double p0 = 1.0, p1 = x;
-            for (int k = 2; k <= nq; ++k) {
-                const double pk = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
-                p0 = p1;
-                p1 = pk;
-            }
-            if (nq == 1) p1 = x, p0 = 1.0;
-            dp = nq * (x * p1 - p0) / (x * x - 1.0);
-            const double dx = p1 / dp;
-            x -= dx;
-            if (std::fabs(dx) < 1e-16) break;
-        }
-        const double w = 2.0 / ((1.0 - x * x) * dp * dp);
-        r.xi[i] = -x;
-        r.w[i] = w;
-        r.xi[nq - 1 - i] = x;
-        r.w[nq - 1 - i] = w;
-    }
+    gauss_legendre_nodes(nq, r.xi, r.w);
     return r;
 }
 
@@ -714,7 +703,7 @@ static int evaluate_filaments(Ctx* c, int nfil, const int64_t* offsets, const in
             StageScope sc(c, LHV_STAGE_M2L);
             fill_level_rows<T>(c, lv, c->tb.counts.as<int>(), 2, L, pl.ld, 0, loc, (T)0);
             const bool tc = sizeof(T) == 4 && ctx_m2l_tc(c) && pl.m2l_tiles[2];
-            const int nc = tc && c->tune_nc == 0 ? TC_PAIRS : ctx_m2l_nc(c, gemm_nc<T>(2 * PL));
+            const int nc = pl.rcr ? pl.rcr->nc : tc && c->tune_nc == 0 ? TC_PAIRS : ctx_m2l_nc(c, gemm_nc<T>(2 * PL));
             m2l_prepare(c, c->ops, c->tb, lv, c->table.as<int>(), c->gp_m2l, nc, pl.uniform, cnt + 1);
             StageScope sg(c, LHV_STAGE_M2L_PRODUCTS);
             m2l_apply<T>(c, pl, lv, c->tb.counts.as<int>(), c->gp_m2l, mult, loc);
@@ -1222,6 +1211,7 @@ void lhv_destroy(lhv_ctx* ctx) {
     for (auto e : c.pool) cudaEventDestroy(e);
     lhv::drop_graph(&c);
     lhv::free_operators(c.ops);
+    lhv::rcr_free(c.rcr);
     for (auto& kv : c.opcache) lhv::release(kv.second);
     c.opcache.clear();
     for (auto& kv : c.spcache) lhv::free_csr(kv.second);
@@ -1618,7 +1608,7 @@ int lhv_autotune_batched(lhv_ctx* ctx, int nsys, const int64_t* offsets, const f
 }
 
 int lhv_set_form(lhv_ctx* ctx, int form) {
-    if (!ctx || (form != LHV_FORM_PHI_CHI && form != LHV_FORM_PSI)) return LHV_EINVAL;
+    if (!ctx || (form != LHV_FORM_PHI_CHI && form != LHV_FORM_PSI && form != LHV_FORM_RCR)) return LHV_EINVAL;
     ctx->c.form = form;
     return LHV_OK;
 }

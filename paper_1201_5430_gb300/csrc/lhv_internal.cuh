@@ -195,6 +195,7 @@ void psi_rows(Ctx* c, int64_t nrows, int P, int64_t ld, T* rows, bool to_psi);
 int m2l_slot_host(int dx, int dy, int dz);   // same mapping as slot_of, on the host
 
 struct Grouped;
+struct RcrTables;
 
 // ---- per-level plan of one evaluation (api.cu) ---------------------------------
 // Truncation number of every level and the operator tables that go with it.
@@ -216,6 +217,7 @@ struct Plan {
     bool scalar = false;                   // scalar reference case: one potential, P x P translation
                                            // tables (the T block of the fused operators), no conversion
     bool psi = false;                      // complex form Psi = phi + i chi: dense 2P x 2P tables
+    const RcrTables* rcr = nullptr;        // M2L by rotation - coaxial - rotation (rcr.cu), FP32
     // output / input split of a fused translation table (its zero block is skipped);
     // 0 (dense) in the complex form
     int split_out(int P) const { return (scalar || psi) ? 0 : P; }
@@ -268,6 +270,36 @@ void m2l_prepare(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& 
 // the products; loc must be zero for levels >= 2; count: boxes per level (device).
 template <typename T>
 void m2l_apply(Ctx* c, const Plan<T>& pl, const Levels& lv, const int* count, Grouped& gp, const T* mult, T* loc);
+
+// ---- RCR translations (rcr.cu) -------------------------------------------------
+// M2L by rotation - coaxial translation - back rotation with the coaxial conversion of
+// Eq. rcr1 (Sec. 4.4), two-potential form, FP32, one truncation number p <= RCR_PMAX.
+constexpr int RCR_PMAX = 20;
+struct RcrTables {
+    int p = 0;
+    int nc = 0;          // box pairs per chunk of the grouped pair list
+    int rot_table = 0;   // floats of one rotation table (forward or back) of one offset slot
+    int coax_dist = 0;   // floats of the coaxial blocks of one distance
+    int smem = 0;        // dynamic shared memory of the products kernel
+    int nsm = 0;         // its CTAs (one per streaming multiprocessor)
+    Buf rot;             // [316][2][rot_table]: forward (S basis), back (R basis)
+    Buf coax;            // [distinct |t|][coax_dist]
+    Buf dist_of;         // int[316]: distance index of each offset slot
+};
+// Builds the tables (FP64 on the GPU, stored FP32); synchronous.  LHV_EUNSUPPORTED above RCR_PMAX.
+void rcr_build(Ctx* c, int p, RcrTables& rt);
+void rcr_free(RcrTables& rt);
+// loc += the RCR translation of mult for every pair of gp (chunks of rt.nc pairs bucketed by
+// offset slot); rows of ld reals (phi then chi).
+void rcr_apply(Ctx* c, const RcrTables& rt, Grouped& gp, const float* mult, float* loc, int64_t ld);
+// Gauss-Legendre nodes and weights on [-1, 1] (nq points).
+void gauss_legendre_nodes(int nq, double* xi, double* w);
+// The 316 M2L offsets (dx, dy, dz of the source box from the target box) in slot order,
+// and the slot of each (dx+3)*49 + (dy+3)*7 + (dz+3).
+void m2l_offsets(std::vector<int>& offs, std::vector<int>& slot_of);
+// FP64 fused M2L tables (k-major [2P][2P] each, S(h=1) -> R(h=1)) at the translation vectors
+// t3 (three reals each, in box sides), into dst on the device; synchronous.
+void build_m2l_at(Ctx* c, int p, const std::vector<double>& t3, Buf& dst);
 
 // ---- P2P (p2p.cu) ------------------------------------------------------------
 template <typename T>

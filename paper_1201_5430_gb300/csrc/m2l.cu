@@ -102,6 +102,12 @@ void m2l_prepare(Ctx* c, const OpTables& ops, const TreeBufs& tb, const Levels& 
 template <typename T>
 void m2l_apply(Ctx* c, const Plan<T>& pl, const Levels& lv, const int* count, Grouped& gp, const T* mult, T* loc) {
     const int L = lv.L;
+    if constexpr (sizeof(T) == 4) {
+        if (pl.rcr) {  // rotation - coaxial - rotation (rcr.cu)
+            rcr_apply(c, *pl.rcr, gp, mult, loc, pl.ld);
+            return;
+        }
+    }
     // the tensor-core products read the multipoles split into TF32 hi/lo once
     const float* mhi = nullptr;
     const float* mlo = nullptr;

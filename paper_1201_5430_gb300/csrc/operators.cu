@@ -481,6 +481,43 @@ void m2l_offsets(std::vector<int>& offs, std::vector<int>& slot_of) {
             }
 }
 
+void build_m2l_at(Ctx* c, int p, const std::vector<double>& t3, Buf& dst) {
+    cudaStream_t s = stream_of(c);
+    const int64_t P = (int64_t)p * p, n = (int64_t)t3.size() / 3;
+    std::vector<Spec> specs;
+    std::vector<int64_t> off;
+    for (int64_t k = 0; k < n; ++k) {
+        Spec sp{};
+        sp.kind = K_M2L;
+        sp.ld = 2 * P;
+        sp.t[0] = t3[3 * k];
+        sp.t[1] = t3[3 * k + 1];
+        sp.t[2] = t3[3 * k + 2];
+        sp.pout = p;
+        sp.pin = p;
+        specs.push_back(sp);
+        off.push_back(k * 4 * P * P);
+    }
+    Buf dspec, doff;
+    try {
+        ensure(c, dspec, n * sizeof(Spec));
+        ensure(c, doff, n * sizeof(int64_t));
+        ensure(c, dst, n * 4 * P * P * sizeof(double));
+        cuda_check(cudaMemcpyAsync(dspec.ptr, specs.data(), n * sizeof(Spec), cudaMemcpyHostToDevice, s), "specs");
+        cuda_check(cudaMemcpyAsync(doff.ptr, off.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, s), "offs");
+        k_build_ops<<<(int)n, 256, 0, s>>>(dspec.as<Spec>(), dst.as<double>(), doff.as<int64_t>());
+        count_launch(c);
+        check_launch("build operators at t");
+        cuda_check(cudaStreamSynchronize(s), "operators at t");
+    } catch (...) {
+        cudaFree(dspec.ptr);
+        cudaFree(doff.ptr);
+        throw;
+    }
+    cudaFree(dspec.ptr);
+    cudaFree(doff.ptr);
+}
+
 template <typename T>
 void build_op(Ctx* c, int kind, int pout, int pin, Buf& dst) {
     cudaStream_t s = stream_of(c);
