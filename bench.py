@@ -395,6 +395,61 @@ def vfm_ring(torch, LHV, n=1 << 20, p=16, reps=3):
     return out
 
 
+def rcr_macs(p, padded=True):
+    """Multiply-adds per M2L pair of the RCR products (Sec. 4.4): the forward and back
+    rotations of both potentials (blocks of 2n+1, padded to 4 output rows in the kernel) and
+    the coaxial products of each order (A on phi, B on chi for the conversion, C on chi)."""
+    rot = sum((2 * n + 1) * ((2 * n + 4) // 4 * 4 if padded else 2 * n + 1) for n in range(p))
+    cx = 0
+    for m in range(p):
+        k = p - m
+        kk = (k + 3) // 4 * 4 if padded else k
+        cx += (2 if m else 1) * kk * k * (3 if m else 2)
+    return 2 * 2 * rot + cx
+
+
+def m2l_forms(torch, LHV, n=1 << 20, ps=(12, 16, 20), reps=2, fma_peak=None):
+    """M2L products by the fused tables on the tensor cores (TF32x3) against RCR translations
+    on the CUDA cores (FP32), uniform cube of n elements, far field only: time per evaluation
+    (CUDA events around the products), box pairs, useful flops and agreement of v."""
+    x, w = workloads.cube(n, 5)
+    X = torch.from_numpy(workloads.to_f4(x)).cuda()
+    W = torch.from_numpy(workloads.to_f4(w)).cuda()
+    out = {"n": n, "workload": "uniform cube", "rows": []}
+    for p in ps:
+        row = {"p": p}
+        vs = {}
+        for form, prec in (("phi_chi", "tf32x3"), ("rcr", "fp32")):
+            c = LHV(p=p, leaf_max=64, core_a=0.0005, eps=1e-6, precision=prec, terms="far")
+            c.set_form(form)
+            v4, s4 = c.evaluate_velocity_stretching(X, W)
+            torch.cuda.synchronize()
+            c.set_timing(True)
+            c.reset_stats()
+            for _ in range(reps):
+                c.evaluate_velocity_stretching(X, W, v4, s4)
+            torch.cuda.synchronize()
+            st = c.stats()
+            key = "fused_tf32x3" if form == "phi_chi" else "rcr_fp32"
+            row[key + "_ms"] = st["stage_ms"]["m2l_products"] / reps
+            row["pairs"] = st["m2l_pairs"]
+            row["leaf_level"] = st["leaf_level"]
+            vs[key] = v4[:, :3].double()
+            c.close()
+        row["rcr_over_fused"] = row["rcr_fp32_ms"] / row["fused_tf32x3_ms"]
+        row["rel_l2_v_rcr_vs_fused"] = float(torch.linalg.norm(vs["rcr_fp32"] - vs["fused_tf32x3"])
+                                             / torch.linalg.norm(vs["fused_tf32x3"]))
+        row["rcr_useful_flops_per_pair"] = 2 * rcr_macs(p, padded=False)
+        row["rcr_issued_flops_per_pair"] = 2 * rcr_macs(p)
+        row["fused_useful_flops_per_pair"] = 6 * p ** 4
+        tf = row["rcr_issued_flops_per_pair"] * row["pairs"] / (row["rcr_fp32_ms"] / 1e3) / 1e12
+        row["rcr_tflops_issued"] = tf
+        if fma_peak:
+            row["rcr_frac_of_fma_peak"] = tf / fma_peak
+        out["rows"].append(row)
+    return out
+
+
 def run_single(args, torch, LHV, local, world, rank, dist):
     from paper_1201_5430_gb300 import _lib, selector
     name = SINGLE[args.workload]
@@ -411,6 +466,9 @@ def run_single(args, torch, LHV, local, world, rank, dist):
 
     if args.profile:  # ncu target: one warm-up evaluation and one evaluation, nothing else
         c = ctx(16, "tf32x3")
+        if args.form == "rcr":
+            c = LHV(p=16, leaf_max=spec["leaf_max"], core_a=spec["a"], eps=spec["eps"], precision="fp32")
+            c.set_form("rcr")
         for _ in range(2):
             c.evaluate_velocity_stretching(x4, w4)
         torch.cuda.synchronize()
@@ -578,6 +636,7 @@ def run_single(args, torch, LHV, local, world, rank, dist):
     ratio = None if args.no_scalar_ratio else scalar_ratio(torch, LHV)
     batched = None if args.no_batched else batched_form(torch, LHV, min(args.steps, 3), 3)
     filaments = None if args.no_filaments else vfm_ring(torch, LHV)
+    rcr = None if args.no_rcr else m2l_forms(torch, LHV, fma_peak=fma_peak)
 
     if rank != 0:
         if dist:
@@ -627,6 +686,7 @@ def run_single(args, torch, LHV, local, world, rank, dist):
         "t_vs_over_t_phigrad": ratio,
         "batched_form_blobs64": batched,
         "filaments_ring": filaments,
+        "m2l_rcr_vs_fused": rcr,
         "cpu_baseline": cb,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(2 * n * 16),
                 "d2h_bytes_per_step": int(2 * n * 16), "steps": e2e_steps},
@@ -799,6 +859,10 @@ def main():
                          "configs' colliding rings), blobs64 (the batched form)")
     ap.add_argument("--precision", default="tf32x3", choices=["tf32x3", "fp32"],
                     help="blobs64 only: tf32x3 (M2L on the tensor cores) or fp32")
+    ap.add_argument("--no-rcr", action="store_true",
+                    help="skip the M2L products by RCR translations against the fused tables (uniform cube)")
+    ap.add_argument("--form", default="phi_chi", choices=["phi_chi", "rcr"],
+                    help="--profile only: the far-field form of the profiled evaluations (rcr: p = 16, FP32)")
     ap.add_argument("--profile", action="store_true",
                     help="ncu target: one warm-up evaluation and one evaluation of the workload, nothing else")
     args = ap.parse_args()
