@@ -396,16 +396,16 @@ def vfm_ring(torch, LHV, n=1 << 20, p=16, reps=3):
 
 
 def rcr_macs(p, padded=True):
-    """Multiply-adds per M2L pair of the RCR products (Sec. 4.4): the forward and back
-    rotations of both potentials (blocks of 2n+1, padded to 4 output rows in the kernel) and
-    the coaxial products of each order (A on phi, B on chi for the conversion, C on chi)."""
-    rot = sum((2 * n + 1) * ((2 * n + 4) // 4 * 4 if padded else 2 * n + 1) for n in range(p))
-    cx = 0
-    for m in range(p):
-        k = p - m
-        kk = (k + 3) // 4 * 4 if padded else k
-        cx += (2 if m else 1) * kk * k * (3 if m else 2)
-    return 2 * 2 * rot + cx
+    """Multiply-adds per M2L pair of the RCR products (Sec. 4.4) as the kernel runs them: the
+    z-phases (2 x 2 per order m > 0) and the y-turn blocks (even class n + 1, odd class n per
+    degree; output rows padded to 4 in the kernel) both ways for both potentials, the coaxial
+    blocks A_m (both potentials, Re and Im) and the conversion of Eq. rcr1."""
+    q = (lambda k: (k + 3) // 4 * 4) if padded else (lambda k: k)
+    y = sum((n + 1) * q(n + 1) + n * q(n) for n in range(p))
+    z = 4 * sum(n for n in range(p))
+    cx = sum((2 if m else 1) * (p - m) * q(p - m) for m in range(p))
+    conv = sum((2 if m else 0) + ((2 if m else 1) if n + 1 < p else 0) for n in range(p) for m in range(n + 1))
+    return 2 * 2 * (y + z) + 2 * cx + conv
 
 
 def m2l_forms(torch, LHV, n=1 << 20, ps=(12, 16, 20), reps=2, fma_peak=None):
@@ -772,6 +772,88 @@ def batched_form(torch, LHV, steps, warmup, rank=0, world=1, precision="tf32x3")
     return out
 
 
+def run_learned_trajectory(args, torch, LHV, rank):
+    """The learned form over the leapfrog pair's trajectory: per-step selection (sampled
+    checks against FP64 direct sums every 10 steps), against uniform TF32x3 p = 16 (the
+    smallest tensor-core p that reaches eps on this workload) over the same consecutive RK4
+    steps from the initial state; L2 flushed before each step, CUDA events around each; the
+    final states' eps_2(v), eps_2(s) at 1000 sampled elements against FP64 direct sums."""
+    from paper_1201_5430_gb300 import selector
+    name = SINGLE["leapfrog"]
+    x, w, spec = workloads.make(name)
+    n = x.shape[0]
+    steps = args.trajectory_steps
+    x0 = torch.from_numpy(workloads.to_f4(x)).cuda()
+    w0 = torch.from_numpy(workloads.to_f4(w)).cuda()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    W, b, _ = selector.load()
+    idx = torch.from_numpy(np.random.default_rng(0).choice(n, 1000, replace=False).astype(np.int32)).cuda()
+    il = idx.long()
+    arms, finals = {}, {}
+    for key in ("uniform_tf32x3_p16", "learned_tf32x3"):
+        learned = key.startswith("learned")
+        c = LHV(p=spec["p"] if learned else 16, leaf_max=spec["leaf_max"], core_a=spec["a"], eps=spec["eps"],
+                precision="tf32x3")
+        if learned:
+            c.set_selector(W, b, eps=EPS, check_every=10, check_samples=1000)
+        x4, w4 = x0.clone(), w0.clone()
+        for _ in range(3):
+            c.step(x4, w4, spec["dt"])
+        x4.copy_(x0)
+        w4.copy_(w0)
+        torch.cuda.synchronize()
+        c.set_timing(True)
+        c.reset_stats()
+        times, schedules = [], {}
+        with Clocks(0) as clk:
+            for _ in range(steps):
+                flush.zero_()
+                ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ea.record(stream)
+                c.step(x4, w4, spec["dt"])
+                eb.record(stream)
+                eb.synchronize()
+                times.append(ea.elapsed_time(eb))
+                if learned:
+                    k = ",".join(str(v) for v in c.stats()["level_p"])
+                    schedules[k] = schedules.get(k, 0) + 1
+        st = c.stats()
+        v, s_ = c.evaluate_velocity_stretching(x4, w4)
+        ref = LHV(p=4, leaf_max=spec["leaf_max"], core_a=spec["a"])
+        vr, sr = ref.direct_sampled(x4, w4, idx)
+        ref.close()
+        rec = {"ms_per_step": float(np.mean(times)), "ms_total": float(np.sum(times)),
+               "ms_per_step_first_last_10": [float(np.mean(times[:10])), float(np.mean(times[-10:]))],
+               "final_err_v": float(torch.linalg.norm(v[il].double()[:, :3] - vr[:, :3])
+                                    / torch.linalg.norm(vr[:, :3])),
+               "final_err_s": float(torch.linalg.norm(s_[il].double()[:, :3] - sr[:, :3])
+                                    / torch.linalg.norm(sr[:, :3])),
+               "leaf_level_final": st["leaf_level"], "clocks": clk.summary()}
+        if learned:
+            rec["schedules"] = schedules
+            rec["checks"] = st["selector"]["checks"]
+            rec["fallbacks"] = st["selector"]["fallbacks"]
+            rec["check_err_v_last"] = st["selector"]["err_v"]
+        arms[key] = rec
+        finals[key] = x4[:, :3].double().clone()
+        c.close()
+    x00 = x0[:, :3].double()
+    drift = float(torch.linalg.norm(finals["learned_tf32x3"] - finals["uniform_tf32x3_p16"])
+                  / torch.linalg.norm(finals["uniform_tf32x3_p16"] - x00))
+    speed = arms["uniform_tf32x3_p16"]["ms_per_step"] / arms["learned_tf32x3"]["ms_per_step"]
+    if rank == 0:
+        print(json.dumps({"metric": METRIC + " (learned form over the trajectory)",
+                          "value": 4 * n / (arms["learned_tf32x3"]["ms_per_step"] / 1e3), "unit": UNIT,
+                          "n_gpus": 1, "steps": steps, "warmup": 3,
+                          "ms_per_step": arms["learned_tf32x3"]["ms_per_step"], "higher_is_better": True,
+                          "scaling": "weak", "vs_baseline": None, "dtype": "f32+tf32x3", "data": "synthetic",
+                          "config": {"workload": name, "n": n, "dt": spec["dt"], "eps": EPS,
+                                     "l2": "flushed before every step (256 MB write)"},
+                          "speedup_learned_vs_uniform_p16": speed,
+                          "final_positions_rel_diff_vs_displacement": drift, "arms": arms}), flush=True)
+
+
 def run_blobs64(args, torch, LHV, local, world, rank, dist):
     """The batched form's own line (see batched_form)."""
     r = batched_form(torch, LHV, args.steps, args.warmup, rank, world, args.precision)
@@ -854,11 +936,14 @@ def main():
                     help="skip the vortex filament ring (segments, Sec. 5.3)")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched form (64 blob systems: batched, CUDA graph, per system)")
-    ap.add_argument("--workload", default="leapfrog", choices=list(SINGLE) + ["blobs64", "offset_rings", "filaments"],
+    ap.add_argument("--workload", default="leapfrog",
+                    choices=list(SINGLE) + ["blobs64", "offset_rings", "filaments", "leapfrog_learned"],
                     help="leapfrog (headline), ring_262144 (single ring), offset_rings (mixed precision on "
                          "configs' colliding rings), blobs64 (the batched form)")
     ap.add_argument("--precision", default="tf32x3", choices=["tf32x3", "fp32"],
                     help="blobs64 only: tf32x3 (M2L on the tensor cores) or fp32")
+    ap.add_argument("--trajectory-steps", type=int, default=100,
+                    help="leapfrog_learned: consecutive RK4 steps of each arm")
     ap.add_argument("--no-rcr", action="store_true",
                     help="skip the M2L products by RCR translations against the fused tables (uniform cube)")
     ap.add_argument("--form", default="phi_chi", choices=["phi_chi", "rcr"],
@@ -892,6 +977,8 @@ def main():
                               "dtype": "f32+tf32x3", "data": "synthetic",
                               "config": {"workload": "vfm_ring", "n": r["n"], "p": r["p"]}, "details": r}),
                   flush=True)
+    elif args.workload == "leapfrog_learned":
+        run_learned_trajectory(args, torch, LHV, rank)
     elif args.workload == "blobs64":
         run_blobs64(args, torch, LHV, local, world, rank, dist)
     elif args.workload == "offset_rings":

@@ -277,14 +277,16 @@ void m2l_apply(Ctx* c, const Plan<T>& pl, const Levels& lv, const int* count, Gr
 constexpr int RCR_PMAX = 20;
 struct RcrTables {
     int p = 0;
-    int nc = 0;          // box pairs per chunk of the grouped pair list
-    int rot_table = 0;   // floats of one rotation table (forward or back) of one offset slot
-    int coax_dist = 0;   // floats of the coaxial blocks of one distance
-    int smem = 0;        // dynamic shared memory of the products kernel
-    int nsm = 0;         // its CTAs (one per streaming multiprocessor)
-    Buf rot;             // [316][2][rot_table]: forward (S basis), back (R basis)
-    Buf coax;            // [distinct |t|][coax_dist]
-    Buf dist_of;         // int[316]: distance index of each offset slot
+    int nc = 0;           // box pairs per chunk of the grouped pair list
+    int slot_floats = 0;  // floats of one offset slot's rotation tables [Y fwd | Y back | Z fwd | Z back]
+    int coax_floats = 0;  // floats of one distance's coaxial blocks and conversion coefficients
+    int smem = 0;         // dynamic shared memory of the products kernel
+    int nsm = 0;          // streaming multiprocessors
+    int ctas_per_sm = 1;  // resident CTAs of the products kernel per SM (its grid: nsm x this)
+    float resid = 0.f;    // largest table entry found outside the assumed structure (FP64 rounding)
+    Buf rot;              // [316][slot_floats]
+    Buf coax;             // [distinct |t|][coax_floats]
+    Buf dist_of;          // int[316]: distance index of each offset slot
 };
 // Builds the tables (FP64 on the GPU, stored FP32); synchronous.  LHV_EUNSUPPORTED above RCR_PMAX.
 void rcr_build(Ctx* c, int p, RcrTables& rt);
