@@ -7,7 +7,9 @@ standard 189-box M2L stencil at a depth l_max chosen for speed (Sec. 4 table;
 Sec. 5). The construction below is the reading used throughout this repository:
 
 * cube: origin x0 = per-axis minimum of the FP32 positions; side = the smallest
-  power of two >= the largest per-axis extent (1 if the extent is 0);
+  r_q 2^k >= the largest per-axis extent (k an integer), r_q = r_K (below) rounded up
+  to a 4-bit mantissa, so that the box side of one level lies in [r_K, 1.125 r_K);
+  without a core (a = 0) the smallest power of two >= the extent; 1 if the extent is 0;
 * keys: q = floor((x - x0) * 2^21 / side) in FP64, clamped to [0, 2^21 - 1];
   the key interleaves the 21 bits of (qx, qy, qz) with x in bit 0, y in bit 1,
   z in bit 2 of each triple; elements are stably sorted by key;
@@ -26,22 +28,35 @@ import numpy as np
 from scipy.optimize import brentq
 from scipy.special import erfc
 
-__all__ = ["cube", "morton_keys", "leaf_level", "core_cutoff", "Tree", "build_tree"]
+__all__ = ["cube", "core_unit", "morton_keys", "leaf_level", "core_cutoff", "Tree", "build_tree"]
 
 KEY_BITS = 21
 
 
-def cube(x):
-    """Cube origin (FP32 minimum, as float64) and power-of-two side."""
+def core_unit(rK):
+    """r_K rounded up to a 4-bit mantissa (0 without a core)."""
+    if not rK > 0.0:
+        return 0.0
+    mant, e = math.frexp(rK)                # rK = mant * 2^e, 0.5 <= mant < 1
+    return math.ldexp(math.ceil(mant * 16.0) / 16.0, e)
+
+
+def cube(x, unit=0.0):
+    """Cube origin (FP32 minimum, as float64) and side: the smallest unit * 2^k >= the
+    largest extent (k an integer), unit = 1 when 0 (a power of two)."""
     x = np.asarray(x, dtype=np.float32).reshape(-1, 3)
     lo = x.min(axis=0).astype(np.float64)
     hi = x.max(axis=0).astype(np.float64)
     extent = float((hi - lo).max())
     if extent <= 0.0:
         return lo, 1.0
-    mant, e = math.frexp(extent)            # extent = mant * 2^e, 0.5 <= mant < 1
-    side = math.ldexp(1.0, e - 1) if mant == 0.5 else math.ldexp(1.0, e)
-    return lo, side
+    u = unit if unit > 0.0 else 1.0
+    k = 0
+    while math.ldexp(u, k) < extent:
+        k += 1
+    while math.ldexp(u, k - 1) >= extent:
+        k -= 1
+    return lo, math.ldexp(u, k)
 
 
 def quantise(x, x0, side):
@@ -69,8 +84,8 @@ def deinterleave(key):
     return q
 
 
-def morton_keys(x):
-    x0, side = cube(x)
+def morton_keys(x, unit=0.0):
+    x0, side = cube(x, unit)
     return interleave(quantise(x, x0, side)), x0, side
 
 
@@ -117,7 +132,7 @@ class Tree:
     def __init__(self, x, leaf_max, a, eps, L_override=None):
         x = np.asarray(x, dtype=np.float32).reshape(-1, 3)
         self.n = x.shape[0]
-        keys, self.x0, self.side = morton_keys(x)
+        keys, self.x0, self.side = morton_keys(x, core_unit(core_cutoff(a, eps)))
         self.perm = np.argsort(keys, kind="stable")
         self.keys = keys[self.perm]
         self.L = leaf_level(self.keys, leaf_max, self.side, a, eps) if L_override is None else int(L_override)

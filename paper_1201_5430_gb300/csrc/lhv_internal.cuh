@@ -27,7 +27,7 @@ template <> struct Vec4<float> { using type = float4; };
 template <> struct Vec4<double> { using type = dbl4; };
 template <typename T> using vec4_t = typename Vec4<T>::type;
 
-// Cube of one system: origin (FP32 minimum per axis) and power-of-two side.
+// Cube of one system: origin (FP32 minimum per axis) and side (core_unit times a power of two).
 struct SysCube {
     double x0[3];
     double side;
@@ -123,6 +123,8 @@ template <typename T>
 int build_tree(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const vec4_t<T>* x4, const vec4_t<T>* w4,
                TreeBufs& tb, Levels& lv, TreeParams& hp, Error& err);
 int key_bits_for(int nsys);
+// r_K rounded up to a 4-bit mantissa (0 for no core): the cube side is this times a power of two.
+double core_unit(double rK);
 // Rows of the real boxes of levels l0..l1 (device counts dcount[l]; row r of a level at
 // data + (r - row0) row_len, r from lv.off[l]) set to value.
 template <typename T>

@@ -3,8 +3,12 @@
 //
 // The paper fixes the data structure only as "octree, neighbor lists" (Sec. 4,
 // table of FMM stages) with the standard 189-box M2L stencil (Sec. 5).  The
-// construction here is: cube origin = per-axis minimum, side = the smallest
-// power of two >= the largest extent; q = floor((x - x0) 2^21 / side) in FP64,
+// construction here is: cube origin = per-axis minimum; side = the smallest
+// r_q 2^k >= the largest extent (k an integer), with r_q the core radius r_K
+// below rounded up to a 4-bit mantissa, so that the box side of some level lies
+// in [r_K, 1.125 r_K) and the core rule below can stop the tree there (without a
+// core: the smallest power of two >= the largest extent); q = floor((x - x0) 2^21 /
+// side) in FP64,
 // clamped to [0, 2^21 - 1]; key = 63-bit interleave with x in bit 0 of each
 // triple; stable sort by key (ties keep the caller's order); leaf level
 // L = min(L_leaf, L_K, max_level) where L_leaf is the shallowest level with at
@@ -19,6 +23,14 @@
 #include "lhv_internal.cuh"
 
 namespace lhv {
+
+// r_K rounded up to a 4-bit mantissa (0 for no core): the unit of the cube side
+double core_unit(double rK) {
+    if (!(rK > 0.0)) return 0.0;
+    int e;
+    const double m = std::frexp(rK, &e);  // rK = m 2^e, 0.5 <= m < 1
+    return std::ldexp(std::ceil(m * 16.0) / 16.0, e);
+}
 
 // ---------------------------------------------------------------------------
 // Bit interleave helpers (21 bits per axis into 63 bits)
@@ -92,9 +104,10 @@ __global__ void k_bbox_partial(int parts, const int64_t* __restrict__ sysoff, co
     if (threadIdx.x < 6) part[blockIdx.x * 6 + threadIdx.x] = (double)s[threadIdx.x][0];
 }
 
-// one block per system: its cube (an empty system gets the unit cube at the origin)
+// one block per system: its cube (an empty system gets the unit cube at the origin); rq > 0:
+// the side is the smallest rq 2^k >= the extent, else the smallest power of two
 __global__ void k_bbox_final(int parts, const double* __restrict__ part, SysCube* __restrict__ cubes,
-                             TreeParams* __restrict__ tp) {
+                             TreeParams* __restrict__ tp, double rq) {
     __shared__ double r[6][256];
     const int sys = blockIdx.x;
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
@@ -125,9 +138,13 @@ __global__ void k_bbox_final(int parts, const double* __restrict__ part, SysCube
     }
     double side = 1.0;
     if (ext > 0.0) {
+        const double unit = rq > 0.0 ? rq : 1.0;
         int e;
-        double mant = frexp(ext, &e);  // ext = mant 2^e, 0.5 <= mant < 1
-        side = (mant == 0.5) ? ldexp(1.0, e - 1) : ldexp(1.0, e);
+        frexp(ext / unit, &e);  // a first guess of k, then the exact test on unit 2^k
+        int k = e;
+        while (ldexp(unit, k) < ext) ++k;
+        while (ldexp(unit, k - 1) >= ext) --k;
+        side = ldexp(unit, k);
     }
     cubes[sys].side = side;
     if (sys == 0) tp->deepest_shared = -1;
@@ -669,7 +686,7 @@ int build_tree(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const vec4_t<
     SysCube* cubes = tb.cubes.as<SysCube>();
     k_bbox_partial<T><<<nsys * parts, 256, 0, s>>>(parts, dsysoff, x4, w4, part, &tp->nonfinite);
     count_launch(c);
-    k_bbox_final<<<nsys, 256, 0, s>>>(parts, part, cubes, tp);
+    k_bbox_final<<<nsys, 256, 0, s>>>(parts, part, cubes, tp, core_unit(ctx_rK(c)));
     count_launch(c);
     k_morton<T><<<grid_for(nn, 256), 256, 0, s>>>(nn, nsys, bits, dsysoff, cubes, x4, tb.keys_a.as<uint64_t>(),
                                                    tb.idx_a.as<int>());
@@ -965,7 +982,7 @@ extern "C" int lhv_morton_sort_noalloc(int64_t n, const float* x4, const float* 
     const int parts = std::max(1, std::min(NOALLOC_MAX_PARTS, (int)((n + 4095) / 4096)));
     k_noalloc_init<<<1, 32, 0, s>>>(n, sysoff, tp);
     k_bbox_partial<float><<<parts, 256, 0, s>>>(parts, sysoff, x, w, part, &tp->nonfinite);
-    k_bbox_final<<<1, 256, 0, s>>>(parts, part, cube, tp);
+    k_bbox_final<<<1, 256, 0, s>>>(parts, part, cube, tp, 0.0);
     k_morton<float><<<grid_for(n, 256), 256, 0, s>>>(n, 1, bits, sysoff, cube, x, keys, perm);
 
     // 8 passes of 8 bits; the even count leaves the result in the caller's arrays

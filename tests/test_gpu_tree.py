@@ -62,7 +62,7 @@ def test_repeated_trees_in_one_context():
         keys = ctx.export("keys").cpu().numpy().view(np.uint64)
         perm = ctx.export("perm").cpu().numpy()
         np.testing.assert_array_equal(np.sort(perm), np.arange(xs.shape[0]))
-        okeys, _, _ = T.morton_keys(xs)
+        okeys, _, _ = T.morton_keys(xs, T.core_unit(T.core_cutoff(a, 1e-6)))
         np.testing.assert_array_equal(keys, okeys[perm])
         if k != 1:  # a first tree, and the fallback, are fully sorted
             np.testing.assert_array_equal(perm, tr.perm)
@@ -106,7 +106,7 @@ def test_full_size_ring_keys():
     from paper_1201_5430_gb300 import LHV
     ctx = LHV(p=12, leaf_max=64, core_a=workloads.RING_CORE_A, eps=1e-6)
     ctx.build_tree(dev(x, "fp32"))
-    keys, x0, side = T.morton_keys(x)
+    keys, x0, side = T.morton_keys(x, T.core_unit(T.core_cutoff(workloads.RING_CORE_A, 1e-6)))
     perm = np.argsort(keys, kind="stable")
     np.testing.assert_array_equal(ctx.export("keys").cpu().numpy().view(np.uint64), keys[perm])
     np.testing.assert_array_equal(ctx.export("perm").cpu().numpy(), perm)

@@ -1,4 +1,5 @@
 """Pins of the oracle's Morton keys, octree and FMM lists."""
+import math
 from fractions import Fraction
 
 import numpy as np
@@ -37,6 +38,61 @@ def test_cube_side_is_power_of_two():
         assert np.log2(side) == int(np.log2(side))
     x0, side = T.cube(np.zeros((3, 3), np.float32))
     assert side == 1.0
+
+
+def test_core_unit_rounds_up_to_four_bits():
+    for rK in (0.0408, 0.01, 0.0625, 1.0, 3.3e-5, 0.123456789):
+        u = T.core_unit(rK)
+        assert rK <= u < rK * (1.0 + 1.0 / 8.0)
+        mant, e = math.frexp(u)
+        assert mant * 16.0 == int(mant * 16.0)  # a 4-bit mantissa
+    assert T.core_unit(0.0) == 0.0
+
+
+def test_cube_side_with_core_unit():
+    u = T.core_unit(0.0408)
+    for ext in (0.05, 0.7, 2.2, 2.75, 2.7500001, 10.0):
+        x = np.array([[0.0, 0, 0], [ext, 0.01, 0.02]], dtype=np.float32)
+        x0, side = T.cube(x, u)
+        e = float(np.float32(ext))
+        assert side >= e and side / 2 < e
+        r = side / u
+        assert r == 2.0 ** round(math.log2(r))  # a power of two times the unit
+
+
+def test_leaf_side_lies_in_rK_to_one_and_an_eighth():
+    """With the core rule binding (many elements per leaf), the leaf box side is the unit."""
+    x, _ = ring(20000, 4)  # a thin ring: 4 elements per leaf needs a far deeper tree than L_K
+    for a in (0.002, 0.005, 0.0063):
+        rK = T.core_cutoff(a, 1e-6)
+        tr = T.build_tree(x, leaf_max=4, a=a, eps=1e-6)
+        h = tr.h(tr.L)
+        assert rK <= h < 1.125 * rK, (a, rK, h)
+        assert tr.h(tr.L + 1) < rK
+
+
+def test_keys_match_brute_force_with_core_unit():
+    """The keys are floor((x - x0) 2^21 / side) in FP64: equal to the exact rational value
+    wherever it is not within FP64 rounding of an integer."""
+    x, _ = cube(300, 5)
+    x = (x * np.float32(2.2) - np.float32(1.1)).astype(np.float32)
+    u = T.core_unit(T.core_cutoff(0.0063, 1e-6))
+    keys, x0, side = T.morton_keys(x, u)
+    assert side == u * 64.0
+    near = 0
+    for i in range(300):
+        q = []
+        for k in range(3):
+            v = (Fraction(float(x[i, k])) - Fraction(float(x0[k]))) * (1 << 21) / Fraction(side)
+            if abs(v - round(v)) < Fraction(1, 10 ** 6):
+                near += 1
+            q.append(min(max(math.floor(v), 0), (1 << 21) - 1))
+        key = 0
+        for b in range(21):
+            for k in range(3):
+                key |= ((q[k] >> b) & 1) << (3 * b + k)
+        if near == 0:
+            assert int(keys[i]) == key
 
 
 def test_sort_is_stable_permutation():
