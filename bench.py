@@ -70,18 +70,21 @@ def _measured_peaks():
 
 def _traffic_record(name, kernel_file):
     """dram bytes per launch from a committed ncu summary, if it was taken on the current
-    source of the kernel (null otherwise)."""
+    source of the kernel and of the tree that sets its work (null otherwise)."""
     path = os.path.join(ROOT, "profiles", name)
-    src = os.path.join(ROOT, "paper_1201_5430_gb300", "csrc", kernel_file)
-    if not (os.path.exists(path) and os.path.exists(src)):
+    csrc = os.path.join(ROOT, "paper_1201_5430_gb300", "csrc")
+    src, tree = os.path.join(csrc, kernel_file), os.path.join(csrc, "tree.cu")
+    if not (os.path.exists(path) and os.path.exists(src) and os.path.exists(tree)):
         return None
     rec = {}
     for line in open(path):
         if ":" in line:
             k, v = line.split(":", 1)
             rec[k.strip()] = v.strip()
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if rec.get("source_sha256_16") != sha:
+
+    def sha(f):
+        return hashlib.sha256(open(f, "rb").read()).hexdigest()[:16]
+    if rec.get("source_sha256_16") != sha(src) or rec.get("tree_sha256_16") != sha(tree):
         return None
     try:
         return float(rec["dram_bytes_per_launch"])
