@@ -148,8 +148,8 @@ const char* lhv_last_error(lhv_ctx* ctx);
  * stable sort, boxes per level, colleague lists (Sec. 4, "Create data
  * structure").  The cube: origin at the per-axis minimum; side the smallest
  * r_q 2^k >= the largest extent, r_q the core radius r_K (where the Gaussian core
- * of Eq. vem1 is 1 to eps/10) rounded up to a 4-bit mantissa, so that one level's
- * box side lies in [r_K, 1.125 r_K); without a core (core_a = 0) the smallest
+ * of Eq. vem1 is 1 to eps/10) rounded up to an 8-bit mantissa, so that one level's
+ * box side lies in [r_K, 1.008 r_K); without a core (core_a = 0) the smallest
  * power of two >= the largest extent.  Leaf level: the shallowest with at most
  * leaf_max elements per box, no deeper than the deepest whose box side is >= r_K.
  * Evaluation calls rebuild it themselves; this entry point exists to time or

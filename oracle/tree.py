@@ -8,7 +8,7 @@ Sec. 5). The construction below is the reading used throughout this repository:
 
 * cube: origin x0 = per-axis minimum of the FP32 positions; side = the smallest
   r_q 2^k >= the largest per-axis extent (k an integer), r_q = r_K (below) rounded up
-  to a 4-bit mantissa, so that the box side of one level lies in [r_K, 1.125 r_K);
+  to an 8-bit mantissa, so that the box side of one level lies in [r_K, 1.008 r_K);
   without a core (a = 0) the smallest power of two >= the extent; 1 if the extent is 0;
 * keys: q = floor((x - x0) * 2^21 / side) in FP64, clamped to [0, 2^21 - 1];
   the key interleaves the 21 bits of (qx, qy, qz) with x in bit 0, y in bit 1,
@@ -34,11 +34,11 @@ KEY_BITS = 21
 
 
 def core_unit(rK):
-    """r_K rounded up to a 4-bit mantissa (0 without a core)."""
+    """r_K rounded up to an 8-bit mantissa (0 without a core)."""
     if not rK > 0.0:
         return 0.0
     mant, e = math.frexp(rK)                # rK = mant * 2^e, 0.5 <= mant < 1
-    return math.ldexp(math.ceil(mant * 16.0) / 16.0, e)
+    return math.ldexp(math.ceil(mant * 256.0) / 256.0, e)
 
 
 def cube(x, unit=0.0):

@@ -123,7 +123,7 @@ template <typename T>
 int build_tree(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const vec4_t<T>* x4, const vec4_t<T>* w4,
                TreeBufs& tb, Levels& lv, TreeParams& hp, Error& err);
 int key_bits_for(int nsys);
-// r_K rounded up to a 4-bit mantissa (0 for no core): the cube side is this times a power of two.
+// r_K rounded up to an 8-bit mantissa (0 for no core): the cube side is this times a power of two.
 double core_unit(double rK);
 // Rows of the real boxes of levels l0..l1 (device counts dcount[l]; row r of a level at
 // data + (r - row0) row_len, r from lv.off[l]) set to value.

@@ -5,8 +5,8 @@
 // table of FMM stages) with the standard 189-box M2L stencil (Sec. 5).  The
 // construction here is: cube origin = per-axis minimum; side = the smallest
 // r_q 2^k >= the largest extent (k an integer), with r_q the core radius r_K
-// below rounded up to a 4-bit mantissa, so that the box side of some level lies
-// in [r_K, 1.125 r_K) and the core rule below can stop the tree there (without a
+// below rounded up to an 8-bit mantissa, so that the box side of some level lies
+// in [r_K, 1.008 r_K) and the core rule below can stop the tree there (without a
 // core: the smallest power of two >= the largest extent); q = floor((x - x0) 2^21 /
 // side) in FP64,
 // clamped to [0, 2^21 - 1]; key = 63-bit interleave with x in bit 0 of each
@@ -24,12 +24,12 @@
 
 namespace lhv {
 
-// r_K rounded up to a 4-bit mantissa (0 for no core): the unit of the cube side
+// r_K rounded up to an 8-bit mantissa (0 for no core): the unit of the cube side
 double core_unit(double rK) {
     if (!(rK > 0.0)) return 0.0;
     int e;
     const double m = std::frexp(rK, &e);  // rK = m 2^e, 0.5 <= m < 1
-    return std::ldexp(std::ceil(m * 16.0) / 16.0, e);
+    return std::ldexp(std::ceil(m * 256.0) / 256.0, e);
 }
 
 // ---------------------------------------------------------------------------

@@ -30,7 +30,7 @@ def cube_fp64():
 
 def test_fp64_cube_parity(cube_fp64):
     x, w, spec, ref, ctx, v, s = cube_fp64
-    assert ctx.stats()["leaf_level"] == ref.tree.L == 3
+    assert ctx.stats()["leaf_level"] == ref.tree.L == 4
     assert rel(v, ref.v) < 1e-10, rel(v, ref.v)
     assert rel(s, ref.s) < 1e-10, rel(s, ref.s)
     v0, _, s0 = direct.direct(x, w, spec["a"])

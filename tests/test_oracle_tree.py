@@ -40,12 +40,12 @@ def test_cube_side_is_power_of_two():
     assert side == 1.0
 
 
-def test_core_unit_rounds_up_to_four_bits():
+def test_core_unit_rounds_up_to_eight_bits():
     for rK in (0.0408, 0.01, 0.0625, 1.0, 3.3e-5, 0.123456789):
         u = T.core_unit(rK)
-        assert rK <= u < rK * (1.0 + 1.0 / 8.0)
+        assert rK <= u < rK * (1.0 + 1.0 / 128.0)
         mant, e = math.frexp(u)
-        assert mant * 16.0 == int(mant * 16.0)  # a 4-bit mantissa
+        assert mant * 256.0 == int(mant * 256.0)  # an 8-bit mantissa
     assert T.core_unit(0.0) == 0.0
 
 
@@ -60,14 +60,14 @@ def test_cube_side_with_core_unit():
         assert r == 2.0 ** round(math.log2(r))  # a power of two times the unit
 
 
-def test_leaf_side_lies_in_rK_to_one_and_an_eighth():
+def test_leaf_side_lies_just_above_rK():
     """With the core rule binding (many elements per leaf), the leaf box side is the unit."""
     x, _ = ring(20000, 4)  # a thin ring: 4 elements per leaf needs a far deeper tree than L_K
     for a in (0.002, 0.005, 0.0063):
         rK = T.core_cutoff(a, 1e-6)
         tr = T.build_tree(x, leaf_max=4, a=a, eps=1e-6)
         h = tr.h(tr.L)
-        assert rK <= h < 1.125 * rK, (a, rK, h)
+        assert rK <= h < (1.0 + 1.0 / 128.0) * rK, (a, rK, h)
         assert tr.h(tr.L + 1) < rK
 
 
