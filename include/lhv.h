@@ -175,7 +175,10 @@ int lhv_step_host(lhv_ctx* ctx, int64_t n, float* x4_host, float* w4_host, doubl
  * [nsys+1], offsets[0] = 0, non-decreasing; 1 <= nsys <= 4096).  Systems do not
  * interact; each gets its own cube and octree, all trees are built, translated
  * and summed by the same launches.  One leaf level serves the whole batch: the
- * deepest any system needs, capped by the core rule of the smallest cube.
+ * deepest any system needs, capped by the core rule of the smallest cube.  With a
+ * core (core_a > 0) every system's cube takes the largest side of the batch (its
+ * origin stays its own), so that the capped leaf level gives every system leaves
+ * of side r_q (see lhv_build_tree).
  * Morton keys keep the system id in their top bits and use
  * floor((63 - ceil(log2 nsys)) / 3) bits per axis.  FP32 / TF32X3 contexts. */
 int lhv_evaluate_batched(lhv_ctx* ctx, int nsys, const int64_t* offsets, const float* x4, const float* w4,

@@ -10,6 +10,9 @@ Sec. 5). The construction below is the reading used throughout this repository:
   r_q 2^k >= the largest per-axis extent (k an integer), r_q = r_K (below) rounded up
   to an 8-bit mantissa, so that the box side of one level lies in [r_K, 1.008 r_K);
   without a core (a = 0) the smallest power of two >= the extent; 1 if the extent is 0;
+  in a batch of independent systems with a core, every system takes the largest of the
+  systems' sides (``batch_side``; origins stay per system), so that the batch's one leaf
+  level gives every system leaves of side r_q;
 * keys: q = floor((x - x0) * 2^21 / side) in FP64, clamped to [0, 2^21 - 1];
   the key interleaves the 21 bits of (qx, qy, qz) with x in bit 0, y in bit 1,
   z in bit 2 of each triple; elements are stably sorted by key;
@@ -28,7 +31,7 @@ import numpy as np
 from scipy.optimize import brentq
 from scipy.special import erfc
 
-__all__ = ["cube", "core_unit", "morton_keys", "leaf_level", "core_cutoff", "Tree", "build_tree"]
+__all__ = ["cube", "core_unit", "batch_side", "morton_keys", "leaf_level", "core_cutoff", "Tree", "build_tree"]
 
 KEY_BITS = 21
 
@@ -41,11 +44,13 @@ def core_unit(rK):
     return math.ldexp(math.ceil(mant * 256.0) / 256.0, e)
 
 
-def cube(x, unit=0.0):
+def cube(x, unit=0.0, side=None):
     """Cube origin (FP32 minimum, as float64) and side: the smallest unit * 2^k >= the
-    largest extent (k an integer), unit = 1 when 0 (a power of two)."""
+    largest extent (k an integer), unit = 1 when 0 (a power of two); ``side`` given: that."""
     x = np.asarray(x, dtype=np.float32).reshape(-1, 3)
     lo = x.min(axis=0).astype(np.float64)
+    if side is not None:
+        return lo, float(side)
     hi = x.max(axis=0).astype(np.float64)
     extent = float((hi - lo).max())
     if extent <= 0.0:
@@ -84,8 +89,8 @@ def deinterleave(key):
     return q
 
 
-def morton_keys(x, unit=0.0):
-    x0, side = cube(x, unit)
+def morton_keys(x, unit=0.0, side=None):
+    x0, side = cube(x, unit, side)
     return interleave(quantise(x, x0, side)), x0, side
 
 
@@ -129,10 +134,10 @@ class Tree:
     sorted order), parent (index at level l-1), children (list of index lists),
     colleagues (list of index lists), il (list of index lists; empty for l < 2)."""
 
-    def __init__(self, x, leaf_max, a, eps, L_override=None):
+    def __init__(self, x, leaf_max, a, eps, L_override=None, side=None):
         x = np.asarray(x, dtype=np.float32).reshape(-1, 3)
         self.n = x.shape[0]
-        keys, self.x0, self.side = morton_keys(x, core_unit(core_cutoff(a, eps)))
+        keys, self.x0, self.side = morton_keys(x, core_unit(core_cutoff(a, eps)), side)
         self.perm = np.argsort(keys, kind="stable")
         self.keys = keys[self.perm]
         self.L = leaf_level(self.keys, leaf_max, self.side, a, eps) if L_override is None else int(L_override)
@@ -195,6 +200,16 @@ class Tree:
         return self.x0 + (self.levels[lev]["coords"][i].astype(np.float64) + 0.5) * self.h(lev)
 
 
-def build_tree(x, leaf_max=64, a=0.0, eps=1e-6, L_override=None):
-    """``L_override`` forces the leaf level (tests use it to switch the L_K rule off)."""
-    return Tree(x, leaf_max, a, eps, L_override)
+def build_tree(x, leaf_max=64, a=0.0, eps=1e-6, L_override=None, side=None):
+    """``L_override`` forces the leaf level (tests use it to switch the L_K rule off);
+    ``side`` the cube side (a system of a batch: ``batch_side``)."""
+    return Tree(x, leaf_max, a, eps, L_override, side)
+
+
+def batch_side(xs, a=0.0, eps=1e-6):
+    """The cube side of every system of a batch (positions xs, one array per system): with
+    a core the largest of the systems' own sides, else None (each keeps its own)."""
+    rK = core_cutoff(a, eps)
+    if not rK > 0.0 or len(xs) < 2:
+        return None
+    return max(cube(x, core_unit(rK))[1] for x in xs)

@@ -8,7 +8,8 @@
 // below rounded up to an 8-bit mantissa, so that the box side of some level lies
 // in [r_K, 1.008 r_K) and the core rule below can stop the tree there (without a
 // core: the smallest power of two >= the largest extent); q = floor((x - x0) 2^21 /
-// side) in FP64,
+// side) in FP64 (in a batch with a core every system takes the largest side of the
+// batch, origins staying per system),
 // clamped to [0, 2^21 - 1]; key = 63-bit interleave with x in bit 0 of each
 // triple; stable sort by key (ties keep the caller's order); leaf level
 // L = min(L_leaf, L_K, max_level) where L_leaf is the shallowest level with at
@@ -148,6 +149,17 @@ __global__ void k_bbox_final(int parts, const double* __restrict__ part, SysCube
     }
     cubes[sys].side = side;
     if (sys == 0) tp->deepest_shared = -1;
+}
+
+// A batch with a core: every system takes the largest side of the batch (origins stay its
+// own), so that the one leaf level of the batch, capped by the core rule, gives every system
+// leaves of side r_q (with its own side, a system with a larger cube would get leaves of
+// 2^j r_q at that level).
+__global__ void k_cube_common(SysCube* __restrict__ cubes, int nsys) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double side = 0.0;
+    for (int k = 0; k < nsys; ++k) side = fmax(side, cubes[k].side);
+    for (int k = 0; k < nsys; ++k) cubes[k].side = side;
 }
 
 __device__ inline int system_of(int64_t i, int nsys, const int64_t* __restrict__ sysoff) {
@@ -688,6 +700,10 @@ int build_tree(Ctx* c, int64_t n, int nsys, const int64_t* sysoff, const vec4_t<
     count_launch(c);
     k_bbox_final<<<nsys, 256, 0, s>>>(parts, part, cubes, tp, core_unit(ctx_rK(c)));
     count_launch(c);
+    if (nsys > 1 && ctx_rK(c) > 0.0) {
+        k_cube_common<<<1, 32, 0, s>>>(cubes, nsys);
+        count_launch(c);
+    }
     k_morton<T><<<grid_for(nn, 256), 256, 0, s>>>(nn, nsys, bits, dsysoff, cubes, x4, tb.keys_a.as<uint64_t>(),
                                                    tb.idx_a.as<int>());
     count_launch(c);

@@ -21,11 +21,23 @@ def _batch(systems):
     return x, w, off
 
 
+def _same_extent(systems, ext=0.9):
+    """The systems scaled to one extent, so that each one's own cube side is the batch's."""
+    out = []
+    for xs, ws in systems:
+        lo = xs.min(axis=0)
+        e = float((xs.max(axis=0) - lo).max())
+        out.append((((xs - lo) * np.float32(ext / e) + lo).astype(np.float32), ws))
+    return out
+
+
 def test_batched_matches_single_systems():
     from paper_1201_5430_gb300 import LHV
-    systems = _systems()
-    x, w, off = _batch(systems)
     a, p = 0.01, 8
+    systems = _same_extent(_systems())
+    sides = {T.cube(xs, T.core_unit(T.core_cutoff(a, 1e-6)))[1] for xs, _ in systems}
+    assert len(sides) == 1  # each system's own side is the batch's
+    x, w, off = _batch(systems)
     ctx = LHV(p=p, leaf_max=64, core_a=a, precision="fp32")
     v4, s4 = ctx.evaluate_batched(off, dev(x, "fp32"), dev(w, "fp32"))
     L = ctx.stats()["leaf_level"]
@@ -46,12 +58,14 @@ def test_batched_against_oracle():
     ctx = LHV(p=p, leaf_max=64, core_a=a, precision="fp32")
     v4, s4 = ctx.evaluate_batched(off, dev(x, "fp32"), dev(w, "fp32"))
     L = ctx.stats()["leaf_level"]
-    # per-system leaf levels of the oracle's rule; the batch uses the deepest, within every core cap
-    Ls = [T.build_tree(xs, leaf_max=64, a=a).L for xs, _ in systems]
+    # per-system leaf levels of the oracle's rule with the batch's common cube side; the batch
+    # uses the deepest, within the core cap
+    bs = T.batch_side([xs for xs, _ in systems], a)
+    Ls = [T.build_tree(xs, leaf_max=64, a=a, side=bs).L for xs, _ in systems]
     assert L == max(Ls)
     v, s = host3(v4), host3(s4)
     for k, (xs, ws) in enumerate(systems):
-        ref = ofmm.fmm(xs, ws, p, a=a, tree=T.build_tree(xs, leaf_max=64, a=a, L_override=L))
+        ref = ofmm.fmm(xs, ws, p, a=a, tree=T.build_tree(xs, leaf_max=64, a=a, L_override=L, side=bs))
         sl = slice(off[k], off[k + 1])
         assert rel(v[sl], ref.v) < 1e-6 and rel(s[sl], ref.s) < 1e-6, (k, rel(v[sl], ref.v), rel(s[sl], ref.s))
 

@@ -95,6 +95,24 @@ def test_keys_match_brute_force_with_core_unit():
             assert int(keys[i]) == key
 
 
+def test_batch_side_is_the_largest_and_gives_leaves_at_the_unit():
+    """A batch with a core: every system takes the largest own side; the core-capped leaf
+    level of that side has leaves of the unit for every system."""
+    a = 0.01
+    u = T.core_unit(T.core_cutoff(a, 1e-6))
+    xs = [(ring(3000, s)[0] * np.float32(f)).astype(np.float32) for s, f in ((1, 0.2), (2, 0.45), (3, 0.9))]
+    own = [T.cube(x, u)[1] for x in xs]
+    assert len(set(own)) > 1
+    bs = T.batch_side(xs, a)
+    assert bs == max(own)
+    lev = round(math.log2(bs / u))
+    assert bs / 2 ** lev == u
+    for x in xs:
+        tr = T.build_tree(x, leaf_max=1, a=a, side=bs)
+        assert tr.side == bs and tr.L == lev and tr.h(tr.L) == u
+    assert T.batch_side(xs, 0.0) is None and T.batch_side(xs[:1], a) is None
+
+
 def test_sort_is_stable_permutation():
     x = np.array([[0.1, 0.1, 0.1]] * 5 + [[0.9, 0.9, 0.9]] * 3 + [[0.1, 0.1, 0.1]] * 2, dtype=np.float32)
     tr = T.build_tree(x, leaf_max=2)
