@@ -17,7 +17,7 @@ def test_error_falls_with_p():
     a = 0.01
     v0, u0, s0 = direct.direct(x, w, a)
     tr = T.build_tree(x, leaf_max=16, a=a)
-    assert tr.L == 3
+    assert tr.L == 4  # the core-aligned cube (side 1.906) puts 16 or fewer per box at level 4
     ev, es = [], []
     for p in (3, 6, 9, 12):
         r = fmm.fmm(x, w, p, tree=tr, a=a)
@@ -31,6 +31,7 @@ def test_error_falls_with_p():
 def test_shallow_tree_is_exact():
     """With fewer than 3 levels no box is well separated: O2 is the direct sum."""
     x, w = cube(150, 5)
+    x = (x * np.float32(0.9)).astype(np.float32)  # a tight cube (side 0.953 = 8 r_q), level 1 splits evenly
     r = fmm.fmm(x, w, 6, leaf_max=64, a=0.02)
     assert r.tree.L < 2
     v0, u0, s0 = direct.direct(x, w, 0.02)
