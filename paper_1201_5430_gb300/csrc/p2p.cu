@@ -1084,7 +1084,11 @@ void run_p2p(Ctx* c, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs, 
         const double xc = sizeof(T) == 4 ? 6.5 : 9.0;
         cc.x2_cut = (T)(xc * xc);
         cc.u_series = (T)(sizeof(T) == 4 ? LHV_CORE_U_SER : 1.0);
-        cc.r2_cut = (T)(xc * xc * a * a);
+        // the packed FP32 kernel's warp vote: the core fit runs for a step only if a pair lies
+        // inside r_K (1 - K < eps/10 beyond it, the criterion of the tree's core rule and of the
+        // far field, which takes K = 1 for every pair it handles), capped at x_cut a
+        const double rv = ctx_rK(c) > 0.0 ? std::min(xc * a, ctx_rK(c)) : xc * a;
+        cc.r2_cut = (T)(rv * rv);
         cc.t_scale = (T)(a * (double)LHV_CORE_Y_SCALE);
         cc.nr_scale = (T)(-s2pi / a);
         cc.c3_3n = (T)(-s2pi / (3.0 * a * a * a));
