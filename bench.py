@@ -678,6 +678,8 @@ def run_single(args, torch, LHV, local, world, rank, dist):
                          "peak_kind": "measured in this run: tcgen05.mma kind::tf32 probe" if tc
                          else "measured FP32 FMA probe", "box_pairs": st["m2l_pairs"],
                          "flops_per_pair": 6 * m2l_p ** 4, "useful_only": "split products issue 3x these flops",
+                         "frac_issued": (3.0 if tc else 1.0) * (m2l_flops / (m2l_ms / 1e3) / 1e12)
+                         / (tf32_peak if tc else fma_peak) if m2l_ms and (tf32_peak if tc else fma_peak) else None,
                          "mean_launch_ms": m2l_ms},
         "peaks_measured": probes,
         "peaks_driver": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained")},
