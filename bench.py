@@ -53,6 +53,10 @@ SINGLE = {"leapfrog": "leapfrog_rings_4194304", "ring_262144": "ring_262144"}
 # g = f'/r (2), w_j x d (9), v += f (w_j x d) (6), sum f w_j (6), (w_i . d) and g (w_i . d) (6),
 # s += g (w_i . d)(w_j x d) (6) = 46 flops
 P2P_FLOPS_PER_PAIR = 46
+# extra FP32 flops of a pair inside the core radius r_K (the evaluation of K, Eq. vem1, on top of
+# the singular terms): u 1, t 2, degree-7 polynomial 14, r and R 3, exp argument 1 (the exp on
+# the SFU), K 2, f K 1, g 2
+P2P_CORE_FLOPS_PER_PAIR = 26
 # the oracle sample of the CPU legs: the headline geometry at 2 x 2048 elements
 CPU_SAMPLE_PER_RING = 2048
 
@@ -90,6 +94,37 @@ def _traffic_record(name, kernel_file):
         return float(rec["dram_bytes_per_launch"])
     except (KeyError, ValueError):
         return None
+
+
+def core_cutoff(a, eps):
+    """r_K = x_K a with 1 - K(x_K a; a) = eps / 10 (Eq. vem1), by bisection (0 without a core)."""
+    import math
+    if a <= 0.0:
+        return 0.0
+
+    def g(x):
+        return math.erfc(x / math.sqrt(2.0)) + math.sqrt(2.0 / math.pi) * x * math.exp(-0.5 * x * x) - eps / 10.0
+    lo, hi = 0.0, 60.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        lo, hi = (mid, hi) if g(mid) > 0.0 else (lo, mid)
+    return 0.5 * (lo + hi) * a
+
+
+def core_pair_fraction(xs, begin, end, colleagues, rK, sample):
+    """Of the near-field pairs (target, colleague-leaf source, j != i) of the sorted targets
+    ``sample``, the share closer than r_K: the pairs that need the core evaluation of Eq. vem1.
+    xs: sorted positions (N, 3); begin/end: leaf element ranges; colleagues: (leaves, 27) leaf
+    indices or -1."""
+    leaf = np.searchsorted(begin, sample, side="right") - 1
+    close = total = 0
+    for i, b in zip(sample, leaf):
+        src = np.concatenate([np.arange(begin[c], end[c]) for c in colleagues[b] if c >= 0])
+        src = src[src != i]
+        d = xs[src] - xs[i]
+        close += int(((d * d).sum(axis=1) < rK * rK).sum())
+        total += src.shape[0]
+    return close / total if total else 0.0
 
 
 def cpu_model():
@@ -610,7 +645,24 @@ def run_single(args, torch, LHV, local, world, rank, dist):
         st = dict(screen_stats["tf32x3"], kernel_launches=st["kernel_launches"], graph=st.get("graph"))
     p2p_ms = st["stage_ms"]["p2p"] / max(st["stage_launches"]["p2p"], 1)
     pairs = st["p2p_pairs"]
-    achieved = P2P_FLOPS_PER_PAIR * pairs / (p2p_ms / 1e3) / 1e12
+    # the share of the pairs inside r_K (the core evaluation they need), on 2000 sampled targets of
+    # the initial tree (a context that builds it uncaptured, so its lists can be exported)
+    rK = core_cutoff(spec["a"], spec["eps"])
+    core_frac = 0.0
+    if rK > 0.0:
+        tc_ = ctx(16, "tf32x3")
+        tc_.build_tree(x0)
+        L = tc_.stats()["leaf_level"]
+        perm = tc_.export("perm").cpu().numpy()
+        rng_ = tc_.export("box_range", L).cpu().numpy().reshape(-1, 2)
+        col = tc_.export("colleagues", L).cpu().numpy().reshape(-1, 27)
+        tc_.close()
+        xs_np = x[perm].astype(np.float64)
+        samp = np.sort(np.random.default_rng(1).choice(n, 2000, replace=False))
+        core_frac = core_pair_fraction(xs_np, rng_[:, 0], rng_[:, 1], col, rK, samp)
+    flops_pair = P2P_FLOPS_PER_PAIR + P2P_CORE_FLOPS_PER_PAIR * core_frac
+    achieved = flops_pair * pairs / (p2p_ms / 1e3) / 1e12
+    achieved_singular = P2P_FLOPS_PER_PAIR * pairs / (p2p_ms / 1e3) / 1e12
     fma_peak = max(probes["ffma"]["rate"] or 0.0, probes["ffma2"]["rate"] or 0.0)
     m2l_ms = st["stage_ms"].get("m2l_products", 0.0) / max(st["stage_launches"].get("m2l_products", 0), 1)
     m2l_p = st["level_p"][-1] if st["level_p"] else spec["p"]
@@ -668,7 +720,12 @@ def run_single(args, torch, LHV, local, world, rank, dist):
                      "traffic": _traffic_record("p2p_leapfrog_traffic.txt", "p2p.cu"),
                      "peak_kind": "measured in this run: FP32 FMA probe (lhv_peak_probe, max of scalar and "
                                   "packed FP32x2), median of 20 launches at the running clocks",
-                     "pairs_per_launch": pairs, "flops_per_pair": P2P_FLOPS_PER_PAIR, "mean_launch_ms": p2p_ms},
+                     "pairs_per_launch": pairs, "flops_per_pair": flops_pair,
+                     "flops_per_pair_parts": {"singular": P2P_FLOPS_PER_PAIR, "core": P2P_CORE_FLOPS_PER_PAIR,
+                                              "core_pair_fraction": core_frac, "r_K": rK,
+                                              "core_fraction_sample": "2000 targets of the initial tree"},
+                     "frac_singular_only": achieved_singular / fma_peak if fma_peak else None,
+                     "mean_launch_ms": p2p_ms},
         "roofline_m2l": {"kernel": "M2L products, " + ("tcgen05 TF32 x3 (k_tc_gemm)" if tc else "CUDA cores"),
                          "bound": "tensor" if tc else "alu",
                          "achieved": m2l_flops / (m2l_ms / 1e3) / 1e12 if m2l_ms else None,
