@@ -761,7 +761,7 @@ def run_single(args, torch, LHV, local, world, rank, dist):
 
 
 def batched_form(torch, LHV, steps, warmup, rank=0, world=1, precision="tf32x3"):
-    """Batched form (configs[3]): 64 independent Gaussian-blob systems (sizes log-uniform in
+    """Batched form: 64 independent Gaussian-blob systems (sizes log-uniform in
     [1e4, 5e5], about 1e7 elements), one RK4 step per timed step from the same state, three
     arms in the same precision: (a) one lhv_step_batched call for all systems, (b) the same
     with the whole step as one CUDA graph replay, (c) the single-system path called once per
