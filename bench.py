@@ -1001,7 +1001,8 @@ def main():
     ap.add_argument("--workload", default="leapfrog",
                     choices=list(SINGLE) + ["blobs64", "offset_rings", "filaments", "leapfrog_learned"],
                     help="leapfrog (headline), ring_262144 (single ring), offset_rings (mixed precision on "
-                         "configs' colliding rings), blobs64 (the batched form)")
+                         "two offset colliding rings of 2,097,152 elements), blobs64 (the batched form), "
+                         "filaments (vortex filament ring), leapfrog_learned (the learned form over 100 steps)")
     ap.add_argument("--precision", default="tf32x3", choices=["tf32x3", "fp32"],
                     help="blobs64 only: tf32x3 (M2L on the tensor cores) or fp32")
     ap.add_argument("--trajectory-steps", type=int, default=100,
