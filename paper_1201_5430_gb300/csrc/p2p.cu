@@ -15,7 +15,9 @@
 //                 the series itself below x = 1;
 //   otherwise   : K = 1 - exp(-x^2/2) R(x), R(x) = exp(x^2/2) erfc(x/sqrt 2) +
 //                 sqrt(2/pi) x with its first term a degree-7 Chebyshev
-//                 interpolant in 1/x (FP32), or Eq. vem1 with erf (FP64).
+//                 interpolant in 1/x (FP32; the packed kernel interpolates
+//                 G = R / x instead, so that K / r^3 = 1/r^3 - exp(-x^2/2) G / (a r^2)),
+//                 or Eq. vem1 with erf (FP64).
 // The self pair j = i is excluded only in the source chunk that can hold it.
 // The far-field result (L2P) of the same element is added and the sum is
 // written in the caller's order.
@@ -37,9 +39,11 @@ template <typename T> struct CoreConsts {
     T a, inv_a, inv_a2, c3, c5;  // a, 1/a, 1/a^2, sqrt(2/pi)/a^3, sqrt(2/pi)/a^5
     T x2_cut;                 // (r/a)^2 beyond which K = 1 in this precision
     T u_series;               // (r/a)^2 below which the Taylor series is used
-    // packed FP32x2 kernel: r^2 cut, a LHV_CORE_Y_SCALE, -sqrt(2/pi)/a,
-    // -sqrt(2/pi)/(3 a^3), -(2/3) sqrt(2/pi)/a^5
-    T r2_cut, t_scale, nr_scale, c3_3n, c5_g;
+    // packed FP32x2 kernel: r^2 cut, a LHV_CORE_Y_SCALE, -sqrt(2/pi)/(3 a^3), -(2/3) sqrt(2/pi)/a^5
+    T r2_cut, t_scale, c3_3n, c5_g;
+    // packed kernel, fit region: log2(exp(-u/2) / a) = ue_scale r^2 + ue_shift; -sqrt(2/pi)/(3 a^2);
+    // (r/a)^2 of the series region as r^2
+    T ue_scale, ue_shift, c3_3a, r2_series;
     int smooth;
 };
 
@@ -353,29 +357,26 @@ __device__ __forceinline__ void fg2_core(const float2 (&r2)[SU], const float2 (&
 #pragma unroll
     for (int v = 1; v < SU; ++v) rmin = fminf(rmin, fminf(r2[v].x, r2[v].y));
     if (!__any_sync(0xffffffffu, rmin < cc.r2_cut)) return;
-    float2 u[SU];
+    // 1 - K = exp(-u/2) x G(y), so f K = f - (exp(-u/2) / a) G / r^2 (f r^3 = 1, x = r/a):
+    // e = exp(-u/2) / a in one fma and one ex2, the fit -G in y = a/r
 #pragma unroll
     for (int v = 0; v < SU; ++v) {
-        u[v] = mul2(r2[v], dup2(cc.inv_a2));
         const float2 t = fma2(ri[v], dup2(cc.t_scale), dup2(LHV_CORE_Y_SHIFT));  // from y = 1/x = a/r
-        float2 nE = kCoreFitN2[LHV_CORE_FIT_DEG];
+        float2 nG = kCoreFitG2[LHV_CORE_FIT_DEG];
 #pragma unroll
-        for (int k = LHV_CORE_FIT_DEG - 1; k >= 0; --k) nE = fma2(nE, t, kCoreFitN2[k]);
-        const float2 nR = fma2(mul2(r2[v], ri[v]), dup2(cc.nr_scale), nE);  // -R(x)
-        const float2 ue = mul2(u[v], dup2(-0.72134752044448170368f));      // exp(-u/2) = 2^(-u/(2 ln 2))
+        for (int k = LHV_CORE_FIT_DEG - 1; k >= 0; --k) nG = fma2(nG, t, kCoreFitG2[k]);  // -G(y)
+        const float2 ue = fma2(r2[v], dup2(cc.ue_scale), dup2(cc.ue_shift));
         float2 e;
         e.x = ex2_ftz(ue.x);
         e.y = ex2_ftz(ue.y);
-        f[v] = fma2(mul2(f[v], e), nR, f[v]);
-        gm[v] = mul2(fma2(e, dup2(cc.c3_3n), f[v]), ri2[v]);
+        f[v] = fma2(mul2(ri2[v], e), nG, f[v]);
+        gm[v] = mul2(fma2(e, dup2(cc.c3_3a), f[v]), ri2[v]);
     }
-    float umin = fminf(u[0].x, u[0].y);
-#pragma unroll
-    for (int v = 1; v < SU; ++v) umin = fminf(umin, fminf(u[v].x, u[v].y));
-    if (!__any_sync(0xffffffffu, umin < cc.u_series)) return;
+    if (!__any_sync(0xffffffffu, rmin < cc.r2_series)) return;
 #pragma unroll
     for (int v = 0; v < SU; ++v) {
-        const float2 s = fma2(u[v], dup2(2.0f / LHV_CORE_U_SER), dup2(-1.0f));
+        const float2 u = mul2(r2[v], dup2(cc.inv_a2));
+        const float2 s = fma2(u, dup2(2.0f / LHV_CORE_U_SER), dup2(-1.0f));
         float2 F = kSerF2[LHV_CORE_SER_DEG], Fp = kSerFp2[LHV_CORE_SER_DEG];
 #pragma unroll
         for (int k = LHV_CORE_SER_DEG - 1; k >= 0; --k) {
@@ -384,11 +385,11 @@ __device__ __forceinline__ void fg2_core(const float2 (&r2)[SU], const float2 (&
         }
         const float2 fs = mul2(dup2(cc.c3), F);
         const float2 gs = mul2(dup2(cc.c5_g), Fp);
-        if (u[v].x < cc.u_series) {
+        if (u.x < cc.u_series) {
             f[v].x = fs.x;
             gm[v].x = gs.x;
         }
-        if (u[v].y < cc.u_series) {
+        if (u.y < cc.u_series) {
             f[v].y = fs.y;
             gm[v].y = gs.y;
         }
@@ -1090,9 +1091,12 @@ void run_p2p(Ctx* c, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs, 
         const double rv = ctx_rK(c) > 0.0 ? std::min(xc * a, ctx_rK(c)) : xc * a;
         cc.r2_cut = (T)(rv * rv);
         cc.t_scale = (T)(a * (double)LHV_CORE_Y_SCALE);
-        cc.nr_scale = (T)(-s2pi / a);
         cc.c3_3n = (T)(-s2pi / (3.0 * a * a * a));
         cc.c5_g = (T)(-2.0 / 3.0 * s2pi / (a * a * a * a * a));
+        cc.ue_scale = (T)(-0.5 / (a * a * 0.69314718055994530942));  // -u/2 in base 2
+        cc.ue_shift = (T)(-std::log2(a));
+        cc.c3_3a = (T)(-s2pi / (3.0 * a * a));
+        cc.r2_series = (T)((sizeof(T) == 4 ? LHV_CORE_U_SER : 1.0) * a * a);
     }
     int* work = reinterpret_cast<int*>(ctx_tmp(c, 6).ptr);
     ensure(c, ctx_tmp(c, 6), 64);
