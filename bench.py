@@ -54,9 +54,9 @@ SINGLE = {"leapfrog": "leapfrog_rings_4194304", "ring_262144": "ring_262144"}
 # s += g (w_i . d)(w_j x d) (6) = 46 flops
 P2P_FLOPS_PER_PAIR = 46
 # extra FP32 flops of a pair inside the core radius r_K (the evaluation of K, Eq. vem1, on top of
-# the singular terms): u 1, t 2, degree-7 polynomial 14, r and R 3, exp argument 1 (the exp on
-# the SFU), K 2, f K 1, g 2
-P2P_CORE_FLOPS_PER_PAIR = 26
+# the singular terms, in the form K / r^3 = 1/r^3 - exp(-x^2/2) G(a/r) / (a r^2)): t 2, degree-7
+# polynomial 14, exp argument 2 (the exp on the SFU), f 3, g 3
+P2P_CORE_FLOPS_PER_PAIR = 24
 # the oracle sample of the CPU legs: the headline geometry at 2 x 2048 elements
 CPU_SAMPLE_PER_RING = 2048
 
