@@ -110,6 +110,21 @@ __device__ inline void for_each_Q(int p, T x, T y, T z, const QTab<T>& q, F&& f)
 constexpr int P2M_THREADS = 128;
 constexpr int P2M_MAX_OUT = (3 * 24 * 24 + P2M_THREADS - 1) / P2M_THREADS;  // W entries per thread, p <= 24
 
+// Row stride of the staged harmonics: odd, so that the lanes of a warp, each writing entry k of
+// its own element's row, fall in 32 different shared-memory banks (a stride of p^2 = 256 put all
+// 32 in one bank).
+__host__ __device__ inline int p2m_row_stride(int P) { return P | 1; }
+
+// Shared memory of k_p2m_w and the elements per chunk: the largest chunk (128, 64 or 32
+// elements) whose rows, strengths and recurrence table fit in 80 KB (two blocks per SM).
+template <typename T>
+size_t p2m_smem(int p, int& chunk) {
+    const size_t row = (size_t)p2m_row_stride(p * p) + 3;
+    chunk = 128;
+    while (chunk > 32 && sizeof(T) * (chunk * row + qtab_reals(p)) > 80 * 1024) chunk /= 2;
+    return sizeof(T) * (chunk * row + qtab_reals(p));
+}
+
 // Work items are the tiles of at most P2P_TILE consecutive elements of one leaf
 // (the near-field tiles), so a crowded leaf is spread over several blocks; each
 // block adds its partial W into the leaf's (zeroed) W with atomics.
@@ -129,9 +144,9 @@ __global__ void __launch_bounds__(P2M_THREADS) k_p2m_w(const int* __restrict__ n
                                                      T* __restrict__ Wout, int64_t ldw, int p, int chunk,
                                                      GaussRule rule = GaussRule{}) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int P = p * p;
-    T* gh = reinterpret_cast<T*>(smem_raw);  // [chunk][P]
-    T* wk = gh + (size_t)chunk * P;          // [chunk][NC]: strength / h
+    const int P = p * p, gs = p2m_row_stride(P);
+    T* gh = reinterpret_cast<T*>(smem_raw);  // [chunk][gs]: the harmonics of an element in a row
+    T* wk = gh + (size_t)chunk * gs;         // [chunk][NC]: strength / h
     const int ntiles = *ntiles_dev;
     const QTab<T> qt = build_qtab(wk + (size_t)chunk * 3, p);  // visible after the tile loop's first barrier
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -160,7 +175,7 @@ __global__ void __launch_bounds__(P2M_THREADS) k_p2m_w(const int* __restrict__ n
                 } else {
                     wk[e] = qs[c0 + e] * invh;
                 }
-                T* g = gh + (size_t)e * P;
+                T* g = gh + (size_t)e * gs;
                 const int nq = SEG ? rule.nq : 1;
                 for (int j = 0; j < nq; ++j) {
                     double px = (double)xv.x, py = (double)xv.y, pz = (double)xv.z;
@@ -200,7 +215,7 @@ __global__ void __launch_bounds__(P2M_THREADS) k_p2m_w(const int* __restrict__ n
                 if (i >= NC * P) break;
                 const int k = i / P, j = i - k * P;
                 T s = 0;
-                for (int e = 0; e < ne; ++e) s += wk[e * NC + k] * gh[(size_t)e * P + j];
+                for (int e = 0; e < ne; ++e) s += wk[e * NC + k] * gh[(size_t)e * gs + j];
                 acc[q] += s;
             }
         }
@@ -413,11 +428,8 @@ template <typename T>
 void run_p2m(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs,
              const vec4_t<T>* ws, T* W, T* mult) {
     const int L = lv.L, nl = lv.nbox[L], o = lv.off[L], p = pl.p[L], P = p * p;
-    // the harmonics of a chunk sit in shared memory: the largest chunk (128, 64 or 32 elements)
-    // that still leaves room for two blocks per SM
-    int chunk = 128;
-    while (chunk > 32 && sizeof(T) * ((size_t)chunk * (P + 3) + qtab_reals(p)) > 80 * 1024) chunk /= 2;
-    const size_t smem = sizeof(T) * ((size_t)chunk * (P + 3) + qtab_reals(p));
+    int chunk;
+    const size_t smem = p2m_smem<T>(p, chunk);
     cuda_check(cudaFuncSetAttribute(k_p2m_w<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                "p2m attr");
     const int* count = tb.counts.as<int>();
@@ -539,9 +551,8 @@ template <typename T>
 void run_p2m_segments(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs,
                       const vec4_t<T>* seg, const GaussRule& rule, T* W, T* mult) {
     const int L = lv.L, nl = lv.nbox[L], o = lv.off[L], p = pl.p[L], P = p * p;
-    int chunk = 128;
-    while (chunk > 32 && sizeof(T) * ((size_t)chunk * (P + 3) + qtab_reals(p)) > 80 * 1024) chunk /= 2;
-    const size_t smem = sizeof(T) * ((size_t)chunk * (P + 3) + qtab_reals(p));
+    int chunk;
+    const size_t smem = p2m_smem<T>(p, chunk);
     cuda_check(cudaFuncSetAttribute(k_p2m_w<T, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                "p2m attr");
     const int* count = tb.counts.as<int>();
@@ -565,10 +576,9 @@ void run_p2m_segments(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Level
 template <typename T>
 void run_p2m_scalar(Ctx* c, const Plan<T>& pl, const TreeBufs& tb, const Levels& lv, const vec4_t<T>* xs,
                     const T* qs, T* mult) {
-    const int L = lv.L, nl = lv.nbox[L], o = lv.off[L], p = pl.p[L], P = p * p;
-    int chunk = 128;
-    while (chunk > 32 && sizeof(T) * ((size_t)chunk * (P + 3) + qtab_reals(p)) > 80 * 1024) chunk /= 2;
-    const size_t smem = sizeof(T) * ((size_t)chunk * (P + 3) + qtab_reals(p));
+    const int L = lv.L, nl = lv.nbox[L], o = lv.off[L], p = pl.p[L];
+    int chunk;
+    const size_t smem = p2m_smem<T>(p, chunk);
     cuda_check(cudaFuncSetAttribute(k_p2m_w<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                "p2m attr");
     T* leaf_rows = mult + (int64_t)o * pl.ld;
