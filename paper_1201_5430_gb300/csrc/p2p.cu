@@ -407,7 +407,10 @@ constexpr float kPadPosition = 1.0e18f;
 // sources, holding each source pair as -x, -y, -z (so that d = x_i + (-x_j) is
 // one add), w and -w (so that each cross-product component is one mul and one
 // fma), and synchronises with __syncwarp only.
-constexpr int P2P_WARPS = 4;  // warps per block of the packed kernel
+// Warps per block of the packed kernels: one.  The warps share nothing, and a block of one
+// warp lets the SM hold as many warps as its registers allow (14 at 144 registers a thread,
+// against 12 in blocks of four).
+constexpr int P2P_WARPS = 1;
 
 template <int TPT, int CH>
 struct P2pWarpSmem {
