@@ -329,6 +329,7 @@ __device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 
 // kernel_fg for two pairs at once, returning f and gm = -g/3 (the factor -3
 // is applied to the finished sums).  fg2_singular gives the packed singular
@@ -405,11 +406,11 @@ constexpr float kPadPosition = 1.0e18f;
 // tile (so a leaf wastes at most one partly filled warp, not one partly filled
 // 128-target tile); empty warp tiles are skipped.  Each warp stages its own
 // sources, holding each source pair as -x, -y, -z (so that d = x_i + (-x_j) is
-// one add), w and -w (so that each cross-product component is one mul and one
-// fma), and synchronises with __syncwarp only.
+// one add) and w (each cross-product component is one mul and one fma with the
+// product negated), and synchronises with __syncwarp only.
 // Warps per block of the packed kernels: one.  The warps share nothing, and a block of one
-// warp lets the SM hold as many warps as its registers allow (14 at 144 registers a thread,
-// against 12 in blocks of four).
+// warp lets the SM hold as many warps as its registers allow (16 at the 123 registers a
+// thread of two targets per lane, against 12 in blocks of four at the earlier 144).
 constexpr int P2P_WARPS = 1;
 
 template <int TPT, int CH>
@@ -418,8 +419,6 @@ struct P2pWarpSmem {
     float4 A[CP];                      // -x pair, -y pair
     float4 B[CP];                      // -z pair, w.x pair
     float4 C[CP];                      // w.y pair, w.z pair
-    float4 D[CP];                      // -w.x pair, -w.y pair
-    float2 E[CP];                      // -w.z pair
     int2 id[CP];                       // sorted indices of the pair (-1: padding)
     float tot[2][9][TPT][32];          // compensated totals (hi, lo) per lane
     int cbeg[27], cpre[28];
@@ -480,20 +479,19 @@ __global__ void __launch_bounds__(32 * P2P_WARPS) k_p2p_x2(const int* __restrict
         if (lane == 26) sm.cpre[27] = incl;
         int ti[TPT];
         bool act[TPT];
-        float4 wi[TPT];
         float2 XI[TPT][3], WI[TPT][3];
 #pragma unroll
         for (int q = 0; q < TPT; ++q) {
             ti[q] = t0 + lane + 32 * q;
             act[q] = ti[q] < tend;
             const float4 x = act[q] ? xs[ti[q]] : float4{};
-            wi[q] = act[q] ? ws[ti[q]] : float4{};
+            const float4 wiq = act[q] ? ws[ti[q]] : float4{};
             XI[q][0] = dup2(x.x);
             XI[q][1] = dup2(x.y);
             XI[q][2] = dup2(x.z);
-            WI[q][0] = dup2(wi[q].x);
-            WI[q][1] = dup2(wi[q].y);
-            WI[q][2] = dup2(wi[q].z);
+            WI[q][0] = dup2(wiq.x);
+            WI[q][1] = dup2(wiq.y);
+            WI[q][2] = dup2(wiq.z);
 #pragma unroll
             for (int a = 0; a < NA; ++a) {
                 sm.tot[0][a][q][lane] = 0;
@@ -524,17 +522,12 @@ __global__ void __launch_bounds__(32 * P2P_WARPS) k_p2p_x2(const int* __restrict
                 float* a = reinterpret_cast<float*>(&sm.A[m]);
                 float* b = reinterpret_cast<float*>(&sm.B[m]);
                 float* c = reinterpret_cast<float*>(&sm.C[m]);
-                float* d = reinterpret_cast<float*>(&sm.D[m]);
-                float* e = reinterpret_cast<float*>(&sm.E[m]);
                 a[l] = -x.x;
                 a[2 + l] = -x.y;
                 b[l] = -x.z;
                 b[2 + l] = w.x;
                 c[l] = w.y;
                 c[2 + l] = w.z;
-                d[l] = -w.x;
-                d[2 + l] = -w.y;
-                e[l] = -w.z;
                 reinterpret_cast<int*>(&sm.id[m])[l] = j;
             }
             __syncwarp();
@@ -545,20 +538,17 @@ __global__ void __launch_bounds__(32 * P2P_WARPS) k_p2p_x2(const int* __restrict
                 for (int q = 0; q < TPT; ++q) acc[a][q] = make_float2(0.0f, 0.0f);
             auto chunk = [&](auto check) {
                 for (int m = 0; m < np; m += SU) {
-                    float2 nxj[SU], nyj[SU], nzj[SU], wx[SU], wy[SU], wz[SU], nwx[SU], nwy[SU], nwz[SU];
+                    float2 nxj[SU], nyj[SU], nzj[SU], wx[SU], wy[SU], wz[SU];
                     int2 j[SU];
 #pragma unroll
                     for (int u = 0; u < SU; ++u) {
-                        const float4 A = sm.A[m + u], B = sm.B[m + u], C = sm.C[m + u], D = sm.D[m + u];
+                        const float4 A = sm.A[m + u], B = sm.B[m + u], C = sm.C[m + u];
                         nxj[u] = make_float2(A.x, A.y);
                         nyj[u] = make_float2(A.z, A.w);
                         nzj[u] = make_float2(B.x, B.y);
                         wx[u] = make_float2(B.z, B.w);
                         wy[u] = make_float2(C.x, C.y);
                         wz[u] = make_float2(C.z, C.w);
-                        nwx[u] = make_float2(D.x, D.y);
-                        nwy[u] = make_float2(D.z, D.w);
-                        nwz[u] = sm.E[m + u];
                         j[u] = make_int2(-1, -1);
                         if (decltype(check)::value) j[u] = sm.id[m + u];
                     }
@@ -586,9 +576,9 @@ __global__ void __launch_bounds__(32 * P2P_WARPS) k_p2p_x2(const int* __restrict
                                     gm[u].y = 0.0f;
                                 }
                             }
-                            const float2 cx = fma2(nwz[u], dy[u], mul2(wy[u], dz[u]));  // w_y d_z - w_z d_y
-                            const float2 cy = fma2(nwx[u], dz[u], mul2(wz[u], dx[u]));  // w_z d_x - w_x d_z
-                            const float2 cz = fma2(nwy[u], dx[u], mul2(wx[u], dy[u]));  // w_x d_y - w_y d_x
+                            const float2 cx = fma2(wy[u], dz[u], neg2(mul2(wz[u], dy[u])));  // w_y d_z - w_z d_y
+                            const float2 cy = fma2(wz[u], dx[u], neg2(mul2(wx[u], dz[u])));  // w_z d_x - w_x d_z
+                            const float2 cz = fma2(wx[u], dy[u], neg2(mul2(wy[u], dx[u])));  // w_x d_y - w_y d_x
                             acc[0][q] = fma2(f[u], cx, acc[0][q]);
                             acc[1][q] = fma2(f[u], cy, acc[1][q]);
                             acc[2][q] = fma2(f[u], cz, acc[2][q]);
@@ -631,9 +621,9 @@ __global__ void __launch_bounds__(32 * P2P_WARPS) k_p2p_x2(const int* __restrict
             vo.z = vf.z + r[2];
             vo.w = 0;
             // the g-terms were summed with gm = -g/3
-            so.x = sf.x + (r[4] * wi[q].z - r[5] * wi[q].y) - 3.0f * r[6];
-            so.y = sf.y + (r[5] * wi[q].x - r[3] * wi[q].z) - 3.0f * r[7];
-            so.z = sf.z + (r[3] * wi[q].y - r[4] * wi[q].x) - 3.0f * r[8];
+            so.x = sf.x + (r[4] * WI[q][2].x - r[5] * WI[q][1].x) - 3.0f * r[6];
+            so.y = sf.y + (r[5] * WI[q][0].x - r[3] * WI[q][2].x) - 3.0f * r[7];
+            so.z = sf.z + (r[3] * WI[q][1].x - r[4] * WI[q][0].x) - 3.0f * r[8];
             so.w = 0;
             const int o = perm[i];
             vout[o] = vo;
