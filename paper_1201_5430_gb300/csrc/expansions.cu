@@ -149,17 +149,34 @@ __global__ void __launch_bounds__(P2M_THREADS) k_p2m_w(const int* __restrict__ n
     T* wk = gh + (size_t)chunk * gs;         // [chunk][NC]: strength / h
     const int ntiles = *ntiles_dev;
     const QTab<T> qt = build_qtab(wk + (size_t)chunk * 3, p);  // visible after the tile loop's first barrier
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    // a block takes a contiguous range of tiles; the tiles of a leaf are consecutive, so the
+    // partial W of a leaf is summed over its tiles in registers and added once per leaf
+    const int t_lo = (int)((int64_t)ntiles * blockIdx.x / gridDim.x);
+    const int t_hi = (int)((int64_t)ntiles * (blockIdx.x + 1) / gridDim.x);
+    T acc[P2M_MAX_OUT];  // outputs i = threadIdx.x + q blockDim.x of the current leaf
+#pragma unroll
+    for (int q = 0; q < P2M_MAX_OUT; ++q) acc[q] = 0;
+    auto flush = [&](int leaf) {
+        T* Wb = Wout + (int64_t)leaf * ldw;
+#pragma unroll
+        for (int q = 0; q < P2M_MAX_OUT; ++q) {
+            const int i = threadIdx.x + q * blockDim.x;
+            if (i < NC * P) atomicAdd(Wb + i, acc[q]);
+            acc[q] = 0;
+        }
+    };
+    int cur = -1;
+    for (int t = t_lo; t < t_hi; ++t) {
         const int2 tw = tiles[t];
         const int b = tw.x;
+        if (b != cur) {
+            if (cur >= 0) flush(cur);
+            cur = b;
+        }
         double cx, cy, cz, h;
         box_geom(cubes, bkey[b], level, cx, cy, cz, h);
         const T invh = (T)(1.0 / h);
-        T* Wb = Wout + (int64_t)b * ldw;
         const int e0 = tw.y, e1 = min(bend[b], tw.y + P2P_TILE);
-        T acc[P2M_MAX_OUT];  // outputs i = threadIdx.x + q blockDim.x of this tile, summed over its chunks
-#pragma unroll
-        for (int q = 0; q < P2M_MAX_OUT; ++q) acc[q] = 0;
         for (int c0 = e0; c0 < e1; c0 += chunk) {
             const int ne = min(chunk, e1 - c0);
             __syncthreads();
@@ -219,14 +236,8 @@ __global__ void __launch_bounds__(P2M_THREADS) k_p2m_w(const int* __restrict__ n
                 acc[q] += s;
             }
         }
-#pragma unroll
-        for (int q = 0; q < P2M_MAX_OUT; ++q) {
-            const int i = threadIdx.x + q * blockDim.x;
-            if (i >= NC * P) break;
-            atomicAdd(Wb + i, acc[q]);
-        }
-        __syncthreads();
     }
+    if (cur >= 0) flush(cur);
 }
 
 // P2M, part 2 (per leaf): M_hat = G W with G the P2M map of Eq. eve4 in row-compressed form
@@ -277,21 +288,29 @@ __global__ void __launch_bounds__(L2P_THREADS) k_l2p_eval(const int* __restrict_
     T* lh = cf + 12 * P;                     // [2P] the leaf's local expansion
     const int ntiles = *ntiles_dev;
     const QTab<T> qt = build_qtab(lh + 2 * P, p);  // visible after the tile loop's first barrier
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    // a block takes a contiguous range of tiles; the tiles of a leaf are consecutive, so the
+    // leaf's coefficient vectors are staged once per leaf, not once per tile
+    const int t_lo = (int)((int64_t)ntiles * blockIdx.x / gridDim.x);
+    const int t_hi = (int)((int64_t)ntiles * (blockIdx.x + 1) / gridDim.x);
+    int staged = -1;
+    for (int t = t_lo; t < t_hi; ++t) {
         const int2 tw = tiles[t];
         const int b = tw.x;
         double cx, cy, cz, h;
         box_geom(cubes, bkey[b], level, cx, cy, cz, h);
-        __syncthreads();
-        for (int i = threadIdx.x; i < 2 * P; i += blockDim.x) lh[i] = loc[(int64_t)b * ld + i];
-        __syncthreads();
-        for (int r = threadIdx.x; r < 12 * P; r += blockDim.x) {  // output r = j P + i: vector j, entry i
-            T acc = 0;
-            for (int k = e.rowptr[r]; k < e.rowptr[r + 1]; ++k) acc += e.val[k] * lh[e.col[k]];
-            const int j = r / P, i = r - j * P;
-            cf[i * 12 + j] = acc;
+        if (b != staged) {
+            __syncthreads();
+            for (int i = threadIdx.x; i < 2 * P; i += blockDim.x) lh[i] = loc[(int64_t)b * ld + i];
+            __syncthreads();
+            for (int r = threadIdx.x; r < 12 * P; r += blockDim.x) {  // output r = j P + i: vector j, entry i
+                T acc = 0;
+                for (int k = e.rowptr[r]; k < e.rowptr[r + 1]; ++k) acc += e.val[k] * lh[e.col[k]];
+                const int j = r / P, i = r - j * P;
+                cf[i * 12 + j] = acc;
+            }
+            __syncthreads();
+            staged = b;
         }
-        __syncthreads();
         const T invh = (T)(1.0 / h);
         const int e1 = min(bend[b], tw.y + P2P_TILE);
         for (int e = tw.y + threadIdx.x; e < e1; e += blockDim.x) {
