@@ -253,7 +253,7 @@ int lhv_direct_sampled_f64(lhv_ctx* ctx, int64_t n, const double* x4, const doub
  * sources staged in shared memory per step) and the
  * fastest M2L grouping (box pairs of one offset per GEMM chunk: 64, 32 or 16 on
  * the CUDA cores; under TF32X3 also the tensor-core kernel with 128 or 64 pairs
- * per chunk), judged by CUDA-event stage times (best of 3 after a warm-up).  v4
+ * per chunk), chosen by CUDA-event stage times (best of 3 after a warm-up).  v4
  * and s4 receive the last evaluation.  The batched twin tunes on a batch
  * (offsets as for lhv_evaluate_batched).  Results do not depend on the choice
  * beyond rounding. */
