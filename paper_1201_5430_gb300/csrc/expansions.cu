@@ -68,9 +68,10 @@ __device__ inline QTab<T> build_qtab(T* base, int p) {
 }
 
 // Walks every (n, m), 0 <= m <= n < p, of the recurrence of Q_n^m at (x, y, z)
-// and calls f(n, m, Re Q, Im Q).  State is O(1).
+// and calls f(n, m, Re Q, Im Q).  State is O(1).  par = 0 or 1 keeps the orders m of that
+// parity only (the diagonal Q_m^m is still advanced through every m).
 template <typename T, typename F>
-__device__ inline void for_each_Q(int p, T x, T y, T z, const QTab<T>& q, F&& f) {
+__device__ inline void for_each_Q(int p, T x, T y, T z, const QTab<T>& q, F&& f, int par = -1) {
     const T r2 = x * x + y * y + z * z;
     T dre = 1, dim = 0;  // Q_m^m
     for (int m = 0; m < p; ++m) {
@@ -81,6 +82,7 @@ __device__ inline void for_each_Q(int p, T x, T y, T z, const QTab<T>& q, F&& f)
             dre = nre;
             dim = nim;
         }
+        if (par >= 0 && (m & 1) != par) continue;
         f(m, m, dre, dim);
         if (m + 1 >= p) continue;
         const T c1 = q.c1[m] * z;
@@ -144,7 +146,9 @@ __global__ void __launch_bounds__(P2M_THREADS) k_p2m_w(const int* __restrict__ n
                                                      T* __restrict__ Wout, int64_t ldw, int p, int chunk,
                                                      GaussRule rule = GaussRule{}) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    static_assert(P2M_THREADS % 64 == 0, "warps pair up by the parity of m");
     const int P = p * p, gs = p2m_row_stride(P);
+    const int par = (threadIdx.x >> 5) & 1;  // parity of the orders m this warp's harmonics take
     T* gh = reinterpret_cast<T*>(smem_raw);  // [chunk][gs]: the harmonics of an element in a row
     T* wk = gh + (size_t)chunk * gs;         // [chunk][NC]: strength / h
     const int ntiles = *ntiles_dev;
@@ -180,17 +184,22 @@ __global__ void __launch_bounds__(P2M_THREADS) k_p2m_w(const int* __restrict__ n
         for (int c0 = e0; c0 < e1; c0 += chunk) {
             const int ne = min(chunk, e1 - c0);
             __syncthreads();
-            for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+            // two warps per 32 elements: the even-numbered one takes the orders m of even
+            // parity, its neighbour the odd ones (disjoint entries of the row; the parity is
+            // uniform across a warp, so its lanes do not diverge)
+            for (int e = (threadIdx.x >> 6) * 32 + (threadIdx.x & 31); e < ne; e += blockDim.x >> 1) {
                 vec4_t<T> xv = xs[c0 + e];
-                if constexpr (NC == 3) {
-                    const vec4_t<T> wv = ws[c0 + e];
-                    // M_hat carries 1/h (P2M scaling); a segment's strength is Gamma l / (8 pi)
-                    const T sc = SEG ? wv.w * (T)(0.039788735772973833942) * invh : invh;  // 1/(8 pi)
-                    wk[e * 3 + 0] = wv.x * sc;
-                    wk[e * 3 + 1] = wv.y * sc;
-                    wk[e * 3 + 2] = wv.z * sc;
-                } else {
-                    wk[e] = qs[c0 + e] * invh;
+                if (par == 0) {
+                    if constexpr (NC == 3) {
+                        const vec4_t<T> wv = ws[c0 + e];
+                        // M_hat carries 1/h (P2M scaling); a segment's strength is Gamma l / (8 pi)
+                        const T sc = SEG ? wv.w * (T)(0.039788735772973833942) * invh : invh;  // 1/(8 pi)
+                        wk[e * 3 + 0] = wv.x * sc;
+                        wk[e * 3 + 1] = wv.y * sc;
+                        wk[e * 3 + 2] = wv.z * sc;
+                    } else {
+                        wk[e] = qs[c0 + e] * invh;
+                    }
                 }
                 T* g = gh + (size_t)e * gs;
                 const int nq = SEG ? rule.nq : 1;
@@ -222,7 +231,7 @@ __global__ void __launch_bounds__(P2M_THREADS) k_p2m_w(const int* __restrict__ n
                             g[k0] += wq * re;
                             if (m > 0) g[k0 + 1] += wq * im;
                         }
-                    });
+                    }, par);
                 }
             }
             __syncthreads();
